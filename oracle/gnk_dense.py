@@ -1,0 +1,292 @@
+"""Dense FP64 CPU oracle for the Nystrom discretisation of the boundary integral
+equations with the generalized Neumann kernel.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+reference that the CUDA library is checked against.  Only the test-suite, the
+package smoke check and the benchmark's CPU-baseline leg may import it; the
+library itself never does.  It shares no code with the CUDA path: every matrix
+is assembled entry by entry from the paper's definitions and every linear
+system is solved by LU (numpy/LAPACK gesv).
+
+Paper sections followed (Nasser, "Fast solution of boundary integral equations
+with the generalized Neumann kernel"):
+  * kernels N, M, N(t,t), M1(t,t)          Sec. 2.2, Eqs. (N), (M), (N-tt), (M1-tt)
+  * Cauchy matrix E                        Sec. 2.5, Eq. (fmm-E)
+  * Nystrom matrix B, system               Sec. 3.2, Eqs. (B), (sys)
+  * D, Wittich-derived circulant L, y      Sec. 3.3, Eqs. (phi-kp2), (y)
+  * h                                      Sec. 3.6, Eq. (bh)
+  * adjoint: e, B^T, P-hat, system         Sec. 4, Eqs. (ei2), (bve), (sys*)
+  * Neumann kernel N_k and N_g(t,t)        Sec. 4.1, Eqs. (Nk), (Ng-tt)
+
+Readings of the paper taken here (each is listed with its reason in the design
+notes of the repository):
+  * The row-sum diagonal of the second-kind system is (2I + diag(B 1) - B), Eq. (sys).
+  * At a corner node of a graded mesh eta'(t) = 0; the diagonal term
+    Im(eta''/eta' - A'/A) takes its one-sided limit, which is 0 for a polygon
+    (eta''/eta' is real along a straight edge and A'/A -> 0).
+  * h is returned as the full node vector of Eq. (bh); h_k is its mean on
+    component k.
+
+Parity: every function here is pinned by tests/test_oracle_pins.py against
+closed forms (disk, unit circle), manufactured analytic solutions, the
+eigen-identities of Eq. (NM-const), and adaptive quadrature of the continuous
+operators.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_ROW_BLOCK = 1024
+
+
+def _sizes(et, n):
+    N = int(np.asarray(et).shape[0])
+    if n <= 0 or n % 2 or N % n:
+        raise ValueError("need n even and len(eta) a multiple of n")
+    return N, N // n
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.5: the Cauchy matrix E, (E)_ij = 1/(eta_i - eta_j), i != j; 0 on i == j
+# ---------------------------------------------------------------------------
+
+def cauchy_matrix(et):
+    """Dense E of Eq. (fmm-E)."""
+    et = np.asarray(et, dtype=np.complex128)
+    N = et.shape[0]
+    E = np.zeros((N, N), dtype=np.complex128)
+    for r0 in range(0, N, _ROW_BLOCK):
+        r1 = min(N, r0 + _ROW_BLOCK)
+        d = et[r0:r1, None] - et[None, :]
+        idx = np.arange(r0, r1)
+        d[idx - r0, idx] = 1.0
+        blk = 1.0 / d
+        blk[idx - r0, idx] = 0.0
+        E[r0:r1] = blk
+    return E
+
+
+def cauchy_rows(et, x, rows):
+    """(E x)_i = sum_{j != i} x_j / (eta_i - eta_j) for the listed rows, one row at
+    a time (used to check sampled outputs at sizes where E does not fit)."""
+    et = np.asarray(et, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.complex128)
+    out = np.empty(len(rows), dtype=np.complex128)
+    for k, i in enumerate(rows):
+        d = et[i] - et
+        d[i] = 1.0
+        terms = x / d
+        terms[i] = 0.0
+        out[k] = terms.sum()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2 / 3.2 / 3.3: the Nystrom blocks of N and M
+# ---------------------------------------------------------------------------
+
+def nystrom_block(et, etp, A, n, rows, cols):
+    """K_ij = (2 pi / n) [M(t_i, t_j) + i N(t_i, t_j)] for i in rows, j in cols, i.e.
+
+        K_ij = (2/n) * A(t_i)/A(t_j) * eta'(t_j) / (eta(t_j) - eta(t_i)),
+
+    with K_ij = 0 where i == j.  Then B = Im K (Eq. B) and D = Re K
+    (the matrix D of Sec. 3.3), since (2 pi/n)(1/pi) = 2/n.
+    """
+    et = np.asarray(et, dtype=np.complex128)
+    etp = np.asarray(etp, dtype=np.complex128)
+    A = np.asarray(A, dtype=np.complex128)
+    rows = np.asarray(rows)
+    cols = np.asarray(cols)
+    S = et[rows][:, None]
+    T = et[cols][None, :]
+    same = rows[:, None] == cols[None, :]
+    diff = np.where(same, 1.0, T - S)
+    K = (A[rows][:, None] / A[cols][None, :]) * etp[cols][None, :] / diff
+    K = np.where(same, 0.0, K) * (2.0 / n)
+    return K
+
+
+def matrices_BD(et, etp, A, n):
+    """Dense B (Eq. B) and D (Sec. 3.3)."""
+    N, _ = _sizes(et, n)
+    B = np.empty((N, N))
+    D = np.empty((N, N))
+    allc = np.arange(N)
+    for r0 in range(0, N, _ROW_BLOCK):
+        r1 = min(N, r0 + _ROW_BLOCK)
+        K = nystrom_block(et, etp, A, n, np.arange(r0, r1), allc)
+        B[r0:r1] = K.imag
+        D[r0:r1] = K.real
+    return B, D
+
+
+def circulant_L(n):
+    """L of Sec. 3.3: L_pq = (-1)^(p-q) (1/n) cot((p-q) pi / n), p != q; 0 on p == q."""
+    if n % 2:
+        raise ValueError("n must be even")
+    p = np.arange(n)
+    d = p[:, None] - p[None, :]
+    with np.errstate(divide="ignore"):
+        L = np.where(d == 0, 0.0,
+                     np.where(d % 2 == 0, 1.0, -1.0) / n / np.tan(d * math.pi / n))
+    L[d == 0] = 0.0
+    return L
+
+
+def block_L(n, m1):
+    """L-hat = diag(L, ..., L) with m+1 blocks (Sec. 3.3)."""
+    return np.kron(np.eye(m1), circulant_L(n))
+
+
+def matrix_IminusN(et, etp, A, n):
+    """2I + diag(B 1) - B: the discretisation of I - N with singularity
+    subtraction (Eqs. ie-sys2, sys)."""
+    B, _ = matrices_BD(et, etp, A, n)
+    N = B.shape[0]
+    return 2.0 * np.eye(N) + np.diag(B.sum(axis=1)) - B
+
+
+def matrix_M(et, etp, A, n):
+    """D - diag(D 1) + L-hat: the discretisation of M (Eq. y, using L-hat 1 = 0)."""
+    N, m1 = _sizes(et, n)
+    _, D = matrices_BD(et, etp, A, n)
+    return D - np.diag(D.sum(axis=1)) + block_L(n, m1)
+
+
+def rhs_y(et, etp, A, n, gam):
+    """y = phi(t) = D gamma - diag(D 1) gamma + L-hat gamma (Eq. y)."""
+    return matrix_M(et, etp, A, n) @ np.asarray(gam, dtype=np.float64)
+
+
+def solve_ie(et, etp, A, n, gam):
+    """mu solving (2I + diag(B1) - B) mu = -y (Eq. sys), by LU."""
+    Mm = matrix_M(et, etp, A, n)
+    y = Mm @ np.asarray(gam, dtype=np.float64)
+    return np.linalg.solve(matrix_IminusN(et, etp, A, n), -y)
+
+
+def compute_h(et, etp, A, n, mu, gam):
+    """h(t) = ([D - diag(D1) + L-hat] mu - [2I + diag(B1) - B] gamma) / 2 (Eq. bh).
+
+    Returns (h at the nodes, h_k = mean of h over component k)."""
+    N, m1 = _sizes(et, n)
+    h = (matrix_M(et, etp, A, n) @ mu - matrix_IminusN(et, etp, A, n) @ gam) / 2.0
+    return h, h.reshape(m1, n).mean(axis=1)
+
+
+def fbie(et, etp, A, n, gam):
+    """The pair (mu, h, h_k) of Sec. 3 computed densely."""
+    mu = solve_ie(et, etp, A, n, gam)
+    h, hk = compute_h(et, etp, A, n, mu, gam)
+    return mu, h, hk
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: diagonal limits of the kernels (used by the pins and by the
+# variant without singularity subtraction)
+# ---------------------------------------------------------------------------
+
+def _ratio_limit(num, den):
+    """num/den with the corner convention 0/0 := 0 (graded-mesh corner nodes)."""
+    num = np.asarray(num, dtype=np.complex128)
+    den = np.asarray(den, dtype=np.complex128)
+    out = np.zeros_like(num)
+    nz = den != 0
+    out[nz] = num[nz] / den[nz]
+    return out
+
+
+def kernel_N_diag(etp, etpp, A, Ap):
+    """N(t,t) = (1/pi) (1/2 Im eta''/eta' - Im A'/A)  (Eq. N-tt)."""
+    return (0.5 * _ratio_limit(etpp, etp).imag - _ratio_limit(Ap, A).imag) / math.pi
+
+
+def kernel_M1_diag(etp, etpp, A, Ap):
+    """M1(t,t) = (1/pi) (1/2 Re eta''/eta' - Re A'/A)  (Eq. M1-tt)."""
+    return (0.5 * _ratio_limit(etpp, etp).real - _ratio_limit(Ap, A).real) / math.pi
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4: the adjoint equation (I + N* + J) mu = gamma
+# ---------------------------------------------------------------------------
+
+def adjoint_e(et, etp, etpp, A, Ap, n, c):
+    """e_i = 1 - c + (2 pi/n) sum_{j != i} N_k(t_i, t_j) + (2 pi/n) N_g(t_i, t_i)
+    (Eq. ei2) with the Neumann kernel N_k(s,t) = (1/pi) Im[eta'(t)/(eta(t)-eta(s))]
+    (Eq. Nk) and N_g(t,t) = (1/pi) Im[eta''/eta' - A'/A] (Eq. Ng-tt)."""
+    N, _ = _sizes(et, n)
+    ones = np.ones(N, dtype=np.complex128)
+    allc = np.arange(N)
+    rowsum = np.empty(N)
+    for r0 in range(0, N, _ROW_BLOCK):
+        r1 = min(N, r0 + _ROW_BLOCK)
+        # nystrom_block with A == 1 is (2/n) eta'_j/(eta_j - eta_i): (2pi/n) pi N_k / pi
+        K = nystrom_block(et, etp, ones, n, np.arange(r0, r1), allc)
+        rowsum[r0:r1] = K.imag.sum(axis=1)
+    ng = (2.0 / n) * (_ratio_limit(etpp, etp) - _ratio_limit(Ap, A)).imag
+    return 1.0 - c + rowsum + ng
+
+
+def matrix_adjoint(et, etp, etpp, A, Ap, n, c):
+    """diag(e) + B^T + P-hat (Eq. sys*), P-hat = diag(P,...,P), P = (1/n) 1 1^T."""
+    N, m1 = _sizes(et, n)
+    B, _ = matrices_BD(et, etp, A, n)
+    e = adjoint_e(et, etp, etpp, A, Ap, n, c)
+    P = np.kron(np.eye(m1), np.full((n, n), 1.0 / n))
+    return np.diag(e) + B.T + P
+
+
+def solve_adjoint_ie(et, etp, etpp, A, Ap, n, c, gam):
+    """mu solving (diag(e) + B^T + P-hat) mu = gamma (Eq. sys*), by LU."""
+    return np.linalg.solve(matrix_adjoint(et, etp, etpp, A, Ap, n, c),
+                           np.asarray(gam, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Row-wise forms for sampled checks at sizes where dense matrices do not fit
+# ---------------------------------------------------------------------------
+
+def rows_IminusN(et, etp, A, n, x, rows):
+    """Rows of (2I + diag(B1) - B) x (Eq. sys), one block of rows at a time."""
+    N, _ = _sizes(et, n)
+    rows = np.asarray(rows)
+    K = nystrom_block(et, etp, A, n, rows, np.arange(N))
+    B = K.imag
+    x = np.asarray(x, dtype=np.float64)
+    return 2.0 * x[rows] + B.sum(axis=1) * x[rows] - B @ x
+
+
+def rows_M(et, etp, A, n, x, rows):
+    """Rows of (D - diag(D1) + L-hat) x (Eq. y)."""
+    N, _ = _sizes(et, n)
+    rows = np.asarray(rows)
+    K = nystrom_block(et, etp, A, n, rows, np.arange(N))
+    D = K.real
+    x = np.asarray(x, dtype=np.float64)
+    L = circulant_L(n)
+    out = D @ x - D.sum(axis=1) * x[rows]
+    for k, i in enumerate(rows):
+        comp, p = divmod(int(i), n)
+        out[k] += L[p] @ x[comp * n:(comp + 1) * n]
+    return out
+
+
+def rows_adjoint(et, etp, etpp, A, Ap, n, c, x, rows):
+    """Rows of (diag(e) + B^T + P-hat) x (Eq. sys*)."""
+    N, _ = _sizes(et, n)
+    rows = np.asarray(rows)
+    x = np.asarray(x, dtype=np.float64)
+    allr = np.arange(N)
+    # (B^T)_{ij} = B_{ji}: the columns `rows` of B
+    BT = nystrom_block(et, etp, A, n, allr, rows).imag.T
+    ones = np.ones(N, dtype=np.complex128)
+    Kk = nystrom_block(et, etp, ones, n, rows, allr).imag
+    ng = (2.0 / n) * (_ratio_limit(np.asarray(etpp)[rows], np.asarray(etp)[rows])
+                      - _ratio_limit(np.asarray(Ap)[rows], np.asarray(A)[rows])).imag
+    e = 1.0 - c + Kk.sum(axis=1) + ng
+    comp = rows // n
+    means = x.reshape(-1, n).mean(axis=1)
+    return e * x[rows] + BT @ x + means[comp]
