@@ -1,0 +1,184 @@
+/*
+ * gnk.h -- C ABI of libgnk: GB300 (sm_103a) Nystrom solver for the boundary
+ * integral equations with the generalized Neumann kernel (Nasser, "Fast
+ * solution of boundary integral equations with the generalized Neumann
+ * kernel").
+ *
+ * Problem statement (Sec. 1): for an (m+1)-connected domain G with boundary
+ * parametrisation eta(t) on the (m+1) n trapezoidal nodes t_{kn+p} = (p-1)2pi/n
+ * (Eq. ti-skp, component-major), coefficient A(t) of Eq. (A) and data gamma,
+ *   (I - N) mu = -M gamma,  h = [M mu - (I - N) gamma] / 2     (Eqs. ie, h)
+ *   (I + N* + J) mu = gamma                                   (Eq. ie*)
+ * discretised with singularity subtraction as (Eqs. sys, y, bh, sys*)
+ *   (2I + diag(B1) - B) mu = -y,  y = (D - diag(D1) + Lhat) gamma,
+ *   (diag(e) + B^T + Phat) mu = gamma.
+ * Every product with B, D, B^T and e reduces to the Cauchy sum
+ *   (E w)_i = sum_{j != i} w_j / (eta_i - eta_j)              (Eq. fmm-E)
+ * which this library evaluates as a direct all-pairs sum on the GPU.
+ *
+ * Conventions for every function below:
+ *   - Return value: GNK_OK (0) or a negative GNK_E* code; gnk_last_error()
+ *     returns the message of the calling thread's last failure.
+ *   - Complex arrays are interleaved (re, im) doubles: length 2*N doubles for
+ *     N = (m+1) n nodes.  Real arrays are N doubles.
+ *   - Pointers may be device memory or host memory; the library checks which
+ *     (cudaPointerGetAttributes).  Host arrays are staged through device
+ *     buffers owned by the boundary handle; a call that writes to a host
+ *     array returns after the data has arrived (it synchronises `stream`).
+ *     Device outputs are written asynchronously on `stream`.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     on one handle must not overlap: the handle's workspace is shared.
+ *   - Argument checks (sizes, NULL pointers, n even) happen before any launch
+ *     and return GNK_EINVAL.  CUDA failures return GNK_ECUDA.
+ *   - The caller owns all arrays it passes; the handle owns its own copies.
+ */
+#ifndef GNK_H
+#define GNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GNK_OK          0
+#define GNK_EINVAL     -1  /* bad argument: sizes, NULL pointer, odd n, ...     */
+#define GNK_ENOTCONV   -2  /* solver stopped at maxit; best iterate written       */
+#define GNK_ENONFINITE -3  /* NaN/Inf met in the input or in the iteration        */
+#define GNK_ECUDA      -4  /* CUDA runtime error                                  */
+#define GNK_ENOMEM     -5  /* device allocation failed                            */
+
+/* Arithmetic of the pair sums (the Cauchy sums E w). */
+#define GNK_PREC_FP64  0   /* FP64 pair sums everywhere                           */
+#define GNK_PREC_MIXED 1   /* FP32 pair sums inside GMRES, wrapped in FP64
+                              iterative refinement (residual, circulant part,
+                              diagonals and Givens rotations stay FP64)          */
+#define GNK_PREC_FP32  2   /* FP32 pair sums (apply/cauchy calls only)            */
+
+typedef struct gnk_boundary gnk_boundary;
+
+/* GMRES controls, with the meaning of MATLAB's gmres(restart, tol, maxit)
+ * used by the paper (Sec. 3.5, Eq. ie-gmres): x0 = 0, no preconditioner,
+ * `restart` inner iterations per cycle, at most `maxit` cycles, stop when
+ * ||b - A x||_2 / ||b||_2 <= tol. */
+typedef struct gnk_options {
+    int restart;       /* inner iterations per cycle (>= 1)                    */
+    int maxit;         /* maximum number of cycles (>= 1)                      */
+    double tol;        /* relative residual target (> 0)                       */
+    int precision;     /* GNK_PREC_FP64 or GNK_PREC_MIXED                      */
+    int max_refine;    /* MIXED: maximum refinement steps                      */
+    double inner_tol;  /* MIXED: relative tolerance of each inner solve        */
+} gnk_options;
+
+typedef struct gnk_result {
+    int status;        /* GNK_OK, GNK_ENOTCONV, GNK_ENONFINITE                  */
+    int iterations;    /* Arnoldi steps over all cycles and refinement steps   */
+    int cycles;        /* GMRES cycles (restarts + 1) over all inner solves    */
+    int refinements;   /* MIXED: refinement steps taken                        */
+    int matvecs_fp64;  /* products with the FP64 operator                      */
+    int matvecs_fp32;  /* products with the FP32 operator                      */
+    double relres;     /* final true relative residual, evaluated in FP64      */
+} gnk_result;
+
+/* Fills `opt` with restart 20, maxit 50, tol 1e-12, FP64, max_refine 10,
+ * inner_tol 1e-5. */
+void gnk_default_options(gnk_options* opt);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to len-1 characters) and returns its length. */
+int gnk_last_error(char* buf, size_t len);
+
+/* Library version string (static storage). */
+const char* gnk_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Boundary handle (Sec. 2.1, 2.4; Eqs. eta, A, ti-skp)
+ *
+ * Builds the device-resident discretised boundary: m1 = m+1 components of n
+ * nodes each (n even, n >= 4), N = m1*n.  et, etp, A are eta(t), eta'(t) and
+ * A(t) at the nodes; etpp (eta'') and Ap (A') are needed only for the adjoint
+ * equation (Eq. bve) and may be NULL otherwise.  bounded = 1 for bounded G
+ * (c = +1 in Eq. c), 0 for unbounded G (c = -1).
+ * The call also precomputes q = eta'/A, Eone = E q and the diagonals
+ * diag(B1) = -(2/n) Im(A Eone), diag(D1) = -(2/n) Re(A Eone) (Sec. 3.3-3.4,
+ * listing of FBIE), and, when etpp is given,
+ * e = 1 - c - (2/n) Im(E eta') + (2/n) Im(eta''/eta' - A'/A) (Eq. bve), with
+ * the corner limit Im(eta''/eta' - A'/A) := 0 where eta' = 0 (graded mesh).
+ * A must not vanish; eta' may vanish only at graded-mesh corner nodes.
+ * Non-finite input returns GNK_ENONFINITE.  *out receives the handle, which
+ * owns all its device memory until gnk_free_boundary.
+ * ------------------------------------------------------------------------- */
+int gnk_build_boundary(gnk_boundary** out, int m1, int n,
+                       const double* et, const double* etp, const double* etpp,
+                       const double* A, const double* Ap, int bounded,
+                       void* stream);
+
+/* Releases the handle and its device memory (NULL is accepted). */
+int gnk_free_boundary(gnk_boundary* b);
+
+/* Reports m1 and n of a handle. */
+int gnk_boundary_size(const gnk_boundary* b, int* m1, int* n);
+
+/* ---------------------------------------------------------------------------
+ * Cauchy sum (Sec. 2.5, Eqs. fmm-1, fmm-E, E-fmm): z = E w,
+ *   z_i = sum_{j != i} w_j / (eta_i - eta_j),   i = 1..N,
+ * w and z complex (2N doubles).  precision: GNK_PREC_FP64 or GNK_PREC_FP32.
+ * ------------------------------------------------------------------------- */
+int gnk_cauchy_sum(const gnk_boundary* b, const double* w, double* z,
+                   int precision, void* stream);
+
+/* y = (2I + diag(B1) - B) x, the discrete I - N (Eqs. sys, (I-B)x, f_B):
+ *   y = 2x - (2/n) Im(A Eone) x + (2/n) Im(A E(q x)).
+ * x, y real (N doubles).  precision: GNK_PREC_FP64 or GNK_PREC_FP32. */
+int gnk_apply_IminusN(const gnk_boundary* b, const double* x, double* y,
+                      int precision, void* stream);
+
+/* y = (D - diag(D1) + Lhat) x, the discrete M (Eqs. y, hD-bt, L-bs):
+ *   y = -(2/n) Re(A E(q x)) + (2/n) Re(A Eone) x + Lhat x,
+ * Lhat x computed per component by FFT with the exact multipliers of the
+ * circulant L (i 2k/n for k < n/2, 0 at k = n/2, i 2(k-n)/n above).
+ * x, y real.  precision applies to the pair sum. */
+int gnk_apply_M(const gnk_boundary* b, const double* x, double* y,
+                int precision, void* stream);
+
+/* y = Lhat x, the block-circulant part alone (Eq. L-bs).  x, y real. */
+int gnk_apply_circulant(const gnk_boundary* b, const double* x, double* y,
+                        void* stream);
+
+/* y = (diag(e) + B^T + Phat) x, the discrete I + N* + J (Eqs. sys*, BTx, g_B):
+ *   y = e x + (2/n) Im(q E(A x)) + Phat x,  Phat x = per-component mean.
+ * Needs a handle built with etpp (else GNK_EINVAL). */
+int gnk_apply_adjoint(const gnk_boundary* b, const double* x, double* y,
+                      int precision, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Solve (I - N) mu = -M gamma (Eq. ie) in the form (2I + diag(B1) - B) mu = -y
+ * (Eq. sys) by restarted GMRES (Eq. ie-gmres), device resident (Arnoldi with
+ * classical Gram-Schmidt and re-orthogonalisation, Givens rotations, and the
+ * convergence test all on the GPU).  gam, mu real (N doubles).  `opt` NULL
+ * means gnk_default_options.  `info` (nullable) receives the counters.
+ * Returns GNK_OK, or GNK_ENOTCONV with the best iterate written to mu.
+ * ------------------------------------------------------------------------- */
+int gnk_solve_ie(const gnk_boundary* b, const double* gam, double* mu,
+                 const gnk_options* opt, gnk_result* info, void* stream);
+
+/* h = ([D - diag(D1) + Lhat] mu - [2I + diag(B1) - B] gamma) / 2 (Eq. bh),
+ * the node values of the piecewise constant h, in FP64.  h (N doubles)
+ * receives the node values; hk (m1 doubles, nullable) the mean of h over
+ * each component. */
+int gnk_compute_h(const gnk_boundary* b, const double* mu, const double* gam,
+                  double* h, double* hk, void* stream);
+
+/* Solve (I + N* + J) mu = gamma (Eq. ie*) in the form
+ * (diag(e) + B^T + Phat) mu = gamma (Eq. sys*) by restarted GMRES
+ * (Eq. ie*-gmres).  Needs a handle built with etpp.  Arguments as
+ * gnk_solve_ie. */
+int gnk_solve_adjoint_ie(const gnk_boundary* b, const double* gam, double* mu,
+                         const gnk_options* opt, gnk_result* info,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNK_H */

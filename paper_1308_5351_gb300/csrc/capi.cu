@@ -1,0 +1,423 @@
+// C ABI of libgnk: argument checks, host/device staging and the handle's
+// lifecycle.  The numerical work is in pairsum.cu, circulant.cu, ops.cu and
+// krylov.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gnk_internal.h"
+
+namespace gnk {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of an input array of `count` doubles: the pointer itself when it
+// is device memory, else a copy in staging slot `slot` of the handle.
+int stage_in(const Boundary& b, const double* p, size_t count, int slot, cudaStream_t st,
+             const double** out) {
+    if (is_device_ptr(p)) {
+        *out = p;
+        return GNK_OK;
+    }
+    double* dst = b.stage + (size_t)slot * 2 * b.N;
+    GNK_TRY_CUDA(cudaMemcpyAsync(dst, p, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    *out = dst;
+    return GNK_OK;
+}
+
+struct Out {
+    double* user = nullptr;
+    double* dev = nullptr;
+    size_t count = 0;
+    bool host = false;
+};
+
+Out stage_out(const Boundary& b, double* p, size_t count, int slot) {
+    Out o;
+    o.user = p;
+    o.count = count;
+    o.host = !is_device_ptr(p);
+    o.dev = o.host ? b.stage + (size_t)slot * 2 * b.N : p;
+    return o;
+}
+
+int finish_out(const Out& o, cudaStream_t st) {
+    if (!o.host) return GNK_OK;
+    GNK_TRY_CUDA(cudaMemcpyAsync(o.user, o.dev, o.count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    return GNK_OK;
+}
+
+int check_handle(const gnk_boundary* h) {
+    if (!h) {
+        set_error("NULL boundary handle");
+        return GNK_EINVAL;
+    }
+    return GNK_OK;
+}
+
+int check_prec(int prec) {
+    if (prec != GNK_PREC_FP64 && prec != GNK_PREC_FP32) {
+        set_error("precision must be GNK_PREC_FP64 or GNK_PREC_FP32 here, got %d", prec);
+        return GNK_EINVAL;
+    }
+    return GNK_OK;
+}
+
+template <class T>
+int dmalloc(T** p, size_t count) {
+    if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed", count * sizeof(T));
+        return GNK_ENOMEM;
+    }
+    return GNK_OK;
+}
+
+void release(Boundary& b) {
+    void* ptrs[] = {b.et, b.etp, b.A, b.q, b.Eone, b.b1, b.d1, b.e, b.ref32, b.off32, b.et32,
+                    b.q32, b.A32, b.twiddle, b.Lcol, b.partial, b.zbuf, b.r0, b.r1, b.r2, b.r3,
+                    b.r4, b.means, b.stage, b.V, b.kry, b.kstate};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (b.hstate) cudaFreeHost(b.hstate);
+}
+
+int options_from(const gnk_options* in, gnk_options* o) {
+    gnk_default_options(o);
+    if (in) *o = *in;
+    if (o->restart < 1 || o->restart > 1000 || o->maxit < 1 || !(o->tol > 0.0) ||
+        (o->precision != GNK_PREC_FP64 && o->precision != GNK_PREC_MIXED) || o->max_refine < 0 ||
+        !(o->inner_tol > 0.0)) {
+        set_error("invalid gnk_options (restart 1..1000, maxit >= 1, tol > 0, precision FP64|MIXED, "
+                  "max_refine >= 0, inner_tol > 0)");
+        return GNK_EINVAL;
+    }
+    return GNK_OK;
+}
+
+int build(Boundary& b, int m1, int n, const double* et, const double* etp, const double* etpp,
+          const double* A, const double* Ap, int bounded, cudaStream_t st) {
+    const size_t N = (size_t)m1 * n;
+    b.m1 = m1;
+    b.n = n;
+    b.N = (int)N;
+    b.bounded = bounded ? 1 : 0;
+    b.has_adjoint = etpp != nullptr;
+    GNK_TRY_CUDA(cudaGetDevice(&b.device));
+    GNK_TRY_CUDA(cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, b.device));
+
+    const int tiles32 = (b.N + kSrcTile32 - 1) / kSrcTile32;
+    GNK_TRY(dmalloc(&b.et, N));
+    GNK_TRY(dmalloc(&b.etp, N));
+    GNK_TRY(dmalloc(&b.A, N));
+    GNK_TRY(dmalloc(&b.q, N));
+    GNK_TRY(dmalloc(&b.Eone, N));
+    GNK_TRY(dmalloc(&b.b1, N));
+    GNK_TRY(dmalloc(&b.d1, N));
+    GNK_TRY(dmalloc(&b.e, N));
+    GNK_TRY(dmalloc(&b.ref32, (size_t)tiles32));
+    GNK_TRY(dmalloc(&b.off32, N));
+    GNK_TRY(dmalloc(&b.et32, N));
+    GNK_TRY(dmalloc(&b.q32, N));
+    GNK_TRY(dmalloc(&b.A32, N));
+    GNK_TRY(dmalloc(&b.twiddle, (size_t)n));
+    GNK_TRY(dmalloc(&b.Lcol, (size_t)n));
+    GNK_TRY(dmalloc(&b.zbuf, kMaxRHS * N));
+    GNK_TRY(dmalloc(&b.r0, N));
+    GNK_TRY(dmalloc(&b.r1, N));
+    GNK_TRY(dmalloc(&b.r2, N));
+    GNK_TRY(dmalloc(&b.r3, N));
+    GNK_TRY(dmalloc(&b.r4, N));
+    GNK_TRY(dmalloc(&b.means, (size_t)m1));
+    GNK_TRY(dmalloc(&b.stage, 4 * 2 * N));
+
+    // geometry copies (host or device sources; cudaMemcpyDefault infers the direction)
+    GNK_TRY_CUDA(cudaMemcpyAsync(b.et, et, N * sizeof(double2), cudaMemcpyDefault, st));
+    GNK_TRY_CUDA(cudaMemcpyAsync(b.etp, etp, N * sizeof(double2), cudaMemcpyDefault, st));
+    GNK_TRY_CUDA(cudaMemcpyAsync(b.A, A, N * sizeof(double2), cudaMemcpyDefault, st));
+    const double* d_etpp = nullptr;
+    const double* d_Ap = nullptr;
+    if (etpp) {
+        double* s0 = b.stage;
+        GNK_TRY_CUDA(cudaMemcpyAsync(s0, etpp, N * sizeof(double2), cudaMemcpyDefault, st));
+        d_etpp = s0;
+        if (Ap) {
+            double* s1 = b.stage + 2 * N;
+            GNK_TRY_CUDA(cudaMemcpyAsync(s1, Ap, N * sizeof(double2), cudaMemcpyDefault, st));
+            d_Ap = s1;
+        }
+    }
+    int* d_flag = nullptr;
+    GNK_TRY(dmalloc(&d_flag, 1));
+    GNK_TRY_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    GNK_TRY_CUDA(cudaMemsetAsync(b.e, 0, N * sizeof(double), st));
+    int s = run_prepare_geometry(b, d_etpp, d_Ap, d_flag, st);
+    int flag = 0;
+    if (s == GNK_OK) {
+        cudaError_t e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("geometry preparation failed: %s", cudaGetErrorString(e));
+            s = GNK_ECUDA;
+        }
+    }
+    cudaFree(d_flag);
+    GNK_TRY(s);
+    if (flag & 1) {
+        set_error("non-finite value in eta, eta', eta'', A or A'");
+        return GNK_ENONFINITE;
+    }
+    if (flag & 2) {
+        set_error("A(t) vanishes at a node");
+        return GNK_EINVAL;
+    }
+
+    // launch plans and the split-source workspace
+    b.plan64 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP64), kThreads64 * kTargets64,
+                         kSrcTile64);
+    b.plan32 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP32), kThreads32 * kTargets32,
+                         kSrcTile32);
+    GNK_TRY(pair_workspace_bytes(b, &b.partial_bytes));
+    GNK_TRY(dmalloc(reinterpret_cast<char**>(&b.partial), b.partial_bytes));
+
+    // Eone = E q with diag(B1), diag(D1); with eta'' also E eta' and e (Eq. bve)
+    PairJob j;
+    j.R = b.has_adjoint ? 2 : 1;
+    j.mode = W_COMPLEX;
+    j.w[0] = b.q;
+    j.w[1] = b.etp;
+    j.epi = EPI_EONE;
+    j.out_c = b.Eone;
+    j.out = b.b1;
+    j.out2 = b.d1;
+    j.out3 = b.e;
+    GNK_TRY(run_pairsum64(b, j, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    return GNK_OK;
+}
+
+}  // namespace
+}  // namespace gnk
+
+using namespace gnk;
+
+extern "C" {
+
+void gnk_default_options(gnk_options* o) {
+    if (!o) return;
+    o->restart = 20;
+    o->maxit = 50;
+    o->tol = 1e-12;
+    o->precision = GNK_PREC_FP64;
+    o->max_refine = 10;
+    o->inner_tol = 1e-5;
+}
+
+int gnk_last_error(char* buf, size_t len) {
+    const int l = (int)strlen(g_err);
+    if (buf && len > 0) {
+        strncpy(buf, g_err, len - 1);
+        buf[len - 1] = '\0';
+    }
+    return l;
+}
+
+const char* gnk_version(void) { return "gnk-gb300 0.1 (sm_103a)"; }
+
+int gnk_build_boundary(gnk_boundary** out, int m1, int n, const double* et, const double* etp,
+                       const double* etpp, const double* A, const double* Ap, int bounded,
+                       void* stream) {
+    if (!out || !et || !etp || !A) {
+        set_error("gnk_build_boundary: out, et, etp and A must not be NULL");
+        return GNK_EINVAL;
+    }
+    *out = nullptr;
+    if (m1 < 1 || n < 4 || (n % 2) != 0) {
+        set_error("gnk_build_boundary: need m1 >= 1 and n even, n >= 4 (got m1=%d n=%d)", m1, n);
+        return GNK_EINVAL;
+    }
+    if ((long long)m1 * n > (1LL << 28)) {
+        set_error("gnk_build_boundary: (m+1) n = %lld exceeds 2^28 nodes", (long long)m1 * n);
+        return GNK_EINVAL;
+    }
+    gnk_boundary* h = new (std::nothrow) gnk_boundary();
+    if (!h) {
+        set_error("host allocation failed");
+        return GNK_ENOMEM;
+    }
+    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, (cudaStream_t)stream);
+    if (s != GNK_OK) {
+        release(h->b);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return GNK_OK;
+}
+
+int gnk_free_boundary(gnk_boundary* h) {
+    if (!h) return GNK_OK;
+    release(h->b);
+    delete h;
+    return GNK_OK;
+}
+
+int gnk_boundary_size(const gnk_boundary* h, int* m1, int* n) {
+    GNK_TRY(check_handle(h));
+    if (m1) *m1 = h->b.m1;
+    if (n) *n = h->b.n;
+    return GNK_OK;
+}
+
+int gnk_cauchy_sum(const gnk_boundary* h, const double* w, double* z, int precision, void* stream) {
+    GNK_TRY(check_handle(h));
+    GNK_TRY(check_prec(precision));
+    if (!w || !z) {
+        set_error("gnk_cauchy_sum: NULL array");
+        return GNK_EINVAL;
+    }
+    const Boundary& b = h->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* dw;
+    GNK_TRY(stage_in(b, w, 2 * (size_t)b.N, 0, st, &dw));
+    Out o = stage_out(b, z, 2 * (size_t)b.N, 1);
+    PairJob j;
+    j.R = 1;
+    j.mode = W_COMPLEX;
+    j.w[0] = reinterpret_cast<const double2*>(dw);
+    j.epi = EPI_Z;
+    j.out_c = reinterpret_cast<double2*>(o.dev);
+    GNK_TRY(run_pairsum(b, j, precision, st));
+    return finish_out(o, st);
+}
+
+typedef int (*unary_op)(const Boundary&, const double*, double*, int, cudaStream_t);
+
+static int apply_unary(const gnk_boundary* h, const double* x, double* y, int prec, void* stream,
+                       int which) {
+    GNK_TRY(check_handle(h));
+    GNK_TRY(check_prec(prec));
+    if (!x || !y) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    const Boundary& b = h->b;
+    if (which == 2 && !b.has_adjoint) {
+        set_error("the adjoint operator needs a handle built with eta''");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* dx;
+    GNK_TRY(stage_in(b, x, b.N, 0, st, &dx));
+    Out o = stage_out(b, y, b.N, 1);
+    if (which == 0) GNK_TRY(op_IminusN(b, dx, o.dev, prec, st));
+    else if (which == 1) GNK_TRY(op_M(b, dx, o.dev, prec, st));
+    else if (which == 2) GNK_TRY(op_adjoint(b, dx, o.dev, prec, st));
+    else GNK_TRY(run_circulant(b, dx, o.dev, st));
+    return finish_out(o, st);
+}
+
+int gnk_apply_IminusN(const gnk_boundary* h, const double* x, double* y, int precision, void* stream) {
+    return apply_unary(h, x, y, precision, stream, 0);
+}
+
+int gnk_apply_M(const gnk_boundary* h, const double* x, double* y, int precision, void* stream) {
+    return apply_unary(h, x, y, precision, stream, 1);
+}
+
+int gnk_apply_adjoint(const gnk_boundary* h, const double* x, double* y, int precision, void* stream) {
+    return apply_unary(h, x, y, precision, stream, 2);
+}
+
+int gnk_apply_circulant(const gnk_boundary* h, const double* x, double* y, void* stream) {
+    return apply_unary(h, x, y, GNK_PREC_FP64, stream, 3);
+}
+
+static int solve_common(const gnk_boundary* h, const double* gam, double* mu, const gnk_options* opt,
+                        gnk_result* info, void* stream, int adjoint) {
+    GNK_TRY(check_handle(h));
+    if (!gam || !mu) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    gnk_options o;
+    GNK_TRY(options_from(opt, &o));
+    const Boundary& b = h->b;
+    if (adjoint && !b.has_adjoint) {
+        set_error("gnk_solve_adjoint_ie needs a handle built with eta''");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* dg;
+    GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
+    Out o_mu = stage_out(b, mu, b.N, 1);
+    const double* rhs = dg;
+    if (!adjoint) {
+        // right-hand side -y = -(D - diag(D1) + Lhat) gamma (Eqs. sys, y)
+        GNK_TRY(op_M(b, dg, b.r4, GNK_PREC_FP64, st));
+        GNK_TRY(op_negate(b.r4, b.N, st));
+        rhs = b.r4;
+    }
+    const int s = solve(b, adjoint, rhs, o_mu.dev, o, info, st);
+    if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+    GNK_TRY(finish_out(o_mu, st));
+    if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles");
+    if (s == GNK_ENONFINITE) set_error("non-finite value in the GMRES iteration");
+    return s;
+}
+
+int gnk_solve_ie(const gnk_boundary* h, const double* gam, double* mu, const gnk_options* opt,
+                 gnk_result* info, void* stream) {
+    return solve_common(h, gam, mu, opt, info, stream, 0);
+}
+
+int gnk_solve_adjoint_ie(const gnk_boundary* h, const double* gam, double* mu, const gnk_options* opt,
+                         gnk_result* info, void* stream) {
+    return solve_common(h, gam, mu, opt, info, stream, 1);
+}
+
+int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,
+                  void* stream) {
+    GNK_TRY(check_handle(h));
+    if (!mu || !gam || !hv) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    const Boundary& b = h->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *dmu, *dg;
+    GNK_TRY(stage_in(b, mu, b.N, 0, st, &dmu));
+    GNK_TRY(stage_in(b, gam, b.N, 1, st, &dg));
+    Out o_h = stage_out(b, hv, b.N, 2);
+    GNK_TRY(op_h(b, dmu, dg, o_h.dev, st));
+    if (hk) {
+        Out o_k = stage_out(b, hk, b.m1, 3);
+        GNK_TRY(run_component_means(b, o_h.dev, o_k.dev, st));
+        GNK_TRY(finish_out(o_k, st));
+    }
+    return finish_out(o_h, st);
+}
+
+}  // extern "C"

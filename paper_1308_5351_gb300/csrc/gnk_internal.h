@@ -1,0 +1,173 @@
+// Internal declarations of libgnk (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/gnk.h"
+
+namespace gnk {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+#define GNK_TRY_CUDA(call)                                                     \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            ::gnk::set_error("%s failed: %s (%s:%d)", #call,                    \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);      \
+            return GNK_ECUDA;                                                  \
+        }                                                                      \
+    } while (0)
+
+#define GNK_TRY(call)                                                          \
+    do {                                                                       \
+        int s_ = (call);                                                       \
+        if (s_ != GNK_OK) return s_;                                           \
+    } while (0)
+
+// ---------------------------------------------------------------- tiling
+// Sources per shared-memory tile of the pair-sum kernels.
+constexpr int kSrcTile64 = 128;   // FP64 kernel
+constexpr int kSrcTile32 = 256;   // FP32 kernel (also the tile of the FP32 reference points)
+constexpr int kThreads64 = 128;   // threads per block, FP64 kernel
+constexpr int kTargets64 = 2;     // targets per thread, FP64 kernel
+constexpr int kThreads32 = 256;   // threads per block, FP32 kernel
+constexpr int kTargets32 = 4;     // targets per thread, FP32 kernel
+constexpr int kMaxRHS = 2;        // right-hand sides per pair-sum launch
+
+// How the sources' complex weights are formed when a source tile is loaded.
+enum WeightMode : int {
+    W_COMPLEX = 0,   // w_j given (complex)
+    W_SCALED = 1,    // w_j = s_j * x_j, s complex, x real
+};
+
+// Pointwise epilogues applied after the partial sums are reduced; they
+// implement the operators of Secs. 3 and 4 around z = E w.
+enum Epilogue : int {
+    EPI_Z = 0,        // out_c = z
+    EPI_IMINUSN = 1,  // out = 2x + b1 x + (2/n) Im(A z)                 (f_B)
+    EPI_M = 2,        // out = -(2/n) Re(A z) - d1 x + Lx               (f_C)
+    EPI_ADJ = 3,      // out = e x + (2/n) Im(q z) + mean_k(x)           (g_B)
+    EPI_RESID = 4,    // out = rhs - f_B(x)
+    EPI_RESID_ADJ = 5,// out = rhs - g_B(x)
+    EPI_H = 6,        // out = (f_C(mu) - f_B(gam)) / 2, z = E(q mu), z2 = E(q gam)
+    EPI_EONE = 7,     // b1 = -(2/n) Im(A z), d1 = -(2/n) Re(A z); if R=2: e from z2
+};
+
+struct PairPlan {
+    int tiles_tgt = 0;     // target tiles (blocks along x)
+    int tiles_src = 0;     // source tiles
+    int chunks = 1;        // source chunks (blocks along y)
+    int tiles_per_chunk = 0;
+};
+
+// Everything a launch of the pair-sum + reduce pipeline needs.
+struct PairJob {
+    int R = 1;                    // right-hand sides
+    int mode = W_SCALED;
+    const double2* w[kMaxRHS] = {nullptr, nullptr};   // W_COMPLEX
+    const double* x[kMaxRHS] = {nullptr, nullptr};    // W_SCALED
+    const double2* s = nullptr;                        // W_SCALED scale (q or A)
+    int epi = EPI_Z;
+    double2* out_c = nullptr;     // EPI_Z: complex output(s), R x N
+    double* out = nullptr;        // real output
+    double* out2 = nullptr;       // EPI_EONE: second real output
+    double* out3 = nullptr;       // EPI_EONE: third real output (e)
+    const double* ex = nullptr;   // epilogue x (the vector the operator acts on)
+    const double* ex2 = nullptr;  // EPI_H: gamma
+    const double* rhs = nullptr;  // EPI_RESID*
+    const double* Lx = nullptr;   // EPI_M / EPI_H: Lhat x
+    const double* means = nullptr;// EPI_ADJ: per-component means of x
+    const int* done = nullptr;    // skip the whole job if *done != 0
+};
+
+// ---------------------------------------------------------------- handle
+struct Boundary {
+    int m1 = 0, n = 0, N = 0;
+    int bounded = 0;
+    int has_adjoint = 0;
+    int device = 0;
+    int sms = 0;
+
+    // FP64 geometry and precomputed diagonals (device)
+    double2* et = nullptr;
+    double2* etp = nullptr;
+    double2* A = nullptr;
+    double2* q = nullptr;       // eta'/A
+    double2* Eone = nullptr;    // E q
+    double* b1 = nullptr;       // diag(B 1)
+    double* d1 = nullptr;       // diag(D 1)
+    double* e = nullptr;        // adjoint diagonal (nullptr without eta'')
+
+    // FP32 geometry: positions relative to one reference node per source tile
+    float4* ref32 = nullptr;    // per source tile: (hi.x, hi.y, lo.x, lo.y) of the reference
+    float2* off32 = nullptr;    // per node: eta_j - ref(tile(j)), rounded to FP32
+    float4* et32 = nullptr;     // per node: hi/lo split of eta (hi.x, hi.y, lo.x, lo.y)
+    float2* q32 = nullptr;
+    float2* A32 = nullptr;
+
+    // circulant part
+    int fft_pow2 = 0;           // n is a power of two
+    double2* twiddle = nullptr; // exp(-2 pi i k / n), k < n/2
+    double* Lcol = nullptr;     // first column of L (direct product fallback)
+
+    // workspace
+    void* partial = nullptr;    // split-source partial sums
+    size_t partial_bytes = 0;
+    double2* zbuf = nullptr;    // complex scratch, kMaxRHS x N
+    double* r0 = nullptr;       // real scratch vectors (N each)
+    double* r1 = nullptr;
+    double* r2 = nullptr;
+    double* r3 = nullptr;
+    double* r4 = nullptr;
+    double* means = nullptr;    // m1
+    double* stage = nullptr;    // host-staging buffers: 4 x 2N doubles
+    PairPlan plan64, plan32;
+
+    // Krylov workspace (allocated on first solve, grown as needed)
+    double* V = nullptr;        // (restart+1) x N
+    int V_cols = 0;
+    double* kry = nullptr;      // small dense state (H, g, cs, sn, y, partials)
+    size_t kry_bytes = 0;
+    void* kstate = nullptr;     // device KrylovState
+    void* hstate = nullptr;     // pinned host mirror of KrylovState
+};
+
+// ---------------------------------------------------------------- pair sums
+PairPlan make_plan(int N, int sms, int blocks_per_sm, int targets_per_block, int src_tile);
+int pair_workspace_bytes(const Boundary& b, size_t* bytes);
+int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st);
+int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st);
+int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st);
+int pair_blocks_per_sm(int precision);
+
+// ---------------------------------------------------------------- circulant / pointwise
+int run_circulant(const Boundary& b, const double* x, double* y, cudaStream_t st);
+int run_component_means(const Boundary& b, const double* x, double* means, cudaStream_t st);
+int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int* d_flag,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------- operators (ops.cu)
+int op_IminusN(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+               const int* done = nullptr);
+int op_M(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st);
+int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+               const int* done = nullptr);
+int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
+             int prec, cudaStream_t st);
+int op_h(const Boundary& b, const double* mu, const double* gam, double* h, cudaStream_t st);
+int op_negate(double* x, int N, cudaStream_t st);
+
+// ---------------------------------------------------------------- Krylov (krylov.cu)
+int solve(const Boundary& b, int adjoint, const double* rhs, double* x,
+          const gnk_options& opt, gnk_result* info, cudaStream_t st);
+
+}  // namespace gnk
+
+struct gnk_boundary {
+    gnk::Boundary b;
+};

@@ -1,0 +1,458 @@
+// Restarted GMRES (Sec. 3.5, Eq. ie-gmres; Sec. 4.5, Eq. ie*-gmres) with
+// every Arnoldi, Givens and convergence step on the device, and FP64
+// iterative refinement around an FP32-operator GMRES for GNK_PREC_MIXED.
+//
+// Semantics follow MATLAB's gmres(A, b, restart, tol, maxit) as used by the
+// paper: x0 = 0, no preconditioner, cycles of at most `restart` Arnoldi
+// steps, at most `maxit` cycles, stop when ||b - A x||_2 <= tol ||b||_2 with
+// the residual recomputed from x at the start of every cycle.
+//
+// Orthogonalisation is classical Gram-Schmidt applied twice (CGS2): each pass
+// is one multi-dot and one update over the basis, which maps to two
+// bandwidth-bound kernels instead of j dependent passes.  Reductions finish
+// in the last block to arrive (atomic ticket + fence, no spinning) and add
+// the per-block partials in a fixed order, so results are reproducible.
+// Inside a cycle every kernel first reads the device flag `done`, so the host
+// enqueues a whole cycle without waiting and synchronises once per cycle.
+#include <cmath>
+#include <cstring>
+
+#include "gnk_internal.h"
+
+namespace gnk {
+namespace {
+
+struct KState {
+    double bnorm;     // ||b||
+    double beta;      // ||r|| at the start of the current cycle
+    double tol;       // relative tolerance
+    double est;       // Givens residual estimate |g_{k}|
+    double hnext;     // h_{j+1,j} of the last step (before rotation)
+    int k;            // Arnoldi steps completed in the current cycle
+    int last_k;       // steps of the previous cycle
+    int done;         // the current cycle has finished
+    int nonfinite;    // a NaN/Inf was met
+    int restart;
+    unsigned counter; // last-block ticket
+};
+
+constexpr int KT = 256;       // threads per block of the vector kernels
+constexpr int KB_MAX = 256;   // maximum blocks of the vector kernels
+
+struct KPtrs {
+    double* H;     // (restart+1) x restart, column-major, ld = restart+1
+    double* g;     // restart+1
+    double* cs;    // restart
+    double* sn;    // restart
+    double* h1;    // restart+1
+    double* h2;    // restart+1
+    double* y;     // restart
+    double* part;  // KB_MAX x ld
+    int ld;
+};
+
+size_t kry_doubles(int restart) {
+    const size_t ld = restart + 1;
+    return ld * restart + ld + 2 * (size_t)restart + 2 * ld + restart + KB_MAX * ld;
+}
+
+KPtrs kry_ptrs(double* base, int restart) {
+    KPtrs p;
+    p.ld = restart + 1;
+    p.H = base;
+    p.g = p.H + (size_t)p.ld * restart;
+    p.cs = p.g + p.ld;
+    p.sn = p.cs + restart;
+    p.h1 = p.sn + restart;
+    p.h2 = p.h1 + p.ld;
+    p.y = p.h2 + p.ld;
+    p.part = p.y + restart;
+    return p;
+}
+
+int vec_blocks(int N) {
+    const int b = (N + KT * 4 - 1) / (KT * 4);
+    return b < 1 ? 1 : (b > KB_MAX ? KB_MAX : b);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < KT / 32; ++w) s += red[w];
+    return s;  // valid in thread 0
+}
+
+// True in every thread of the last block to finish writing its partials.
+__device__ __forceinline__ bool arrive_last(unsigned* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last;
+}
+
+// ||x||^2 partials -> last block: mode 0 stores bnorm; mode 1 starts a cycle.
+__global__ void __launch_bounds__(KT) k_norm(const double* __restrict__ x, int N, KPtrs p,
+                                             KState* s, int mode) {
+    __shared__ double red[KT / 32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) acc = fma(x[i], x[i], acc);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = acc;
+    if (!arrive_last(&s->counter)) return;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < gridDim.x; ++b) t += p.part[b];
+        const double nrm = sqrt(t);
+        if (mode == 0) {
+            s->bnorm = nrm;
+        } else {
+            s->beta = nrm;
+            s->est = nrm;
+            s->last_k = s->k;
+            s->k = 0;
+            if (!isfinite(nrm)) s->nonfinite = 1;
+            s->done = (!(nrm > s->tol * s->bnorm)) ? 1 : 0;  // also stops on NaN
+            p.g[0] = nrm;
+            for (int k = 1; k <= s->restart; ++k) p.g[k] = 0.0;
+        }
+        s->counter = 0;
+    }
+}
+
+// v0 = r / beta
+__global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r, double* __restrict__ v0,
+                                                    int N, const KState* s) {
+    if (s->done) return;
+    const double inv = 1.0 / s->beta;
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) v0[i] = r[i] * inv;
+}
+
+// h[k] = <v_k, w>, k < nv
+__global__ void __launch_bounds__(KT) k_dots(const double* __restrict__ V, int N, int nv,
+                                             const double* __restrict__ w, KPtrs p, double* hout,
+                                             KState* s) {
+    if (s->done) return;
+    __shared__ double red[KT / 32];
+    for (int k = 0; k < nv; ++k) {
+        const double* v = V + (size_t)k * N;
+        double acc = 0.0;
+        for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) acc = fma(v[i], w[i], acc);
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) p.part[(size_t)blockIdx.x * p.ld + k] = acc;
+    }
+    if (!arrive_last(&s->counter)) return;
+    for (int k = threadIdx.x; k < nv; k += KT) {
+        double t = 0.0;
+        for (int b = 0; b < gridDim.x; ++b) t += p.part[(size_t)b * p.ld + k];
+        hout[k] = t;
+    }
+    if (threadIdx.x == 0) s->counter = 0;
+}
+
+// w -= V h (first pass)
+__global__ void __launch_bounds__(KT) k_update(const double* __restrict__ V, int N, int nv,
+                                               double* __restrict__ w, const double* __restrict__ h,
+                                               const KState* s) {
+    if (s->done) return;
+    __shared__ double hs[1024];
+    for (int k = threadIdx.x; k < nv; k += KT) hs[k] = h[k];
+    __syncthreads();
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+        double acc = w[i];
+        for (int k = 0; k < nv; ++k) acc = fma(-hs[k], V[(size_t)k * N + i], acc);
+        w[i] = acc;
+    }
+}
+
+// w -= V h2 (second pass), ||w|| -> H(j+1, j); H(:, j) = h1 + h2; Givens
+// rotations; residual estimate; end-of-cycle test and the small triangular
+// solve H y = g when the cycle ends.
+__global__ void __launch_bounds__(KT) k_update_norm_givens(const double* __restrict__ V, int N, int j,
+                                                           double* __restrict__ w, KPtrs p, KState* s) {
+    if (s->done) return;
+    __shared__ double red[KT / 32];
+    __shared__ double hs[1024];
+    const int nv = j + 1;
+    for (int k = threadIdx.x; k < nv; k += KT) hs[k] = p.h2[k];
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+        double wi = w[i];
+        for (int k = 0; k < nv; ++k) wi = fma(-hs[k], V[(size_t)k * N + i], wi);
+        w[i] = wi;
+        acc = fma(wi, wi, acc);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = acc;
+    if (!arrive_last(&s->counter)) return;
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < gridDim.x; ++b) t += p.part[b];
+    const double hn = sqrt(t);
+    double* col = p.H + (size_t)j * p.ld;
+    for (int k = 0; k < nv; ++k) col[k] = p.h1[k] + p.h2[k];
+    col[j + 1] = hn;
+    s->hnext = hn;
+    for (int k = 0; k < j; ++k) {  // previous rotations
+        const double a = col[k], b = col[k + 1];
+        col[k] = p.cs[k] * a + p.sn[k] * b;
+        col[k + 1] = -p.sn[k] * a + p.cs[k] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double r = hypot(a, b);
+    const double c = (r > 0.0) ? a / r : 1.0;
+    const double sn = (r > 0.0) ? b / r : 0.0;
+    p.cs[j] = c;
+    p.sn[j] = sn;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    p.g[j + 1] = -sn * p.g[j];
+    p.g[j] = c * p.g[j];
+    const double est = fabs(p.g[j + 1]);
+    s->est = est;
+    s->k = j + 1;
+    const bool bad = !isfinite(est) || !isfinite(hn);
+    if (bad) s->nonfinite = 1;
+    const bool stop = bad || est <= s->tol * s->bnorm || j + 1 == s->restart || hn == 0.0;
+    if (stop) {
+        // back substitution H(0:k, 0:k) y = g(0:k)
+        const int kk = j + 1;
+        for (int row = kk - 1; row >= 0; --row) {
+            double v = p.g[row];
+            for (int cidx = row + 1; cidx < kk; ++cidx) v -= p.H[(size_t)cidx * p.ld + row] * p.y[cidx];
+            const double d = p.H[(size_t)row * p.ld + row];
+            p.y[row] = (d != 0.0) ? v / d : 0.0;
+        }
+        s->done = 1;
+    }
+    s->counter = 0;
+}
+
+// v_{j+1} = w / h_{j+1,j} (in place)
+__global__ void __launch_bounds__(KT) k_scale_next(double* __restrict__ w, int N, const KState* s) {
+    if (s->done) return;
+    const double inv = 1.0 / s->hnext;
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) w[i] *= inv;
+}
+
+// x += V(:, 0:k) y at the end of a cycle
+__global__ void __launch_bounds__(KT) k_update_x(const double* __restrict__ V, int N, KPtrs p,
+                                                 double* __restrict__ x, const KState* s) {
+    const int kk = s->k;
+    if (kk == 0) return;
+    __shared__ double ys[1024];
+    for (int k = threadIdx.x; k < kk; k += KT) ys[k] = p.y[k];
+    __syncthreads();
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+        double acc = x[i];
+        for (int k = 0; k < kk; ++k) acc = fma(ys[k], V[(size_t)k * N + i], acc);
+        x[i] = acc;
+    }
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) x[i] += d[i];
+}
+
+__global__ void k_init_state(KState* s, double tol, int restart) {
+    s->bnorm = 0.0;
+    s->beta = 0.0;
+    s->tol = tol;
+    s->est = 0.0;
+    s->hnext = 0.0;
+    s->k = 0;
+    s->last_k = 0;
+    s->done = 0;
+    s->nonfinite = 0;
+    s->restart = restart;
+    s->counter = 0;
+}
+
+int ensure_krylov(Boundary& b, int restart) {
+    if (restart + 1 > 1024) {
+        set_error("restart must be below 1024");
+        return GNK_EINVAL;
+    }
+    if (b.V_cols < restart + 1) {
+        if (b.V) cudaFree(b.V);
+        b.V = nullptr;
+        b.V_cols = 0;
+        if (cudaMalloc(&b.V, (size_t)(restart + 1) * b.N * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate the Krylov basis: %d x %d doubles", restart + 1, b.N);
+            return GNK_ENOMEM;
+        }
+        b.V_cols = restart + 1;
+    }
+    const size_t need = kry_doubles(restart) * sizeof(double);
+    if (b.kry_bytes < need) {
+        if (b.kry) cudaFree(b.kry);
+        b.kry = nullptr;
+        b.kry_bytes = 0;
+        GNK_TRY_CUDA(cudaMalloc(&b.kry, need));
+        b.kry_bytes = need;
+    }
+    if (!b.kstate) {
+        GNK_TRY_CUDA(cudaMalloc(&b.kstate, sizeof(KState)));
+        GNK_TRY_CUDA(cudaMemset(b.kstate, 0, sizeof(KState)));
+    }
+    if (!b.hstate) GNK_TRY_CUDA(cudaMallocHost(&b.hstate, sizeof(KState)));
+    return GNK_OK;
+}
+
+int apply_op(const Boundary& b, int adjoint, const double* x, double* y, int prec, cudaStream_t st,
+             const int* done) {
+    return adjoint ? op_adjoint(b, x, y, prec, st, done) : op_IminusN(b, x, y, prec, st, done);
+}
+
+int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
+    GNK_TRY_CUDA(cudaMemcpyAsync(b.hstate, b.kstate, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(hs, b.hstate, sizeof(KState));
+    return GNK_OK;
+}
+
+// One restarted GMRES solve of A x = rhs with the operator in precision prec.
+// r is a work vector.  Counters are added to *res; *relres receives the final
+// true relative residual (in prec).
+int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, double* r,
+          int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st) {
+    GNK_TRY(ensure_krylov(b, restart));
+    const int N = b.N;
+    KState* ks = static_cast<KState*>(b.kstate);
+    KPtrs p = kry_ptrs(b.kry, restart);
+    const int nb = vec_blocks(N);
+    KState hs;
+    k_init_state<<<1, 1, 0, st>>>(ks, tol, restart);
+    k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0);
+    GNK_TRY_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), st));
+    GNK_TRY_CUDA(cudaGetLastError());
+    int status = GNK_ENOTCONV;
+    for (int cycle = 0;; ++cycle) {
+        if (cycle == 0) {
+            GNK_TRY_CUDA(cudaMemcpyAsync(r, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            GNK_TRY(op_resid(b, adjoint, rhs, x, r, prec, st));
+            if (prec == GNK_PREC_FP32) res->matvecs_fp32++; else res->matvecs_fp64++;
+        }
+        k_norm<<<nb, KT, 0, st>>>(r, N, p, ks, 1);
+        k_scale_first<<<nb, KT, 0, st>>>(r, b.V, N, ks);
+        GNK_TRY_CUDA(cudaGetLastError());
+        GNK_TRY(read_state(b, &hs, st));
+        if (cycle > 0) {  // the previous cycle's step count is known only now
+            res->iterations += hs.last_k;
+            if (prec == GNK_PREC_FP32) res->matvecs_fp32 += hs.last_k; else res->matvecs_fp64 += hs.last_k;
+        }
+        if (hs.bnorm == 0.0) {
+            *relres = 0.0;
+            status = GNK_OK;
+            break;
+        }
+        *relres = hs.beta / hs.bnorm;
+        if (hs.nonfinite || !std::isfinite(*relres)) {
+            status = GNK_ENONFINITE;
+            break;
+        }
+        if (*relres <= tol) {
+            status = GNK_OK;
+            break;
+        }
+        if (cycle == maxit) {
+            status = GNK_ENOTCONV;
+            break;
+        }
+        res->cycles++;
+        for (int j = 0; j < restart; ++j) {
+            double* vj = b.V + (size_t)j * N;
+            double* w = b.V + (size_t)(j + 1) * N;
+            GNK_TRY(apply_op(b, adjoint, vj, w, prec, st, &ks->done));
+            k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h1, ks);
+            k_update<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p.h1, ks);
+            k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h2, ks);
+            k_update_norm_givens<<<nb, KT, 0, st>>>(b.V, N, j, w, p, ks);
+            k_scale_next<<<nb, KT, 0, st>>>(w, N, ks);
+            GNK_TRY_CUDA(cudaGetLastError());
+        }
+        k_update_x<<<nb, KT, 0, st>>>(b.V, N, p, x, ks);
+        GNK_TRY_CUDA(cudaGetLastError());
+    }
+    return status;
+}
+
+int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
+    KState* ks = static_cast<KState*>(b.kstate);
+    KPtrs p = kry_ptrs(b.kry, b.V_cols - 1);
+    k_norm<<<vec_blocks(b.N), KT, 0, st>>>(v, b.N, p, ks, 0);
+    GNK_TRY_CUDA(cudaGetLastError());
+    KState hs;
+    GNK_TRY(read_state(b, &hs, st));
+    *out = hs.bnorm;
+    return GNK_OK;
+}
+
+}  // namespace
+
+int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const gnk_options& opt,
+          gnk_result* info, cudaStream_t st) {
+    Boundary& b = const_cast<Boundary&>(bc);  // workspace only
+    gnk_result res;
+    std::memset(&res, 0, sizeof(res));
+    double relres = 0.0;
+    int status;
+    if (opt.precision == GNK_PREC_FP64) {
+        status = gmres(b, adjoint, GNK_PREC_FP64, rhs, x, b.r0, opt.restart, opt.maxit, opt.tol, &res,
+                       &relres, st);
+    } else {
+        // FP64 iterative refinement: r = rhs - A x (FP64), A d = r with the
+        // FP32 operator to inner_tol, x += d.
+        GNK_TRY(ensure_krylov(b, opt.restart));
+        double* rr = b.r1;
+        double* dd = b.r2;
+        const int N = b.N;
+        GNK_TRY_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), st));
+        GNK_TRY_CUDA(cudaMemcpyAsync(rr, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        double bnorm = 0.0;
+        GNK_TRY(norm_host(b, rhs, &bnorm, st));
+        status = GNK_ENOTCONV;
+        for (int it = 0;; ++it) {
+            double rn = 0.0;
+            GNK_TRY(norm_host(b, rr, &rn, st));
+            relres = (bnorm > 0.0) ? rn / bnorm : 0.0;
+            if (!std::isfinite(relres)) {
+                status = GNK_ENONFINITE;
+                break;
+            }
+            if (relres <= opt.tol) {
+                status = GNK_OK;
+                break;
+            }
+            if (it == opt.max_refine) break;
+            double inner_rel = 0.0;
+            const int s = gmres(b, adjoint, GNK_PREC_FP32, rr, dd, b.r0, opt.restart, opt.maxit,
+                                opt.inner_tol, &res, &inner_rel, st);
+            if (s == GNK_ENONFINITE) {
+                status = s;
+                break;
+            }
+            k_axpy<<<(N + 255) / 256, 256, 0, st>>>(x, dd, N);
+            GNK_TRY_CUDA(cudaGetLastError());
+            GNK_TRY(op_resid(b, adjoint, rhs, x, rr, GNK_PREC_FP64, st));
+            res.matvecs_fp64++;
+            res.refinements++;
+        }
+    }
+    res.status = status;
+    res.relres = relres;
+    if (info) *info = res;
+    return status;
+}
+
+}  // namespace gnk

@@ -1,0 +1,108 @@
+// The discrete operators of Secs. 3 and 4 as sequences of launches on one
+// stream: an optional circulant or mean pass, then one pair-sum job whose
+// epilogue forms the operator's output.
+#include "gnk_internal.h"
+
+namespace gnk {
+
+// y = (2I + diag(B1) - B) x   (Eqs. sys, (I-B)x, f_B)
+int op_IminusN(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+               const int* done) {
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.s = b.q;
+    j.epi = EPI_IMINUSN;
+    j.out = y;
+    j.ex = x;
+    j.done = done;
+    return run_pairsum(b, j, prec, st);
+}
+
+// y = (D - diag(D1) + Lhat) x   (Eqs. y, hD-bt, L-bs)
+int op_M(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st) {
+    GNK_TRY(run_circulant(b, x, b.r3, st));
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.s = b.q;
+    j.epi = EPI_M;
+    j.out = y;
+    j.ex = x;
+    j.Lx = b.r3;
+    return run_pairsum(b, j, prec, st);
+}
+
+// y = (diag(e) + B^T + Phat) x   (Eqs. sys*, BTx, g_B)
+int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+               const int* done) {
+    GNK_TRY(run_component_means(b, x, b.means, st));
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.s = b.A;
+    j.epi = EPI_ADJ;
+    j.out = y;
+    j.ex = x;
+    j.means = b.means;
+    j.done = done;
+    return run_pairsum(b, j, prec, st);
+}
+
+// r = rhs - A x for A = f_B (adjoint = 0) or g_B (adjoint = 1)
+int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
+             int prec, cudaStream_t st) {
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.ex = x;
+    j.rhs = rhs;
+    j.out = r;
+    if (adjoint) {
+        GNK_TRY(run_component_means(b, x, b.means, st));
+        j.s = b.A;
+        j.epi = EPI_RESID_ADJ;
+        j.means = b.means;
+    } else {
+        j.s = b.q;
+        j.epi = EPI_RESID;
+    }
+    return run_pairsum(b, j, prec, st);
+}
+
+// h = ([D - diag(D1) + Lhat] mu - [2I + diag(B1) - B] gamma) / 2   (Eq. bh);
+// both Cauchy sums E(q mu) and E(q gamma) come from one two-RHS launch.
+int op_h(const Boundary& b, const double* mu, const double* gam, double* h, cudaStream_t st) {
+    GNK_TRY(run_circulant(b, mu, b.r3, st));
+    PairJob j;
+    j.R = 2;
+    j.mode = W_SCALED;
+    j.x[0] = mu;
+    j.x[1] = gam;
+    j.s = b.q;
+    j.epi = EPI_H;
+    j.out = h;
+    j.ex = mu;
+    j.ex2 = gam;
+    j.Lx = b.r3;
+    return run_pairsum(b, j, GNK_PREC_FP64, st);
+}
+
+namespace {
+__global__ void negate_kernel(double* x, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) x[i] = -x[i];
+}
+}  // namespace
+
+int op_negate(double* x, int N, cudaStream_t st) {
+    negate_kernel<<<(N + 255) / 256, 256, 0, st>>>(x, N);
+    GNK_TRY_CUDA(cudaGetLastError());
+    return GNK_OK;
+}
+
+}  // namespace gnk

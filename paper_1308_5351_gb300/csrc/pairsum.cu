@@ -1,0 +1,548 @@
+// All-pairs Cauchy sums z_i = sum_{j != i} w_j / (eta_i - eta_j)  (Sec. 2.5,
+// Eqs. fmm-1, fmm-E) and the pointwise operators built on them (Secs. 3.3,
+// 3.4, 4.3, 4.4).
+//
+// Layout of a launch: blocks along x own a tile of targets held in registers
+// (T per thread); blocks along y own a contiguous chunk of source tiles, which
+// they stream through shared memory.  Each block writes its partial sums to a
+// [chunk][rhs][N] buffer; a second kernel adds the chunks in a fixed order
+// (deterministic) in FP64 and applies the operator's epilogue.
+//
+// Per pair the FP64 kernel spends 13 FP64-pipe instructions:
+//   2 DADD (d = eta_i - eta_j), DMUL + DFMA (|d|^2), 3 DFMA to refine the
+//   hardware reciprocal seed, 2 DMUL (Re, Im of 1/d), 4 DFMA (w / d);
+// the FP32 kernel spends 10 FP32-pipe instructions and one MUFU reciprocal.
+#include <algorithm>
+#include <cmath>
+
+#include "gnk_internal.h"
+
+namespace gnk {
+namespace {
+
+// ------------------------------------------------------------------ reciprocal
+__device__ __forceinline__ double rcp_seed_f64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+// 1/x in full FP64 from the hardware seed y0 (relative error below 2^-19):
+// with e = 1 - x y0 we have 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...), so
+// y0 (1 + e + e^2) leaves the relative error e^3 < 2^-57, below half an ulp
+// after rounding for all but a vanishing set of inputs.
+__device__ __forceinline__ double recip_f64(double x) {
+    const double y0 = rcp_seed_f64(x);
+    const double e = fma(-x, y0, 1.0);
+    const double t = fma(e, e, e);
+    return fma(y0, t, y0);
+}
+
+__device__ __forceinline__ float recip_f32(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Far-away position for padded sources of a ragged last tile: |d|^2 stays
+// finite and the zero weight contributes exactly 0.
+constexpr double kFar64 = 1e150;
+constexpr float kFar32 = 1e18f;
+
+// ------------------------------------------------------------------ FP64
+struct Pair64Args {
+    const double2* et;
+    int N;
+    const double2* w0;
+    const double2* w1;
+    const double* x0;
+    const double* x1;
+    const double2* s;
+    double2* partial;
+    int tiles_src;
+    int tiles_per_chunk;
+    const int* done;
+};
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads64) pairsum64_kernel(Pair64Args a) {
+    constexpr int S = kSrcTile64, T = kTargets64, NT = kThreads64;
+    __shared__ double2 s_pos[S];
+    __shared__ double2 s_w[R][S];
+    if (a.done != nullptr && *a.done) return;
+    const int N = a.N;
+    const int tgt0 = blockIdx.x * (NT * T);
+
+    double px[T], py[T], ax[T][R], ay[T][R];
+    int idx[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        idx[t] = tgt0 + t * NT + threadIdx.x;
+        const double2 p = a.et[min(idx[t], N - 1)];
+        px[t] = p.x;
+        py[t] = p.y;
+#pragma unroll
+        for (int r = 0; r < R; ++r) ax[t][r] = ay[t][r] = 0.0;
+    }
+
+    const int tb = blockIdx.y * a.tiles_per_chunk;
+    const int te = min(tb + a.tiles_per_chunk, a.tiles_src);
+    for (int tile = tb; tile < te; ++tile) {
+        const int j0 = tile * S;
+        __syncthreads();
+        for (int k = threadIdx.x; k < S; k += NT) {
+            const int j = j0 + k;
+            if (j < N) {
+                s_pos[k] = a.et[j];
+                if (MODE == W_COMPLEX) {
+                    s_w[0][k] = a.w0[j];
+                    if (R > 1) s_w[R - 1][k] = a.w1[j];
+                } else {
+                    const double2 sc = a.s[j];
+                    const double x0 = a.x0[j];
+                    s_w[0][k] = make_double2(sc.x * x0, sc.y * x0);
+                    if (R > 1) {
+                        const double x1 = a.x1[j];
+                        s_w[R - 1][k] = make_double2(sc.x * x1, sc.y * x1);
+                    }
+                }
+            } else {
+                s_pos[k] = make_double2(kFar64, kFar64);
+#pragma unroll
+                for (int r = 0; r < R; ++r) s_w[r][k] = make_double2(0.0, 0.0);
+            }
+        }
+        __syncthreads();
+        const bool diag = (j0 < tgt0 + NT * T) && (tgt0 < j0 + S);
+        if (!diag) {
+#pragma unroll 2
+            for (int k = 0; k < S; ++k) {
+                const double2 sp = s_pos[k];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const double dx = px[t] - sp.x, dy = py[t] - sp.y;
+                    const double inv = recip_f64(fma(dx, dx, dy * dy));
+                    const double ar = dx * inv, ai = dy * inv;  // 1/d = ar - i ai
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const double2 w = s_w[r][k];
+                        ax[t][r] = fma(w.x, ar, ax[t][r]);
+                        ax[t][r] = fma(w.y, ai, ax[t][r]);
+                        ay[t][r] = fma(w.y, ar, ay[t][r]);
+                        ay[t][r] = fma(-w.x, ai, ay[t][r]);
+                    }
+                }
+            }
+        } else {
+            for (int k = 0; k < S; ++k) {
+                const double2 sp = s_pos[k];
+                const int j = j0 + k;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const double dx = px[t] - sp.x, dy = py[t] - sp.y;
+                    double inv = recip_f64(fma(dx, dx, dy * dy));
+                    inv = (j == idx[t]) ? 0.0 : inv;  // the i = j term is excluded (Eq. fmm-E)
+                    const double ar = dx * inv, ai = dy * inv;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const double2 w = s_w[r][k];
+                        ax[t][r] = fma(w.x, ar, ax[t][r]);
+                        ax[t][r] = fma(w.y, ai, ax[t][r]);
+                        ay[t][r] = fma(w.y, ar, ay[t][r]);
+                        ay[t][r] = fma(-w.x, ai, ay[t][r]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (idx[t] < N) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                a.partial[((size_t)blockIdx.y * R + r) * N + idx[t]] = make_double2(ax[t][r], ay[t][r]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP32
+// Source positions are stored relative to one reference node per source tile
+// (off32), and each target forms its own offset to that reference from its
+// hi/lo split, so that the difference eta_i - eta_j of two nearby nodes keeps
+// its leading bits instead of being lost to the magnitude of eta.
+struct Pair32Args {
+    const float4* et32;
+    const float4* ref32;
+    const float2* off32;
+    int N;
+    const double2* w0;
+    const double2* w1;
+    const double* x0;
+    const double* x1;
+    const float2* s32;
+    float2* partial;
+    int tiles_src;
+    int tiles_per_chunk;
+    const int* done;
+};
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads32) pairsum32_kernel(Pair32Args a) {
+    constexpr int S = kSrcTile32, T = kTargets32, NT = kThreads32;
+    static_assert(S == NT, "one source per thread per tile load");
+    __shared__ float4 s_src[S];          // (off.x, off.y, w0.x, w0.y)
+    __shared__ float2 s_w1[R > 1 ? S : 1];
+    if (a.done != nullptr && *a.done) return;
+    const int N = a.N;
+    const int tgt0 = blockIdx.x * (NT * T);
+
+    float4 th[T];
+    float ox[T], oy[T], ax[T][R], ay[T][R];
+    int idx[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        idx[t] = tgt0 + t * NT + threadIdx.x;
+        th[t] = a.et32[min(idx[t], N - 1)];
+#pragma unroll
+        for (int r = 0; r < R; ++r) ax[t][r] = ay[t][r] = 0.0f;
+    }
+
+    const int tb = blockIdx.y * a.tiles_per_chunk;
+    const int te = min(tb + a.tiles_per_chunk, a.tiles_src);
+    for (int tile = tb; tile < te; ++tile) {
+        const int j0 = tile * S;
+        const float4 ref = a.ref32[tile];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            ox[t] = (th[t].x - ref.x) + (th[t].z - ref.z);
+            oy[t] = (th[t].y - ref.y) + (th[t].w - ref.w);
+        }
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            const int j = j0 + k;
+            float4 v;
+            float2 w1 = make_float2(0.f, 0.f);
+            if (j < N) {
+                const float2 off = a.off32[j];
+                float2 w0;
+                if (MODE == W_COMPLEX) {
+                    const double2 w = a.w0[j];
+                    w0 = make_float2((float)w.x, (float)w.y);
+                    if (R > 1) {
+                        const double2 u = a.w1[j];
+                        w1 = make_float2((float)u.x, (float)u.y);
+                    }
+                } else {
+                    const float2 sc = a.s32[j];
+                    const float x0 = (float)a.x0[j];
+                    w0 = make_float2(sc.x * x0, sc.y * x0);
+                    if (R > 1) {
+                        const float x1 = (float)a.x1[j];
+                        w1 = make_float2(sc.x * x1, sc.y * x1);
+                    }
+                }
+                v = make_float4(off.x, off.y, w0.x, w0.y);
+            } else {
+                v = make_float4(kFar32, kFar32, 0.f, 0.f);
+            }
+            s_src[k] = v;
+            if (R > 1) s_w1[k] = w1;
+        }
+        __syncthreads();
+        const bool diag = (j0 < tgt0 + NT * T) && (tgt0 < j0 + S);
+        if (!diag) {
+#pragma unroll 4
+            for (int k = 0; k < S; ++k) {
+                const float4 sv = s_src[k];
+                float2 u;
+                if (R > 1) u = s_w1[k];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float dx = ox[t] - sv.x, dy = oy[t] - sv.y;
+                    const float inv = recip_f32(fmaf(dx, dx, dy * dy));
+                    const float ar = dx * inv, ai = dy * inv;
+                    ax[t][0] = fmaf(sv.z, ar, ax[t][0]);
+                    ax[t][0] = fmaf(sv.w, ai, ax[t][0]);
+                    ay[t][0] = fmaf(sv.w, ar, ay[t][0]);
+                    ay[t][0] = fmaf(-sv.z, ai, ay[t][0]);
+                    if (R > 1) {
+                        ax[t][R - 1] = fmaf(u.x, ar, ax[t][R - 1]);
+                        ax[t][R - 1] = fmaf(u.y, ai, ax[t][R - 1]);
+                        ay[t][R - 1] = fmaf(u.y, ar, ay[t][R - 1]);
+                        ay[t][R - 1] = fmaf(-u.x, ai, ay[t][R - 1]);
+                    }
+                }
+            }
+        } else {
+            for (int k = 0; k < S; ++k) {
+                const float4 sv = s_src[k];
+                float2 u;
+                if (R > 1) u = s_w1[k];
+                const int j = j0 + k;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float dx = ox[t] - sv.x, dy = oy[t] - sv.y;
+                    float inv = recip_f32(fmaf(dx, dx, dy * dy));
+                    inv = (j == idx[t]) ? 0.0f : inv;
+                    const float ar = dx * inv, ai = dy * inv;
+                    ax[t][0] = fmaf(sv.z, ar, ax[t][0]);
+                    ax[t][0] = fmaf(sv.w, ai, ax[t][0]);
+                    ay[t][0] = fmaf(sv.w, ar, ay[t][0]);
+                    ay[t][0] = fmaf(-sv.z, ai, ay[t][0]);
+                    if (R > 1) {
+                        ax[t][R - 1] = fmaf(u.x, ar, ax[t][R - 1]);
+                        ax[t][R - 1] = fmaf(u.y, ai, ax[t][R - 1]);
+                        ay[t][R - 1] = fmaf(u.y, ar, ay[t][R - 1]);
+                        ay[t][R - 1] = fmaf(-u.x, ai, ay[t][R - 1]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (idx[t] < N) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                a.partial[((size_t)blockIdx.y * R + r) * N + idx[t]] = make_float2(ax[t][r], ay[t][r]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reduce + epilogue
+struct ReduceArgs {
+    int N, n, R, chunks, is32;
+    double c;
+    const double2* p64;
+    const float2* p32;
+    const double2* A;
+    const double2* q;
+    const double* b1;
+    const double* d1;
+    const double* e;
+    PairJob job;
+};
+
+__global__ void reduce_epilogue_kernel(ReduceArgs a) {
+    const PairJob& j = a.job;
+    if (j.done != nullptr && *j.done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int N = a.N;
+    double zx[kMaxRHS] = {0.0, 0.0}, zy[kMaxRHS] = {0.0, 0.0};
+    for (int r = 0; r < a.R; ++r) {
+        double sx = 0.0, sy = 0.0;
+        if (a.is32) {
+            for (int ch = 0; ch < a.chunks; ++ch) {
+                const float2 p = a.p32[((size_t)ch * a.R + r) * N + i];
+                sx += (double)p.x;
+                sy += (double)p.y;
+            }
+        } else {
+            for (int ch = 0; ch < a.chunks; ++ch) {
+                const double2 p = a.p64[((size_t)ch * a.R + r) * N + i];
+                sx += p.x;
+                sy += p.y;
+            }
+        }
+        zx[r] = sx;
+        zy[r] = sy;
+    }
+    const double s2n = 2.0 / a.n;
+    switch (j.epi) {
+        case EPI_Z:
+            for (int r = 0; r < a.R; ++r) j.out_c[(size_t)r * N + i] = make_double2(zx[r], zy[r]);
+            break;
+        case EPI_IMINUSN:
+        case EPI_RESID: {
+            // f_B(x) = 2x + diag(B1) x - B x, -B x = (2/n) Im(A E(q x))  (Eq. (I-B)x)
+            const double2 A = a.A[i];
+            const double x = j.ex[i];
+            const double fb = 2.0 * x + a.b1[i] * x + s2n * (A.x * zy[0] + A.y * zx[0]);
+            j.out[i] = (j.epi == EPI_RESID) ? j.rhs[i] - fb : fb;
+            break;
+        }
+        case EPI_M: {
+            // f_C(x) = D x - diag(D1) x + Lhat x, D x = -(2/n) Re(A E(q x))  (Eq. hD-bt)
+            const double2 A = a.A[i];
+            const double x = j.ex[i];
+            j.out[i] = -s2n * (A.x * zx[0] - A.y * zy[0]) - a.d1[i] * x + j.Lx[i];
+            break;
+        }
+        case EPI_ADJ:
+        case EPI_RESID_ADJ: {
+            // g_B(x) = e x + B^T x + Phat x, B^T x = (2/n) Im(q E(A x))  (Eq. BTx)
+            const double2 q = a.q[i];
+            const double x = j.ex[i];
+            const double gb = a.e[i] * x + s2n * (q.x * zy[0] + q.y * zx[0]) + j.means[i / a.n];
+            j.out[i] = (j.epi == EPI_RESID_ADJ) ? j.rhs[i] - gb : gb;
+            break;
+        }
+        case EPI_H: {
+            // h = (f_C(mu) - f_B(gamma)) / 2  (Eq. bh); z0 = E(q mu), z1 = E(q gamma)
+            const double2 A = a.A[i];
+            const double mu = j.ex[i];
+            const double ga = j.ex2[i];
+            const double fc = -s2n * (A.x * zx[0] - A.y * zy[0]) - a.d1[i] * mu + j.Lx[i];
+            const double fb = 2.0 * ga + a.b1[i] * ga + s2n * (A.x * zy[1] + A.y * zx[1]);
+            j.out[i] = 0.5 * (fc - fb);
+            break;
+        }
+        case EPI_EONE: {
+            // diag(B1) = -(2/n) Im(A Eone), diag(D1) = -(2/n) Re(A Eone)  (listing of FBIE);
+            // with a second right-hand side z1 = E eta':
+            // e = 1 - c - (2/n) Im(E eta') + [(2/n) Im(eta''/eta' - A'/A)]  (Eq. bve),
+            // the bracket having been stored in out3 beforehand.
+            const double2 A = a.A[i];
+            j.out_c[i] = make_double2(zx[0], zy[0]);
+            j.out[i] = -s2n * (A.x * zy[0] + A.y * zx[0]);
+            j.out2[i] = -s2n * (A.x * zx[0] - A.y * zy[0]);
+            if (a.R > 1) j.out3[i] = 1.0 - a.c - s2n * zy[1] + j.out3[i];
+            break;
+        }
+        default:
+            break;
+    }
+}
+
+cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int is32,
+                          cudaStream_t st) {
+    ReduceArgs ra;
+    ra.N = b.N;
+    ra.n = b.n;
+    ra.R = job.R;
+    ra.chunks = chunks;
+    ra.is32 = is32;
+    ra.c = b.bounded ? 1.0 : -1.0;
+    ra.p64 = static_cast<const double2*>(b.partial);
+    ra.p32 = static_cast<const float2*>(b.partial);
+    ra.A = b.A;
+    ra.q = b.q;
+    ra.b1 = b.b1;
+    ra.d1 = b.d1;
+    ra.e = b.e;
+    ra.job = job;
+    const int threads = 256;
+    reduce_epilogue_kernel<<<(b.N + threads - 1) / threads, threads, 0, st>>>(ra);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Chunking of the source range: choose the number of source tiles per chunk
+// that maximises the fraction of useful block-slots over the launch's waves,
+// so the grid covers all SMs even when few target tiles exist.
+PairPlan make_plan(int N, int sms, int blocks_per_sm, int targets_per_block, int src_tile) {
+    PairPlan p;
+    p.tiles_tgt = (N + targets_per_block - 1) / targets_per_block;
+    p.tiles_src = (N + src_tile - 1) / src_tile;
+    const long slots = std::max(1L, (long)sms * blocks_per_sm);
+    double best = -1.0;
+    int best_tpc = p.tiles_src;
+    const int max_chunks = 64;
+    for (int tpc = p.tiles_src; tpc >= 1; --tpc) {
+        const int chunks = (p.tiles_src + tpc - 1) / tpc;
+        if (chunks > max_chunks) break;
+        const long blocks = (long)p.tiles_tgt * chunks;
+        const long waves = (blocks + slots - 1) / slots;
+        const double eff = (double)p.tiles_tgt * p.tiles_src / ((double)waves * slots * tpc);
+        if (eff > best * 1.02) {  // prefer fewer chunks unless clearly better
+            best = eff;
+            best_tpc = tpc;
+        }
+    }
+    p.tiles_per_chunk = best_tpc;
+    p.chunks = (p.tiles_src + best_tpc - 1) / best_tpc;
+    return p;
+}
+
+int pair_workspace_bytes(const Boundary& b, size_t* bytes) {
+    const size_t b64 = (size_t)b.plan64.chunks * kMaxRHS * b.N * sizeof(double2);
+    const size_t b32 = (size_t)b.plan32.chunks * kMaxRHS * b.N * sizeof(float2);
+    *bytes = std::max(b64, b32);
+    return GNK_OK;
+}
+
+int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
+    const PairPlan& p = b.plan64;
+    Pair64Args a;
+    a.et = b.et;
+    a.N = b.N;
+    a.w0 = job.w[0];
+    a.w1 = job.w[1];
+    a.x0 = job.x[0];
+    a.x1 = job.x[1];
+    a.s = job.s;
+    a.partial = static_cast<double2*>(b.partial);
+    a.tiles_src = p.tiles_src;
+    a.tiles_per_chunk = p.tiles_per_chunk;
+    a.done = job.done;
+    dim3 grid(p.tiles_tgt, p.chunks);
+    if (job.R == 1 && job.mode == W_SCALED)
+        pairsum64_kernel<1, W_SCALED><<<grid, kThreads64, 0, st>>>(a);
+    else if (job.R == 1)
+        pairsum64_kernel<1, W_COMPLEX><<<grid, kThreads64, 0, st>>>(a);
+    else if (job.mode == W_SCALED)
+        pairsum64_kernel<2, W_SCALED><<<grid, kThreads64, 0, st>>>(a);
+    else
+        pairsum64_kernel<2, W_COMPLEX><<<grid, kThreads64, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaGetLastError());
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 0, st));
+    return GNK_OK;
+}
+
+int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
+    const PairPlan& p = b.plan32;
+    Pair32Args a;
+    a.et32 = b.et32;
+    a.ref32 = b.ref32;
+    a.off32 = b.off32;
+    a.N = b.N;
+    a.w0 = job.w[0];
+    a.w1 = job.w[1];
+    a.x0 = job.x[0];
+    a.x1 = job.x[1];
+    a.s32 = (job.s == b.q) ? b.q32 : b.A32;
+    a.partial = static_cast<float2*>(b.partial);
+    a.tiles_src = p.tiles_src;
+    a.tiles_per_chunk = p.tiles_per_chunk;
+    a.done = job.done;
+    if (job.mode == W_SCALED && job.s != b.q && job.s != b.A) {
+        set_error("FP32 pair sum: the scale must be q or A of the handle");
+        return GNK_EINVAL;
+    }
+    dim3 grid(p.tiles_tgt, p.chunks);
+    if (job.R == 1 && job.mode == W_SCALED)
+        pairsum32_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+    else if (job.R == 1)
+        pairsum32_kernel<1, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+    else if (job.mode == W_SCALED)
+        pairsum32_kernel<2, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+    else
+        pairsum32_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaGetLastError());
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st));
+    return GNK_OK;
+}
+
+int pair_blocks_per_sm(int precision) {
+    int nb = 1;
+    cudaError_t e;
+    if (precision == GNK_PREC_FP32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pairsum32_kernel<2, W_SCALED>, kThreads32, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pairsum64_kernel<2, W_SCALED>, kThreads64, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st) {
+    if (precision == GNK_PREC_FP32) return run_pairsum32(b, job, st);
+    return run_pairsum64(b, job, st);
+}
+
+}  // namespace gnk

@@ -1,0 +1,312 @@
+"""Python binding of the C ABI of libgnk (include/gnk.h).
+
+Argument marshalling only: every function below passes pointers and sizes to
+the function of the same name in libgnk.so; all arithmetic runs in the CUDA
+library.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays: real
+arrays are float64, complex arrays complex128 (or float64 with a trailing
+dimension of 2).  The library loads from this package's _lib/ directory and
+raises if it has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+try:  # torch is plumbing only: device memory and streams
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgnk.so")
+
+GNK_OK = 0
+GNK_EINVAL = -1
+GNK_ENOTCONV = -2
+GNK_ENONFINITE = -3
+GNK_ECUDA = -4
+GNK_ENOMEM = -5
+
+GNK_PREC_FP64 = 0
+GNK_PREC_MIXED = 1
+GNK_PREC_FP32 = 2
+
+EXPORTED = (
+    "gnk_default_options", "gnk_last_error", "gnk_version", "gnk_build_boundary",
+    "gnk_free_boundary", "gnk_boundary_size", "gnk_cauchy_sum", "gnk_apply_IminusN",
+    "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
+    "gnk_compute_h", "gnk_solve_adjoint_ie",
+)
+
+
+class gnk_options(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
+
+
+class gnk_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("matvecs_fp64", ctypes.c_int),
+                ("matvecs_fp32", ctypes.c_int), ("relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GnkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libgnk error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgnk.so (built by paper_1308_5351_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(python paper_1308_5351_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.gnk_default_options.argtypes = [ctypes.POINTER(gnk_options)]
+    lib.gnk_default_options.restype = None
+    lib.gnk_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.gnk_last_error.restype = I
+    lib.gnk_version.argtypes = []
+    lib.gnk_version.restype = ctypes.c_char_p
+    lib.gnk_build_boundary.argtypes = [ctypes.POINTER(P), I, I, P, P, P, P, P, I, P]
+    lib.gnk_free_boundary.argtypes = [P]
+    lib.gnk_boundary_size.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.gnk_cauchy_sum.argtypes = [P, P, P, I, P]
+    for name in ("gnk_apply_IminusN", "gnk_apply_M", "gnk_apply_adjoint"):
+        getattr(lib, name).argtypes = [P, P, P, I, P]
+    lib.gnk_apply_circulant.argtypes = [P, P, P, P]
+    for name in ("gnk_solve_ie", "gnk_solve_adjoint_ie"):
+        getattr(lib, name).argtypes = [P, P, P, ctypes.POINTER(gnk_options),
+                                       ctypes.POINTER(gnk_result), P]
+    lib.gnk_compute_h.argtypes = [P, P, P, P, P, P]
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load().gnk_last_error(buf, len(buf))
+    return buf.value.decode()
+
+
+def _check(code, ok=(GNK_OK,)):
+    if code not in ok:
+        raise GnkError(code, last_error())
+    return code
+
+
+# --------------------------------------------------------------- marshalling
+def _ptr(a, complex_: bool = False):
+    """Pointer to the data of a contiguous float64 / complex128 array."""
+    if a is None:
+        return None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        ok = (torch.complex128,) if complex_ else (torch.float64,)
+        if a.dtype not in ok + ((torch.float64,) if complex_ else ()):
+            raise TypeError(f"expected {ok[0]}, got {a.dtype}")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        ok = (np.complex128, np.float64) if complex_ else (np.float64,)
+        if a.dtype.type not in ok:
+            raise TypeError(f"expected {ok[0]}, got {a.dtype}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        if torch is not None and torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return None
+    if torch is not None and isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _like(a, shape, dtype_np, dtype_t):
+    if torch is not None and isinstance(a, torch.Tensor):
+        return torch.empty(shape, dtype=dtype_t, device=a.device)
+    return np.empty(shape, dtype=dtype_np)
+
+
+def _real_like(a, n):
+    return _like(a, (n,), np.float64, torch.float64 if torch is not None else None)
+
+
+# --------------------------------------------------------------- C-ABI mirrors
+def gnk_default_options() -> gnk_options:
+    o = gnk_options()
+    load().gnk_default_options(ctypes.byref(o))
+    return o
+
+
+def gnk_version() -> str:
+    return load().gnk_version().decode()
+
+
+def gnk_build_boundary(m1, n, et, etp, A, etpp=None, Ap=None, bounded=True, stream=None):
+    """Returns an opaque handle (ctypes.c_void_p)."""
+    h = ctypes.c_void_p()
+    _check(load().gnk_build_boundary(ctypes.byref(h), int(m1), int(n), _ptr(et, True),
+                                     _ptr(etp, True), _ptr(etpp, True), _ptr(A, True),
+                                     _ptr(Ap, True), 1 if bounded else 0, _stream(stream)))
+    return h
+
+
+def gnk_free_boundary(h):
+    return _check(load().gnk_free_boundary(h))
+
+
+def gnk_boundary_size(h):
+    m1, n = ctypes.c_int(), ctypes.c_int()
+    _check(load().gnk_boundary_size(h, ctypes.byref(m1), ctypes.byref(n)))
+    return m1.value, n.value
+
+
+def gnk_cauchy_sum(h, w, z, precision=GNK_PREC_FP64, stream=None):
+    return _check(load().gnk_cauchy_sum(h, _ptr(w, True), _ptr(z, True), int(precision),
+                                        _stream(stream)))
+
+
+def gnk_apply_IminusN(h, x, y, precision=GNK_PREC_FP64, stream=None):
+    return _check(load().gnk_apply_IminusN(h, _ptr(x), _ptr(y), int(precision), _stream(stream)))
+
+
+def gnk_apply_M(h, x, y, precision=GNK_PREC_FP64, stream=None):
+    return _check(load().gnk_apply_M(h, _ptr(x), _ptr(y), int(precision), _stream(stream)))
+
+
+def gnk_apply_adjoint(h, x, y, precision=GNK_PREC_FP64, stream=None):
+    return _check(load().gnk_apply_adjoint(h, _ptr(x), _ptr(y), int(precision), _stream(stream)))
+
+
+def gnk_apply_circulant(h, x, y, stream=None):
+    return _check(load().gnk_apply_circulant(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def gnk_solve_ie(h, gam, mu, options: Optional[gnk_options] = None, stream=None):
+    res = gnk_result()
+    code = load().gnk_solve_ie(h, _ptr(gam), _ptr(mu),
+                               ctypes.byref(options) if options is not None else None,
+                               ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
+def gnk_solve_adjoint_ie(h, gam, mu, options: Optional[gnk_options] = None, stream=None):
+    res = gnk_result()
+    code = load().gnk_solve_adjoint_ie(h, _ptr(gam), _ptr(mu),
+                                       ctypes.byref(options) if options is not None else None,
+                                       ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
+def gnk_compute_h(h, mu, gam, hv, hk=None, stream=None):
+    return _check(load().gnk_compute_h(h, _ptr(mu), _ptr(gam), _ptr(hv), _ptr(hk),
+                                       _stream(stream)))
+
+
+def options(**kw) -> gnk_options:
+    o = gnk_default_options()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+# --------------------------------------------------------------- convenience
+class Boundary:
+    """Owns one gnk_boundary handle built from a domain's arrays (numpy complex
+    arrays on the host, or complex128 CUDA tensors)."""
+
+    def __init__(self, m1, n, et, etp, A, etpp=None, Ap=None, bounded=True, stream=None):
+        self.m1, self.n, self.N = int(m1), int(n), int(m1) * int(n)
+        self.handle = gnk_build_boundary(m1, n, et, etp, A, etpp, Ap, bounded, stream)
+
+    @classmethod
+    def from_domain(cls, dom, adjoint=True, device=None, stream=None):
+        arrs = [dom.et, dom.etp, dom.A, dom.etpp if adjoint else None, dom.Ap if adjoint else None]
+        if device is not None:
+            arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a), device=device)
+                    for a in arrs]
+        return cls(dom.m1, dom.n, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], dom.bounded, stream)
+
+    def close(self):
+        if self.handle is not None:
+            gnk_free_boundary(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def cauchy_sum(self, w, precision=GNK_PREC_FP64, out=None, stream=None):
+        z = out if out is not None else _like(w, tuple(w.shape), np.complex128,
+                                              torch.complex128 if torch is not None else None)
+        gnk_cauchy_sum(self.handle, w, z, precision, stream)
+        return z
+
+    def _unary(self, fn, x, precision, out, stream):
+        y = out if out is not None else _real_like(x, self.N)
+        if precision is None:
+            fn(self.handle, x, y, stream=stream)
+        else:
+            fn(self.handle, x, y, precision, stream)
+        return y
+
+    def apply_IminusN(self, x, precision=GNK_PREC_FP64, out=None, stream=None):
+        return self._unary(gnk_apply_IminusN, x, precision, out, stream)
+
+    def apply_M(self, x, precision=GNK_PREC_FP64, out=None, stream=None):
+        return self._unary(gnk_apply_M, x, precision, out, stream)
+
+    def apply_adjoint(self, x, precision=GNK_PREC_FP64, out=None, stream=None):
+        return self._unary(gnk_apply_adjoint, x, precision, out, stream)
+
+    def apply_circulant(self, x, out=None, stream=None):
+        return self._unary(gnk_apply_circulant, x, None, out, stream)
+
+    def solve_ie(self, gam, out=None, stream=None, **opts):
+        mu = out if out is not None else _real_like(gam, self.N)
+        res = gnk_solve_ie(self.handle, gam, mu, options(**opts), stream)
+        return mu, res
+
+    def solve_adjoint_ie(self, gam, out=None, stream=None, **opts):
+        mu = out if out is not None else _real_like(gam, self.N)
+        res = gnk_solve_adjoint_ie(self.handle, gam, mu, options(**opts), stream)
+        return mu, res
+
+    def compute_h(self, mu, gam, out=None, hk=None, stream=None):
+        h = out if out is not None else _real_like(mu, self.N)
+        hk = hk if hk is not None else _real_like(mu, self.m1)
+        gnk_compute_h(self.handle, mu, gam, h, hk, stream)
+        return h, hk
