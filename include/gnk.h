@@ -91,6 +91,23 @@ int gnk_last_error(char* buf, size_t len);
 /* Library version string (static storage). */
 const char* gnk_version(void);
 
+/* Number of CUDA kernel launches the library has issued in this process
+ * (all handles, all devices): a host-side counter for instrumentation. */
+unsigned long long gnk_kernel_launches(void);
+
+/* Per-launch device timing for instrumentation.  gnk_profile_enable(1) clears
+ * the records and starts recording a CUDA event pair on the launching stream
+ * around every kernel launch of the library; gnk_profile_enable(0) stops.
+ * gnk_profile_query sums, over the recorded launches of one kind, the number
+ * of launches, their device time in ms and their algorithmic work (it waits
+ * for the recorded events).  Kinds: 0 FP64 pair-sum kernel and 1 FP32
+ * pair-sum kernel (work = pair evaluations R N (N-1)), 2 reduction/epilogue,
+ * 3 circulant, 4 GMRES vector kernels (work = bytes moved).  Launches that
+ * a converged GMRES cycle turned into no-ops are not counted. */
+int gnk_profile_enable(int on);
+int gnk_profile_query(int kind, long long* launches, double* total_ms,
+                      double* work);
+
 /* ---------------------------------------------------------------------------
  * Boundary handle (Sec. 2.1, 2.4; Eqs. eta, A, ti-skp)
  *

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "gnk_internal.h"
@@ -13,6 +14,9 @@
 namespace gnk {
 
 static thread_local char g_err[1024] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -245,6 +249,8 @@ int gnk_last_error(char* buf, size_t len) {
 }
 
 const char* gnk_version(void) { return "gnk-gb300 0.1 (sm_103a)"; }
+
+unsigned long long gnk_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int gnk_build_boundary(gnk_boundary** out, int m1, int n, const double* et, const double* etp,
                        const double* etpp, const double* A, const double* Ap, int bounded,

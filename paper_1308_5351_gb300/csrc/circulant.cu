@@ -173,6 +173,7 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
 }  // namespace
 
 int run_circulant(const Boundary& b, const double* x, double* y, cudaStream_t st) {
+    const ProfToken tok = prof_begin(st);
     if (b.fft_pow2) {
         const int pairs = (b.m1 + 1) / 2;
         const int threads = std::min(512, std::max(32, b.n / 2));
@@ -184,12 +185,15 @@ int run_circulant(const Boundary& b, const double* x, double* y, cudaStream_t st
         circulant_direct_kernel<<<grid, threads, b.n * sizeof(double), st>>>(x, y, b.n, b.Lcol);
     }
     GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_CIRC, 16.0 * b.N, st);
+    count_launches(1);
     return GNK_OK;
 }
 
 int run_component_means(const Boundary& b, const double* x, double* means, cudaStream_t st) {
     component_means_kernel<<<b.m1, 256, 0, st>>>(x, means, b.n);
     GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(1);
     return GNK_OK;
 }
 
@@ -215,6 +219,7 @@ int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int*
     a.flag = d_flag;
     prepare_geometry_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(1);
 
     // circulant tables (host, FP64 libm)
     const int n = b.n;

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/gnk.h"
 
@@ -28,6 +29,32 @@ void set_error(const char* fmt, ...);
         int s_ = (call);                                                       \
         if (s_ != GNK_OK) return s_;                                           \
     } while (0)
+
+// ---------------------------------------------------------------- launch counter
+// Host-side count of kernel launches made by the library (all devices).
+void count_launches(unsigned long long n);
+
+// ---------------------------------------------------------------- profiling
+// Kinds of instrumented launches (gnk_profile_query's `kind`).
+enum ProfKind : int {
+    PK_PAIR64 = 0,   // FP64 pair-sum kernel; work = pair evaluations (R N (N-1))
+    PK_PAIR32 = 1,   // FP32 pair-sum kernel; work = pair evaluations
+    PK_REDUCE = 2,   // chunk reduction + epilogue; work = bytes moved
+    PK_CIRC = 3,     // circulant FFT / direct kernel; work = bytes moved
+    PK_KRYLOV = 4,   // GMRES vector kernels; work = bytes moved
+    PK_OTHER = 5,
+};
+struct ProfToken {
+    void* ev = nullptr;
+};
+ProfToken prof_begin(cudaStream_t st);
+long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st);
+void prof_skip(long idx);
+// Collect the record indices of the launches made between begin and end
+// (calling thread only), to mark launches that a device flag turned into
+// no-ops after the fact.
+void prof_collect_begin();
+void prof_collect_end(std::vector<long>* out);
 
 // ---------------------------------------------------------------- tiling
 // Sources per shared-memory tile of the pair-sum kernels.

@@ -16,6 +16,7 @@
 // enqueues a whole cycle without waiting and synchronises once per cycle.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gnk_internal.h"
 
@@ -320,6 +321,14 @@ int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
     return GNK_OK;
 }
 
+// Wraps one vector-kernel launch in a profiling event pair (bytes moved as work).
+#define KLAUNCH(bytes, launch)                                 \
+    do {                                                       \
+        const ProfToken t_ = prof_begin(st);                   \
+        launch;                                                \
+        prof_end(t_, PK_KRYLOV, (double)(bytes), st);          \
+    } while (0)
+
 // One restarted GMRES solve of A x = rhs with the operator in precision prec.
 // r is a work vector.  Counters are added to *res; *relres receives the final
 // true relative residual (in prec).
@@ -327,14 +336,19 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
           int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st) {
     GNK_TRY(ensure_krylov(b, restart));
     const int N = b.N;
+    const double vb = 8.0 * N;  // bytes of one vector
     KState* ks = static_cast<KState*>(b.kstate);
     KPtrs p = kry_ptrs(b.kry, restart);
     const int nb = vec_blocks(N);
     KState hs;
     k_init_state<<<1, 1, 0, st>>>(ks, tol, restart);
-    k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0);
+    KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0)));
+    count_launches(2);
     GNK_TRY_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), st));
     GNK_TRY_CUDA(cudaGetLastError());
+    // launches of each Arnoldi step of the current cycle, to discount those
+    // that the device flag turned into no-ops once the cycle had converged
+    std::vector<std::vector<long>> step_ids(restart);
     int status = GNK_ENOTCONV;
     for (int cycle = 0;; ++cycle) {
         if (cycle == 0) {
@@ -343,13 +357,16 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
             GNK_TRY(op_resid(b, adjoint, rhs, x, r, prec, st));
             if (prec == GNK_PREC_FP32) res->matvecs_fp32++; else res->matvecs_fp64++;
         }
-        k_norm<<<nb, KT, 0, st>>>(r, N, p, ks, 1);
-        k_scale_first<<<nb, KT, 0, st>>>(r, b.V, N, ks);
+        KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(r, N, p, ks, 1)));
+        KLAUNCH(2 * vb, (k_scale_first<<<nb, KT, 0, st>>>(r, b.V, N, ks)));
+        count_launches(2);
         GNK_TRY_CUDA(cudaGetLastError());
         GNK_TRY(read_state(b, &hs, st));
         if (cycle > 0) {  // the previous cycle's step count is known only now
             res->iterations += hs.last_k;
             if (prec == GNK_PREC_FP32) res->matvecs_fp32 += hs.last_k; else res->matvecs_fp64 += hs.last_k;
+            for (int j = hs.last_k; j < restart; ++j)
+                for (long id : step_ids[j]) prof_skip(id);
         }
         if (hs.bnorm == 0.0) {
             *relres = 0.0;
@@ -373,16 +390,21 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
         for (int j = 0; j < restart; ++j) {
             double* vj = b.V + (size_t)j * N;
             double* w = b.V + (size_t)(j + 1) * N;
+            const double nv = j + 1;
+            prof_collect_begin();
             GNK_TRY(apply_op(b, adjoint, vj, w, prec, st, &ks->done));
-            k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h1, ks);
-            k_update<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p.h1, ks);
-            k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h2, ks);
-            k_update_norm_givens<<<nb, KT, 0, st>>>(b.V, N, j, w, p, ks);
-            k_scale_next<<<nb, KT, 0, st>>>(w, N, ks);
+            KLAUNCH((nv + 1) * vb, (k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h1, ks)));
+            KLAUNCH((nv + 2) * vb, (k_update<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p.h1, ks)));
+            KLAUNCH((nv + 1) * vb, (k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h2, ks)));
+            KLAUNCH((nv + 2) * vb, (k_update_norm_givens<<<nb, KT, 0, st>>>(b.V, N, j, w, p, ks)));
+            KLAUNCH(2 * vb, (k_scale_next<<<nb, KT, 0, st>>>(w, N, ks)));
+            prof_collect_end(&step_ids[j]);
             GNK_TRY_CUDA(cudaGetLastError());
+            count_launches(5);
         }
-        k_update_x<<<nb, KT, 0, st>>>(b.V, N, p, x, ks);
+        KLAUNCH((restart + 2) * vb, (k_update_x<<<nb, KT, 0, st>>>(b.V, N, p, x, ks)));
         GNK_TRY_CUDA(cudaGetLastError());
+        count_launches(1);
     }
     return status;
 }
@@ -390,8 +412,13 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
 int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
     KState* ks = static_cast<KState*>(b.kstate);
     KPtrs p = kry_ptrs(b.kry, b.V_cols - 1);
-    k_norm<<<vec_blocks(b.N), KT, 0, st>>>(v, b.N, p, ks, 0);
+    {
+        const ProfToken t_ = prof_begin(st);
+        k_norm<<<vec_blocks(b.N), KT, 0, st>>>(v, b.N, p, ks, 0);
+        prof_end(t_, PK_KRYLOV, 8.0 * b.N, st);
+    }
     GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(1);
     KState hs;
     GNK_TRY(read_state(b, &hs, st));
     *out = hs.bnorm;
@@ -444,6 +471,7 @@ int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const g
             }
             k_axpy<<<(N + 255) / 256, 256, 0, st>>>(x, dd, N);
             GNK_TRY_CUDA(cudaGetLastError());
+            count_launches(1);
             GNK_TRY(op_resid(b, adjoint, rhs, x, rr, GNK_PREC_FP64, st));
             res.matvecs_fp64++;
             res.refinements++;

@@ -102,6 +102,7 @@ __global__ void negate_kernel(double* x, int N) {
 int op_negate(double* x, int N, cudaStream_t st) {
     negate_kernel<<<(N + 255) / 256, 256, 0, st>>>(x, N);
     GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(1);
     return GNK_OK;
 }
 

@@ -424,8 +424,13 @@ cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int
     ra.e = b.e;
     ra.job = job;
     const int threads = 256;
+    const ProfToken tok = prof_begin(st);
     reduce_epilogue_kernel<<<(b.N + threads - 1) / threads, threads, 0, st>>>(ra);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    // bytes: the partials read plus about four N-vectors of operands and output
+    prof_end(tok, PK_REDUCE,
+             (double)chunks * job.R * b.N * (is32 ? 8.0 : 16.0) + 4.0 * 8.0 * b.N, st);
+    return e;
 }
 
 }  // namespace
@@ -479,6 +484,7 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.tiles_per_chunk = p.tiles_per_chunk;
     a.done = job.done;
     dim3 grid(p.tiles_tgt, p.chunks);
+    const ProfToken tok = prof_begin(st);
     if (job.R == 1 && job.mode == W_SCALED)
         pairsum64_kernel<1, W_SCALED><<<grid, kThreads64, 0, st>>>(a);
     else if (job.R == 1)
@@ -488,7 +494,9 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsum64_kernel<2, W_COMPLEX><<<grid, kThreads64, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_PAIR64, (double)job.R * b.N * (b.N - 1.0), st);
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 0, st));
+    count_launches(2);
     return GNK_OK;
 }
 
@@ -513,6 +521,7 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
         return GNK_EINVAL;
     }
     dim3 grid(p.tiles_tgt, p.chunks);
+    const ProfToken tok = prof_begin(st);
     if (job.R == 1 && job.mode == W_SCALED)
         pairsum32_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
     else if (job.R == 1)
@@ -522,7 +531,9 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsum32_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st);
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st));
+    count_launches(2);
     return GNK_OK;
 }
 

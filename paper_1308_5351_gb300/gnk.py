@@ -38,8 +38,11 @@ EXPORTED = (
     "gnk_default_options", "gnk_last_error", "gnk_version", "gnk_build_boundary",
     "gnk_free_boundary", "gnk_boundary_size", "gnk_cauchy_sum", "gnk_apply_IminusN",
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
-    "gnk_compute_h", "gnk_solve_adjoint_ie",
+    "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
+    "gnk_profile_query",
 )
+
+PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV = range(5)
 
 
 class gnk_options(ctypes.Structure):
@@ -94,6 +97,11 @@ def load(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [P, P, P, ctypes.POINTER(gnk_options),
                                        ctypes.POINTER(gnk_result), P]
     lib.gnk_compute_h.argtypes = [P, P, P, P, P, P]
+    lib.gnk_profile_enable.argtypes = [I]
+    lib.gnk_profile_query.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.gnk_kernel_launches.argtypes = []
+    lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
     return lib
 
@@ -157,6 +165,21 @@ def gnk_default_options() -> gnk_options:
     o = gnk_options()
     load().gnk_default_options(ctypes.byref(o))
     return o
+
+
+def gnk_kernel_launches() -> int:
+    return int(load().gnk_kernel_launches())
+
+
+def gnk_profile_enable(on: bool):
+    return _check(load().gnk_profile_enable(1 if on else 0))
+
+
+def gnk_profile_query(kind: int):
+    """(launches, total device ms, total work) of one instrumented kernel kind."""
+    n, ms, wk = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    _check(load().gnk_profile_query(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk)))
+    return n.value, ms.value, wk.value
 
 
 def gnk_version() -> str:
