@@ -194,6 +194,28 @@ int gnk_solve_adjoint_ie(const gnk_boundary* b, const double* gam, double* mu,
                          const gnk_options* opt, gnk_result* info,
                          void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Cauchy sum without any device allocation (no counterpart in the paper).
+ *
+ * z = E w exactly as gnk_cauchy_sum in FP64, for callers that cannot allocate
+ * device memory: code running during CUDA graph capture, plugins whose host
+ * framework owns all device memory, and latency-critical loops that cannot
+ * afford an allocation.  No handle is needed: et (eta at the N nodes), w and
+ * z are interleaved complex arrays of 2N doubles that must already be in
+ * device memory (host pointers return GNK_EINVAL; nothing is staged).  The
+ * split-source partial sums go to a fixed 4 MiB array inside the library's
+ * device image, which every GPU that loads the library keeps until the
+ * process exits; it limits N to 1..65536 (larger N returns GNK_EINVAL before
+ * any launch).  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * can overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Each call overwrites every entry it reads, so no
+ * clearing is needed between calls.  Never calls cudaMalloc or cudaFree.
+ * ------------------------------------------------------------------------- */
+int gnk_cauchy_sum_noalloc(int N, const double* et, const double* w,
+                           double* z, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ EXPORTED = (
     "gnk_free_boundary", "gnk_boundary_size", "gnk_cauchy_sum", "gnk_apply_IminusN",
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
-    "gnk_profile_query",
+    "gnk_profile_query", "gnk_cauchy_sum_noalloc",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV = range(5)
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.gnk_profile_enable.argtypes = [I]
     lib.gnk_profile_query.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.gnk_cauchy_sum_noalloc.argtypes = [I, P, P, P, P]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -208,6 +209,12 @@ def gnk_boundary_size(h):
 def gnk_cauchy_sum(h, w, z, precision=GNK_PREC_FP64, stream=None):
     return _check(load().gnk_cauchy_sum(h, _ptr(w, True), _ptr(z, True), int(precision),
                                         _stream(stream)))
+
+
+def gnk_cauchy_sum_noalloc(N, et, w, z, stream=None):
+    """z = E w with no device allocation (device arrays only, N <= 65536)."""
+    return _check(load().gnk_cauchy_sum_noalloc(int(N), _ptr(et, True), _ptr(w, True),
+                                                _ptr(z, True), _stream(stream)))
 
 
 def gnk_apply_IminusN(h, x, y, precision=GNK_PREC_FP64, stream=None):
