@@ -6,9 +6,11 @@ U[0.1,0.4], min gap 0.05) with n = 1024 nodes per boundary (65,536 unknowns),
 gamma = log|eta - alpha| with alpha the centre of the first ellipse.
 
 One step = build the boundary handle from device-resident eta, eta', A (this
-includes Eone = E q and the diagonals), solve by FP32-inner / FP64-refined
-GMRES (restart 20) to ||b - A mu|| <= 1e-10 ||b||, compute h and h_k, free the
-handle.  The plain FP64 GPU solve of the same problem is timed beside it.
+includes Eone = E q and the diagonals), run the fused FBIE computation (right-
+hand side, GMRES to ||b - A mu|| <= 1e-10 ||b||, h and h_k), free the handle.
+The headline form is FP32 pair sums inside GMRES with double-float (FP64-class,
+on the FP32 pipe) refinement residuals; the plain FP64 GPU path, the FP32-inner
+form with native FP64 residuals, and the adjoint equation are timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own seeded domain of the same shape
@@ -39,10 +41,19 @@ SMS, SM_MAX_MHZ = 152, 2070.0
 #   FP32: 128 lanes/SM; a pair costs 10 FP32-pipe instructions + 1 MUFU.
 #   FP64: 2 DFMA lanes/SM (1.25 TFLOP/s nominal); a pair costs 13 FP64-pipe
 #   instructions (10 arithmetic + 3 to refine the reciprocal seed).
+#   double-float: ~97 FP32-pipe instructions per pair + 1 MUFU.
 PEAK_PAIRS = {
     "pair32": SMS * SM_MAX_MHZ * 1e6 * 128 / 10,
     "pair64": SMS * SM_MAX_MHZ * 1e6 * 2 / 13,
+    "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128 / 97,
 }
+PEAK_BASIS = {
+    "pair64": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz / 13 FP64 instr per pair",
+    "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz / 10 FP32 instr per pair",
+    "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz / 97 FP32 instr per double-float pair",
+}
+KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32_kernel", "pairdf": "pairsumdf_kernel"}
+MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3}
 
 
 def parse():
@@ -54,7 +65,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1024, help="nodes per boundary")
     ap.add_argument("--count", type=int, default=64, help="ellipses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves")
+    ap.add_argument("--precision", choices=list(MODES), default="mixed_df")
     return ap.parse_args()
 
 
@@ -204,21 +216,26 @@ def main():
     hk = torch.empty(dom.m1, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = G.options(tol=TOL, restart=20, maxit=50, precision=G.GNK_PREC_MIXED, inner_tol=1e-5)
+    mode = MODES[args.precision]
+    bprec = G.GNK_PREC_DF32 if args.precision in ("mixed_df", "df32") else G.GNK_PREC_FP64
+    opts = G.options(tol=TOL, restart=20, maxit=50, precision=mode, inner_tol=1e-5)
     results = {}
 
-    def step(o):
-        hnd = G.gnk_build_boundary(dom.m1, dom.n, et, etp, A, None, None, dom.bounded, stream)
-        res = G.gnk_solve_ie(hnd, gam, mu, o, stream)
-        G.gnk_compute_h(hnd, mu, gam, h, hk, stream)
+    def step(o, build_prec):
+        hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, None, None, dom.bounded,
+                                      build_prec, stream)
+        res = G.gnk_fbie(hnd, gam, mu, h, hk, o, stream)
         G.gnk_free_boundary(hnd)
         results["last"] = res
         return res
 
     for _ in range(args.warmup):
         flush.zero_()
-        step(opts)
+        step(opts, bprec)
     torch.cuda.synchronize()
+
+    kinds = (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
+             ("reduce", G.PROF_REDUCE), ("circ", G.PROF_CIRC), ("krylov", G.PROF_KRYLOV))
 
     # ---- timed region
     launches0 = G.gnk_kernel_launches()
@@ -232,7 +249,7 @@ def main():
     ev0.record(stream)
     for _ in range(args.steps):
         flush.zero_()
-        res = step(opts)
+        res = step(opts, bprec)
         if res.status != 0 or res.relres > TOL:
             raise SystemExit(f"solve failed: {res.as_dict()}")
     ev1.record(stream)
@@ -241,32 +258,63 @@ def main():
     t_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     gpu_launches = G.gnk_kernel_launches() - launches0
-    prof = {k: G.gnk_profile_query(i) for k, i in (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32),
-                                                    ("reduce", G.PROF_REDUCE), ("circ", G.PROF_CIRC),
-                                                    ("krylov", G.PROF_KRYLOV))}
+    prof = {k: G.gnk_profile_query(i) for k, i in kinds}
     G.gnk_profile_enable(False)
     t_ms = max_over_ranks(dist, t_ms, dev)
     ms_per_step = t_ms / args.steps
     res = results["last"]
+    mu_main = mu.clone()
+    h_main = hk.clone()
 
-    # ---- plain FP64 GPU solve of the same problem (the comparison)
-    fp64 = None
+    # ---- the same problem in the other forms (one timed run each, after one untimed)
+    compare = {}
+    kernel_rates = {}
     if not args.no_fp64:
-        o64 = G.options(tol=TOL, restart=20, maxit=50, precision=G.GNK_PREC_FP64)
-        flush.zero_()
+        for name in ("fp64", "mixed", "mixed_df"):
+            if name == args.precision:
+                continue
+            o = G.options(tol=TOL, restart=20, maxit=50, precision=MODES[name], inner_tol=1e-5)
+            bp = G.GNK_PREC_DF32 if name in ("mixed_df", "df32") else G.GNK_PREC_FP64
+            if name != "fp64":
+                step(o, bp)
+            flush.zero_()
+            torch.cuda.synchronize()
+            G.gnk_profile_enable(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step(o, bp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pk = {k: G.gnk_profile_query(i) for k, i in kinds}
+            G.gnk_profile_enable(False)
+            compare[name] = {
+                "time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": r.iterations,
+                "refinements": r.refinements, "relres": r.relres,
+                "max_rel_diff_mu_vs_headline": float((mu - mu_main).abs().max() / mu_main.abs().max()),
+                "max_abs_diff_hk_vs_headline": float((hk - h_main).abs().max()),
+            }
+            for k in ("pair64", "pair32", "pairdf"):
+                if pk[k][1] > 0 and k not in kernel_rates:
+                    kernel_rates[k] = pk[k][2] / (pk[k][1] / 1e3)
+        # adjoint equation (I + N* + J) phi = gamma, headline precision
+        etpp, Ap = (torch.as_tensor(a, device=dev) for a in (dom.etpp, dom.Ap))
+        hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, etpp, Ap, dom.bounded, bprec, stream)
+        phi = torch.empty_like(gam)
+        G.gnk_solve_adjoint_ie(hnd, gam, phi, opts, stream)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r64 = step(o64)
+        ra = G.gnk_solve_adjoint_ie(hnd, gam, phi, opts, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        mu64 = mu.clone()
-        step(opts)
-        torch.cuda.synchronize()
-        fp64 = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": r64.iterations,
-                "relres": r64.relres,
-                "mixed_vs_fp64_max_rel_diff_mu": float((mu - mu64).abs().max() / mu64.abs().max())}
+        G.gnk_free_boundary(hnd)
+        compare["adjoint_" + args.precision] = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3,
+                                                "iterations": ra.iterations, "relres": ra.relres}
+    for k in ("pair64", "pair32", "pairdf"):
+        if prof[k][1] > 0:
+            kernel_rates[k] = prof[k][2] / (prof[k][1] / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers
     def pinned(a):
@@ -279,9 +327,9 @@ def main():
     h_hk = pinned(np.zeros(dom.m1))
 
     def step_host():
-        hnd = G.gnk_build_boundary(dom.m1, dom.n, h_et, h_etp, h_A, None, None, dom.bounded, stream)
-        r = G.gnk_solve_ie(hnd, h_gam, h_mu, opts, stream)
-        G.gnk_compute_h(hnd, h_mu, h_gam, h_h, h_hk, stream)
+        hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, h_et, h_etp, h_A, None, None, dom.bounded,
+                                      bprec, stream)
+        r = G.gnk_fbie(hnd, h_gam, h_mu, h_h, h_hk, opts, stream)
         G.gnk_free_boundary(hnd)
         return r
     step_host()
@@ -293,7 +341,7 @@ def main():
         step_host()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps, dev)
-    h2d = 3 * 16 * dom.N + 8 * dom.N + 16 * dom.N
+    h2d = 3 * 16 * dom.N + 8 * dom.N
     d2h = 8 * dom.N + 8 * dom.N + 8 * dom.m1
 
     if rank != 0:
@@ -302,21 +350,19 @@ def main():
         return
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
-    dom_kind = max(("pair64", "pair32"), key=lambda k: prof[k][1])
+    dom_kind = max(("pair64", "pair32", "pairdf"), key=lambda k: prof[k][1])
     n_l, ms_l, work = prof[dom_kind]
     achieved = work / (ms_l / 1e3) if ms_l > 0 else 0.0
     peak = PEAK_PAIRS[dom_kind]
     total_prof_ms = sum(v[1] for v in prof.values())
-    pair_evals = prof["pair64"][2] + prof["pair32"][2]
+    pair_evals = sum(prof[k][2] for k in ("pair64", "pair32", "pairdf"))
     roofline = {
-        "bound": "alu", "kernel": "pairsum64_kernel" if dom_kind == "pair64" else "pairsum32_kernel",
+        "bound": "alu", "kernel": KERNEL_NAME[dom_kind],
         "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
         "frac": achieved / peak, "traffic": None,
         "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1),
         "share_of_instrumented_time": {k: v[1] / total_prof_ms for k, v in prof.items()},
-        "peak_basis": ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz / 13 FP64 instr per pair"
-                       if dom_kind == "pair64" else
-                       "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz / 10 FP32 instr per pair"),
+        "peak_basis": PEAK_BASIS[dom_kind],
     }
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -326,20 +372,20 @@ def main():
     line = {
         "metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
+                  "fp64": "f64", "df32": "double-float f32 pairs, f64 vectors"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
-                   "restart": 20, "precision": "FP32 pair sums in GMRES, FP64 refinement",
+                   "restart": 20, "precision": args.precision,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "pair_evals_per_s": pair_evals / (total_prof_ms / 1e3) if total_prof_ms else None,
-        "pair_evals_per_s_fp64_kernel": (prof["pair64"][2] / (prof["pair64"][1] / 1e3)
-                                          if prof["pair64"][1] else None),
-        "pair_evals_per_s_fp32_kernel": (prof["pair32"][2] / (prof["pair32"][1] / 1e3)
-                                          if prof["pair32"][1] else None),
-        "solve": {"iterations": res.iterations, "refinements": res.refinements,
-                  "matvecs_fp64": res.matvecs_fp64, "matvecs_fp32": res.matvecs_fp32,
-                  "relres": res.relres},
-        "fp64_plain": fp64,
+        "pair_evals_per_s_by_kernel": {KERNEL_NAME[k]: v for k, v in kernel_rates.items()},
+        "solve": {"precision": args.precision, "iterations": res.iterations,
+                  "refinements": res.refinements, "matvecs_fp64_class": res.matvecs_fp64,
+                  "matvecs_fp32": res.matvecs_fp32, "relres": res.relres},
+        "compare": compare,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

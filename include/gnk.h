@@ -54,6 +54,12 @@ extern "C" {
                               iterative refinement (residual, circulant part,
                               diagonals and Givens rotations stay FP64)          */
 #define GNK_PREC_FP32  2   /* FP32 pair sums (apply/cauchy calls only)            */
+#define GNK_PREC_DF32  3   /* double-float pair sums: pairs of FP32 values carried
+                              through error-free transformations on the FP32
+                              pipe, about 2^-46 relative per term (FP64-class
+                              accuracy; GB300's FP64 pipe is 1/64 of FP32)     */
+#define GNK_PREC_MIXED_DF 4 /* as GNK_PREC_MIXED, with the refinement residual,
+                              right-hand side and h in double-float pair sums  */
 
 typedef struct gnk_boundary gnk_boundary;
 
@@ -65,7 +71,7 @@ typedef struct gnk_options {
     int restart;       /* inner iterations per cycle (>= 1)                    */
     int maxit;         /* maximum number of cycles (>= 1)                      */
     double tol;        /* relative residual target (> 0)                       */
-    int precision;     /* GNK_PREC_FP64 or GNK_PREC_MIXED                      */
+    int precision;     /* GNK_PREC_FP64, _DF32, _MIXED or _MIXED_DF            */
     int max_refine;    /* MIXED: maximum refinement steps                      */
     double inner_tol;  /* MIXED: relative tolerance of each inner solve        */
 } gnk_options;
@@ -75,7 +81,7 @@ typedef struct gnk_result {
     int iterations;    /* Arnoldi steps over all cycles and refinement steps   */
     int cycles;        /* GMRES cycles (restarts + 1) over all inner solves    */
     int refinements;   /* MIXED: refinement steps taken                        */
-    int matvecs_fp64;  /* products with the FP64 operator                      */
+    int matvecs_fp64;  /* products with the FP64-class (FP64 or DF32) operator */
     int matvecs_fp32;  /* products with the FP32 operator                      */
     double relres;     /* final true relative residual, evaluated in FP64      */
 } gnk_result;
@@ -130,6 +136,14 @@ int gnk_build_boundary(gnk_boundary** out, int m1, int n,
                        const double* A, const double* Ap, int bounded,
                        void* stream);
 
+/* As gnk_build_boundary, with the arithmetic of the precomputed Cauchy sums
+ * (Eone and E eta') chosen by `precision` (GNK_PREC_FP64 or GNK_PREC_DF32);
+ * gnk_build_boundary uses GNK_PREC_FP64. */
+int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n,
+                          const double* et, const double* etp, const double* etpp,
+                          const double* A, const double* Ap, int bounded,
+                          int precision, void* stream);
+
 /* Releases the handle and its device memory (NULL is accepted). */
 int gnk_free_boundary(gnk_boundary* b);
 
@@ -139,14 +153,14 @@ int gnk_boundary_size(const gnk_boundary* b, int* m1, int* n);
 /* ---------------------------------------------------------------------------
  * Cauchy sum (Sec. 2.5, Eqs. fmm-1, fmm-E, E-fmm): z = E w,
  *   z_i = sum_{j != i} w_j / (eta_i - eta_j),   i = 1..N,
- * w and z complex (2N doubles).  precision: GNK_PREC_FP64 or GNK_PREC_FP32.
+ * w and z complex (2N doubles).  precision: GNK_PREC_FP64, _FP32 or _DF32.
  * ------------------------------------------------------------------------- */
 int gnk_cauchy_sum(const gnk_boundary* b, const double* w, double* z,
                    int precision, void* stream);
 
 /* y = (2I + diag(B1) - B) x, the discrete I - N (Eqs. sys, (I-B)x, f_B):
  *   y = 2x - (2/n) Im(A Eone) x + (2/n) Im(A E(q x)).
- * x, y real (N doubles).  precision: GNK_PREC_FP64 or GNK_PREC_FP32. */
+ * x, y real (N doubles).  precision: GNK_PREC_FP64, _FP32 or _DF32. */
 int gnk_apply_IminusN(const gnk_boundary* b, const double* x, double* y,
                       int precision, void* stream);
 
@@ -185,6 +199,18 @@ int gnk_solve_ie(const gnk_boundary* b, const double* gam, double* mu,
  * each component. */
 int gnk_compute_h(const gnk_boundary* b, const double* mu, const double* gam,
                   double* h, double* hk, void* stream);
+
+/* The whole computation of the paper's FBIE function (Sec. 3, listing of
+ * FBIE): mu solving (I - N) mu = -M gamma and h of Eq. (bh), with the fewest
+ * Cauchy sums: E(q gamma) gives both the right-hand side -y and
+ * f_B(gamma) = (2I + diag(B1) - B) gamma, and the last true residual of the
+ * solve gives f_C(mu) = (D - diag(D1) + Lhat) mu, so h = (f_C(mu) - f_B(gamma))/2
+ * needs no further sum.  Products outside the inner GMRES use FP64 for
+ * GNK_PREC_FP64 / _MIXED and double-float for _DF32 / _MIXED_DF.  mu, h
+ * (N doubles) and hk (m1 doubles, nullable) are outputs.  Returns as
+ * gnk_solve_ie. */
+int gnk_fbie(const gnk_boundary* b, const double* gam, double* mu, double* h,
+             double* hk, const gnk_options* opt, gnk_result* info, void* stream);
 
 /* Solve (I + N* + J) mu = gamma (Eq. ie*) in the form
  * (diag(e) + B^T + Phat) mu = gamma (Eq. sys*) by restarted GMRES

@@ -82,8 +82,8 @@ int check_handle(const gnk_boundary* h) {
 }
 
 int check_prec(int prec) {
-    if (prec != GNK_PREC_FP64 && prec != GNK_PREC_FP32) {
-        set_error("precision must be GNK_PREC_FP64 or GNK_PREC_FP32 here, got %d", prec);
+    if (prec != GNK_PREC_FP64 && prec != GNK_PREC_FP32 && prec != GNK_PREC_DF32) {
+        set_error("precision must be GNK_PREC_FP64, GNK_PREC_FP32 or GNK_PREC_DF32 here, got %d", prec);
         return GNK_EINVAL;
     }
     return GNK_OK;
@@ -101,8 +101,8 @@ int dmalloc(T** p, size_t count) {
 
 void release(Boundary& b) {
     void* ptrs[] = {b.et, b.etp, b.A, b.q, b.Eone, b.b1, b.d1, b.e, b.ref32, b.off32, b.et32,
-                    b.q32, b.A32, b.twiddle, b.Lcol, b.partial, b.zbuf, b.r0, b.r1, b.r2, b.r3,
-                    b.r4, b.means, b.stage, b.V, b.kry, b.kstate};
+                    b.q32, b.A32, b.ref64, b.offdf, b.twiddle, b.Lcol, b.partial, b.zbuf, b.r0,
+                    b.r1, b.r2, b.r3, b.r4, b.r5, b.r6, b.means, b.stage, b.V, b.kry, b.kstate};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b.hstate) cudaFreeHost(b.hstate);
@@ -112,17 +112,18 @@ int options_from(const gnk_options* in, gnk_options* o) {
     gnk_default_options(o);
     if (in) *o = *in;
     if (o->restart < 1 || o->restart > 1000 || o->maxit < 1 || !(o->tol > 0.0) ||
-        (o->precision != GNK_PREC_FP64 && o->precision != GNK_PREC_MIXED) || o->max_refine < 0 ||
-        !(o->inner_tol > 0.0)) {
-        set_error("invalid gnk_options (restart 1..1000, maxit >= 1, tol > 0, precision FP64|MIXED, "
-                  "max_refine >= 0, inner_tol > 0)");
+        (o->precision != GNK_PREC_FP64 && o->precision != GNK_PREC_MIXED &&
+         o->precision != GNK_PREC_DF32 && o->precision != GNK_PREC_MIXED_DF) ||
+        o->max_refine < 0 || !(o->inner_tol > 0.0)) {
+        set_error("invalid gnk_options (restart 1..1000, maxit >= 1, tol > 0, precision "
+                  "FP64|MIXED|DF32|MIXED_DF, max_refine >= 0, inner_tol > 0)");
         return GNK_EINVAL;
     }
     return GNK_OK;
 }
 
 int build(Boundary& b, int m1, int n, const double* et, const double* etp, const double* etpp,
-          const double* A, const double* Ap, int bounded, cudaStream_t st) {
+          const double* A, const double* Ap, int bounded, int eone_prec, cudaStream_t st) {
     const size_t N = (size_t)m1 * n;
     b.m1 = m1;
     b.n = n;
@@ -146,6 +147,8 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     GNK_TRY(dmalloc(&b.et32, N));
     GNK_TRY(dmalloc(&b.q32, N));
     GNK_TRY(dmalloc(&b.A32, N));
+    GNK_TRY(dmalloc(&b.ref64, (size_t)tiles32));
+    GNK_TRY(dmalloc(&b.offdf, N));
     GNK_TRY(dmalloc(&b.twiddle, (size_t)n));
     GNK_TRY(dmalloc(&b.Lcol, (size_t)n));
     GNK_TRY(dmalloc(&b.zbuf, kMaxRHS * N));
@@ -154,6 +157,8 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     GNK_TRY(dmalloc(&b.r2, N));
     GNK_TRY(dmalloc(&b.r3, N));
     GNK_TRY(dmalloc(&b.r4, N));
+    GNK_TRY(dmalloc(&b.r5, N));
+    GNK_TRY(dmalloc(&b.r6, N));
     GNK_TRY(dmalloc(&b.means, (size_t)m1));
     GNK_TRY(dmalloc(&b.stage, 4 * 2 * N));
 
@@ -203,6 +208,8 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
                          kSrcTile64);
     b.plan32 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP32), kThreads32 * kTargets32,
                          kSrcTile32);
+    b.plandf = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_DF32), kThreadsDF * kTargetsDF,
+                         kSrcTile32);
     GNK_TRY(pair_workspace_bytes(b, &b.partial_bytes));
     GNK_TRY(dmalloc(reinterpret_cast<char**>(&b.partial), b.partial_bytes));
 
@@ -217,7 +224,8 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     j.out = b.b1;
     j.out2 = b.d1;
     j.out3 = b.e;
-    GNK_TRY(run_pairsum64(b, j, st));
+    b.eone_prec = eone_prec;
+    GNK_TRY(run_pairsum(b, j, eone_prec, st));
     GNK_TRY_CUDA(cudaStreamSynchronize(st));
     return GNK_OK;
 }
@@ -255,6 +263,16 @@ unsigned long long gnk_kernel_launches(void) { return g_launches.load(std::memor
 int gnk_build_boundary(gnk_boundary** out, int m1, int n, const double* et, const double* etp,
                        const double* etpp, const double* A, const double* Ap, int bounded,
                        void* stream) {
+    return gnk_build_boundary_ex(out, m1, n, et, etp, etpp, A, Ap, bounded, GNK_PREC_FP64, stream);
+}
+
+int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, const double* etp,
+                          const double* etpp, const double* A, const double* Ap, int bounded,
+                          int precision, void* stream) {
+    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
+        set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64 or GNK_PREC_DF32");
+        return GNK_EINVAL;
+    }
     if (!out || !et || !etp || !A) {
         set_error("gnk_build_boundary: out, et, etp and A must not be NULL");
         return GNK_EINVAL;
@@ -273,7 +291,7 @@ int gnk_build_boundary(gnk_boundary** out, int m1, int n, const double* et, cons
         set_error("host allocation failed");
         return GNK_ENOMEM;
     }
-    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, (cudaStream_t)stream);
+    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, precision, (cudaStream_t)stream);
     if (s != GNK_OK) {
         release(h->b);
         delete h;
@@ -382,7 +400,7 @@ static int solve_common(const gnk_boundary* h, const double* gam, double* mu, co
     const double* rhs = dg;
     if (!adjoint) {
         // right-hand side -y = -(D - diag(D1) + Lhat) gamma (Eqs. sys, y)
-        GNK_TRY(op_M(b, dg, b.r4, GNK_PREC_FP64, st));
+        GNK_TRY(op_M(b, dg, b.r4, outer_precision(o.precision), st));
         GNK_TRY(op_negate(b.r4, b.N, st));
         rhs = b.r4;
     }
@@ -402,6 +420,41 @@ int gnk_solve_ie(const gnk_boundary* h, const double* gam, double* mu, const gnk
 int gnk_solve_adjoint_ie(const gnk_boundary* h, const double* gam, double* mu, const gnk_options* opt,
                          gnk_result* info, void* stream) {
     return solve_common(h, gam, mu, opt, info, stream, 1);
+}
+
+int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, double* hk,
+             const gnk_options* opt, gnk_result* info, void* stream) {
+    GNK_TRY(check_handle(hd));
+    if (!gam || !mu || !hv) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    gnk_options o;
+    GNK_TRY(options_from(opt, &o));
+    const Boundary& b = hd->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int outer = outer_precision(o.precision);
+    const double* dg;
+    GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
+    Out o_mu = stage_out(b, mu, b.N, 1);
+    Out o_h = stage_out(b, hv, b.N, 2);
+    // -y and f_B(gamma) from one Cauchy sum
+    GNK_TRY(op_rhs_fb(b, dg, b.r4, b.r5, outer, st));
+    int fc_valid = 0;
+    const int s = solve(b, 0, b.r4, o_mu.dev, o, info, st, b.r6, &fc_valid);
+    if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+    if (!fc_valid) GNK_TRY(op_M(b, o_mu.dev, b.r6, outer, st));  // f_C(mu)
+    GNK_TRY(op_half_diff(b.r6, b.r5, o_h.dev, b.N, st));
+    if (hk) {
+        Out o_k = stage_out(b, hk, b.m1, 3);
+        GNK_TRY(run_component_means(b, o_h.dev, o_k.dev, st));
+        GNK_TRY(finish_out(o_k, st));
+    }
+    GNK_TRY(finish_out(o_mu, st));
+    GNK_TRY(finish_out(o_h, st));
+    if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles");
+    if (s == GNK_ENONFINITE) set_error("non-finite value in the GMRES iteration");
+    return s;
 }
 
 int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,

@@ -125,6 +125,8 @@ struct PrepArgs {
     float4* ref32;
     float2* q32;
     float2* A32;
+    double2* ref64;
+    float4* offdf;
     double* ediag;       // (2/n) Im(eta''/eta' - A'/A), corner limit 0
     int* flag;           // bit 1: non-finite input, bit 2: A == 0
 };
@@ -156,7 +158,14 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
     const int r = j0 + cnt / 2;  // reference node of the source tile
     const double2 er = a.et[r];
     a.off32[i] = make_float2((float)(et.x - er.x), (float)(et.y - er.y));
-    if (i == r) a.ref32[tile] = split_hilo(er);
+    if (i == r) {
+        a.ref32[tile] = split_hilo(er);
+        a.ref64[tile] = er;
+    }
+    // df32 offset to the same reference: hi/lo split of the FP64 difference
+    const double ox = et.x - er.x, oy = et.y - er.y;
+    const float ohx = (float)ox, ohy = (float)oy;
+    a.offdf[i] = make_float4(ohx, ohy, (float)(ox - (double)ohx), (float)(oy - (double)ohy));
     if (a.has_adj) {
         const double2 epp = make_double2(a.etpp[2 * i], a.etpp[2 * i + 1]);
         const double2 Ap = a.Ap ? make_double2(a.Ap[2 * i], a.Ap[2 * i + 1]) : make_double2(0.0, 0.0);
@@ -215,6 +224,8 @@ int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int*
     a.ref32 = b.ref32;
     a.q32 = b.q32;
     a.A32 = b.A32;
+    a.ref64 = b.ref64;
+    a.offdf = b.offdf;
     a.ediag = b.e;
     a.flag = d_flag;
     prepare_geometry_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);

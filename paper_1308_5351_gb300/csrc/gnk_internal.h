@@ -43,6 +43,7 @@ enum ProfKind : int {
     PK_CIRC = 3,     // circulant FFT / direct kernel; work = bytes moved
     PK_KRYLOV = 4,   // GMRES vector kernels; work = bytes moved
     PK_OTHER = 5,
+    PK_PAIRDF = 6,   // double-float pair-sum kernel; work = pair evaluations
 };
 struct ProfToken {
     void* ev = nullptr;
@@ -64,6 +65,8 @@ constexpr int kThreads64 = 128;   // threads per block, FP64 kernel
 constexpr int kTargets64 = 2;     // targets per thread, FP64 kernel
 constexpr int kThreads32 = 256;   // threads per block, FP32 kernel
 constexpr int kTargets32 = 4;     // targets per thread, FP32 kernel
+constexpr int kThreadsDF = 256;   // threads per block, double-float kernel
+constexpr int kTargetsDF = 2;     // targets per thread, double-float kernel
 constexpr int kMaxRHS = 2;        // right-hand sides per pair-sum launch
 
 // How the sources' complex weights are formed when a source tile is loaded.
@@ -83,6 +86,8 @@ enum Epilogue : int {
     EPI_RESID_ADJ = 5,// out = rhs - g_B(x)
     EPI_H = 6,        // out = (f_C(mu) - f_B(gam)) / 2, z = E(q mu), z2 = E(q gam)
     EPI_EONE = 7,     // b1 = -(2/n) Im(A z), d1 = -(2/n) Re(A z); if R=2: e from z2
+    EPI_RHS_FB = 8,   // out = -f_C(x) (the right-hand side -y), out2 = f_B(x)
+    EPI_RESID_FC = 9, // out = rhs - f_B(x), out2 = f_C(x)
 };
 
 struct PairPlan {
@@ -136,6 +141,9 @@ struct Boundary {
     float4* et32 = nullptr;     // per node: hi/lo split of eta (hi.x, hi.y, lo.x, lo.y)
     float2* q32 = nullptr;
     float2* A32 = nullptr;
+    // double-float geometry: FP64 reference node per source tile, df32 offsets
+    double2* ref64 = nullptr;   // per source tile
+    float4* offdf = nullptr;    // per node: (dx.h, dy.h, dx.l, dy.l)
 
     // circulant part
     int fft_pow2 = 0;           // n is a power of two
@@ -151,9 +159,12 @@ struct Boundary {
     double* r2 = nullptr;
     double* r3 = nullptr;
     double* r4 = nullptr;
+    double* r5 = nullptr;
+    double* r6 = nullptr;
     double* means = nullptr;    // m1
     double* stage = nullptr;    // host-staging buffers: 4 x 2N doubles
-    PairPlan plan64, plan32;
+    PairPlan plan64, plan32, plandf;
+    int eone_prec = GNK_PREC_FP64;  // arithmetic of the precomputed sums
 
     // Krylov workspace (allocated on first solve, grown as needed)
     double* V = nullptr;        // (restart+1) x N
@@ -169,6 +180,7 @@ PairPlan make_plan(int N, int sms, int blocks_per_sm, int targets_per_block, int
 int pair_workspace_bytes(const Boundary& b, size_t* bytes);
 int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st);
+int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st);
 int pair_blocks_per_sm(int precision);
 
@@ -185,13 +197,22 @@ int op_M(const Boundary& b, const double* x, double* y, int prec, cudaStream_t s
 int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
                const int* done = nullptr);
 int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
-             int prec, cudaStream_t st);
+             int prec, cudaStream_t st, double* fc_out = nullptr);
+int op_rhs_fb(const Boundary& b, const double* gam, double* rhs, double* fb, int prec,
+              cudaStream_t st);
+int op_half_diff(const double* a, const double* b, double* out, int N, cudaStream_t st);
 int op_h(const Boundary& b, const double* mu, const double* gam, double* h, cudaStream_t st);
 int op_negate(double* x, int N, cudaStream_t st);
 
 // ---------------------------------------------------------------- Krylov (krylov.cu)
+// Solves with the operator of the handle (adjoint = 0: f_B, 1: g_B).  When
+// fc_out is given, the last true residual also writes f_C(x) of the returned
+// x there and *fc_valid is set (f_C(mu) is the first half of h, Eq. bh).
 int solve(const Boundary& b, int adjoint, const double* rhs, double* x,
-          const gnk_options& opt, gnk_result* info, cudaStream_t st);
+          const gnk_options& opt, gnk_result* info, cudaStream_t st,
+          double* fc_out = nullptr, int* fc_valid = nullptr);
+// Arithmetic of the outer (refinement) products for a solve precision.
+int outer_precision(int solve_precision);
 
 }  // namespace gnk
 

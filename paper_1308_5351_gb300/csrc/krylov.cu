@@ -333,7 +333,9 @@ int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
 // r is a work vector.  Counters are added to *res; *relres receives the final
 // true relative residual (in prec).
 int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, double* r,
-          int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st) {
+          int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st,
+          double* fc_out, int* fc_valid) {
+    if (fc_valid) *fc_valid = 0;
     GNK_TRY(ensure_krylov(b, restart));
     const int N = b.N;
     const double vb = 8.0 * N;  // bytes of one vector
@@ -354,8 +356,9 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
         if (cycle == 0) {
             GNK_TRY_CUDA(cudaMemcpyAsync(r, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         } else {
-            GNK_TRY(op_resid(b, adjoint, rhs, x, r, prec, st));
+            GNK_TRY(op_resid(b, adjoint, rhs, x, r, prec, st, fc_out));
             if (prec == GNK_PREC_FP32) res->matvecs_fp32++; else res->matvecs_fp64++;
+            if (fc_valid && fc_out) *fc_valid = 1;  // f_C of the current x
         }
         KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(r, N, p, ks, 1)));
         KLAUNCH(2 * vb, (k_scale_first<<<nb, KT, 0, st>>>(r, b.V, N, ks)));
@@ -405,6 +408,7 @@ int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, doub
         KLAUNCH((restart + 2) * vb, (k_update_x<<<nb, KT, 0, st>>>(b.V, N, p, x, ks)));
         GNK_TRY_CUDA(cudaGetLastError());
         count_launches(1);
+        if (fc_valid) *fc_valid = 0;  // x moved
     }
     return status;
 }
@@ -427,16 +431,23 @@ int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
 
 }  // namespace
 
+int outer_precision(int solve_precision) {
+    return (solve_precision == GNK_PREC_DF32 || solve_precision == GNK_PREC_MIXED_DF) ? GNK_PREC_DF32
+                                                                                     : GNK_PREC_FP64;
+}
+
 int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const gnk_options& opt,
-          gnk_result* info, cudaStream_t st) {
+          gnk_result* info, cudaStream_t st, double* fc_out, int* fc_valid) {
     Boundary& b = const_cast<Boundary&>(bc);  // workspace only
     gnk_result res;
     std::memset(&res, 0, sizeof(res));
     double relres = 0.0;
     int status;
-    if (opt.precision == GNK_PREC_FP64) {
-        status = gmres(b, adjoint, GNK_PREC_FP64, rhs, x, b.r0, opt.restart, opt.maxit, opt.tol, &res,
-                       &relres, st);
+    const int outer = outer_precision(opt.precision);
+    if (fc_valid) *fc_valid = 0;
+    if (opt.precision == GNK_PREC_FP64 || opt.precision == GNK_PREC_DF32) {
+        status = gmres(b, adjoint, outer, rhs, x, b.r0, opt.restart, opt.maxit, opt.tol, &res,
+                       &relres, st, fc_out, fc_valid);
     } else {
         // FP64 iterative refinement: r = rhs - A x (FP64), A d = r with the
         // FP32 operator to inner_tol, x += d.
@@ -464,7 +475,7 @@ int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const g
             if (it == opt.max_refine) break;
             double inner_rel = 0.0;
             const int s = gmres(b, adjoint, GNK_PREC_FP32, rr, dd, b.r0, opt.restart, opt.maxit,
-                                opt.inner_tol, &res, &inner_rel, st);
+                                opt.inner_tol, &res, &inner_rel, st, nullptr, nullptr);
             if (s == GNK_ENONFINITE) {
                 status = s;
                 break;
@@ -472,7 +483,8 @@ int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const g
             k_axpy<<<(N + 255) / 256, 256, 0, st>>>(x, dd, N);
             GNK_TRY_CUDA(cudaGetLastError());
             count_launches(1);
-            GNK_TRY(op_resid(b, adjoint, rhs, x, rr, GNK_PREC_FP64, st));
+            GNK_TRY(op_resid(b, adjoint, rhs, x, rr, outer, st, fc_out));
+            if (fc_valid && fc_out) *fc_valid = 1;
             res.matvecs_fp64++;
             res.refinements++;
         }

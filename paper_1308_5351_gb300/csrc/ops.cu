@@ -52,9 +52,11 @@ int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStre
     return run_pairsum(b, j, prec, st);
 }
 
-// r = rhs - A x for A = f_B (adjoint = 0) or g_B (adjoint = 1)
+// r = rhs - A x for A = f_B (adjoint = 0) or g_B (adjoint = 1); with fc_out
+// (adjoint = 0 only) also f_C(x) from the same Cauchy sum.
 int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
-             int prec, cudaStream_t st) {
+             int prec, cudaStream_t st, double* fc_out) {
+    if (fc_out && !adjoint) GNK_TRY(run_circulant(b, x, b.r3, st));
     PairJob j;
     j.R = 1;
     j.mode = W_SCALED;
@@ -69,8 +71,28 @@ int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x,
         j.means = b.means;
     } else {
         j.s = b.q;
-        j.epi = EPI_RESID;
+        j.epi = fc_out ? EPI_RESID_FC : EPI_RESID;
+        j.out2 = fc_out;
+        j.Lx = b.r3;
     }
+    return run_pairsum(b, j, prec, st);
+}
+
+// rhs = -y = -(D - diag(D1) + Lhat) gamma and fb = f_B(gamma) from one Cauchy
+// sum E(q gamma) (Eqs. y, sys; f_B(gamma) is the second half of h, Eq. bh).
+int op_rhs_fb(const Boundary& b, const double* gam, double* rhs, double* fb, int prec,
+              cudaStream_t st) {
+    GNK_TRY(run_circulant(b, gam, b.r3, st));
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = gam;
+    j.s = b.q;
+    j.epi = EPI_RHS_FB;
+    j.out = rhs;
+    j.out2 = fb;
+    j.ex = gam;
+    j.Lx = b.r3;
     return run_pairsum(b, j, prec, st);
 }
 
@@ -98,6 +120,21 @@ __global__ void negate_kernel(double* x, int N) {
     if (i < N) x[i] = -x[i];
 }
 }  // namespace
+
+namespace {
+__global__ void half_diff_kernel(const double* a, const double* b, double* out, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[i] = 0.5 * (a[i] - b[i]);
+}
+}  // namespace
+
+// out = (a - b) / 2: h = (f_C(mu) - f_B(gamma)) / 2 (Eq. bh)
+int op_half_diff(const double* a, const double* b, double* out, int N, cudaStream_t st) {
+    half_diff_kernel<<<(N + 255) / 256, 256, 0, st>>>(a, b, out, N);
+    GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(1);
+    return GNK_OK;
+}
 
 int op_negate(double* x, int N, cudaStream_t st) {
     negate_kernel<<<(N + 255) / 256, 256, 0, st>>>(x, N);

@@ -11,7 +11,8 @@
 // Per pair the FP64 kernel spends 13 FP64-pipe instructions:
 //   2 DADD (d = eta_i - eta_j), DMUL + DFMA (|d|^2), 3 DFMA to refine the
 //   hardware reciprocal seed, 2 DMUL (Re, Im of 1/d), 4 DFMA (w / d);
-// the FP32 kernel spends 10 FP32-pipe instructions and one MUFU reciprocal.
+// the FP32 kernel spends 10 FP32-pipe instructions and one MUFU reciprocal;
+// the double-float kernel about 97 FP32-pipe instructions and one MUFU.
 #include <algorithm>
 #include <cmath>
 
@@ -310,12 +311,202 @@ __global__ void __launch_bounds__(kThreads32) pairsum32_kernel(Pair32Args a) {
     }
 }
 
+// ------------------------------------------------------------------ double-float (df32)
+// FP64-class Cauchy sums on the FP32 pipe.  A df32 number is an unevaluated
+// sum hi + lo of two floats (about 48 significant bits).  Error-free
+// transformations (Knuth's TwoSum, Dekker's product via FMA) carry the
+// rounding errors of every step; positions are taken relative to the source
+// tile's FP64 reference node (each target forms its offset in FP64 once per
+// tile), so the difference of two nearby nodes keeps its leading bits.  Per
+// pair: ~22 flops for d, 16 for |d|^2, 3 for the reciprocal (one Newton step
+// from rcp.approx), 8 for 1/d, 16 for the four weight products and 32 for
+// the two compensated accumulations, all on the FP32 pipe.
+struct df {
+    float h, l;
+};
+
+// The _rn intrinsics are never contracted into FMAs by the compiler, which
+// the error-free transformations below rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// a - b for df32 operands (Bailey's add with a final renormalisation)
+__device__ __forceinline__ df df_sub(float ah, float al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e = __fadd_rn(e, __fsub_rn(al, bl));
+    df r;
+    fast_two_sum(s, e, r.h, r.l);
+    return r;
+}
+
+// product of two df32 values, unnormalised (hi = fl(a.h b.h), lo = error + cross terms)
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df r;
+    r.h = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -r.h);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    r.l = e;
+    return r;
+}
+
+// acc += p (compensated: the hi sum's rounding error goes to acc.l)
+__device__ __forceinline__ void df_acc(df& acc, df p) {
+    float s, e;
+    two_sum(acc.h, p.h, s, e);
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(e, p.l));
+}
+
+__device__ __forceinline__ df df_split(double v) {
+    df r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+}
+
+struct PairDFArgs {
+    const double2* et;
+    const double2* ref64;
+    const float4* offdf;   // per node: (dx.h, dy.h, dx.l, dy.l) of eta_j - ref(tile(j))
+    int N;
+    const double2* w0;
+    const double2* w1;
+    const double* x0;
+    const double* x1;
+    const double2* s;
+    float4* partial;       // [chunk][rhs][N]: (re.h, re.l, im.h, im.l)
+    int tiles_src;
+    int tiles_per_chunk;
+    const int* done;
+};
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreadsDF) pairsumdf_kernel(PairDFArgs a) {
+    constexpr int S = kSrcTile32, T = kTargetsDF, NT = kThreadsDF;
+    static_assert(S == NT, "one source per thread per tile load");
+    __shared__ float4 s_off[S];
+    __shared__ float4 s_w[R][S];  // (wx.h, wx.l, wy.h, wy.l)
+    if (a.done != nullptr && *a.done) return;
+    const int N = a.N;
+    const int tgt0 = blockIdx.x * (NT * T);
+
+    double2 p[T];
+    df acc_re[T][R], acc_im[T][R];
+    int idx[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        idx[t] = tgt0 + t * NT + threadIdx.x;
+        p[t] = a.et[min(idx[t], N - 1)];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc_re[t][r] = acc_im[t][r] = df{0.f, 0.f};
+    }
+
+    const int tb = blockIdx.y * a.tiles_per_chunk;
+    const int te = min(tb + a.tiles_per_chunk, a.tiles_src);
+    for (int tile = tb; tile < te; ++tile) {
+        const int j0 = tile * S;
+        const double2 ref = a.ref64[tile];
+        df ox[T], oy[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {  // target offsets, once per tile, in FP64
+            ox[t] = df_split(p[t].x - ref.x);
+            oy[t] = df_split(p[t].y - ref.y);
+        }
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            const int j = j0 + k;
+            if (j < N) {
+                s_off[k] = a.offdf[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double2 w;
+                    if (MODE == W_COMPLEX) {
+                        w = (r == 0) ? a.w0[j] : a.w1[j];
+                    } else {
+                        const double2 sc = a.s[j];
+                        const double x = (r == 0) ? a.x0[j] : a.x1[j];
+                        w = make_double2(sc.x * x, sc.y * x);
+                    }
+                    const df wx = df_split(w.x), wy = df_split(w.y);
+                    s_w[r][k] = make_float4(wx.h, wx.l, wy.h, wy.l);
+                }
+            } else {
+                s_off[k] = make_float4(kFar32, kFar32, 0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < R; ++r) s_w[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const bool diag = (j0 < tgt0 + NT * T) && (tgt0 < j0 + S);
+#pragma unroll 2
+        for (int k = 0; k < S; ++k) {
+            const float4 so = s_off[k];
+            const int j = j0 + k;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const df dx = df_sub(ox[t].h, ox[t].l, so.x, so.z);
+                const df dy = df_sub(oy[t].h, oy[t].l, so.y, so.w);
+                // |d|^2 = dx.h^2 + dy.h^2 + 2 dx.h dx.l + 2 dy.h dy.l  (lo^2 terms below 2^-48)
+                const float px = __fmul_rn(dx.h, dx.h);
+                float ex = fmaf(dx.h, dx.h, -px);
+                ex = fmaf(dx.h, dx.l + dx.l, ex);
+                const float py = __fmul_rn(dy.h, dy.h);
+                float ey = fmaf(dy.h, dy.h, -py);
+                ey = fmaf(dy.h, dy.l + dy.l, ey);
+                float rh, re;
+                two_sum(px, py, rh, re);
+                const float rl = __fadd_rn(__fadd_rn(ex, ey), re);
+                // 1/|d|^2: one Newton step from the 2^-23 seed gives ~2^-46
+                float y = recip_f32(rh);
+                if (diag && j == idx[t]) y = 0.0f;  // the i = j term is excluded (Eq. fmm-E)
+                float e = fmaf(-rh, y, 1.0f);
+                e = fmaf(-rl, y, e);
+                const df inv = df{y, __fmul_rn(y, e)};
+                const df ar = df_mul(dx, inv);  // 1/d = ar - i ai
+                const df ai = df_mul(dy, inv);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 w = s_w[r][k];
+                    const df wx{w.x, w.y}, wy{w.z, w.w};
+                    // z += w (ar - i ai): re += wx ar + wy ai, im += wy ar - wx ai
+                    df_acc(acc_re[t][r], df_mul(wx, ar));
+                    df_acc(acc_re[t][r], df_mul(wy, ai));
+                    df_acc(acc_im[t][r], df_mul(wy, ar));
+                    const df q = df_mul(wx, ai);
+                    df_acc(acc_im[t][r], df{-q.h, -q.l});
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (idx[t] < N) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                a.partial[((size_t)blockIdx.y * R + r) * N + idx[t]] =
+                    make_float4(acc_re[t][r].h, acc_re[t][r].l, acc_im[t][r].h, acc_im[t][r].l);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ reduce + epilogue
 struct ReduceArgs {
-    int N, n, R, chunks, is32;
+    int N, n, R, chunks, ptype;  // partial type: 0 double2, 1 float2, 2 df32 float4
     double c;
     const double2* p64;
     const float2* p32;
+    const float4* pdf;
     const double2* A;
     const double2* q;
     const double* b1;
@@ -333,11 +524,17 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
     double zx[kMaxRHS] = {0.0, 0.0}, zy[kMaxRHS] = {0.0, 0.0};
     for (int r = 0; r < a.R; ++r) {
         double sx = 0.0, sy = 0.0;
-        if (a.is32) {
+        if (a.ptype == 1) {
             for (int ch = 0; ch < a.chunks; ++ch) {
                 const float2 p = a.p32[((size_t)ch * a.R + r) * N + i];
                 sx += (double)p.x;
                 sy += (double)p.y;
+            }
+        } else if (a.ptype == 2) {
+            for (int ch = 0; ch < a.chunks; ++ch) {
+                const float4 p = a.pdf[((size_t)ch * a.R + r) * N + i];
+                sx += (double)p.x + (double)p.y;
+                sy += (double)p.z + (double)p.w;
             }
         } else {
             for (int ch = 0; ch < a.chunks; ++ch) {
@@ -389,6 +586,24 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
             j.out[i] = 0.5 * (fc - fb);
             break;
         }
+        case EPI_RHS_FB: {
+            // z = E(q gamma): out = -f_C(gamma) = -y (Eq. y), out2 = f_B(gamma) (kept for h)
+            const double2 A = a.A[i];
+            const double x = j.ex[i];
+            const double fc = -s2n * (A.x * zx[0] - A.y * zy[0]) - a.d1[i] * x + j.Lx[i];
+            j.out[i] = -fc;
+            j.out2[i] = 2.0 * x + a.b1[i] * x + s2n * (A.x * zy[0] + A.y * zx[0]);
+            break;
+        }
+        case EPI_RESID_FC: {
+            // out = rhs - f_B(x) and out2 = f_C(x) from the same z = E(q x)
+            const double2 A = a.A[i];
+            const double x = j.ex[i];
+            const double fb = 2.0 * x + a.b1[i] * x + s2n * (A.x * zy[0] + A.y * zx[0]);
+            j.out[i] = j.rhs[i] - fb;
+            j.out2[i] = -s2n * (A.x * zx[0] - A.y * zy[0]) - a.d1[i] * x + j.Lx[i];
+            break;
+        }
         case EPI_EONE: {
             // diag(B1) = -(2/n) Im(A Eone), diag(D1) = -(2/n) Re(A Eone)  (listing of FBIE);
             // with a second right-hand side z1 = E eta':
@@ -406,14 +621,15 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
     }
 }
 
-cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int is32,
+cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int ptype,
                           cudaStream_t st) {
     ReduceArgs ra;
     ra.N = b.N;
     ra.n = b.n;
     ra.R = job.R;
     ra.chunks = chunks;
-    ra.is32 = is32;
+    ra.ptype = ptype;
+    ra.pdf = static_cast<const float4*>(b.partial);
     ra.c = b.bounded ? 1.0 : -1.0;
     ra.p64 = static_cast<const double2*>(b.partial);
     ra.p32 = static_cast<const float2*>(b.partial);
@@ -429,7 +645,7 @@ cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int
     const cudaError_t e = cudaGetLastError();
     // bytes: the partials read plus about four N-vectors of operands and output
     prof_end(tok, PK_REDUCE,
-             (double)chunks * job.R * b.N * (is32 ? 8.0 : 16.0) + 4.0 * 8.0 * b.N, st);
+             (double)chunks * job.R * b.N * (ptype == 1 ? 8.0 : 16.0) + 4.0 * 8.0 * b.N, st);
     return e;
 }
 
@@ -465,7 +681,8 @@ PairPlan make_plan(int N, int sms, int blocks_per_sm, int targets_per_block, int
 int pair_workspace_bytes(const Boundary& b, size_t* bytes) {
     const size_t b64 = (size_t)b.plan64.chunks * kMaxRHS * b.N * sizeof(double2);
     const size_t b32 = (size_t)b.plan32.chunks * kMaxRHS * b.N * sizeof(float2);
-    *bytes = std::max(b64, b32);
+    const size_t bdf = (size_t)b.plandf.chunks * kMaxRHS * b.N * sizeof(float4);
+    *bytes = std::max(std::max(b64, b32), bdf);
     return GNK_OK;
 }
 
@@ -537,11 +754,46 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     return GNK_OK;
 }
 
+int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
+    const PairPlan& p = b.plandf;
+    PairDFArgs a;
+    a.et = b.et;
+    a.ref64 = b.ref64;
+    a.offdf = b.offdf;
+    a.N = b.N;
+    a.w0 = job.w[0];
+    a.w1 = job.w[1];
+    a.x0 = job.x[0];
+    a.x1 = job.x[1];
+    a.s = job.s;
+    a.partial = static_cast<float4*>(b.partial);
+    a.tiles_src = p.tiles_src;
+    a.tiles_per_chunk = p.tiles_per_chunk;
+    a.done = job.done;
+    dim3 grid(p.tiles_tgt, p.chunks);
+    const ProfToken tok = prof_begin(st);
+    if (job.R == 1 && job.mode == W_SCALED)
+        pairsumdf_kernel<1, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+    else if (job.R == 1)
+        pairsumdf_kernel<1, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+    else if (job.mode == W_SCALED)
+        pairsumdf_kernel<2, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+    else
+        pairsumdf_kernel<2, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st);
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 2, st));
+    count_launches(2);
+    return GNK_OK;
+}
+
 int pair_blocks_per_sm(int precision) {
     int nb = 1;
     cudaError_t e;
     if (precision == GNK_PREC_FP32)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pairsum32_kernel<2, W_SCALED>, kThreads32, 0);
+    else if (precision == GNK_PREC_DF32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pairsumdf_kernel<2, W_SCALED>, kThreadsDF, 0);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pairsum64_kernel<2, W_SCALED>, kThreads64, 0);
     if (e != cudaSuccess) {
@@ -553,6 +805,7 @@ int pair_blocks_per_sm(int precision) {
 
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st) {
     if (precision == GNK_PREC_FP32) return run_pairsum32(b, job, st);
+    if (precision == GNK_PREC_DF32) return run_pairsumdf(b, job, st);
     return run_pairsum64(b, job, st);
 }
 

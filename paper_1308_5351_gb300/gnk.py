@@ -33,16 +33,18 @@ GNK_ENOMEM = -5
 GNK_PREC_FP64 = 0
 GNK_PREC_MIXED = 1
 GNK_PREC_FP32 = 2
+GNK_PREC_DF32 = 3
+GNK_PREC_MIXED_DF = 4
 
 EXPORTED = (
     "gnk_default_options", "gnk_last_error", "gnk_version", "gnk_build_boundary",
     "gnk_free_boundary", "gnk_boundary_size", "gnk_cauchy_sum", "gnk_apply_IminusN",
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
-    "gnk_profile_query", "gnk_cauchy_sum_noalloc",
+    "gnk_profile_query", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
 )
 
-PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV = range(5)
+PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
 
 
 class gnk_options(ctypes.Structure):
@@ -87,6 +89,8 @@ def load(path: str = LIB_PATH):
     lib.gnk_version.argtypes = []
     lib.gnk_version.restype = ctypes.c_char_p
     lib.gnk_build_boundary.argtypes = [ctypes.POINTER(P), I, I, P, P, P, P, P, I, P]
+    lib.gnk_build_boundary_ex.argtypes = [ctypes.POINTER(P), I, I, P, P, P, P, P, I, I, P]
+    lib.gnk_fbie.argtypes = [P, P, P, P, P, ctypes.POINTER(gnk_options), ctypes.POINTER(gnk_result), P]
     lib.gnk_free_boundary.argtypes = [P]
     lib.gnk_boundary_size.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gnk_cauchy_sum.argtypes = [P, P, P, I, P]
@@ -196,6 +200,25 @@ def gnk_build_boundary(m1, n, et, etp, A, etpp=None, Ap=None, bounded=True, stre
     return h
 
 
+def gnk_build_boundary_ex(m1, n, et, etp, A, etpp=None, Ap=None, bounded=True,
+                          precision=GNK_PREC_FP64, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().gnk_build_boundary_ex(ctypes.byref(h), int(m1), int(n), _ptr(et, True),
+                                        _ptr(etp, True), _ptr(etpp, True), _ptr(A, True),
+                                        _ptr(Ap, True), 1 if bounded else 0, int(precision),
+                                        _stream(stream)))
+    return h
+
+
+def gnk_fbie(h, gam, mu, hv, hk=None, options: Optional[gnk_options] = None, stream=None):
+    res = gnk_result()
+    code = load().gnk_fbie(h, _ptr(gam), _ptr(mu), _ptr(hv), _ptr(hk),
+                           ctypes.byref(options) if options is not None else None,
+                           ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
 def gnk_free_boundary(h):
     return _check(load().gnk_free_boundary(h))
 
@@ -270,17 +293,20 @@ class Boundary:
     """Owns one gnk_boundary handle built from a domain's arrays (numpy complex
     arrays on the host, or complex128 CUDA tensors)."""
 
-    def __init__(self, m1, n, et, etp, A, etpp=None, Ap=None, bounded=True, stream=None):
+    def __init__(self, m1, n, et, etp, A, etpp=None, Ap=None, bounded=True, stream=None,
+                 precision=GNK_PREC_FP64):
         self.m1, self.n, self.N = int(m1), int(n), int(m1) * int(n)
-        self.handle = gnk_build_boundary(m1, n, et, etp, A, etpp, Ap, bounded, stream)
+        self.handle = None
+        self.handle = gnk_build_boundary_ex(m1, n, et, etp, A, etpp, Ap, bounded, precision, stream)
 
     @classmethod
-    def from_domain(cls, dom, adjoint=True, device=None, stream=None):
+    def from_domain(cls, dom, adjoint=True, device=None, stream=None, precision=GNK_PREC_FP64):
         arrs = [dom.et, dom.etp, dom.A, dom.etpp if adjoint else None, dom.Ap if adjoint else None]
         if device is not None:
             arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a), device=device)
                     for a in arrs]
-        return cls(dom.m1, dom.n, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], dom.bounded, stream)
+        return cls(dom.m1, dom.n, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], dom.bounded, stream,
+                   precision)
 
     def close(self):
         if self.handle is not None:
@@ -334,6 +360,14 @@ class Boundary:
         mu = out if out is not None else _real_like(gam, self.N)
         res = gnk_solve_adjoint_ie(self.handle, gam, mu, options(**opts), stream)
         return mu, res
+
+    def fbie(self, gam, stream=None, **opts):
+        """(mu, h, h_k, result) of the FBIE computation in one call."""
+        mu = _real_like(gam, self.N)
+        h = _real_like(gam, self.N)
+        hk = _real_like(gam, self.m1)
+        res = gnk_fbie(self.handle, gam, mu, h, hk, options(**opts), stream)
+        return mu, h, hk, res
 
     def compute_h(self, mu, gam, out=None, hk=None, stream=None):
         h = out if out is not None else _real_like(mu, self.N)

@@ -8,6 +8,11 @@ Tolerances (derived from the arithmetic, u = 2^-53, u32 = 2^-24):
     covered by a factor 8.
   * Operators y = A x: the same bound on |A| |x| with a factor 4 for the
     epilogue (diagonal and circulant terms are FP64).
+  * Double-float (df32) Cauchy sums: each term carries ~2^-46 relative error
+    from the error-free transformations plus the rounding of the tile-relative
+    positions, at most 2^-47 (|o_i| + |delta_j|) / |d_ij| with |o_i| <= |d_ij| +
+    |delta_j| and |delta_j| <= D (the largest node-to-reference distance of a
+    source tile); hence |dz_i| <= (64 + N) 2^-45 S_i + 2^-45 D sum_j |w_j|/|d_ij|^2.
   * Solves: mu within 1e-10 relative (max norm) of the oracle's LU solution,
     h within 1e-10 per component relative to max(1, |h|_inf); GMRES runs to
     the paper's gmrestol 1e-12 and the test geometries have condition
@@ -70,8 +75,21 @@ def _bnd(G, d):
 
 
 # ------------------------------------------------------------------ Cauchy sums
+PREC = {"fp64": 0, "fp32": 2, "df32": 3}
+UDF = 2.0 ** -45
+
+
+def _tile_span(et, S=256):
+    """Largest distance from a node to its source tile's reference node."""
+    D = 0.0
+    for j0 in range(0, len(et), S):
+        blk = et[j0:j0 + S]
+        D = max(D, float(np.abs(blk - blk[len(blk) // 2]).max()))
+    return D
+
+
 @pytest.mark.parametrize("name", list(DOMS))
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df32"])
 def test_cauchy_sum(G, name, prec):
     d = DOMS[name]
     rng = np.random.default_rng(3)
@@ -80,11 +98,14 @@ def test_cauchy_sum(G, name, prec):
     ref = E @ w
     S = np.abs(E) @ np.abs(w)
     with _bnd(G, d) as b:
-        p = G.GNK_PREC_FP64 if prec == "fp64" else G.GNK_PREC_FP32
-        z = _host(b.cauchy_sum(_dev(w), precision=p))
-    u = U64 if prec == "fp64" else 8 * U32
+        z = _host(b.cauchy_sum(_dev(w), precision=PREC[prec]))
     err = np.abs(z - ref)
-    assert np.all(err <= (64 + d.N) * u * S), (name, prec, float((err / S).max()))
+    if prec == "df32":
+        tol = (64 + d.N) * UDF * S + UDF * _tile_span(d.et) * (np.abs(E) ** 2 @ np.abs(w))
+    else:
+        u = U64 if prec == "fp64" else 8 * U32
+        tol = (64 + d.N) * u * S
+    assert np.all(err <= tol), (name, prec, float((err / S).max()))
 
 
 # ------------------------------------------------------------------ operators
@@ -128,6 +149,31 @@ def test_operators_fp32(G, name):
         assert np.abs(y - A @ x).max() <= 4 * 8 * (64 + d.N) * U32 * scale
 
 
+@pytest.mark.parametrize("name", ["three_circles_n256", "ellipses5_n512", "graded_square_n128",
+                                  "ellipses7_n300"])
+def test_operators_df32(G, name):
+    d = DOMS[name]
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=d.N)
+    IN = O.matrix_IminusN(d.et, d.etp, d.A, d.n)
+    Mm = O.matrix_M(d.et, d.etp, d.A, d.n)
+    Ad = O.matrix_adjoint(d.et, d.etp, d.etpp, d.A, d.Ap, d.n, d.c)
+    E = O.cauchy_matrix(d.et)
+    xd = _dev(x)
+    with _bnd(G, d) as b:
+        got = [_host(b.apply_IminusN(xd, precision=G.GNK_PREC_DF32)),
+               _host(b.apply_M(xd, precision=G.GNK_PREC_DF32)),
+               _host(b.apply_adjoint(xd, precision=G.GNK_PREC_DF32))]
+    # the Cauchy-sum bound above, carried through |A| and the (2/n)|q| or |A| factors
+    span = _tile_span(d.et)
+    for A, y, sc in ((IN, got[0], d.etp / d.A), (Mm, got[1], d.etp / d.A), (Ad, got[2], d.A)):
+        w = np.abs(sc * x)
+        zb = (64 + d.N) * UDF * (np.abs(E) @ w) + UDF * span * (np.abs(E) ** 2 @ w)
+        fac = np.abs(d.A) if A is not Ad else np.abs(d.etp / d.A)
+        tol = 4 * ((2.0 / d.n) * fac * zb + (64 + d.N) * U64 * (np.abs(A) @ np.abs(x)))
+        assert np.all(np.abs(y - A @ x) <= tol), name
+
+
 # ------------------------------------------------------------------ solves
 def _solve_cases():
     rng = np.random.default_rng(21)
@@ -148,12 +194,15 @@ def _solve_cases():
 SOLVE = _solve_cases()
 
 
+SOLVE_PREC = {"fp64": 0, "mixed": 1, "df32": 3, "mixed_df": 4}
+
+
 @pytest.mark.parametrize("case", list(SOLVE))
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", list(SOLVE_PREC))
 def test_solve_ie_and_h(G, case, prec):
     d, gam = SOLVE[case]
     mu_ref, h_ref, hk_ref = O.fbie(d.et, d.etp, d.A, d.n, gam)
-    p = G.GNK_PREC_FP64 if prec == "fp64" else G.GNK_PREC_MIXED
+    p = SOLVE_PREC[prec]
     with _bnd(G, d) as b:
         gd = _dev(gam)
         mu, res = b.solve_ie(gd, tol=1e-12, restart=20, maxit=50, precision=p)
@@ -164,16 +213,35 @@ def test_solve_ie_and_h(G, case, prec):
     hs = max(1.0, np.abs(h_ref).max())
     assert np.abs(h - h_ref).max() <= 1e-10 * hs
     assert np.abs(hk - hk_ref).max() <= 1e-10 * hs
-    if prec == "mixed":
+    if prec.startswith("mixed"):
         assert res.matvecs_fp32 > 0 and res.refinements >= 1
 
 
+@pytest.mark.parametrize("case", list(SOLVE))
+@pytest.mark.parametrize("prec", list(SOLVE_PREC))
+def test_fbie_fused(G, case, prec):
+    """gnk_fbie: mu and h from the fewest Cauchy sums, handle built with the
+    matching precision of the precomputed sums."""
+    d, gam = SOLVE[case]
+    mu_ref, h_ref, hk_ref = O.fbie(d.et, d.etp, d.A, d.n, gam)
+    p = SOLVE_PREC[prec]
+    bp = G.GNK_PREC_DF32 if prec in ("df32", "mixed_df") else G.GNK_PREC_FP64
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda", precision=bp) as b:
+        mu, h, hk, res = b.fbie(_dev(gam), tol=1e-12, precision=p)
+        assert res.status == 0 and res.relres <= 1e-12
+        mu, h, hk = _host(mu), _host(h), _host(hk)
+    assert np.abs(mu - mu_ref).max() <= 1e-10 * np.abs(mu_ref).max()
+    hs = max(1.0, np.abs(h_ref).max())
+    assert np.abs(h - h_ref).max() <= 1e-10 * hs
+    assert np.abs(hk - hk_ref).max() <= 1e-10 * hs
+
+
 @pytest.mark.parametrize("case", ["config1_log", "ellipses_log", "graded_manufactured"])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", list(SOLVE_PREC))
 def test_solve_adjoint_ie(G, case, prec):
     d, gam = SOLVE[case]
     ref = O.solve_adjoint_ie(d.et, d.etp, d.etpp, d.A, d.Ap, d.n, d.c, gam)
-    p = G.GNK_PREC_FP64 if prec == "fp64" else G.GNK_PREC_MIXED
+    p = SOLVE_PREC[prec]
     with _bnd(G, d) as b:
         mu, res = b.solve_adjoint_ie(_dev(gam), tol=1e-12, precision=p)
         assert res.status == 0
