@@ -221,6 +221,36 @@ int gnk_solve_adjoint_ie(const gnk_boundary* b, const double* gam, double* mu,
                          void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Differentiation of the FBIE computation (no counterpart in the paper; it
+ * uses the transposed system of Eq. sys with the products of Eq. BTx).
+ * ------------------------------------------------------------------------- */
+
+/* Solve (2I + diag(B1) - B)^T x = rhs by GMRES, where
+ * (2I + diag(B1) - B)^T x = 2x + diag(B1) x - (2/n) Im(q E(A x)).  Arguments
+ * as gnk_solve_ie (rhs and x real, N doubles). */
+int gnk_solve_ie_transpose(const gnk_boundary* b, const double* rhs, double* x,
+                           const gnk_options* opt, gnk_result* info,
+                           void* stream);
+
+/* Gradient of a loss L(mu, h) of the FBIE outputs with respect to the inputs.
+ * Given mu (the solution for gam), gam, grad_mu = dL/dmu and grad_h = dL/dh
+ * (N doubles each), writes dL/d eta, dL/d eta', dL/dA (interleaved complex,
+ * 2N doubles each: real part = derivative with respect to the real part of
+ * the input, imaginary part = derivative with respect to its imaginary part)
+ * and dL/dgam (N doubles).  Method: one transposed solve
+ * lambda = K^-T (grad_mu + M^T grad_h / 2) with K = 2I + diag(B1) - B and
+ * M = D - diag(D1) + Lhat, then one FP64 pass of six Cauchy sums and six sums
+ * of the derivative kernel 1/(eta_i - eta_j)^2.  `opt` controls the
+ * transposed solve (its precision also sets the arithmetic of M^T).  Host
+ * arrays are staged through temporary device buffers.  Returns GNK_OK or
+ * GNK_ENOTCONV (gradient from the best iterate). */
+int gnk_fbie_backward(const gnk_boundary* b, const double* mu, const double* gam,
+                      const double* grad_mu, const double* grad_h,
+                      double* grad_et, double* grad_etp, double* grad_A,
+                      double* grad_gam, const gnk_options* opt,
+                      gnk_result* info, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Cauchy sum without any device allocation (no counterpart in the paper).
  *
  * z = E w exactly as gnk_cauchy_sum in FP64, for callers that cannot allocate

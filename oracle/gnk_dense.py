@@ -290,3 +290,50 @@ def rows_adjoint(et, etp, etpp, A, Ap, n, c, x, rows):
     comp = rows // n
     means = x.reshape(-1, n).mean(axis=1)
     return e * x[rows] + BT @ x + means[comp]
+
+
+# ---------------------------------------------------------------------------
+# Gradient of a loss L(mu, h) of the FBIE outputs (dense adjoint)
+# ---------------------------------------------------------------------------
+
+def fbie_gradient(et, etp, A, n, gam, g_mu, g_h):
+    """dL/d(eta, eta', A, gamma) for a loss with dL/dmu = g_mu and dL/dh = g_h,
+    where mu solves K mu = -M gamma and h = (M mu - K gamma)/2 with
+    K = 2I + diag(B1) - B, M = D - diag(D1) + L-hat (Eqs. sys, y, bh).
+
+    Dense adjoint: lambda = K^-T (g_mu + M^T g_h / 2) by LU; the geometry enters
+    through Z_ij = A_i eta'_j / (A_j (eta_j - eta_i)) (i != j), B = (2/n) Im Z,
+    D = (2/n) Re Z, and the loss varies with the geometry as
+      S = sum_{i != j} WB_ij B_ij + WD_ij D_ij,
+      WB_ij = -g_h,i (gam_i - gam_j)/2 - lambda_i (mu_i - mu_j),
+      WD_ij =  g_h,i (mu_j - mu_i)/2 - lambda_i (gam_j - gam_i),
+    differentiated entry by entry.  Complex gradients are packed as
+    dL/dRe + i dL/dIm.  Returns (g_et, g_etp, g_A, g_gam, mu, h)."""
+    et = np.asarray(et, dtype=np.complex128)
+    etp = np.asarray(etp, dtype=np.complex128)
+    A = np.asarray(A, dtype=np.complex128)
+    gam = np.asarray(gam, dtype=np.float64)
+    g_mu = np.asarray(g_mu, dtype=np.float64)
+    g_h = np.asarray(g_h, dtype=np.float64)
+    N, m1 = _sizes(et, n)
+    K = matrix_IminusN(et, etp, A, n)
+    M = matrix_M(et, etp, A, n)
+    mu = np.linalg.solve(K, -(M @ gam))
+    h = (M @ mu - K @ gam) / 2.0
+    lam = np.linalg.solve(K.T, g_mu + 0.5 * (M.T @ g_h))
+    # entries and their holomorphic derivatives
+    diff = et[None, :] - et[:, None]            # eta_j - eta_i
+    off = ~np.eye(N, dtype=bool)
+    dsafe = np.where(off, diff, 1.0)
+    Z = np.where(off, (A[:, None] / A[None, :]) * etp[None, :] / dsafe, 0.0)
+    Y = np.where(off, (A[:, None] / A[None, :]) / dsafe, 0.0)          # dZ_ij / d eta'_j
+    WB = -0.5 * g_h[:, None] * (gam[:, None] - gam[None, :]) - lam[:, None] * (mu[:, None] - mu[None, :])
+    WD = 0.5 * g_h[:, None] * (mu[None, :] - mu[:, None]) - lam[:, None] * (gam[None, :] - gam[:, None])
+    C = np.where(off, (2.0 / n) * (WD - 1j * WB), 0.0)                # S = Re sum C_ij Z_ij
+    R = C * Z / dsafe                                                # d/d eta_i of C_ij Z_ij
+    d_et = R.sum(axis=1) - R.sum(axis=0)
+    d_etp = (C * Y).sum(axis=0)
+    CZ = C * Z
+    d_A = (CZ.sum(axis=1) - CZ.sum(axis=0)) / A
+    g_gam = -0.5 * (K.T @ g_h) - M.T @ lam
+    return np.conj(d_et), np.conj(d_etp), np.conj(d_A), g_gam, mu, h

@@ -457,6 +457,97 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
     return s;
 }
 
+int gnk_solve_ie_transpose(const gnk_boundary* hd, const double* rhs, double* x, const gnk_options* opt,
+                           gnk_result* info, void* stream) {
+    GNK_TRY(check_handle(hd));
+    if (!rhs || !x) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    gnk_options o;
+    GNK_TRY(options_from(opt, &o));
+    const Boundary& b = hd->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* dr;
+    GNK_TRY(stage_in(b, rhs, b.N, 0, st, &dr));
+    Out ox = stage_out(b, x, b.N, 1);
+    const int s = solve(b, OP_KT, dr, ox.dev, o, info, st);
+    if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+    GNK_TRY(finish_out(ox, st));
+    if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles");
+    return s;
+}
+
+namespace {
+// A device view of a caller array for the backward pass: the array itself if
+// it is device memory, else a temporary device copy (inputs) or buffer
+// (outputs) that is released, after copying back, by the destructor's owner.
+struct DevArr {
+    void* user = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool tmp = false;
+};
+
+int dev_view(const void* p, size_t bytes, bool input, cudaStream_t st, DevArr* out) {
+    out->user = const_cast<void*>(p);
+    out->bytes = bytes;
+    if (is_device_ptr(p)) {
+        out->dev = const_cast<void*>(p);
+        return GNK_OK;
+    }
+    if (cudaMalloc(&out->dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("staging allocation failed");
+        return GNK_ENOMEM;
+    }
+    out->tmp = true;
+    if (input) GNK_TRY_CUDA(cudaMemcpyAsync(out->dev, p, bytes, cudaMemcpyHostToDevice, st));
+    return GNK_OK;
+}
+}  // namespace
+
+int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* gam, const double* grad_mu,
+                      const double* grad_h, double* grad_et, double* grad_etp, double* grad_A,
+                      double* grad_gam, const gnk_options* opt, gnk_result* info, void* stream) {
+    GNK_TRY(check_handle(hd));
+    if (!mu || !gam || !grad_mu || !grad_h || !grad_et || !grad_etp || !grad_A || !grad_gam) {
+        set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    gnk_options o;
+    GNK_TRY(options_from(opt, &o));
+    const Boundary& b = hd->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rN = (size_t)b.N * sizeof(double), cN = 2 * rN;
+    DevArr v[8];
+    const void* src[8] = {mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam};
+    const size_t sz[8] = {rN, rN, rN, rN, cN, cN, cN, rN};
+    int rc = GNK_OK;
+    for (int k = 0; k < 8 && rc == GNK_OK; ++k) rc = dev_view(src[k], sz[k], k < 4, st, &v[k]);
+    int s = rc;
+    if (rc == GNK_OK) {
+        s = fbie_backward(b, (const double*)v[0].dev, (const double*)v[1].dev, (const double*)v[2].dev,
+                          (const double*)v[3].dev, (double2*)v[4].dev, (double2*)v[5].dev,
+                          (double2*)v[6].dev, (double*)v[7].dev, o, info, st);
+        if (s == GNK_OK || s == GNK_ENOTCONV) {
+            for (int k = 4; k < 8; ++k)
+                if (v[k].tmp && cudaMemcpyAsync(v[k].user, v[k].dev, v[k].bytes, cudaMemcpyDeviceToHost,
+                                                st) != cudaSuccess) {
+                    cudaGetLastError();
+                    s = GNK_ECUDA;
+                }
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                cudaGetLastError();
+                s = GNK_ECUDA;
+            }
+        }
+    }
+    for (int k = 0; k < 8; ++k)
+        if (v[k].tmp) cudaFree(v[k].dev);
+    return s;
+}
+
 int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,
                   void* stream) {
     GNK_TRY(check_handle(h));

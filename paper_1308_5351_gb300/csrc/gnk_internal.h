@@ -88,6 +88,16 @@ enum Epilogue : int {
     EPI_EONE = 7,     // b1 = -(2/n) Im(A z), d1 = -(2/n) Re(A z); if R=2: e from z2
     EPI_RHS_FB = 8,   // out = -f_C(x) (the right-hand side -y), out2 = f_B(x)
     EPI_RESID_FC = 9, // out = rhs - f_B(x), out2 = f_C(x)
+    EPI_IMINUSN_T = 10,  // out = (2I + diag(B1) - B)^T x, z = E(A x)
+    EPI_RESID_T = 11,    // out = rhs - (2I + diag(B1) - B)^T x
+    EPI_MT = 12,         // out = (D - diag(D1) + Lhat)^T x, z = E(A x), Lx = Lhat x
+};
+
+// Operators a GMRES solve can use.
+enum OpId : int {
+    OP_K = 0,    // 2I + diag(B1) - B        (discrete I - N, Eq. sys)
+    OP_ADJ = 1,  // diag(e) + B^T + Phat     (discrete I + N* + J, Eq. sys*)
+    OP_KT = 2,   // (2I + diag(B1) - B)^T    (transposed system of the gradient)
 };
 
 struct PairPlan {
@@ -196,8 +206,11 @@ int op_IminusN(const Boundary& b, const double* x, double* y, int prec, cudaStre
 int op_M(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st);
 int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
                const int* done = nullptr);
-int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
+int op_resid(const Boundary& b, int op, const double* rhs, const double* x, double* r,
              int prec, cudaStream_t st, double* fc_out = nullptr);
+int op_IminusN_T(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+                 const int* done = nullptr);
+int op_MT(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st);
 int op_rhs_fb(const Boundary& b, const double* gam, double* rhs, double* fb, int prec,
               cudaStream_t st);
 int op_half_diff(const double* a, const double* b, double* out, int N, cudaStream_t st);
@@ -205,14 +218,19 @@ int op_h(const Boundary& b, const double* mu, const double* gam, double* h, cuda
 int op_negate(double* x, int N, cudaStream_t st);
 
 // ---------------------------------------------------------------- Krylov (krylov.cu)
-// Solves with the operator of the handle (adjoint = 0: f_B, 1: g_B).  When
+// Solves with operator `op` (OpId).  When
 // fc_out is given, the last true residual also writes f_C(x) of the returned
 // x there and *fc_valid is set (f_C(mu) is the first half of h, Eq. bh).
-int solve(const Boundary& b, int adjoint, const double* rhs, double* x,
+int solve(const Boundary& b, int op, const double* rhs, double* x,
           const gnk_options& opt, gnk_result* info, cudaStream_t st,
           double* fc_out = nullptr, int* fc_valid = nullptr);
 // Arithmetic of the outer (refinement) products for a solve precision.
 int outer_precision(int solve_precision);
+
+// ---------------------------------------------------------------- gradients (grad.cu)
+int fbie_backward(const Boundary& b, const double* mu, const double* gam, const double* gm,
+                  const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
+                  const gnk_options& opt, gnk_result* info, cudaStream_t st);
 
 }  // namespace gnk
 

@@ -309,9 +309,11 @@ int ensure_krylov(Boundary& b, int restart) {
     return GNK_OK;
 }
 
-int apply_op(const Boundary& b, int adjoint, const double* x, double* y, int prec, cudaStream_t st,
+int apply_op(const Boundary& b, int op, const double* x, double* y, int prec, cudaStream_t st,
              const int* done) {
-    return adjoint ? op_adjoint(b, x, y, prec, st, done) : op_IminusN(b, x, y, prec, st, done);
+    if (op == OP_ADJ) return op_adjoint(b, x, y, prec, st, done);
+    if (op == OP_KT) return op_IminusN_T(b, x, y, prec, st, done);
+    return op_IminusN(b, x, y, prec, st, done);
 }
 
 int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
@@ -332,7 +334,7 @@ int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
 // One restarted GMRES solve of A x = rhs with the operator in precision prec.
 // r is a work vector.  Counters are added to *res; *relres receives the final
 // true relative residual (in prec).
-int gmres(Boundary& b, int adjoint, int prec, const double* rhs, double* x, double* r,
+int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, double* x, double* r,
           int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st,
           double* fc_out, int* fc_valid) {
     if (fc_valid) *fc_valid = 0;
@@ -436,7 +438,7 @@ int outer_precision(int solve_precision) {
                                                                                      : GNK_PREC_FP64;
 }
 
-int solve(const Boundary& bc, int adjoint, const double* rhs, double* x, const gnk_options& opt,
+int solve(const Boundary& bc, int adjoint /* OpId */, const double* rhs, double* x, const gnk_options& opt,
           gnk_result* info, cudaStream_t st, double* fc_out, int* fc_valid) {
     Boundary& b = const_cast<Boundary&>(bc);  // workspace only
     gnk_result res;

@@ -52,11 +52,42 @@ int op_adjoint(const Boundary& b, const double* x, double* y, int prec, cudaStre
     return run_pairsum(b, j, prec, st);
 }
 
-// r = rhs - A x for A = f_B (adjoint = 0) or g_B (adjoint = 1); with fc_out
-// (adjoint = 0 only) also f_C(x) from the same Cauchy sum.
-int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x, double* r,
+// y = (2I + diag(B1) - B)^T x = 2x + diag(B1) x - (2/n) Im(q E(A x))
+int op_IminusN_T(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,
+                 const int* done) {
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.s = b.A;
+    j.epi = EPI_IMINUSN_T;
+    j.out = y;
+    j.ex = x;
+    j.done = done;
+    return run_pairsum(b, j, prec, st);
+}
+
+// y = (D - diag(D1) + Lhat)^T x = (2/n) Re(q E(A x)) - diag(D1) x - Lhat x
+int op_MT(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st) {
+    GNK_TRY(run_circulant(b, x, b.r3, st));
+    PairJob j;
+    j.R = 1;
+    j.mode = W_SCALED;
+    j.x[0] = x;
+    j.s = b.A;
+    j.epi = EPI_MT;
+    j.out = y;
+    j.ex = x;
+    j.Lx = b.r3;
+    return run_pairsum(b, j, prec, st);
+}
+
+// r = rhs - A x for the operator `op` (OpId); with fc_out (OP_K only) also
+// f_C(x) from the same Cauchy sum.
+int op_resid(const Boundary& b, int op, const double* rhs, const double* x, double* r,
              int prec, cudaStream_t st, double* fc_out) {
-    if (fc_out && !adjoint) GNK_TRY(run_circulant(b, x, b.r3, st));
+    if (op != OP_K) fc_out = nullptr;
+    if (fc_out) GNK_TRY(run_circulant(b, x, b.r3, st));
     PairJob j;
     j.R = 1;
     j.mode = W_SCALED;
@@ -64,7 +95,10 @@ int op_resid(const Boundary& b, int adjoint, const double* rhs, const double* x,
     j.ex = x;
     j.rhs = rhs;
     j.out = r;
-    if (adjoint) {
+    if (op == OP_KT) {
+        j.s = b.A;
+        j.epi = EPI_RESID_T;
+    } else if (op == OP_ADJ) {
         GNK_TRY(run_component_means(b, x, b.means, st));
         j.s = b.A;
         j.epi = EPI_RESID_ADJ;

@@ -586,6 +586,22 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
             j.out[i] = 0.5 * (fc - fb);
             break;
         }
+        case EPI_IMINUSN_T:
+        case EPI_RESID_T: {
+            // K^T x = 2x + diag(B1) x - B^T x, B^T x = (2/n) Im(q E(A x))  (Eq. BTx)
+            const double2 q = a.q[i];
+            const double x = j.ex[i];
+            const double kt = 2.0 * x + a.b1[i] * x - s2n * (q.x * zy[0] + q.y * zx[0]);
+            j.out[i] = (j.epi == EPI_RESID_T) ? j.rhs[i] - kt : kt;
+            break;
+        }
+        case EPI_MT: {
+            // M^T x = D^T x - diag(D1) x - Lhat x, D^T x = (2/n) Re(q E(A x)), L^T = -L
+            const double2 q = a.q[i];
+            const double x = j.ex[i];
+            j.out[i] = s2n * (q.x * zx[0] - q.y * zy[0]) - a.d1[i] * x - j.Lx[i];
+            break;
+        }
         case EPI_RHS_FB: {
             // z = E(q gamma): out = -f_C(gamma) = -y (Eq. y), out2 = f_B(gamma) (kept for h)
             const double2 A = a.A[i];

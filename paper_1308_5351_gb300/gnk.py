@@ -42,6 +42,7 @@ EXPORTED = (
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
     "gnk_profile_query", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
+    "gnk_solve_ie_transpose", "gnk_fbie_backward",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
@@ -105,6 +106,10 @@ def load(path: str = LIB_PATH):
     lib.gnk_profile_query.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_sum_noalloc.argtypes = [I, P, P, P, P]
+    lib.gnk_solve_ie_transpose.argtypes = [P, P, P, ctypes.POINTER(gnk_options),
+                                           ctypes.POINTER(gnk_result), P]
+    lib.gnk_fbie_backward.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(gnk_options),
+                                      ctypes.POINTER(gnk_result), P]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -270,6 +275,27 @@ def gnk_solve_adjoint_ie(h, gam, mu, options: Optional[gnk_options] = None, stre
     code = load().gnk_solve_adjoint_ie(h, _ptr(gam), _ptr(mu),
                                        ctypes.byref(options) if options is not None else None,
                                        ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
+def gnk_solve_ie_transpose(h, rhs, x, options: Optional[gnk_options] = None, stream=None):
+    res = gnk_result()
+    code = load().gnk_solve_ie_transpose(h, _ptr(rhs), _ptr(x),
+                                         ctypes.byref(options) if options is not None else None,
+                                         ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
+def gnk_fbie_backward(h, mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam,
+                      options: Optional[gnk_options] = None, stream=None):
+    res = gnk_result()
+    code = load().gnk_fbie_backward(h, _ptr(mu), _ptr(gam), _ptr(grad_mu), _ptr(grad_h),
+                                    _ptr(grad_et, True), _ptr(grad_etp, True), _ptr(grad_A, True),
+                                    _ptr(grad_gam),
+                                    ctypes.byref(options) if options is not None else None,
+                                    ctypes.byref(res), _stream(stream))
     _check(code, (GNK_OK, GNK_ENOTCONV))
     return res
 
