@@ -251,6 +251,52 @@ int gnk_fbie_backward(const gnk_boundary* b, const double* mu, const double* gam
                       gnk_result* info, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched FBIE over many independent domains and right-hand sides (no
+ * counterpart in the paper: many instances of Sec. 3 solved together).
+ *
+ * Domain d has m1[d] components of n[d] nodes (N_d = m1[d] n[d]), nrhs[d]
+ * right-hand sides and boundedness bounded[d]; et, etp, A hold the domains'
+ * nodes one after the other (interleaved complex, 2 sum_d N_d doubles).
+ * System s = (d, r) is the r-th right-hand side of domain d; batch vectors
+ * (gamma, mu, h) store the systems one after the other, domain by domain and
+ * right-hand side by right-hand side (length L = sum_d nrhs[d] N_d), and hk
+ * stores the m1[d] component means of each system in the same order.
+ * Each operator product is one persistent kernel launch over a work list of
+ * (domain, target tile, right-hand-side group) items; the Arnoldi steps of a
+ * restart cycle are captured in a CUDA graph.  With autotune != 0 the tile
+ * shapes (targets per thread, right-hand sides per group) of the FP32 and
+ * double-float kernels are chosen by timing each variant on a sample of the
+ * batch; otherwise fixed defaults are used.  Arrays may be host or device
+ * memory.
+ * ------------------------------------------------------------------------- */
+typedef struct gnk_batch gnk_batch;
+
+int gnk_build_batch(gnk_batch** out, int ndomains, const int* m1, const int* n,
+                    const int* nrhs, const int* bounded, const double* et,
+                    const double* etp, const double* A, int autotune,
+                    void* stream);
+int gnk_free_batch(gnk_batch* b);
+
+/* Vector length L, number of systems, and length of the hk array. */
+int gnk_batch_sizes(const gnk_batch* b, long long* vec_len, int* systems,
+                    int* hk_len);
+
+/* Chosen tile shapes and the tuning times (ms) of the seven variants:
+ * FP32 (T, RG) = (1,8), (2,4), (2,8), (4,4), double-float (1,2), (1,4), (2,2). */
+int gnk_batch_tuning(const gnk_batch* b, int* fp32_targets, int* fp32_group,
+                     int* df_targets, int* df_group, float* variant_ms);
+
+/* mu and h of every system (FBIE: Eqs. sys, y, bh) with FP32 pair sums inside
+ * GMRES and double-float refinement (opt->precision must be
+ * GNK_PREC_MIXED_DF; NULL opt means the defaults with that precision).  Each
+ * system stops when its own ||b - A mu|| <= tol ||b||.  info->relres is the
+ * largest final relative residual; relres_per_system (nullable, one double
+ * per system) receives each.  hk is nullable. */
+int gnk_batch_fbie(const gnk_batch* b, const double* gam, double* mu,
+                   double* h, double* hk, const gnk_options* opt,
+                   gnk_result* info, double* relres_per_system, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Cauchy sum without any device allocation (no counterpart in the paper).
  *
  * z = E w exactly as gnk_cauchy_sum in FP64, for callers that cannot allocate

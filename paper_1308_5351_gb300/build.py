@@ -28,7 +28,8 @@ def sources():
 
 
 def _newest_input_mtime():
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                         if f.endswith(".h") or f.endswith(".cuh")]
     files.append(os.path.join(ROOT, "include", "gnk.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

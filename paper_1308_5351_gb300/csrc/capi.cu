@@ -16,7 +16,13 @@ namespace gnk {
 static thread_local char g_err[1024] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
-void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local bool g_count_off = false;
+
+void count_launches(unsigned long long n) {
+    if (!g_count_off) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void count_suppress(bool on) { g_count_off = on; }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -286,6 +292,7 @@ int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, c
         set_error("gnk_build_boundary: (m+1) n = %lld exceeds 2^28 nodes", (long long)m1 * n);
         return GNK_EINVAL;
     }
+    cudaGetLastError();  // a stale, non-sticky error of earlier calls is not ours
     gnk_boundary* h = new (std::nothrow) gnk_boundary();
     if (!h) {
         set_error("host allocation failed");
@@ -382,6 +389,7 @@ int gnk_apply_circulant(const gnk_boundary* h, const double* x, double* y, void*
 static int solve_common(const gnk_boundary* h, const double* gam, double* mu, const gnk_options* opt,
                         gnk_result* info, void* stream, int adjoint) {
     GNK_TRY(check_handle(h));
+    cudaGetLastError();
     if (!gam || !mu) {
         set_error("NULL array");
         return GNK_EINVAL;
@@ -429,6 +437,7 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
         set_error("NULL array");
         return GNK_EINVAL;
     }
+    cudaGetLastError();
     gnk_options o;
     GNK_TRY(options_from(opt, &o));
     const Boundary& b = hd->b;

@@ -206,8 +206,7 @@ int run_component_means(const Boundary& b, const double* x, double* means, cudaS
     return GNK_OK;
 }
 
-int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int* d_flag,
-                         cudaStream_t st) {
+int run_prepare_nodes(Boundary& b, const double* etpp, const double* Ap, int* d_flag, cudaStream_t st) {
     PrepArgs a;
     a.N = b.N;
     a.n = b.n;
@@ -231,6 +230,98 @@ int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int*
     prepare_geometry_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
     count_launches(1);
+    return GNK_OK;
+}
+
+// Circulant multipliers of one n: twiddles exp(-2 pi i k/n) (k < n/2) when n is
+// a power of two up to 4096, else the first column b of L.
+void circulant_tables(int n, std::vector<double2>* tw, std::vector<double>* col) {
+    if (((n & (n - 1)) == 0) && n <= 4096) {
+        tw->resize(n / 2);
+        for (int k = 0; k < n / 2; ++k) {
+            const double ang = -2.0 * M_PI * (double)k / (double)n;
+            (*tw)[k] = make_double2(std::cos(ang), std::sin(ang));
+        }
+    } else {
+        col->resize(n);
+        (*col)[0] = 0.0;
+        for (int i = 1; i < n; ++i) (*col)[i] = ((i % 2) ? -1.0 : 1.0) / n / std::tan(M_PI * i / n);
+    }
+}
+
+namespace {
+// Batched circulant: one block per (system, component pair); descriptor
+// (vector offset of the system, n, m1, table offset | pow2 << 30).
+__global__ void batch_circulant_kernel(const int4* __restrict__ desc, const long long* __restrict__ base,
+                                       const double* __restrict__ x, double* __restrict__ y,
+                                       const double2* __restrict__ tw, const double* __restrict__ col) {
+    extern __shared__ double2 sm[];
+    const int4 dd = desc[blockIdx.x];
+    const int n = dd.x, m1 = dd.y, pair = dd.z;
+    const bool pow2 = (dd.w >> 30) & 1;
+    const int toff = dd.w & ((1 << 30) - 1);
+    const long long b0 = base[blockIdx.x];
+    const int ca = 2 * pair, cb = ca + 1;
+    const bool has_b = cb < m1;
+    double2* X = sm;
+    double2* Y = sm + n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x)
+        X[p] = make_double2(x[b0 + (long long)ca * n + p], has_b ? x[b0 + (long long)cb * n + p] : 0.0);
+    __syncthreads();
+    if (pow2) {
+        double2* F = stockham(X, Y, n, tw + toff, false);
+        double2* G = (F == X) ? Y : X;
+        const int half = n >> 1;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const double s = (k < half) ? (2.0 * k) / n : (k == half ? 0.0 : (2.0 * (k - n)) / n);
+            const double2 v = F[k];
+            F[k] = make_double2(-s * v.y, s * v.x);
+        }
+        __syncthreads();
+        double2* Z = stockham(F, G, n, tw + toff, true);
+        const double inv_n = 1.0 / n;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            y[b0 + (long long)ca * n + p] = Z[p].x * inv_n;
+            if (has_b) y[b0 + (long long)cb * n + p] = Z[p].y * inv_n;
+        }
+    } else {
+        const double* bc = col + toff;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            double ra = 0.0, rb = 0.0;
+            for (int q = 0; q < n; ++q) {
+                int d = p - q;
+                d += (d < 0) ? n : 0;
+                ra = fma(bc[d], X[q].x, ra);
+                rb = fma(bc[d], X[q].y, rb);
+            }
+            y[b0 + (long long)ca * n + p] = ra;
+            if (has_b) y[b0 + (long long)cb * n + p] = rb;
+        }
+    }
+}
+}  // namespace
+
+int run_batch_circulant(const int4* desc, const long long* base, int nblocks, int nmax,
+                        const double* x, double* y, const double2* tw, const double* col, cudaStream_t st) {
+    if (nblocks == 0) return GNK_OK;
+    const size_t smem = 2 * (size_t)nmax * sizeof(double2);
+    static bool attr_set = false;
+    if (smem > 48 * 1024 && !attr_set) {
+        GNK_TRY_CUDA(cudaFuncSetAttribute(batch_circulant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          2 * 4096 * (int)sizeof(double2)));
+        attr_set = true;
+    }
+    const ProfToken tok = prof_begin(st);
+    batch_circulant_kernel<<<nblocks, 256, smem, st>>>(desc, base, x, y, tw, col);
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_CIRC, 0.0, st);
+    count_launches(1);
+    return GNK_OK;
+}
+
+int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int* d_flag,
+                         cudaStream_t st) {
+    GNK_TRY(run_prepare_nodes(b, etpp, Ap, d_flag, st));
 
     // circulant tables (host, FP64 libm)
     const int n = b.n;

@@ -33,6 +33,9 @@ void set_error(const char* fmt, ...);
 // ---------------------------------------------------------------- launch counter
 // Host-side count of kernel launches made by the library (all devices).
 void count_launches(unsigned long long n);
+// While on (calling thread), launches are not counted: used while a stream is
+// captured into a graph, whose replays are counted instead.
+void count_suppress(bool on);
 
 // ---------------------------------------------------------------- profiling
 // Kinds of instrumented launches (gnk_profile_query's `kind`).
@@ -199,6 +202,10 @@ int run_circulant(const Boundary& b, const double* x, double* y, cudaStream_t st
 int run_component_means(const Boundary& b, const double* x, double* means, cudaStream_t st);
 int run_prepare_geometry(Boundary& b, const double* etpp, const double* Ap, int* d_flag,
                          cudaStream_t st);
+int run_prepare_nodes(Boundary& b, const double* etpp, const double* Ap, int* d_flag, cudaStream_t st);
+void circulant_tables(int n, std::vector<double2>* tw, std::vector<double>* col);
+int run_batch_circulant(const int4* desc, const long long* base, int nblocks, int nmax,
+                        const double* x, double* y, const double2* tw, const double* col, cudaStream_t st);
 
 // ---------------------------------------------------------------- operators (ops.cu)
 int op_IminusN(const Boundary& b, const double* x, double* y, int prec, cudaStream_t st,

@@ -1,0 +1,95 @@
+// Per-pair arithmetic shared by the pair-sum kernels (device code only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gnk {
+
+// ------------------------------------------------------------------ reciprocal
+static __device__ __forceinline__ double rcp_seed_f64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+// 1/x in full FP64 from the hardware seed y0 (relative error below 2^-19):
+// with e = 1 - x y0 we have 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...), so
+// y0 (1 + e + e^2) leaves the relative error e^3 < 2^-57, below half an ulp
+// after rounding for all but a vanishing set of inputs.
+static __device__ __forceinline__ double recip_f64(double x) {
+    const double y0 = rcp_seed_f64(x);
+    const double e = fma(-x, y0, 1.0);
+    const double t = fma(e, e, e);
+    return fma(y0, t, y0);
+}
+
+static __device__ __forceinline__ float recip_f32(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ double-float (df32)
+// FP64-class Cauchy sums on the FP32 pipe.  A df32 number is an unevaluated
+// sum hi + lo of two floats (about 48 significant bits).  Error-free
+// transformations (Knuth's TwoSum, Dekker's product via FMA) carry the
+// rounding errors of every step; positions are taken relative to the source
+// tile's FP64 reference node (each target forms its offset in FP64 once per
+// tile), so the difference of two nearby nodes keeps its leading bits.  Per
+// pair: ~22 flops for d, 16 for |d|^2, 3 for the reciprocal (one Newton step
+// from rcp.approx), 8 for 1/d, 16 for the four weight products and 32 for
+// the two compensated accumulations, all on the FP32 pipe.
+struct df {
+    float h, l;
+};
+
+// The _rn intrinsics are never contracted into FMAs by the compiler, which
+// the error-free transformations below rely on.
+static __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+static __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// a - b for df32 operands (Bailey's add with a final renormalisation)
+static __device__ __forceinline__ df df_sub(float ah, float al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e = __fadd_rn(e, __fsub_rn(al, bl));
+    df r;
+    fast_two_sum(s, e, r.h, r.l);
+    return r;
+}
+
+// product of two df32 values, unnormalised (hi = fl(a.h b.h), lo = error + cross terms)
+static __device__ __forceinline__ df df_mul(df a, df b) {
+    df r;
+    r.h = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -r.h);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    r.l = e;
+    return r;
+}
+
+// acc += p (compensated: the hi sum's rounding error goes to acc.l)
+static __device__ __forceinline__ void df_acc(df& acc, df p) {
+    float s, e;
+    two_sum(acc.h, p.h, s, e);
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(e, p.l));
+}
+
+static __device__ __forceinline__ df df_split(double v) {
+    df r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+}
+
+}  // namespace gnk

@@ -52,6 +52,12 @@ ProfToken prof_begin(cudaStream_t st) {
     ProfToken t;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return t;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return t;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return t;  // no event timing inside captured graphs
     t.ev = take_event();
     if (t.ev) cudaEventRecord(static_cast<cudaEvent_t>(t.ev), st);
     return t;

@@ -42,7 +42,8 @@ EXPORTED = (
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
     "gnk_profile_query", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
-    "gnk_solve_ie_transpose", "gnk_fbie_backward",
+    "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
+    "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
@@ -106,6 +107,13 @@ def load(path: str = LIB_PATH):
     lib.gnk_profile_query.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_sum_noalloc.argtypes = [I, P, P, P, P]
+    IP = ctypes.POINTER(I)
+    lib.gnk_build_batch.argtypes = [ctypes.POINTER(P), I, IP, IP, IP, IP, P, P, P, I, P]
+    lib.gnk_free_batch.argtypes = [P]
+    lib.gnk_batch_sizes.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), IP, IP]
+    lib.gnk_batch_tuning.argtypes = [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_float)]
+    lib.gnk_batch_fbie.argtypes = [P, P, P, P, P, ctypes.POINTER(gnk_options),
+                                   ctypes.POINTER(gnk_result), P, P]
     lib.gnk_solve_ie_transpose.argtypes = [P, P, P, ctypes.POINTER(gnk_options),
                                            ctypes.POINTER(gnk_result), P]
     lib.gnk_fbie_backward.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(gnk_options),
@@ -400,3 +408,73 @@ class Boundary:
         hk = hk if hk is not None else _real_like(mu, self.m1)
         gnk_compute_h(self.handle, mu, gam, h, hk, stream)
         return h, hk
+
+
+# --------------------------------------------------------------- batches
+def _ints(v):
+    arr = (ctypes.c_int * len(v))(*[int(x) for x in v])
+    return arr
+
+
+class Batch:
+    """Owns one gnk_batch: domains given as lists of Domain-like objects
+    (numpy complex arrays et, etp, A) with a right-hand-side count each."""
+
+    def __init__(self, domains, nrhs, autotune=True, device=None, stream=None):
+        self.m1 = [d.m1 for d in domains]
+        self.n = [d.n for d in domains]
+        self.nrhs = [int(r) for r in nrhs]
+        bounded = [1 if d.bounded else 0 for d in domains]
+        arrs = [np.ascontiguousarray(np.concatenate([getattr(d, k) for d in domains]))
+                for k in ("et", "etp", "A")]
+        if device is not None:
+            arrs = [torch.as_tensor(a, device=device) for a in arrs]
+        h = ctypes.c_void_p()
+        self.handle = None
+        _check(load().gnk_build_batch(ctypes.byref(h), len(domains), _ints(self.m1), _ints(self.n),
+                                      _ints(self.nrhs), _ints(bounded), _ptr(arrs[0], True),
+                                      _ptr(arrs[1], True), _ptr(arrs[2], True), 1 if autotune else 0,
+                                      _stream(stream)))
+        self.handle = h
+        L, ns, nhk = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        _check(load().gnk_batch_sizes(h, ctypes.byref(L), ctypes.byref(ns), ctypes.byref(nhk)))
+        self.L, self.nsys, self.nhk = L.value, ns.value, nhk.value
+
+    def tuning(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        ms = (ctypes.c_float * 7)()
+        _check(load().gnk_batch_tuning(self.handle, *[ctypes.byref(x) for x in v], ms))
+        return {"fp32_targets": v[0].value, "fp32_group": v[1].value, "df_targets": v[2].value,
+                "df_group": v[3].value, "variant_ms": list(ms)}
+
+    def fbie(self, gam, stream=None, **opts):
+        o = options(precision=GNK_PREC_MIXED_DF)
+        for k, v in opts.items():
+            setattr(o, k, v)
+        mu = _real_like(gam, self.L)
+        h = _real_like(gam, self.L)
+        hk = _real_like(gam, self.nhk)
+        rel = np.zeros(self.nsys)
+        res = gnk_result()
+        code = load().gnk_batch_fbie(self.handle, _ptr(gam), _ptr(mu), _ptr(h), _ptr(hk),
+                                     ctypes.byref(o), ctypes.byref(res),
+                                     ctypes.c_void_p(rel.ctypes.data), _stream(stream))
+        _check(code, (GNK_OK, GNK_ENOTCONV))
+        return mu, h, hk, res, rel
+
+    def close(self):
+        if self.handle is not None:
+            load().gnk_free_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
