@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves")
     ap.add_argument("--precision", choices=list(MODES), default="mixed_df")
+    ap.add_argument("--workload", choices=["ellipses64", "close1024", "batched256", "stars20"],
+                    default="ellipses64", help="ellipses64 is the headline; the others are extra lines")
+    ap.add_argument("--with-fp64", action="store_true",
+                    help="close1024: also time the plain FP64 solve (minutes)")
     return ap.parse_args()
 
 
@@ -191,6 +195,8 @@ def main():
     dist, rank, ws, local = dist_init(args.gpus)
     if args.impl == "reference":
         return run_reference(args, dist, rank, ws)
+    if args.workload != "ellipses64":
+        return run_extra(args, dist, rank, ws, local)
 
     import numpy as np
     import torch
@@ -393,6 +399,225 @@ def main():
         "clocks": clk,
     }
     print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ extra workloads
+def _timed(fn, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def run_extra(args, dist, rank, ws, local):
+    """Extra measurement lines (same JSON contract) for the other workloads:
+    close1024  - 1024 close curves, n = 512 (524,288 unknowns), FBIE solve + h;
+    batched256 - 256 domains, m+1 in 2..64, n in 128..1024, m+1 right-hand sides each;
+    stars20    - gradient of h_1 - h_0 w.r.t. the Fourier coefficients of 16 star curves
+                 (plus 4 graded polygons, n = 2048, N = 40,960) by one adjoint solve."""
+    import numpy as np
+    import torch
+    from paper_1308_5351_gb300 import build as B
+    from paper_1308_5351_gb300 import domains as Dm
+    from paper_1308_5351_gb300 import gnk as G
+    from oracle import gnk_dense as O
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        B.build()
+    barrier(dist)
+    G.load()
+    stream = torch.cuda.current_stream(dev)
+    line = {"metric": METRIC, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    launches0 = G.gnk_kernel_launches()
+    if args.workload == "close1024":
+        dom = Dm.close_curves(seed=3 + 1000 * rank, n=512)
+        gam_np = Dm.gamma_log(dom, dom.holes[0])
+        et, etp, A = (torch.as_tensor(a, device=dev) for a in (dom.et, dom.etp, dom.A))
+        gam = torch.as_tensor(gam_np, device=dev)
+        mu, h = torch.empty_like(gam), torch.empty_like(gam)
+        hk = torch.empty(dom.m1, dtype=torch.float64, device=dev)
+
+        def step(prec):
+            o = G.options(tol=TOL, restart=30, maxit=60, precision=MODES[prec], inner_tol=1e-5)
+            bp = G.GNK_PREC_DF32 if prec in ("mixed_df", "df32") else G.GNK_PREC_FP64
+            hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, None, None, False, bp, stream)
+            r = G.gnk_fbie(hnd, gam, mu, h, hk, o, stream)
+            G.gnk_free_boundary(hnd)
+            return r
+        for _ in range(args.warmup):
+            step("mixed_df")
+        times, res = [], None
+        for _ in range(args.steps):
+            res, t = _timed(lambda: step("mixed_df"), stream)
+            times.append(t)
+        mu_np, h_np = mu.cpu().numpy(), h.cpu().numpy()
+        # rows of the discrete equation (2I + diag(B1) - B) mu = -(D - diag(D1) + Lhat) gamma
+        rows = np.random.default_rng(0).choice(dom.N, size=24, replace=False)
+        lhs = O.rows_IminusN(dom.et, dom.etp, dom.A, dom.n, mu_np, rows)
+        rhs = -O.rows_M(dom.et, dom.etp, dom.A, dom.n, gam_np, rows)
+        compare = {}
+        _, t_mixed = _timed(lambda: step("mixed"), stream)
+        compare["mixed"] = {"time_to_solution_s": t_mixed,
+                            "max_rel_diff_mu_vs_headline": float(np.abs(mu.cpu().numpy() - mu_np).max()
+                                                                 / np.abs(mu_np).max())}
+        if args.with_fp64:
+            _, t64 = _timed(lambda: step("fp64"), stream)
+            compare["fp64"] = {"time_to_solution_s": t64,
+                               "max_rel_diff_mu_vs_headline": float(np.abs(mu.cpu().numpy() - mu_np).max()
+                                                                    / np.abs(mu_np).max())}
+        # error against the dense oracle on the first 64 boundaries at n = 128
+        sub = Dm.build_domain(dom.curves[:64], 128, bounded=False)
+        gs = Dm.gamma_log(sub, dom.holes[0])
+        with G.Boundary.from_domain(sub, adjoint=False, device=dev, precision=G.GNK_PREC_DF32) as bs:
+            ms, hs_, hks, rs = bs.fbie(torch.as_tensor(gs, device=dev), tol=TOL, precision=4, restart=30)
+        mo, ho, hko = O.fbie(sub.et, sub.etp, sub.A, sub.n, gs)
+        line.update({
+            "value": statistics.median(times), "ms_per_step": 1e3 * statistics.median(times),
+            "dtype": "f32 + double-float f32 pairs, f64 vectors",
+            "config": {"workload": "1024 close curves (circles, ellipses, 32 graded squares; gaps to "
+                                   "1e-3 r), unbounded, n=512 (524,288 unknowns): FBIE solve + h",
+                       "N": dom.N, "tol": TOL, "restart": 30, "precision": "mixed_df",
+                       "l2": "working set larger than L2 (basis 130 MB)"},
+            "solve": {"iterations": res.iterations, "refinements": res.refinements, "relres": res.relres},
+            "sampled_row_residual_rel": float(np.abs(lhs - rhs).max() / np.abs(rhs).max()),
+            "subset64_n128_vs_oracle": {"N": sub.N, "mu_rel_err": float(np.abs(ms.cpu().numpy() - mo).max()
+                                                                        / np.abs(mo).max()),
+                                        "h_err": float(np.abs(hs_.cpu().numpy() - ho).max()
+                                                       / max(1.0, np.abs(ho).max()))},
+            "compare": compare,
+        })
+    elif args.workload == "batched256":
+        doms = Dm.batch_domains(seed=4 + 1000 * rank, count=256)
+        nrhs = [d.m1 for d in doms]
+        gam_np = np.concatenate([Dm.gamma_log(d, d.holes[k]) for d in doms for k in range(d.m1)])
+        t0 = time.perf_counter()
+        b = G.Batch(doms, nrhs, autotune=True, device=dev)
+        t_build = time.perf_counter() - t0
+        gam = torch.as_tensor(gam_np, device=dev)
+        for _ in range(args.warmup):
+            b.fbie(gam, tol=TOL, restart=20, inner_tol=1e-6)
+        times = []
+        G.gnk_profile_enable(True)
+        for _ in range(args.steps):
+            (mu, h, hk, res, rel), t = _timed(lambda: b.fbie(gam, tol=TOL, restart=20, inner_tol=1e-6),
+                                              stream)
+            times.append(t)
+        prof = {k: G.gnk_profile_query(i) for k, i in (("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
+                                                        ("circ", G.PROF_CIRC))}
+        G.gnk_profile_enable(False)
+        # pair work of one batched product: sum_d nrhs_d N_d (N_d - 1); rate of a full product
+        work = float(sum(r * d.N * (d.N - 1) for d, r in zip(doms, nrhs)))
+        xs = torch.ones_like(gam)
+        b.apply_IminusN(xs, G.GNK_PREC_FP32)
+        _, t32 = _timed(lambda: b.apply_IminusN(xs, G.GNK_PREC_FP32), stream)
+        _, tdf = _timed(lambda: b.apply_IminusN(xs, G.GNK_PREC_DF32), stream)
+        # oracle check of the systems of the 4 smallest domains
+        order = sorted(range(len(doms)), key=lambda i: doms[i].N)[:4]
+        mu_np = mu.cpu().numpy()
+        offs = np.cumsum([0] + [d.N * r for d, r in zip(doms, nrhs)])
+        errs = []
+        for i in order:
+            d = doms[i]
+            for k in range(nrhs[i]):
+                a = offs[i] + k * d.N
+                mo, _, _ = O.fbie(d.et, d.etp, d.A, d.n, gam_np[a:a + d.N])
+                errs.append(float(np.abs(mu_np[a:a + d.N] - mo).max() / np.abs(mo).max()))
+        tun = b.tuning()
+        med = statistics.median(times)
+        line.update({
+            "value": med, "ms_per_step": 1e3 * med,
+            "dtype": "f32 + double-float f32 pairs, f64 vectors",
+            "config": {"workload": "256 unbounded domains, m+1 ~ U{2..64}, n ~ U{128,256,512,1024}, "
+                                   "m+1 right-hand sides log|eta - c_k| each: batched FBIE",
+                       "systems": b.nsys, "vector_length": b.L, "nodes": int(sum(d.N for d in doms)),
+                       "tol": TOL, "restart": 20, "precision": "mixed_df",
+                       "l2": "working set larger than L2"},
+            "build_with_autotune_s": t_build, "tuning": tun,
+            "solve": {"iterations": res.iterations, "refinements": res.refinements,
+                      "max_relres": float(rel.max())},
+            "pair_evals_per_batched_product": work,
+            "kernel_time_s": {k: v[1] / 1e3 / args.steps for k, v in prof.items()},
+            "full_product_s": {"fp32": t32, "df32": tdf},
+            "pair_evals_per_s_full_product": {"fp32": work / t32, "df32": work / tdf},
+            "oracle_check_smallest4_domains_max_rel_err_mu": max(errs),
+        })
+        b.close()
+    else:  # stars20: gradient through the Fourier coefficients
+        from paper_1308_5351_gb300 import autograd as AG
+        rng = np.random.default_rng(5 + 1000 * rank)
+        n, r0 = 2048, 0.3
+        slots = [complex(x, y) for y in range(4) for x in range(5)]
+        poly_slots = {3, 6, 13, 16}
+        results = {}
+        for kmax in (64, 128):
+            k = np.arange(1, kmax + 1)
+            params, centres, polys = [], [], []
+            for sidx, c in enumerate(slots):
+                if sidx in poly_slots:
+                    polys.append(Dm.square(c, r0 * 0.8, ccw=False) if len(polys) % 2 == 0 else
+                                 Dm.GradedPolygon([c + r0 * np.exp(-2j * np.pi * q / 3) for q in range(3)]))
+                else:
+                    centres.append(c)
+                    params.append((torch.tensor(rng.normal(0, 0.05 / k), device=dev, requires_grad=True),
+                                   torch.tensor(rng.normal(0, 0.05 / k), device=dev, requires_grad=True)))
+            t_nodes = Dm.nodes(n)
+            poly_et = [torch.as_tensor(pl.eval(t_nodes)[0], device=dev) for pl in polys]
+            poly_etp = [torch.as_tensor(pl.eval(t_nodes)[1], device=dev) for pl in polys]
+            m1 = len(centres) + len(polys)
+
+            def J(ps):
+                ets, etps = [], []
+                for c, (ak, bk) in zip(centres, ps):
+                    z, zp = AG.star_boundary(c, r0, ak, bk, n)
+                    ets.append(z)
+                    etps.append(zp)
+                et = torch.cat(ets + poly_et)
+                etp = torch.cat(etps + poly_etp)
+                gam = torch.log(torch.abs(et - centres[0]))
+                mu, h = AG.fbie(et, etp, torch.ones_like(et), gam, m1, n, bounded=False,
+                                precision=G.GNK_PREC_MIXED_DF, tol=1e-12, restart=30)
+                hk = AG.component_means(h, m1, n)
+                return hk[1] - hk[0]
+            val, t_fwd = _timed(lambda: J(params), stream)
+            _, t_bwd = _timed(lambda: val.backward(), stream)
+            grads = torch.cat([torch.cat([a.grad, b_.grad]) for a, b_ in params]).cpu().numpy()
+            # central differences on three coefficients
+            fd_err = 0.0
+            for (si, which, kk) in ((0, 0, 0), (5, 1, 3), (11, 0, kmax - 1)):
+                def shifted(delta):
+                    ps = []
+                    for t, (a, b_) in enumerate(params):
+                        a2, b2 = a.detach().clone(), b_.detach().clone()
+                        if t == si:
+                            (a2 if which == 0 else b2)[kk] += delta
+                        ps.append((a2, b2))
+                    with torch.no_grad():
+                        return float(J(ps))
+                fd = (shifted(1e-6) - shifted(-1e-6)) / 2e-6
+                an = float(params[si][which].grad[kk])
+                fd_err = max(fd_err, abs(fd - an) / np.abs(grads).max())
+            results[kmax] = {"parameters": int(grads.size), "forward_s": t_fwd, "backward_s": t_bwd,
+                             "grad_norm": float(np.linalg.norm(grads)), "fd_max_err_3_coeffs_rel_to_max_grad": fd_err}
+        tot = results[64]["forward_s"] + results[64]["backward_s"]
+        line.update({
+            "value": tot, "ms_per_step": 1e3 * tot, "dtype": "f32 + double-float f32 pairs, f64 vectors",
+            "config": {"workload": "16 star curves (a_k, b_k ~ N(0,(0.05/k)^2)) + 4 graded polygons, "
+                                   "n=2048 (40,960 unknowns): d(h_1 - h_0)/d(a_k, b_k)",
+                       "N": 20 * n, "tol": 1e-12, "precision": "mixed_df"},
+            "gradient": results,
+        })
+    line["gpu_launches"] = G.gnk_kernel_launches() - launches0
+    if rank == 0:
+        print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 

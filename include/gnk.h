@@ -286,6 +286,12 @@ int gnk_batch_sizes(const gnk_batch* b, long long* vec_len, int* systems,
 int gnk_batch_tuning(const gnk_batch* b, int* fp32_targets, int* fp32_group,
                      int* df_targets, int* df_group, float* variant_ms);
 
+/* y = (2I + diag(B1) - B) x for every system of the batch (Eq. sys), with FP32
+ * (GNK_PREC_FP32) or double-float (GNK_PREC_DF32) pair sums; x and y are batch
+ * vectors (host or device).  One persistent launch. */
+int gnk_batch_apply_IminusN(const gnk_batch* b, const double* x, double* y,
+                            int precision, void* stream);
+
 /* mu and h of every system (FBIE: Eqs. sys, y, bh) with FP32 pair sums inside
  * GMRES and double-float refinement (opt->precision must be
  * GNK_PREC_MIXED_DF; NULL opt means the defaults with that precision).  Each

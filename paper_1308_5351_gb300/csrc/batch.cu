@@ -535,7 +535,8 @@ __global__ void __launch_bounds__(KB) bk_update_x(BKry k, double* __restrict__ x
 // Outer check: relres_s = ||r_s|| / ||b_s||; converged systems get r_s = 0 so
 // that the inner solve leaves them alone; counts the unconverged ones.
 __global__ void __launch_bounds__(KB) bk_outer_check(BKry k, double* __restrict__ r, const double* __restrict__ bn,
-                                                     double* __restrict__ relres, double tol, unsigned* unconv) {
+                                                     double* __restrict__ relres, double tol, unsigned* unconv,
+                                                     int* __restrict__ conv) {
     __shared__ double red[KB / 32 + 1];
     __shared__ int s_conv;
     const int s = blockIdx.x;
@@ -551,6 +552,7 @@ __global__ void __launch_bounds__(KB) bk_outer_check(BKry k, double* __restrict_
         relres[s] = rel;
         if (!isfinite(rel)) atomicOr(k.nonfinite, 1);
         s_conv = (rel <= tol) ? 1 : 0;
+        conv[s] = s_conv;
         if (!s_conv) atomicAdd(unconv, 1u);
     }
     __syncthreads();
@@ -629,6 +631,7 @@ struct BatchImpl {
     int R = 0;
     BKry k;
     double *bnorm_in = nullptr, *bnorm_out = nullptr, *relres = nullptr;
+    int* oconv = nullptr;  // per system: converged at the outer (refinement) level
     cudaGraphExec_t graph = nullptr;
     int graph_R = -1;
     double graph_tol = -1.0;
@@ -803,7 +806,7 @@ void release_batch(BatchImpl& B) {
                  B.et32, B.ref32, B.offdf, B.off32, B.q32, B.A32, B.twid, B.lcol, B.cdesc, B.cbase, B.items32,
                  B.itemsdf, B.itemsdf1, B.counter, B.rhs, B.x, B.r, B.rr, B.dd, B.fb, B.fc, B.Lx, B.k.V, B.k.H,
                  B.k.g, B.k.cs, B.k.sn, B.k.y, B.k.h1, B.k.h2, B.k.beta, B.k.done, B.k.kst,
-                 B.k.unconv, B.k.nonfinite, B.bnorm_in, B.bnorm_out, B.relres};
+                 B.k.unconv, B.k.nonfinite, B.bnorm_in, B.bnorm_out, B.relres, B.oconv};
     for (void* q : p)
         if (q) cudaFree(q);
     if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -1078,6 +1081,7 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
     TRYB(dalloc(&B.bnorm_in, nsys));
     TRYB(dalloc(&B.bnorm_out, nsys));
     TRYB(dalloc(&B.relres, nsys));
+    TRYB(dalloc(&B.oconv, nsys));
     B.k.sys = B.sys;
     B.k.nsys = nsys;
     B.k.L = L;
@@ -1202,6 +1206,29 @@ int gnk_batch_tuning(const gnk_batch* h, int* fp32_targets, int* fp32_group, int
     return GNK_OK;
 }
 
+int gnk_batch_apply_IminusN(const gnk_batch* hc, const double* x, double* y, int precision, void* stream) {
+    if (!hc || !x || !y || (precision != GNK_PREC_FP32 && precision != GNK_PREC_DF32)) {
+        set_error("gnk_batch_apply_IminusN: NULL argument or precision not FP32/DF32");
+        return GNK_EINVAL;
+    }
+    BatchImpl& B = const_cast<gnk_batch*>(hc)->b;
+    cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t Lb = (size_t)B.L * sizeof(double);
+    GNK_TRY_CUDA(cudaMemcpyAsync(B.r, x, Lb, cudaMemcpyDefault, st));
+    BPairArgs a = base_args(B, B.dom);
+    a.x = B.r;
+    a.out = B.dd;
+    a.epi = BE_K;
+    if (precision == GNK_PREC_FP32)
+        GNK_TRY(launch32(B, a, B.T32, B.RG32, B.items32, B.nitems32, st));
+    else
+        GNK_TRY(launchdf(B, a, B.Tdf, B.RGdf, B.itemsdf, B.nitemsdf, st));
+    GNK_TRY_CUDA(cudaMemcpyAsync(y, B.dd, Lb, cudaMemcpyDefault, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    return GNK_OK;
+}
+
 int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* hv, double* hk,
                    const gnk_options* opt, gnk_result* info, double* relres_per_system, void* stream) {
     if (!hc || !gam || !mu || !hv) {
@@ -1243,11 +1270,12 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
     bk_norm<<<ns, KB, 0, st>>>(B.k, B.rhs, B.bnorm_out);
     count_launches(1);
     GNK_TRY_CUDA(cudaMemsetAsync(B.x, 0, Lb, st));
+    GNK_TRY_CUDA(cudaMemsetAsync(B.fc, 0, Lb, st));  // f_C(0) = 0 for systems that never move
     bool fc_valid = false;
     int status = GNK_ENOTCONV;
     for (int it = 0;; ++it) {
         GNK_TRY_CUDA(cudaMemsetAsync(B.k.unconv, 0, sizeof(unsigned), st));
-        bk_outer_check<<<ns, KB, 0, st>>>(B.k, B.rr, B.bnorm_out, B.relres, o.tol, B.k.unconv);
+        bk_outer_check<<<ns, KB, 0, st>>>(B.k, B.rr, B.bnorm_out, B.relres, o.tol, B.k.unconv, B.oconv);
         count_launches(1);
         unsigned unconv = 0;
         int nonfin = 0;
@@ -1271,6 +1299,8 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
         count_launches(1);
         // outer residual and f_C(x) in double-float
         GNK_TRY(run_batch_circulant(B.cdesc, B.cbase, B.ncirc, B.nmax, B.x, B.Lx, B.twid, B.lcol, st));
+        // groups whose systems had all converged are skipped: their x did not
+        // move, their residual stays 0 and their f_C(x) stays valid
         BPairArgs a = base_args(B, B.dom);
         a.x = B.x;
         a.rhs = B.rhs;
@@ -1278,14 +1308,13 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
         a.out = B.rr;
         a.out2 = B.fc;
         a.epi = BE_RESID_FC;
+        a.sys_done = B.oconv;
         GNK_TRY(launchdf(B, a, B.Tdf, B.RGdf, B.itemsdf, B.nitemsdf, st));
         res.matvecs_fp64++;
         res.refinements++;
         fc_valid = true;
     }
-    if (!fc_valid) {  // f_C(x) for x = 0 is 0 (right-hand side already converged)
-        GNK_TRY_CUDA(cudaMemsetAsync(B.fc, 0, Lb, st));
-    }
+    (void)fc_valid;
     // h = (f_C(mu) - f_B(gamma)) / 2, h_k per system
     bk_half_diff<<<(unsigned)((B.L + 255) / 256), 256, 0, st>>>(B.L, B.fc, B.fb, B.dd);
     count_launches(1);

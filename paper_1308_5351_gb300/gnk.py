@@ -43,7 +43,7 @@ EXPORTED = (
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
     "gnk_profile_query", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
-    "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie",
+    "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
     IP = ctypes.POINTER(I)
     lib.gnk_build_batch.argtypes = [ctypes.POINTER(P), I, IP, IP, IP, IP, P, P, P, I, P]
     lib.gnk_free_batch.argtypes = [P]
+    lib.gnk_batch_apply_IminusN.argtypes = [P, P, P, I, P]
     lib.gnk_batch_sizes.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), IP, IP]
     lib.gnk_batch_tuning.argtypes = [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_float)]
     lib.gnk_batch_fbie.argtypes = [P, P, P, P, P, ctypes.POINTER(gnk_options),
@@ -461,6 +462,12 @@ class Batch:
                                      ctypes.c_void_p(rel.ctypes.data), _stream(stream))
         _check(code, (GNK_OK, GNK_ENOTCONV))
         return mu, h, hk, res, rel
+
+    def apply_IminusN(self, x, precision=GNK_PREC_FP32, stream=None):
+        y = _real_like(x, self.L)
+        _check(load().gnk_batch_apply_IminusN(self.handle, _ptr(x), _ptr(y), int(precision),
+                                              _stream(stream)))
+        return y
 
     def close(self):
         if self.handle is not None:

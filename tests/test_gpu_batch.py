@@ -76,3 +76,24 @@ def test_batch_rejects_bad_domains(G):
     d = Dm.three_circles(16)
     with pytest.raises(G.GnkError):
         G.Batch([d], [0])
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_batch_apply_matches_oracle(G, prec):
+    """One persistent launch applies (2I + diag(B1) - B) to every system; the
+    FP32 bound of the single-domain tests (8 u32 per term, factor 4) and the
+    double-float bound scaled by |A||x| cover it."""
+    doms, nrhs, _ = _batch_case(seed=9)
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=sum(d.N * r for d, r in zip(doms, nrhs)))
+    with G.Batch(doms, nrhs, autotune=False, device="cuda") as b:
+        y = b.apply_IminusN(torch.as_tensor(x, device="cuda"), prec).cpu().numpy()
+    off = 0
+    for d, r in zip(doms, nrhs):
+        K = O.matrix_IminusN(d.et, d.etp, d.A, d.n)
+        for k in range(r):
+            xs = x[off:off + d.N]
+            scale = (np.abs(K) @ np.abs(xs)).max()
+            tol = (4 * 8 * (64 + d.N) * 2.0 ** -24 if prec == 2 else 1e-11) * scale
+            assert np.abs(y[off:off + d.N] - K @ xs).max() <= tol
+            off += d.N
