@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--precision", choices=list(MODES), default="mixed_df")
     ap.add_argument("--workload", choices=["ellipses64", "close1024", "batched256", "stars20"],
                     default="ellipses64", help="ellipses64 is the headline; the others are extra lines")
+    ap.add_argument("--domains", type=int, default=256, help="batched256: number of domains")
     ap.add_argument("--with-fp64", action="store_true",
                     help="close1024: also time the plain FP64 solve (minutes)")
     return ap.parse_args()
@@ -496,7 +497,7 @@ def run_extra(args, dist, rank, ws, local):
             "compare": compare,
         })
     elif args.workload == "batched256":
-        doms = Dm.batch_domains(seed=4 + 1000 * rank, count=256)
+        doms = Dm.batch_domains(seed=4 + 1000 * rank, count=args.domains)
         nrhs = [d.m1 for d in doms]
         gam_np = np.concatenate([Dm.gamma_log(d, d.holes[k]) for d in doms for k in range(d.m1)])
         t0 = time.perf_counter()
