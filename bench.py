@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=1024, help="nodes per boundary")
+    ap.add_argument("--boundary-nodes", "--n", dest="n", type=int, default=1024,
+                    help="nodes per boundary (use --boundary-nodes under torchrun)")
     ap.add_argument("--count", type=int, default=64, help="ellipses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves")
