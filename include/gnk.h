@@ -113,6 +113,11 @@ unsigned long long gnk_kernel_launches(void);
 int gnk_profile_enable(int on);
 int gnk_profile_query(int kind, long long* launches, double* total_ms,
                       double* work);
+/* As gnk_profile_query, plus the launches' algorithmic instruction count on
+ * their limiting pipe (pair kernels: per pair, FP64 9 + 4R, FP32 6 + 4R,
+ * double-float 49 + 48R, R the right-hand sides of the launch). */
+int gnk_profile_query_ex(int kind, long long* launches, double* total_ms,
+                         double* work, double* instr);
 
 /* ---------------------------------------------------------------------------
  * Boundary handle (Sec. 2.1, 2.4; Eqs. eta, A, ti-skp)
@@ -138,7 +143,11 @@ int gnk_build_boundary(gnk_boundary** out, int m1, int n,
 
 /* As gnk_build_boundary, with the arithmetic of the precomputed Cauchy sums
  * (Eone and E eta') chosen by `precision` (GNK_PREC_FP64 or GNK_PREC_DF32);
- * gnk_build_boundary uses GNK_PREC_FP64. */
+ * gnk_build_boundary uses GNK_PREC_FP64.  With GNK_BUILD_DEFER or-ed into
+ * `precision`, those sums are formed by the first call that needs them, and
+ * gnk_fbie on a handle without eta'' forms Eone together with E(q gamma) in a
+ * single two-right-hand-side launch. */
+#define GNK_BUILD_DEFER 0x100
 int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n,
                           const double* et, const double* etp, const double* etpp,
                           const double* A, const double* Ap, int bounded,

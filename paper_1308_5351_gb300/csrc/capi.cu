@@ -8,6 +8,8 @@
 #include <cstring>
 #include <atomic>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "gnk_internal.h"
 
@@ -106,13 +108,35 @@ int dmalloc(T** p, size_t count) {
 }
 
 void release(Boundary& b) {
-    void* ptrs[] = {b.et, b.etp, b.A, b.q, b.Eone, b.b1, b.d1, b.e, b.ref32, b.off32, b.et32,
-                    b.q32, b.A32, b.ref64, b.offdf, b.twiddle, b.Lcol, b.partial, b.zbuf, b.r0,
-                    b.r1, b.r2, b.r3, b.r4, b.r5, b.r6, b.means, b.stage, b.V, b.kry, b.kstate};
+    void* ptrs[] = {b.arena, b.V, b.kry, b.kstate};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (b.hstate) cudaFreeHost(b.hstate);
 }
+
+// Carves the handle's fixed-size buffers out of one device allocation
+// (256-byte aligned pieces).
+struct Arena {
+    std::vector<std::pair<void**, size_t>> parts;
+    template <class T>
+    void add(T** p, size_t count) {
+        parts.emplace_back(reinterpret_cast<void**>(p), count * sizeof(T));
+    }
+    int allocate(void** base) {
+        size_t total = 0;
+        for (auto& pr : parts) total += (pr.second + 255) / 256 * 256;
+        if (cudaMalloc(base, total + 256) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of %zu bytes failed", total);
+            return GNK_ENOMEM;
+        }
+        char* c = static_cast<char*>(*base);
+        for (auto& pr : parts) {
+            *pr.first = c;
+            c += (pr.second + 255) / 256 * 256;
+        }
+        return GNK_OK;
+    }
+};
 
 int options_from(const gnk_options* in, gnk_options* o) {
     gnk_default_options(o);
@@ -129,7 +153,7 @@ int options_from(const gnk_options* in, gnk_options* o) {
 }
 
 int build(Boundary& b, int m1, int n, const double* et, const double* etp, const double* etpp,
-          const double* A, const double* Ap, int bounded, int eone_prec, cudaStream_t st) {
+          const double* A, const double* Ap, int bounded, int eone_prec, int defer, cudaStream_t st) {
     const size_t N = (size_t)m1 * n;
     b.m1 = m1;
     b.n = n;
@@ -140,33 +164,47 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     GNK_TRY_CUDA(cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, b.device));
 
     const int tiles32 = (b.N + kSrcTile32 - 1) / kSrcTile32;
-    GNK_TRY(dmalloc(&b.et, N));
-    GNK_TRY(dmalloc(&b.etp, N));
-    GNK_TRY(dmalloc(&b.A, N));
-    GNK_TRY(dmalloc(&b.q, N));
-    GNK_TRY(dmalloc(&b.Eone, N));
-    GNK_TRY(dmalloc(&b.b1, N));
-    GNK_TRY(dmalloc(&b.d1, N));
-    GNK_TRY(dmalloc(&b.e, N));
-    GNK_TRY(dmalloc(&b.ref32, (size_t)tiles32));
-    GNK_TRY(dmalloc(&b.off32, N));
-    GNK_TRY(dmalloc(&b.et32, N));
-    GNK_TRY(dmalloc(&b.q32, N));
-    GNK_TRY(dmalloc(&b.A32, N));
-    GNK_TRY(dmalloc(&b.ref64, (size_t)tiles32));
-    GNK_TRY(dmalloc(&b.offdf, N));
-    GNK_TRY(dmalloc(&b.twiddle, (size_t)n));
-    GNK_TRY(dmalloc(&b.Lcol, (size_t)n));
-    GNK_TRY(dmalloc(&b.zbuf, kMaxRHS * N));
-    GNK_TRY(dmalloc(&b.r0, N));
-    GNK_TRY(dmalloc(&b.r1, N));
-    GNK_TRY(dmalloc(&b.r2, N));
-    GNK_TRY(dmalloc(&b.r3, N));
-    GNK_TRY(dmalloc(&b.r4, N));
-    GNK_TRY(dmalloc(&b.r5, N));
-    GNK_TRY(dmalloc(&b.r6, N));
-    GNK_TRY(dmalloc(&b.means, (size_t)m1));
-    GNK_TRY(dmalloc(&b.stage, 4 * 2 * N));
+    // launch plans (they fix the size of the split-source workspace)
+    b.plan64 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP64), kThreads64 * kTargets64,
+                         kSrcTile64);
+    b.plan32 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP32), kThreads32 * kTargets32,
+                         kSrcTile32);
+    b.plandf = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_DF32), kThreadsDF * kTargetsDF,
+                         kSrcTile32);
+    GNK_TRY(pair_workspace_bytes(b, &b.partial_bytes));
+    // every fixed-size buffer of the handle lives in one device allocation
+    Arena ar;
+    ar.add(&b.et, N);
+    ar.add(&b.etp, N);
+    ar.add(&b.A, N);
+    ar.add(&b.q, N);
+    ar.add(&b.Eone, N);
+    ar.add(&b.b1, N);
+    ar.add(&b.d1, N);
+    ar.add(&b.e, N);
+    ar.add(&b.ref32, (size_t)tiles32);
+    ar.add(&b.off32, N);
+    ar.add(&b.et32, N);
+    ar.add(&b.q32, N);
+    ar.add(&b.A32, N);
+    ar.add(&b.ref64, (size_t)tiles32);
+    ar.add(&b.offdf, N);
+    ar.add(&b.twiddle, (size_t)n);
+    ar.add(&b.Lcol, (size_t)n);
+    ar.add(&b.zbuf, kMaxRHS * N);
+    ar.add(&b.r0, N);
+    ar.add(&b.r1, N);
+    ar.add(&b.r2, N);
+    ar.add(&b.r3, N);
+    ar.add(&b.r4, N);
+    ar.add(&b.r5, N);
+    ar.add(&b.r6, N);
+    ar.add(&b.ones, N);
+    ar.add(&b.means, (size_t)m1);
+    ar.add(&b.stage, 4 * 2 * N);
+    ar.add(reinterpret_cast<char**>(&b.partial), b.partial_bytes);
+    ar.add(&b.flag, 1);
+    GNK_TRY(ar.allocate(&b.arena));
 
     // geometry copies (host or device sources; cudaMemcpyDefault infers the direction)
     GNK_TRY_CUDA(cudaMemcpyAsync(b.et, et, N * sizeof(double2), cudaMemcpyDefault, st));
@@ -184,8 +222,7 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
             d_Ap = s1;
         }
     }
-    int* d_flag = nullptr;
-    GNK_TRY(dmalloc(&d_flag, 1));
+    int* d_flag = b.flag;
     GNK_TRY_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
     GNK_TRY_CUDA(cudaMemsetAsync(b.e, 0, N * sizeof(double), st));
     int s = run_prepare_geometry(b, d_etpp, d_Ap, d_flag, st);
@@ -198,7 +235,6 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
             s = GNK_ECUDA;
         }
     }
-    cudaFree(d_flag);
     GNK_TRY(s);
     if (flag & 1) {
         set_error("non-finite value in eta, eta', eta'', A or A'");
@@ -209,15 +245,6 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
         return GNK_EINVAL;
     }
 
-    // launch plans and the split-source workspace
-    b.plan64 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP64), kThreads64 * kTargets64,
-                         kSrcTile64);
-    b.plan32 = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_FP32), kThreads32 * kTargets32,
-                         kSrcTile32);
-    b.plandf = make_plan(b.N, b.sms, pair_blocks_per_sm(GNK_PREC_DF32), kThreadsDF * kTargetsDF,
-                         kSrcTile32);
-    GNK_TRY(pair_workspace_bytes(b, &b.partial_bytes));
-    GNK_TRY(dmalloc(reinterpret_cast<char**>(&b.partial), b.partial_bytes));
 
     // Eone = E q with diag(B1), diag(D1); with eta'' also E eta' and e (Eq. bve)
     PairJob j;
@@ -231,6 +258,10 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     j.out2 = b.d1;
     j.out3 = b.e;
     b.eone_prec = eone_prec;
+    if (defer) {
+        b.eone_pending = 1;  // formed by the first call that needs them
+        return GNK_OK;
+    }
     GNK_TRY(run_pairsum(b, j, eone_prec, st));
     GNK_TRY_CUDA(cudaStreamSynchronize(st));
     return GNK_OK;
@@ -275,8 +306,11 @@ int gnk_build_boundary(gnk_boundary** out, int m1, int n, const double* et, cons
 int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, const double* etp,
                           const double* etpp, const double* A, const double* Ap, int bounded,
                           int precision, void* stream) {
+    const int defer = (precision & GNK_BUILD_DEFER) ? 1 : 0;
+    precision &= ~GNK_BUILD_DEFER;
     if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
-        set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64 or GNK_PREC_DF32");
+        set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64 or GNK_PREC_DF32 "
+                  "(optionally | GNK_BUILD_DEFER)");
         return GNK_EINVAL;
     }
     if (!out || !et || !etp || !A) {
@@ -298,7 +332,8 @@ int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, c
         set_error("host allocation failed");
         return GNK_ENOMEM;
     }
-    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, precision, (cudaStream_t)stream);
+    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, precision, defer,
+                        (cudaStream_t)stream);
     if (s != GNK_OK) {
         release(h->b);
         delete h;
@@ -360,6 +395,7 @@ static int apply_unary(const gnk_boundary* h, const double* x, double* y, int pr
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (which != 3) GNK_TRY(ensure_eone(b, st));
     const double* dx;
     GNK_TRY(stage_in(b, x, b.N, 0, st, &dx));
     Out o = stage_out(b, y, b.N, 1);
@@ -402,6 +438,7 @@ static int solve_common(const gnk_boundary* h, const double* gam, double* mu, co
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    GNK_TRY(ensure_eone(b, st));
     const double* dg;
     GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
     Out o_mu = stage_out(b, mu, b.N, 1);
@@ -447,8 +484,13 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
     GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
     Out o_mu = stage_out(b, mu, b.N, 1);
     Out o_h = stage_out(b, hv, b.N, 2);
-    // -y and f_B(gamma) from one Cauchy sum
-    GNK_TRY(op_rhs_fb(b, dg, b.r4, b.r5, outer, st));
+    // -y and f_B(gamma) from one Cauchy sum; a deferred handle forms Eone in the same launch
+    if (b.eone_pending && !b.has_adjoint && b.eone_prec == outer) {
+        GNK_TRY(op_eone_rhs_fb(b, dg, b.r4, b.r5, b.eone_prec, st));
+    } else {
+        GNK_TRY(ensure_eone(b, st));
+        GNK_TRY(op_rhs_fb(b, dg, b.r4, b.r5, outer, st));
+    }
     int fc_valid = 0;
     const int s = solve(b, 0, b.r4, o_mu.dev, o, info, st, b.r6, &fc_valid);
     if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
@@ -477,6 +519,7 @@ int gnk_solve_ie_transpose(const gnk_boundary* hd, const double* rhs, double* x,
     GNK_TRY(options_from(opt, &o));
     const Boundary& b = hd->b;
     cudaStream_t st = (cudaStream_t)stream;
+    GNK_TRY(ensure_eone(b, st));
     const double* dr;
     GNK_TRY(stage_in(b, rhs, b.N, 0, st, &dr));
     Out ox = stage_out(b, x, b.N, 1);
@@ -528,6 +571,7 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
     GNK_TRY(options_from(opt, &o));
     const Boundary& b = hd->b;
     cudaStream_t st = (cudaStream_t)stream;
+    GNK_TRY(ensure_eone(b, st));
     const size_t rN = (size_t)b.N * sizeof(double), cN = 2 * rN;
     DevArr v[8];
     const void* src[8] = {mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam};
@@ -566,6 +610,7 @@ int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, do
     }
     const Boundary& b = h->b;
     cudaStream_t st = (cudaStream_t)stream;
+    GNK_TRY(ensure_eone(b, st));
     const double *dmu, *dg;
     GNK_TRY(stage_in(b, mu, b.N, 0, st, &dmu));
     GNK_TRY(stage_in(b, gam, b.N, 1, st, &dg));

@@ -128,6 +128,7 @@ struct PrepArgs {
     double2* ref64;
     float4* offdf;
     double* ediag;       // (2/n) Im(eta''/eta' - A'/A), corner limit 0
+    double* ones;        // nullable: filled with 1
     int* flag;           // bit 1: non-finite input, bit 2: A == 0
 };
 
@@ -152,6 +153,7 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
     a.q32[i] = make_float2((float)q.x, (float)q.y);
     a.A32[i] = make_float2((float)A.x, (float)A.y);
     a.et32[i] = split_hilo(et);
+    if (a.ones) a.ones[i] = 1.0;
     const int tile = i / a.S;
     const int j0 = tile * a.S;
     const int cnt = min(a.S, a.N - j0);
@@ -226,6 +228,7 @@ int run_prepare_nodes(Boundary& b, const double* etpp, const double* Ap, int* d_
     a.ref64 = b.ref64;
     a.offdf = b.offdf;
     a.ediag = b.e;
+    a.ones = b.ones;
     a.flag = d_flag;
     prepare_geometry_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());

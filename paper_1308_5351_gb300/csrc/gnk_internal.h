@@ -52,7 +52,9 @@ struct ProfToken {
     void* ev = nullptr;
 };
 ProfToken prof_begin(cudaStream_t st);
-long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st);
+// `instr`: algorithmic instructions of the launch on its limiting pipe
+// (FP32 pipe for the FP32 and double-float pair kernels, FP64 pipe for the FP64 one).
+long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr = 0.0);
 void prof_skip(long idx);
 // Collect the record indices of the launches made between begin and end
 // (calling thread only), to mark launches that a device flag turned into
@@ -94,6 +96,7 @@ enum Epilogue : int {
     EPI_IMINUSN_T = 10,  // out = (2I + diag(B1) - B)^T x, z = E(A x)
     EPI_RESID_T = 11,    // out = rhs - (2I + diag(B1) - B)^T x
     EPI_MT = 12,         // out = (D - diag(D1) + Lhat)^T x, z = E(A x), Lx = Lhat x
+    EPI_EONE_RHS = 13,   // z0 = E q, z1 = E(q gamma): Eone, diag(B1), diag(D1), -y, f_B(gamma)
 };
 
 // Operators a GMRES solve can use.
@@ -174,6 +177,10 @@ struct Boundary {
     double* r4 = nullptr;
     double* r5 = nullptr;
     double* r6 = nullptr;
+    double* ones = nullptr;     // N ones (weights q = q * 1)
+    int* flag = nullptr;        // input checks of the geometry preparation
+    void* arena = nullptr;      // the one allocation that holds the buffers above
+    int eone_pending = 0;       // Eone, diag(B1), diag(D1), e not yet formed
     double* means = nullptr;    // m1
     double* stage = nullptr;    // host-staging buffers: 4 x 2N doubles
     PairPlan plan64, plan32, plandf;
@@ -185,7 +192,6 @@ struct Boundary {
     double* kry = nullptr;      // small dense state (H, g, cs, sn, y, partials)
     size_t kry_bytes = 0;
     void* kstate = nullptr;     // device KrylovState
-    void* hstate = nullptr;     // pinned host mirror of KrylovState
 };
 
 // ---------------------------------------------------------------- pair sums
@@ -221,6 +227,11 @@ int op_MT(const Boundary& b, const double* x, double* y, int prec, cudaStream_t 
 int op_rhs_fb(const Boundary& b, const double* gam, double* rhs, double* fb, int prec,
               cudaStream_t st);
 int op_half_diff(const double* a, const double* b, double* out, int N, cudaStream_t st);
+// Forms Eone, diag(B1), diag(D1) (and e) if the handle deferred them.
+int ensure_eone(const Boundary& b, cudaStream_t st);
+// Deferred handles: Eone and the first right-hand side in one two-RHS launch.
+int op_eone_rhs_fb(const Boundary& b, const double* gam, double* rhs, double* fb, int prec,
+                   cudaStream_t st);
 int op_h(const Boundary& b, const double* mu, const double* gam, double* h, cudaStream_t st);
 int op_negate(double* x, int N, cudaStream_t st);
 

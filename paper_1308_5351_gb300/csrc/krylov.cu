@@ -305,7 +305,6 @@ int ensure_krylov(Boundary& b, int restart) {
         GNK_TRY_CUDA(cudaMalloc(&b.kstate, sizeof(KState)));
         GNK_TRY_CUDA(cudaMemset(b.kstate, 0, sizeof(KState)));
     }
-    if (!b.hstate) GNK_TRY_CUDA(cudaMallocHost(&b.hstate, sizeof(KState)));
     return GNK_OK;
 }
 
@@ -317,9 +316,8 @@ int apply_op(const Boundary& b, int op, const double* x, double* y, int prec, cu
 }
 
 int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
-    GNK_TRY_CUDA(cudaMemcpyAsync(b.hstate, b.kstate, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaMemcpyAsync(hs, b.kstate, sizeof(KState), cudaMemcpyDeviceToHost, st));
     GNK_TRY_CUDA(cudaStreamSynchronize(st));
-    std::memcpy(hs, b.hstate, sizeof(KState));
     return GNK_OK;
 }
 

@@ -155,6 +155,45 @@ __global__ void negate_kernel(double* x, int N) {
 }
 }  // namespace
 
+int ensure_eone(const Boundary& bc, cudaStream_t st) {
+    if (!bc.eone_pending) return GNK_OK;
+    Boundary& b = const_cast<Boundary&>(bc);  // handle state; calls on a handle do not overlap
+    PairJob j;
+    j.R = b.has_adjoint ? 2 : 1;
+    j.mode = W_COMPLEX;
+    j.w[0] = b.q;
+    j.w[1] = b.etp;
+    j.epi = EPI_EONE;
+    j.out_c = b.Eone;
+    j.out = b.b1;
+    j.out2 = b.d1;
+    j.out3 = b.e;
+    GNK_TRY(run_pairsum(b, j, b.eone_prec, st));
+    b.eone_pending = 0;
+    return GNK_OK;
+}
+
+int op_eone_rhs_fb(const Boundary& bc, const double* gam, double* rhs, double* fb, int prec,
+                   cudaStream_t st) {
+    Boundary& b = const_cast<Boundary&>(bc);
+    GNK_TRY(run_circulant(b, gam, b.r3, st));
+    PairJob j;
+    j.R = 2;
+    j.mode = W_SCALED;
+    j.x[0] = b.ones;
+    j.x[1] = gam;
+    j.s = b.q;
+    j.epi = EPI_EONE_RHS;
+    j.out_c = b.Eone;
+    j.out = rhs;
+    j.out2 = fb;
+    j.ex = gam;
+    j.Lx = b.r3;
+    GNK_TRY(run_pairsum(b, j, prec, st));
+    b.eone_pending = 0;
+    return GNK_OK;
+}
+
 namespace {
 __global__ void half_diff_kernel(const double* a, const double* b, double* out, int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

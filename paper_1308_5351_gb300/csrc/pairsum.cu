@@ -428,6 +428,8 @@ struct ReduceArgs {
     const double* b1;
     const double* d1;
     const double* e;
+    double* b1w;  // EPI_EONE_RHS writes diag(B1), diag(D1)
+    double* d1w;
     PairJob job;
 };
 
@@ -502,6 +504,20 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
             j.out[i] = 0.5 * (fc - fb);
             break;
         }
+        case EPI_EONE_RHS: {
+            // z0 = E q (Eone), z1 = E(q gamma): the diagonals, -y and f_B(gamma) at once
+            const double2 A = a.A[i];
+            const double b1v = -s2n * (A.x * zy[0] + A.y * zx[0]);
+            const double d1v = -s2n * (A.x * zx[0] - A.y * zy[0]);
+            j.out_c[i] = make_double2(zx[0], zy[0]);
+            a.b1w[i] = b1v;
+            a.d1w[i] = d1v;
+            const double x = j.ex[i];
+            const double fc = -s2n * (A.x * zx[1] - A.y * zy[1]) - d1v * x + j.Lx[i];
+            j.out[i] = -fc;
+            j.out2[i] = 2.0 * x + b1v * x + s2n * (A.x * zy[1] + A.y * zx[1]);
+            break;
+        }
         case EPI_IMINUSN_T:
         case EPI_RESID_T: {
             // K^T x = 2x + diag(B1) x - B^T x, B^T x = (2/n) Im(q E(A x))  (Eq. BTx)
@@ -570,6 +586,8 @@ cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int
     ra.b1 = b.b1;
     ra.d1 = b.d1;
     ra.e = b.e;
+    ra.b1w = b.b1;
+    ra.d1w = b.d1;
     ra.job = job;
     const int threads = 256;
     const ProfToken tok = prof_begin(st);
@@ -643,7 +661,9 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsum64_kernel<2, W_COMPLEX><<<grid, kThreads64, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_PAIR64, (double)job.R * b.N * (b.N - 1.0), st);
+    // FP64 pipe per pair: 9 shared (d, |d|^2, reciprocal, 1/d) + 4 per right-hand side
+    prof_end(tok, PK_PAIR64, (double)job.R * b.N * (b.N - 1.0), st,
+             (9.0 + 4.0 * job.R) * b.N * (b.N - 1.0));
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 0, st));
     count_launches(2);
     return GNK_OK;
@@ -680,7 +700,9 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsum32_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st);
+    // FP32 pipe per pair: 6 shared + 4 per right-hand side (plus one MUFU reciprocal)
+    prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st,
+             (6.0 + 4.0 * job.R) * b.N * (b.N - 1.0));
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st));
     count_launches(2);
     return GNK_OK;
@@ -713,7 +735,9 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsumdf_kernel<2, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st);
+    // FP32 pipe per pair: 49 shared (d, |d|^2, reciprocal, 1/d) + 48 per right-hand side
+    prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st,
+             (49.0 + 48.0 * job.R) * b.N * (b.N - 1.0));
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 2, st));
     count_launches(2);
     return GNK_OK;

@@ -14,6 +14,7 @@ struct Rec {
     cudaEvent_t a, b;
     int kind;
     double work;
+    double instr;
     bool skipped;
 };
 
@@ -63,7 +64,7 @@ ProfToken prof_begin(cudaStream_t st) {
     return t;
 }
 
-long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st) {
+long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr) {
     if (!t.ev) return -1;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) {
@@ -73,7 +74,7 @@ long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st) {
     cudaEvent_t b = take_event();
     if (!b) return -1;
     cudaEventRecord(b, st);
-    g_recs.push_back(Rec{static_cast<cudaEvent_t>(t.ev), b, kind, work, false});
+    g_recs.push_back(Rec{static_cast<cudaEvent_t>(t.ev), b, kind, work, instr, false});
     const long id = (long)g_recs.size() - 1;
     if (t_collect) t_ids.push_back(id);
     return id;
@@ -111,9 +112,13 @@ int gnk_profile_enable(int on) {
 }
 
 int gnk_profile_query(int kind, long long* launches, double* total_ms, double* work) {
+    return gnk_profile_query_ex(kind, launches, total_ms, work, nullptr);
+}
+
+int gnk_profile_query_ex(int kind, long long* launches, double* total_ms, double* work, double* instr) {
     std::lock_guard<std::mutex> lk(g_mu);
     long long n = 0;
-    double ms = 0.0, wk = 0.0;
+    double ms = 0.0, wk = 0.0, ins = 0.0;
     for (const Rec& r : g_recs) {
         if (r.kind != kind || r.skipped) continue;
         if (cudaEventSynchronize(r.b) != cudaSuccess) {
@@ -129,10 +134,12 @@ int gnk_profile_query(int kind, long long* launches, double* total_ms, double* w
         ++n;
         ms += t;
         wk += r.work;
+        ins += r.instr;
     }
     if (launches) *launches = n;
     if (total_ms) *total_ms = ms;
     if (work) *work = wk;
+    if (instr) *instr = ins;
     return GNK_OK;
 }
 

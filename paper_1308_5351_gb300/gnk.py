@@ -35,13 +35,14 @@ GNK_PREC_MIXED = 1
 GNK_PREC_FP32 = 2
 GNK_PREC_DF32 = 3
 GNK_PREC_MIXED_DF = 4
+GNK_BUILD_DEFER = 0x100
 
 EXPORTED = (
     "gnk_default_options", "gnk_last_error", "gnk_version", "gnk_build_boundary",
     "gnk_free_boundary", "gnk_boundary_size", "gnk_cauchy_sum", "gnk_apply_IminusN",
     "gnk_apply_M", "gnk_apply_circulant", "gnk_apply_adjoint", "gnk_solve_ie",
     "gnk_compute_h", "gnk_solve_adjoint_ie", "gnk_kernel_launches", "gnk_profile_enable",
-    "gnk_profile_query", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
+    "gnk_profile_query", "gnk_profile_query_ex", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
 )
@@ -119,6 +120,9 @@ def load(path: str = LIB_PATH):
                                            ctypes.POINTER(gnk_result), P]
     lib.gnk_fbie_backward.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(gnk_options),
                                       ctypes.POINTER(gnk_result), P]
+    lib.gnk_profile_query_ex.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -199,6 +203,14 @@ def gnk_profile_query(kind: int):
     n, ms, wk = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
     _check(load().gnk_profile_query(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk)))
     return n.value, ms.value, wk.value
+
+
+def gnk_profile_query_ex(kind: int):
+    """(launches, total device ms, total work, algorithmic pipe instructions)."""
+    n, ms, wk, ins = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().gnk_profile_query_ex(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk),
+                                       ctypes.byref(ins)))
+    return n.value, ms.value, wk.value, ins.value
 
 
 def gnk_version() -> str:

@@ -322,3 +322,27 @@ def test_bad_options_rejected(G):
             b.solve_ie(_dev(np.ones(d.N)), restart=0)
         with pytest.raises(G.GnkError):
             b.solve_ie(_dev(np.ones(d.N)), precision=7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_df"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_deferred_precompute(G, prec, adjoint):
+    """GNK_BUILD_DEFER: Eone and the diagonals are formed by the first call that
+    needs them (fused with E(q gamma) inside gnk_fbie when possible); results
+    match the immediate build."""
+    d, gam = SOLVE["ellipses_log"]
+    mu_ref, h_ref, hk_ref = O.fbie(d.et, d.etp, d.A, d.n, gam)
+    p = SOLVE_PREC[prec]
+    bp = (G.GNK_PREC_DF32 if prec == "mixed_df" else G.GNK_PREC_FP64) | G.GNK_BUILD_DEFER
+    with G.Boundary.from_domain(d, adjoint=adjoint, device="cuda", precision=bp) as b:
+        mu, h, hk, res = b.fbie(_dev(gam), tol=1e-12, precision=p)
+        mu, h, hk = _host(mu), _host(h), _host(hk)
+        y = _host(b.apply_IminusN(_dev(gam)))
+    assert np.abs(mu - mu_ref).max() <= 1e-10 * np.abs(mu_ref).max()
+    assert np.abs(hk - hk_ref).max() <= 1e-10 * max(1.0, np.abs(h_ref).max())
+    K = O.matrix_IminusN(d.et, d.etp, d.A, d.n)
+    assert np.abs(y - K @ gam).max() <= 1e-11 * (np.abs(K) @ np.abs(gam)).max()
+    with G.Boundary.from_domain(d, adjoint=True, device="cuda", precision=bp) as b:
+        phi, r2 = b.solve_adjoint_ie(_dev(gam), tol=1e-12)
+    ref = O.solve_adjoint_ie(d.et, d.etp, d.etpp, d.A, d.Ap, d.n, d.c, gam)
+    assert np.abs(_host(phi) - ref).max() <= 1e-10 * np.abs(ref).max()
