@@ -55,7 +55,7 @@ PEAK_BASIS = {
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
 }
-KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32_kernel", "pairdf": "pairsumdf_kernel"}
+KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel"}
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3}
 
 

@@ -181,6 +181,8 @@ struct Boundary {
     int* flag = nullptr;        // input checks of the geometry preparation
     void* arena = nullptr;      // the one allocation that holds the buffers above
     int eone_pending = 0;       // Eone, diag(B1), diag(D1), e not yet formed
+    int df_scalar = 0;          // 1: scalar double-float kernel instead of the packed one
+    int f32_scalar = 0;         // 1: scalar FP32 kernel instead of the packed one
     double* means = nullptr;    // m1
     double* stage = nullptr;    // host-staging buffers: 4 x 2N doubles
     PairPlan plan64, plan32, plandf;

@@ -92,4 +92,68 @@ static __device__ __forceinline__ df df_split(double v) {
     return r;
 }
 
+// ------------------------------------------------------------------ packed double-float
+// Two independent double-float values per float2 (lane x, lane y) with the
+// sm_100 packed FP32 intrinsics: one instruction issues both lanes, so the
+// FP32 pipe rather than instruction issue bounds the kernels.  The _rn forms
+// are never contracted.  Subtraction is written as an FMA with -1, which is
+// exact and rounds once like a subtraction.
+struct df2 {
+    float2 h, l;
+};
+
+static __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+static __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+static __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+static __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+static __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+static __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+static __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+static __device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+    s = sub2(a, b);
+    const float2 bb = sub2(s, a);
+    e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+
+// a - b, b the same for both lanes (Bailey's add, renormalised)
+static __device__ __forceinline__ df2 df2_sub(float2 ah, float2 al, float2 bh, float2 bl) {
+    float2 s, e;
+    two_diff2(ah, bh, s, e);
+    e = add2(e, sub2(al, bl));
+    df2 r;
+    r.h = add2(s, e);
+    r.l = sub2(e, sub2(r.h, s));
+    return r;
+}
+
+static __device__ __forceinline__ df2 df2_mul(df2 a, df2 b) {
+    df2 r;
+    r.h = mul2(a.h, b.h);
+    float2 e = fma2(a.h, b.h, neg2(r.h));
+    e = fma2(a.h, b.l, e);
+    e = fma2(a.l, b.h, e);
+    r.l = e;
+    return r;
+}
+
+static __device__ __forceinline__ void df2_acc(df2& acc, df2 p) {
+    float2 s, e;
+    two_sum2(acc.h, p.h, s, e);
+    acc.h = s;
+    acc.l = add2(acc.l, add2(e, p.l));
+}
+
+static __device__ __forceinline__ void df2_dec(df2& acc, df2 p) {
+    float2 s, e;
+    two_diff2(acc.h, p.h, s, e);
+    acc.h = s;
+    acc.l = sub2(acc.l, sub2(p.l, e));
+}
+
 }  // namespace gnk

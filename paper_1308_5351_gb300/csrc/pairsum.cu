@@ -288,6 +288,129 @@ __global__ void __launch_bounds__(kThreads32) pairsum32_kernel(Pair32Args a) {
     }
 }
 
+// Packed FP32 variant: each thread owns 2 x kPairs32 targets, two per float2
+// (x and y lanes); sources are stored duplicated so that one packed
+// instruction serves both lanes.
+constexpr int kPairs32 = kTargets32 / 2;
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads32) pairsum32x2_kernel(Pair32Args a) {
+    constexpr int S = kSrcTile32, NT = kThreads32, P = kPairs32;
+    static_assert(S == NT, "one source per thread per tile load");
+    __shared__ float4 s_o[S];          // (ox, ox, oy, oy)
+    __shared__ float4 s_w[R][S];       // (wx, wx, wy, wy)
+    if (a.done != nullptr && *a.done) return;
+    const int N = a.N;
+    const int tgt0 = blockIdx.x * (NT * kTargets32);
+    float4 th[2 * P];
+    int idx[2 * P];
+    float2 ax[P][R], ay[P][R];
+#pragma unroll
+    for (int t = 0; t < 2 * P; ++t) {
+        idx[t] = tgt0 + t * NT + threadIdx.x;
+        th[t] = a.et32[min(idx[t], N - 1)];
+    }
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) ax[u][r] = ay[u][r] = f2(0.f);
+    const int tb = blockIdx.y * a.tiles_per_chunk;
+    const int te = min(tb + a.tiles_per_chunk, a.tiles_src);
+    for (int tile = tb; tile < te; ++tile) {
+        const int j0 = tile * S;
+        const float4 ref = a.ref32[tile];
+        float2 ox[P], oy[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const float4 ta = th[2 * u], tb2 = th[2 * u + 1];
+            ox[u] = make_float2((ta.x - ref.x) + (ta.z - ref.z), (tb2.x - ref.x) + (tb2.z - ref.z));
+            oy[u] = make_float2((ta.y - ref.y) + (ta.w - ref.w), (tb2.y - ref.y) + (tb2.w - ref.w));
+        }
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            const int j = j0 + k;
+            if (j < N) {
+                const float2 off = a.off32[j];
+                s_o[k] = make_float4(off.x, off.x, off.y, off.y);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float2 w;
+                    if (MODE == W_COMPLEX) {
+                        const double2 wd = (r == 0) ? a.w0[j] : a.w1[j];
+                        w = make_float2((float)wd.x, (float)wd.y);
+                    } else {
+                        const float2 sc = a.s32[j];
+                        const float xv = (float)((r == 0) ? a.x0[j] : a.x1[j]);
+                        w = make_float2(sc.x * xv, sc.y * xv);
+                    }
+                    s_w[r][k] = make_float4(w.x, w.x, w.y, w.y);
+                }
+            } else {
+                s_o[k] = make_float4(kFar32, kFar32, kFar32, kFar32);
+#pragma unroll
+                for (int r = 0; r < R; ++r) s_w[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const bool diag = (j0 < tgt0 + NT * kTargets32) && (tgt0 < j0 + S);
+        if (!diag) {
+#pragma unroll 4
+            for (int k = 0; k < S; ++k) {
+                const float4 so = s_o[k];
+                const float2 sx = make_float2(so.x, so.y), sy = make_float2(so.z, so.w);
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    const float2 dx = sub2(ox[u], sx), dy = sub2(oy[u], sy);
+                    const float2 r2 = fma2(dy, dy, mul2(dx, dx));
+                    const float2 inv = make_float2(recip_f32(r2.x), recip_f32(r2.y));
+                    const float2 ar = mul2(dx, inv), ai = mul2(dy, inv);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float4 w = s_w[r][k];
+                        const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+                        ax[u][r] = fma2(wx, ar, fma2(wy, ai, ax[u][r]));
+                        ay[u][r] = fma2(wy, ar, fma2(neg2(wx), ai, ay[u][r]));
+                    }
+                }
+            }
+        } else {
+            for (int k = 0; k < S; ++k) {
+                const float4 so = s_o[k];
+                const float2 sx = make_float2(so.x, so.y), sy = make_float2(so.z, so.w);
+                const int j = j0 + k;
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    const float2 dx = sub2(ox[u], sx), dy = sub2(oy[u], sy);
+                    const float2 r2 = fma2(dy, dy, mul2(dx, dx));
+                    float i0 = recip_f32(r2.x), i1 = recip_f32(r2.y);
+                    i0 = (j == idx[2 * u]) ? 0.f : i0;
+                    i1 = (j == idx[2 * u + 1]) ? 0.f : i1;
+                    const float2 inv = make_float2(i0, i1);
+                    const float2 ar = mul2(dx, inv), ai = mul2(dy, inv);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float4 w = s_w[r][k];
+                        const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+                        ax[u][r] = fma2(wx, ar, fma2(wy, ai, ax[u][r]));
+                        ay[u][r] = fma2(wy, ar, fma2(neg2(wx), ai, ay[u][r]));
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (idx[2 * u] < N)
+                a.partial[((size_t)blockIdx.y * R + r) * N + idx[2 * u]] = make_float2(ax[u][r].x, ay[u][r].x);
+            if (idx[2 * u + 1] < N)
+                a.partial[((size_t)blockIdx.y * R + r) * N + idx[2 * u + 1]] = make_float2(ax[u][r].y, ay[u][r].y);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ double-float (df32)
 // (arithmetic helpers in pairmath.cuh)
 struct PairDFArgs {
@@ -413,6 +536,119 @@ __global__ void __launch_bounds__(kThreadsDF) pairsumdf_kernel(PairDFArgs a) {
                 a.partial[((size_t)blockIdx.y * R + r) * N + idx[t]] =
                     make_float4(acc_re[t][r].h, acc_re[t][r].l, acc_im[t][r].h, acc_im[t][r].l);
         }
+    }
+}
+
+// Packed variant: each thread owns two targets held in the x and y lanes of
+// float2 registers; every double-float operation of a pair is one packed
+// instruction for both targets.  Source values are stored duplicated (v, v)
+// in shared memory so that they broadcast to both lanes.
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreadsDF) pairsumdf2_kernel(PairDFArgs a) {
+    constexpr int S = kSrcTile32, NT = kThreadsDF;
+    static_assert(S == NT, "one source per thread per tile load");
+    static_assert(kTargetsDF == 2, "two targets per thread, one per lane");
+    __shared__ float4 s_off[2][S];       // (xh, xh, yh, yh), (xl, xl, yl, yl)
+    __shared__ float4 s_w[R][2][S];      // (wxh, wxh, wxl, wxl), (wyh, wyh, wyl, wyl)
+    if (a.done != nullptr && *a.done) return;
+    const int N = a.N;
+    const int tgt0 = blockIdx.x * (NT * 2);
+    const int i0 = tgt0 + threadIdx.x, i1 = tgt0 + NT + threadIdx.x;
+    const double2 p0 = a.et[min(i0, N - 1)], p1 = a.et[min(i1, N - 1)];
+    df2 are[R], aim[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        are[r] = df2{f2(0.f), f2(0.f)};
+        aim[r] = df2{f2(0.f), f2(0.f)};
+    }
+    const int tb = blockIdx.y * a.tiles_per_chunk;
+    const int te = min(tb + a.tiles_per_chunk, a.tiles_src);
+    for (int tile = tb; tile < te; ++tile) {
+        const int j0 = tile * S;
+        const double2 ref = a.ref64[tile];
+        const df ox0 = df_split(p0.x - ref.x), ox1 = df_split(p1.x - ref.x);
+        const df oy0 = df_split(p0.y - ref.y), oy1 = df_split(p1.y - ref.y);
+        const float2 oxh = make_float2(ox0.h, ox1.h), oxl = make_float2(ox0.l, ox1.l);
+        const float2 oyh = make_float2(oy0.h, oy1.h), oyl = make_float2(oy0.l, oy1.l);
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            const int j = j0 + k;
+            if (j < N) {
+                const float4 o = a.offdf[j];
+                s_off[0][k] = make_float4(o.x, o.x, o.y, o.y);
+                s_off[1][k] = make_float4(o.z, o.z, o.w, o.w);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double2 w;
+                    if (MODE == W_COMPLEX) {
+                        w = (r == 0) ? a.w0[j] : a.w1[j];
+                    } else {
+                        const double2 sc = a.s[j];
+                        const double x = (r == 0) ? a.x0[j] : a.x1[j];
+                        w = make_double2(sc.x * x, sc.y * x);
+                    }
+                    const df wx = df_split(w.x), wy = df_split(w.y);
+                    s_w[r][0][k] = make_float4(wx.h, wx.h, wx.l, wx.l);
+                    s_w[r][1][k] = make_float4(wy.h, wy.h, wy.l, wy.l);
+                }
+            } else {
+                s_off[0][k] = make_float4(kFar32, kFar32, kFar32, kFar32);
+                s_off[1][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    s_w[r][0][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    s_w[r][1][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        __syncthreads();
+        const bool diag = (j0 < tgt0 + NT * 2) && (tgt0 < j0 + S);
+#pragma unroll 2
+        for (int k = 0; k < S; ++k) {
+            const float4 oa = s_off[0][k], ob = s_off[1][k];
+            const df2 dx = df2_sub(oxh, oxl, make_float2(oa.x, oa.y), make_float2(ob.x, ob.y));
+            const df2 dy = df2_sub(oyh, oyl, make_float2(oa.z, oa.w), make_float2(ob.z, ob.w));
+            const float2 px = mul2(dx.h, dx.h);
+            float2 ex = fma2(dx.h, dx.h, neg2(px));
+            ex = fma2(dx.h, add2(dx.l, dx.l), ex);
+            const float2 py = mul2(dy.h, dy.h);
+            float2 ey = fma2(dy.h, dy.h, neg2(py));
+            ey = fma2(dy.h, add2(dy.l, dy.l), ey);
+            float2 rh, re;
+            two_sum2(px, py, rh, re);
+            const float2 rl = add2(add2(ex, ey), re);
+            float y0 = recip_f32(rh.x), y1 = recip_f32(rh.y);
+            if (diag) {  // the i = j term is excluded (Eq. fmm-E)
+                y0 = (j0 + k == i0) ? 0.f : y0;
+                y1 = (j0 + k == i1) ? 0.f : y1;
+            }
+            const float2 y = make_float2(y0, y1);
+            float2 e = fma2(neg2(rh), y, f2(1.0f));
+            e = fma2(neg2(rl), y, e);
+            const df2 inv{y, mul2(y, e)};
+            const df2 ar = df2_mul(dx, inv);  // 1/d = ar - i ai
+            const df2 ai = df2_mul(dy, inv);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float4 wa = s_w[r][0][k], wb = s_w[r][1][k];
+                const df2 wx{make_float2(wa.x, wa.y), make_float2(wa.z, wa.w)};
+                const df2 wy{make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+                df2_acc(are[r], df2_mul(wx, ar));
+                df2_acc(are[r], df2_mul(wy, ai));
+                df2_acc(aim[r], df2_mul(wy, ar));
+                df2_dec(aim[r], df2_mul(wx, ai));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (i0 < N)
+            a.partial[((size_t)blockIdx.y * R + r) * N + i0] =
+                make_float4(are[r].h.x, are[r].l.x, aim[r].h.x, aim[r].l.x);
+        if (i1 < N)
+            a.partial[((size_t)blockIdx.y * R + r) * N + i1] =
+                make_float4(are[r].h.y, are[r].l.y, aim[r].h.y, aim[r].l.y);
     }
 }
 
@@ -691,7 +927,16 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     }
     dim3 grid(p.tiles_tgt, p.chunks);
     const ProfToken tok = prof_begin(st);
-    if (job.R == 1 && job.mode == W_SCALED)
+    if (!b.f32_scalar) {
+        if (job.R == 1 && job.mode == W_SCALED)
+            pairsum32x2_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+        else if (job.R == 1)
+            pairsum32x2_kernel<1, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+        else if (job.mode == W_SCALED)
+            pairsum32x2_kernel<2, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+        else
+            pairsum32x2_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+    } else if (job.R == 1 && job.mode == W_SCALED)
         pairsum32_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
     else if (job.R == 1)
         pairsum32_kernel<1, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
@@ -726,7 +971,16 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.done = job.done;
     dim3 grid(p.tiles_tgt, p.chunks);
     const ProfToken tok = prof_begin(st);
-    if (job.R == 1 && job.mode == W_SCALED)
+    if (!b.df_scalar) {
+        if (job.R == 1 && job.mode == W_SCALED)
+            pairsumdf2_kernel<1, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+        else if (job.R == 1)
+            pairsumdf2_kernel<1, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+        else if (job.mode == W_SCALED)
+            pairsumdf2_kernel<2, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+        else
+            pairsumdf2_kernel<2, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+    } else if (job.R == 1 && job.mode == W_SCALED)
         pairsumdf_kernel<1, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
     else if (job.R == 1)
         pairsumdf_kernel<1, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
