@@ -260,6 +260,28 @@ int gnk_fbie_backward(const gnk_boundary* b, const double* mu, const double* gam
                       gnk_result* info, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Cauchy integral formula with singularity subtraction (Sec. 5, Eqs. cauchy4
+ * and cauchy6): values at points z of G of the function f analytic in G whose
+ * boundary values f(eta_j) are given, from the trapezoidal sums
+ *   S1(z) = sum_j f_j eta'_j / (z - eta_j),   S2(z) = sum_j eta'_j / (z - eta_j)
+ * over all N nodes of the handle:
+ *   bounded G:   f(z) = S1 / S2,
+ *   unbounded G: f(z) = (f_inf - S1 / (n i)) / (1 - S2 / (n i)).
+ * z (nz points) and fz are interleaved complex arrays of 2 nz doubles, f of
+ * 2N doubles; host or device pointers (host arrays are copied through a
+ * temporary device buffer).  finf (2 doubles: f at infinity) is read on the
+ * host and used only for unbounded G; NULL means 0.  precision: GNK_PREC_FP64
+ * or GNK_PREC_DF32.  Points on the boundary itself are not excluded: a point
+ * equal to a node returns a non-finite value there.  nz == 0 returns GNK_OK
+ * without a launch and reads no array; nz < 0, NULL arrays (nz > 0) or
+ * another precision return GNK_EINVAL.  Allocates a temporary workspace of 2 nz x (<= 32 chunks)
+ * complex partial sums and synchronises `stream` before returning.
+ * ------------------------------------------------------------------------- */
+int gnk_cauchy_eval(const gnk_boundary* b, int nz, const double* z,
+                    const double* f, const double* finf, double* fz,
+                    int precision, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched FBIE over many independent domains and right-hand sides (no
  * counterpart in the paper: many instances of Sec. 3 solved together).
  *

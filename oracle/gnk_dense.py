@@ -337,3 +337,29 @@ def fbie_gradient(et, etp, A, n, gam, g_mu, g_h):
     d_A = (CZ.sum(axis=1) - CZ.sum(axis=0)) / A
     g_gam = -0.5 * (K.T @ g_h) - M.T @ lam
     return np.conj(d_et), np.conj(d_etp), np.conj(d_A), g_gam, mu, h
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5: the Cauchy integral formula with singularity subtraction
+# ---------------------------------------------------------------------------
+
+def cauchy_formula(et, etp, n, f_nodes, z, bounded, finf=0.0):
+    """f(z) from its boundary values by the ratio forms of Eq. (cauchy4):
+    bounded G:   f(z) = sum_j f_j eta'_j/(eta_j - z) / sum_j eta'_j/(eta_j - z),
+    unbounded G: f(z) = (f_inf + (1/(n i)) sum_j f_j eta'_j/(eta_j - z))
+                        / (1 + (1/(n i)) sum_j eta'_j/(eta_j - z)).
+    Direct sums over all nodes for each point z (z off the boundary)."""
+    et = np.asarray(et, dtype=np.complex128)
+    etp = np.asarray(etp, dtype=np.complex128)
+    f_nodes = np.asarray(f_nodes, dtype=np.complex128)
+    z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+    out = np.empty(z.shape, dtype=np.complex128)
+    for k, zk in enumerate(z):
+        c = etp / (et - zk)
+        s1 = np.sum(f_nodes * c)
+        s2 = np.sum(c)
+        if bounded:
+            out[k] = s1 / s2
+        else:
+            out[k] = (finf + s1 / (n * 1j)) / (1.0 + s2 / (n * 1j))
+    return out

@@ -601,6 +601,48 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
     return s;
 }
 
+int gnk_cauchy_eval(const gnk_boundary* hd, int nz, const double* z, const double* f, const double* finf,
+                    double* fz, int precision, void* stream) {
+    cudaGetLastError();
+    GNK_TRY(check_handle(hd));
+    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
+        set_error("gnk_cauchy_eval: precision must be GNK_PREC_FP64 or GNK_PREC_DF32, got %d", precision);
+        return GNK_EINVAL;
+    }
+    if (nz < 0) {
+        set_error("gnk_cauchy_eval: nz = %d < 0", nz);
+        return GNK_EINVAL;
+    }
+    if (nz == 0) return GNK_OK;
+    if (!z || !f || !fz) {
+        set_error("gnk_cauchy_eval: NULL array");
+        return GNK_EINVAL;
+    }
+    const Boundary& b = hd->b;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double2 fi = finf ? make_double2(finf[0], finf[1]) : make_double2(0.0, 0.0);
+    DevArr v[3];
+    const void* src[3] = {z, f, fz};
+    const size_t sz[3] = {2 * sizeof(double) * (size_t)nz, 2 * sizeof(double) * (size_t)b.N,
+                          2 * sizeof(double) * (size_t)nz};
+    int rc = GNK_OK;
+    for (int k = 0; k < 3 && rc == GNK_OK; ++k) rc = dev_view(src[k], sz[k], k < 2, st, &v[k]);
+    if (rc == GNK_OK)
+        rc = cauchy_eval(b, nz, (const double2*)v[0].dev, (const double2*)v[1].dev, fi, (double2*)v[2].dev,
+                         precision, st);
+    if (rc == GNK_OK && v[2].tmp) {
+        if (cudaMemcpyAsync(v[2].user, v[2].dev, v[2].bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("gnk_cauchy_eval: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = GNK_ECUDA;
+        }
+    }
+    if (rc != GNK_OK) cudaStreamSynchronize(st);
+    for (int k = 0; k < 3; ++k)
+        if (v[k].tmp) cudaFree(v[k].dev);
+    return rc;
+}
+
 int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,
                   void* stream) {
     GNK_TRY(check_handle(h));

@@ -252,6 +252,10 @@ int fbie_backward(const Boundary& b, const double* mu, const double* gam, const 
                   const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
                   const gnk_options& opt, gnk_result* info, cudaStream_t st);
 
+// ---------------------------------------------------------------- Cauchy formula (cauchy_eval.cu)
+int cauchy_eval(const Boundary& b, int M, const double2* z, const double2* f, double2 finf, double2* out,
+                int precision, cudaStream_t st);
+
 }  // namespace gnk
 
 struct gnk_boundary {

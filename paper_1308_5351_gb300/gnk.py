@@ -45,6 +45,7 @@ EXPORTED = (
     "gnk_profile_query", "gnk_profile_query_ex", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
+    "gnk_cauchy_eval",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
     lib.gnk_profile_query_ex.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
+    lib.gnk_cauchy_eval.argtypes = [P, I, P, P, P, P, I, P]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -266,6 +268,17 @@ def gnk_cauchy_sum_noalloc(N, et, w, z, stream=None):
                                                 _ptr(z, True), _stream(stream)))
 
 
+def gnk_cauchy_eval(h, z, f, fz, finf=None, precision=GNK_PREC_FP64, stream=None):
+    """fz = f(z) at points z of G by the Cauchy integral formula (Eqs. cauchy4, cauchy6)."""
+    fi = None
+    if finf is not None:
+        c = complex(finf)
+        fi = (ctypes.c_double * 2)(c.real, c.imag)
+    nz = int(z.numel() if torch is not None and isinstance(z, torch.Tensor) else z.size)
+    return _check(load().gnk_cauchy_eval(h, nz, _ptr(z, True), _ptr(f, True), fi, _ptr(fz, True),
+                                         int(precision), _stream(stream)))
+
+
 def gnk_apply_IminusN(h, x, y, precision=GNK_PREC_FP64, stream=None):
     return _check(load().gnk_apply_IminusN(h, _ptr(x), _ptr(y), int(precision), _stream(stream)))
 
@@ -377,6 +390,13 @@ class Boundary:
                                               torch.complex128 if torch is not None else None)
         gnk_cauchy_sum(self.handle, w, z, precision, stream)
         return z
+
+    def cauchy_eval(self, z, f_nodes, finf=None, precision=GNK_PREC_FP64, out=None, stream=None):
+        """f at the points z of G from its boundary values f_nodes (complex, N)."""
+        fz = out if out is not None else _like(z, tuple(z.shape), np.complex128,
+                                               torch.complex128 if torch is not None else None)
+        gnk_cauchy_eval(self.handle, z, f_nodes, fz, finf, precision, stream)
+        return fz
 
     def _unary(self, fn, x, precision, out, stream):
         y = out if out is not None else _real_like(x, self.N)
