@@ -17,6 +17,9 @@ with the generalized Neumann kernel"):
   * h                                      Sec. 3.6, Eq. (bh)
   * adjoint: e, B^T, P-hat, system         Sec. 4, Eqs. (ei2), (bve), (sys*)
   * Neumann kernel N_k and N_g(t,t)        Sec. 4.1, Eqs. (Nk), (Ng-tt)
+  * variant without singularity subtraction Sec. 7 (Ex. 2), Eqs. (ie-sys), (phi-kp),
+                                           (N-tt), (M1-tt)
+  * Cauchy integral formula                Sec. 5, Eqs. (cauchy4), (cauchy6)
 
 Readings of the paper taken here (each is listed with its reason in the design
 notes of the repository):
@@ -26,6 +29,9 @@ notes of the repository):
     (eta''/eta' is real along a straight edge and A'/A -> 0).
   * h is returned as the full node vector of Eq. (bh); h_k is its mean on
     component k.
+  * Without singularity subtraction, M keeps Wittich's rule for its cotangent
+    part (the method of Eq. (phi-kp) applied to gamma itself), and at a corner
+    node both parts of eta''/eta' take the value 0, as in the diagonal above.
 
 Parity: every function here is pinned by tests/test_oracle_pins.py against
 closed forms (disk, unit circle), manufactured analytic solutions, the
@@ -242,6 +248,72 @@ def matrix_adjoint(et, etp, etpp, A, Ap, n, c):
 def solve_adjoint_ie(et, etp, etpp, A, Ap, n, c, gam):
     """mu solving (diag(e) + B^T + P-hat) mu = gamma (Eq. sys*), by LU."""
     return np.linalg.solve(matrix_adjoint(et, etp, etpp, A, Ap, n, c),
+                           np.asarray(gam, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 7, Ex. 2 comparison: the same Nystrom method without singularity
+# subtraction.  The kernels keep their diagonal values (Eqs. N-tt, M1-tt)
+# instead of the row-sum terms of Eqs. (ie-m), (ie-phi).
+# ---------------------------------------------------------------------------
+
+def matrix_IminusN_plain(et, etp, etpp, A, Ap, n):
+    """I - N by the trapezoidal rule with N(t_i, t_i) of Eq. (N-tt) on the
+    diagonal: (I - N)_ij = delta_ij - (2 pi/n) N(t_i, t_j)."""
+    B, _ = matrices_BD(et, etp, A, n)
+    Nd = (2.0 * math.pi / n) * kernel_N_diag(etp, etpp, A, Ap)
+    return np.eye(B.shape[0]) - B - np.diag(Nd)
+
+
+def matrix_M_plain(et, etp, etpp, A, Ap, n):
+    """M discretised term by term as in Eq. (phi-kp) but applied to gamma itself
+    (no gamma(s) subtracted): on the block of a component, Wittich's matrix -K
+    for the cotangent part plus the trapezoidal rule for M_1 of Eq. (M-M1),
+    with M_1(t, t) of Eq. (M1-tt) on the diagonal; off the block the
+    trapezoidal rule for M."""
+    N, m1 = _sizes(et, n)
+    _, D = matrices_BD(et, etp, A, n)      # D_ij = (2 pi/n) M(t_i, t_j), i != j
+    p = np.arange(n)
+    d = p[:, None] - p[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        cot = np.where(d == 0, 0.0, 1.0 / np.tan(d * math.pi / n))
+    wittich = np.where(d % 2 != 0, (2.0 / n) * cot, 0.0)        # K_pq
+    M1d = (2.0 * math.pi / n) * kernel_M1_diag(etp, etpp, A, Ap)
+    out = D.copy()
+    for k in range(m1):
+        blk = slice(k * n, (k + 1) * n)
+        # (2 pi/n) M1(s_p, s_q) = (2 pi/n) M(s_p, s_q) + (1/n) cot((p - q) pi / n), p != q
+        m1_blk = D[blk, blk] + cot / n
+        out[blk, blk] = -wittich + m1_blk + np.diag(M1d[blk])
+    return out
+
+
+def fbie_plain(et, etp, etpp, A, Ap, n, gam):
+    """mu of (I - N) mu = -M gamma and h = (M mu - (I - N) gamma)/2 with the
+    plain matrices above, by LU.  Returns (mu, h, h_k)."""
+    N, m1 = _sizes(et, n)
+    K = matrix_IminusN_plain(et, etp, etpp, A, Ap, n)
+    M = matrix_M_plain(et, etp, etpp, A, Ap, n)
+    gam = np.asarray(gam, dtype=np.float64)
+    mu = np.linalg.solve(K, -(M @ gam))
+    h = (M @ mu - K @ gam) / 2.0
+    return mu, h, h.reshape(m1, n).mean(axis=1)
+
+
+def matrix_adjoint_plain(et, etp, etpp, A, Ap, n):
+    """I + N* + J by the trapezoidal rule: N*(s, t) = N(t, s) (Eq. Nt-N*), so the
+    off-diagonal part is B^T and the diagonal is N(t, t) (Eq. N-tt); J gives
+    P-hat."""
+    N, m1 = _sizes(et, n)
+    B, _ = matrices_BD(et, etp, A, n)
+    Nd = (2.0 * math.pi / n) * kernel_N_diag(etp, etpp, A, Ap)
+    P = np.kron(np.eye(m1), np.full((n, n), 1.0 / n))
+    return np.eye(N) + np.diag(Nd) + B.T + P
+
+
+def solve_adjoint_plain(et, etp, etpp, A, Ap, n, gam):
+    """mu solving (I + N* + J) mu = gamma with the plain matrix, by LU."""
+    return np.linalg.solve(matrix_adjoint_plain(et, etp, etpp, A, Ap, n),
                            np.asarray(gam, dtype=np.float64))
 
 
