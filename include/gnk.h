@@ -148,6 +148,18 @@ int gnk_build_boundary(gnk_boundary** out, int m1, int n,
  * gnk_fbie on a handle without eta'' forms Eone together with E(q gamma) in a
  * single two-right-hand-side launch. */
 #define GNK_BUILD_DEFER 0x100
+/* With GNK_BUILD_PLAIN or-ed into `precision`, the handle holds the Nystrom
+ * discretisation WITHOUT singularity subtraction (the comparison of Sec. 7,
+ * Ex. 2): the trapezoidal rule keeps the kernels' diagonal values N(t,t) and
+ * M_1(t,t) (Eqs. N-tt, M1-tt), and every operator and solver of the handle uses
+ *   I - N      ->  I - B - diag((2 pi/n) N(t,t)),
+ *   M          ->  D + L-hat + diag((2 pi/n) M_1(t,t)),
+ *   I + N* + J ->  I + diag((2 pi/n) N(t,t)) + B^T + P-hat
+ * in place of Eqs. sys, y and sys*.  Needs etpp (Ap NULL means A' = 0); no
+ * precomputed Cauchy sum is formed.  At a graded-mesh corner (eta' = 0) both
+ * parts of eta''/eta' are taken as 0.  gnk_fbie_backward rejects such a handle
+ * (GNK_EINVAL): its geometry derivative is that of the subtracted form. */
+#define GNK_BUILD_PLAIN 0x200
 int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n,
                           const double* et, const double* etp, const double* etpp,
                           const double* A, const double* Ap, int bounded,

@@ -153,13 +153,15 @@ int options_from(const gnk_options* in, gnk_options* o) {
 }
 
 int build(Boundary& b, int m1, int n, const double* et, const double* etp, const double* etpp,
-          const double* A, const double* Ap, int bounded, int eone_prec, int defer, cudaStream_t st) {
+          const double* A, const double* Ap, int bounded, int eone_prec, int defer, int plain,
+          cudaStream_t st) {
     const size_t N = (size_t)m1 * n;
     b.m1 = m1;
     b.n = n;
     b.N = (int)N;
     b.bounded = bounded ? 1 : 0;
     b.has_adjoint = etpp != nullptr;
+    b.plain = plain;
     GNK_TRY_CUDA(cudaGetDevice(&b.device));
     GNK_TRY_CUDA(cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, b.device));
 
@@ -246,6 +248,13 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     }
 
 
+    b.eone_prec = eone_prec;
+    if (plain) {
+        // the diagonals came from the geometry preparation; no Cauchy sum is needed
+        GNK_TRY_CUDA(cudaMemsetAsync(b.Eone, 0, N * sizeof(double2), st));
+        GNK_TRY_CUDA(cudaStreamSynchronize(st));
+        return GNK_OK;
+    }
     // Eone = E q with diag(B1), diag(D1); with eta'' also E eta' and e (Eq. bve)
     PairJob j;
     j.R = b.has_adjoint ? 2 : 1;
@@ -257,7 +266,6 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     j.out = b.b1;
     j.out2 = b.d1;
     j.out3 = b.e;
-    b.eone_prec = eone_prec;
     if (defer) {
         b.eone_pending = 1;  // formed by the first call that needs them
         return GNK_OK;
@@ -307,10 +315,15 @@ int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, c
                           const double* etpp, const double* A, const double* Ap, int bounded,
                           int precision, void* stream) {
     const int defer = (precision & GNK_BUILD_DEFER) ? 1 : 0;
-    precision &= ~GNK_BUILD_DEFER;
+    const int plain = (precision & GNK_BUILD_PLAIN) ? 1 : 0;
+    precision &= ~(GNK_BUILD_DEFER | GNK_BUILD_PLAIN);
     if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
         set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64 or GNK_PREC_DF32 "
-                  "(optionally | GNK_BUILD_DEFER)");
+                  "(optionally | GNK_BUILD_DEFER | GNK_BUILD_PLAIN)");
+        return GNK_EINVAL;
+    }
+    if (plain && !etpp) {
+        set_error("gnk_build_boundary_ex: GNK_BUILD_PLAIN needs eta'' (the diagonal N(t,t))");
         return GNK_EINVAL;
     }
     if (!out || !et || !etp || !A) {
@@ -332,7 +345,7 @@ int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, c
         set_error("host allocation failed");
         return GNK_ENOMEM;
     }
-    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, precision, defer,
+    const int s = build(h->b, m1, n, et, etp, etpp, A, Ap, bounded, precision, defer, plain,
                         (cudaStream_t)stream);
     if (s != GNK_OK) {
         release(h->b);
@@ -565,6 +578,10 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
     GNK_TRY(check_handle(hd));
     if (!mu || !gam || !grad_mu || !grad_h || !grad_et || !grad_etp || !grad_A || !grad_gam) {
         set_error("NULL array");
+        return GNK_EINVAL;
+    }
+    if (hd->b.plain) {
+        set_error("gnk_fbie_backward: the handle holds the form without singularity subtraction");
         return GNK_EINVAL;
     }
     gnk_options o;

@@ -127,7 +127,10 @@ struct PrepArgs {
     float2* A32;
     double2* ref64;
     float4* offdf;
-    double* ediag;       // (2/n) Im(eta''/eta' - A'/A), corner limit 0
+    double* ediag;       // (2/n) Im(eta''/eta' - A'/A), corner limit 0; plain form: 1 + Nd
+    int plain;           // plain form: also writes b1 = -1 - Nd and d1 = -M1d
+    double* b1;
+    double* d1;
     double* ones;        // nullable: filled with 1
     int* flag;           // bit 1: non-finite input, bit 2: A == 0
 };
@@ -176,7 +179,18 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
         // Im(eta''/eta') = Im(eta'' conj(eta')) / |eta'|^2 ; Im(A'/A) likewise
         const double im1 = (pp > 0.0) ? (epp.y * etp.x - epp.x * etp.y) / pp : 0.0;
         const double im2 = (Ap.y * A.x - Ap.x * A.y) / aa;
-        a.ediag[i] = (2.0 / a.n) * (im1 - im2);
+        if (a.plain) {
+            // (2 pi/n) N(t,t) and (2 pi/n) M_1(t,t) (Eqs. N-tt, M1-tt)
+            const double re1 = (pp > 0.0) ? (epp.x * etp.x + epp.y * etp.y) / pp : 0.0;
+            const double re2 = (Ap.x * A.x + Ap.y * A.y) / aa;
+            const double Nd = (2.0 / a.n) * (0.5 * im1 - im2);
+            const double M1d = (2.0 / a.n) * (0.5 * re1 - re2);
+            a.b1[i] = -1.0 - Nd;   // 2x + b1 x - Bx = (I - B - diag(Nd)) x
+            a.d1[i] = -M1d;        // Dx - d1 x + L x = (D + diag(M1d) + L) x
+            a.ediag[i] = 1.0 + Nd; // e x + B^T x + P x = (I + diag(Nd) + B^T + P) x
+        } else {
+            a.ediag[i] = (2.0 / a.n) * (im1 - im2);
+        }
     }
     if (bad) atomicOr(a.flag, bad);
 }
@@ -228,6 +242,9 @@ int run_prepare_nodes(Boundary& b, const double* etpp, const double* Ap, int* d_
     a.ref64 = b.ref64;
     a.offdf = b.offdf;
     a.ediag = b.e;
+    a.plain = b.plain;
+    a.b1 = b.b1;
+    a.d1 = b.d1;
     a.ones = b.ones;
     a.flag = d_flag;
     prepare_geometry_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);

@@ -181,6 +181,7 @@ struct Boundary {
     int* flag = nullptr;        // input checks of the geometry preparation
     void* arena = nullptr;      // the one allocation that holds the buffers above
     int eone_pending = 0;       // Eone, diag(B1), diag(D1), e not yet formed
+    int plain = 0;              // 1: diagonals of the form without singularity subtraction
     int df_scalar = 0;          // 1: scalar double-float kernel instead of the packed one
     int f32_scalar = 0;         // 1: scalar FP32 kernel instead of the packed one
     double* means = nullptr;    // m1

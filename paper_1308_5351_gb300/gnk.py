@@ -36,6 +36,7 @@ GNK_PREC_FP32 = 2
 GNK_PREC_DF32 = 3
 GNK_PREC_MIXED_DF = 4
 GNK_BUILD_DEFER = 0x100
+GNK_BUILD_PLAIN = 0x200
 
 EXPORTED = (
     "gnk_default_options", "gnk_last_error", "gnk_version", "gnk_build_boundary",
@@ -360,7 +361,13 @@ class Boundary:
         self.handle = gnk_build_boundary_ex(m1, n, et, etp, A, etpp, Ap, bounded, precision, stream)
 
     @classmethod
-    def from_domain(cls, dom, adjoint=True, device=None, stream=None, precision=GNK_PREC_FP64):
+    def from_domain(cls, dom, adjoint=True, device=None, stream=None, precision=GNK_PREC_FP64,
+                    plain=False):
+        """plain=True: the discretisation without singularity subtraction (needs
+        eta'', so adjoint is implied)."""
+        if plain:
+            adjoint = True
+            precision |= GNK_BUILD_PLAIN
         arrs = [dom.et, dom.etp, dom.A, dom.etpp if adjoint else None, dom.Ap if adjoint else None]
         if device is not None:
             arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a), device=device)

@@ -151,3 +151,100 @@ def test_planted_mistakes_are_caught(monkeypatch):
         assert not _plain_pins_pass(), name
         monkeypatch.undo()
     assert O.kernel_N_diag is orig_N and O.kernel_M1_diag is orig_M1
+
+
+# ------------------------------------------------------------------ GPU
+torch = pytest.importorskip("torch")
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1308_5351_gb300 import build, gnk
+    build.build()
+    gnk.load()
+    return gnk
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _plain_domains():
+    rng = np.random.default_rng(11)
+    ell = Dm.random_ellipses(rng, 5, 1.6)
+    return {
+        "three_circles_n170": Dm.three_circles(170),                  # ragged, direct circulant
+        "ellipses5_n512": Dm.build_domain(ell, 512, bounded=False),   # unbounded, odd m+1
+        "graded_square_n128": Dm.build_domain([Dm.Circle(0j, 1.6, ccw=True),
+                                               Dm.square(0.3 + 0.1j, 0.5, ccw=False)], 128,
+                                              bounded=True, alpha=-1.2 + 0.3j),
+        "ex2_theta_n64": Dm.ex2_circles(0.1, 64, theta=[math.pi / 2, 0, math.pi / 2, 0, math.pi / 2]),
+    }
+
+
+PDOMS = _plain_domains()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", list(PDOMS))
+def test_plain_operators_match_oracle(G, name):
+    """Tolerance as for the subtracted operators: 4 (64 + N) u max(|A| |x|)."""
+    d = PDOMS[name]
+    x = np.random.default_rng(5).normal(size=d.N)
+    mats = {"IminusN": O.matrix_IminusN_plain(*_args(d)), "M": O.matrix_M_plain(*_args(d)),
+            "adjoint": O.matrix_adjoint_plain(*_args(d))}
+    with G.Boundary.from_domain(d, device="cuda", plain=True) as b:
+        xd = _dev(x)
+        got = {"IminusN": _host(b.apply_IminusN(xd)), "M": _host(b.apply_M(xd)),
+               "adjoint": _host(b.apply_adjoint(xd))}
+    for key, A in mats.items():
+        tol = 4 * (64 + d.N) * U64 * (np.abs(A) @ np.abs(x)).max()
+        err = np.abs(got[key] - A @ x).max()
+        assert err <= tol, (name, key, err, tol)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["three_circles_n170", "ellipses5_n512", "ex2_theta_n64"])
+@pytest.mark.parametrize("prec", [0, 4])
+def test_plain_fbie_and_adjoint_match_oracle(G, name, prec):
+    """mu within 1e-10 relative of the oracle's LU solution, h within 1e-10 of
+    max(1, |h|_inf), in FP64 and in FP32 GMRES with double-float refinement."""
+    d = PDOMS[name]
+    gam = np.log(np.abs(d.et - (d.holes[0] if d.holes else 0.05j)))
+    mu_ref, h_ref, hk_ref = O.fbie_plain(*_args(d), gam)
+    phi_ref = O.solve_adjoint_plain(*_args(d), gam)
+    bp = G.GNK_PREC_DF32 if prec == 4 else G.GNK_PREC_FP64
+    with G.Boundary.from_domain(d, device="cuda", plain=True, precision=bp) as b:
+        mu, h, hk, res = b.fbie(_dev(gam), tol=1e-12, precision=prec)
+        assert res.status == 0
+        mu2, res2 = b.solve_ie(_dev(gam), tol=1e-12, precision=prec)
+        assert res2.status == 0
+        phi, res3 = b.solve_adjoint_ie(_dev(gam), tol=1e-12, precision=prec)
+        assert res3.status == 0
+        mu, h, hk, mu2, phi = map(_host, (mu, h, hk, mu2, phi))
+    for m in (mu, mu2):
+        assert np.abs(m - mu_ref).max() <= 1e-10 * np.abs(mu_ref).max()
+    hs = max(1.0, np.abs(h_ref).max())
+    assert np.abs(h - h_ref).max() <= 1e-10 * hs and np.abs(hk - hk_ref).max() <= 1e-10 * hs
+    assert np.abs(phi - phi_ref).max() <= 1e-10 * np.abs(phi_ref).max()
+
+
+@pytest.mark.gpu
+def test_plain_needs_second_derivative_and_has_no_gradient(G):
+    d = Dm.three_circles(64)
+    with pytest.raises(G.GnkError):
+        G.gnk_build_boundary_ex(d.m1, d.n, d.et, d.etp, d.A, None, None, True,
+                                G.GNK_PREC_FP64 | G.GNK_BUILD_PLAIN)
+    gam = np.log(np.abs(d.et - 0.05j))
+    with G.Boundary.from_domain(d, device="cuda", plain=True) as b:
+        mu, h, hk, res = b.fbie(_dev(gam))
+        z = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+        zc = torch.zeros(d.N, dtype=torch.complex128, device="cuda")
+        with pytest.raises(G.GnkError):
+            G.gnk_fbie_backward(b.handle, mu, _dev(gam), z, z, zc, zc.clone(), zc.clone(), z.clone(),
+                                G.options())
