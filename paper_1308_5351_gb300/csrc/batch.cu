@@ -1134,7 +1134,7 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
     cudaStreamSynchronize(st);
     cudaFree(flag);
     if (rc != GNK_OK) return fail(rc);
-    if (hflag) {
+    if (hflag & 3) {  // bit 4 (Im A != 0) is information, not an error
         set_error("gnk_build_batch: non-finite geometry or A = 0 at a node");
         return fail(hflag & 1 ? GNK_ENONFINITE : GNK_EINVAL);
     }

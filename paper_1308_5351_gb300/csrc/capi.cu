@@ -246,6 +246,7 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
         set_error("A(t) vanishes at a node");
         return GNK_EINVAL;
     }
+    b.A_real = (flag & 4) ? 0 : 1;
 
 
     b.eone_prec = eone_prec;

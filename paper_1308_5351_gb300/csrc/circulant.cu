@@ -132,7 +132,7 @@ struct PrepArgs {
     double* b1;
     double* d1;
     double* ones;        // nullable: filled with 1
-    int* flag;           // bit 1: non-finite input, bit 2: A == 0
+    int* flag;           // bit 1: non-finite input, bit 2: A == 0, bit 4: Im A != 0
 };
 
 __device__ __forceinline__ float4 split_hilo(double2 z) {
@@ -150,6 +150,7 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
     if (!finite2(et) || !finite2(etp) || !finite2(A)) bad |= 1;
     const double aa = A.x * A.x + A.y * A.y;
     if (aa == 0.0) bad |= 2;
+    if (A.y != 0.0) bad |= 4;  // not an error: A is not real-valued
     // q = eta'/A
     const double2 q = make_double2((etp.x * A.x + etp.y * A.y) / aa, (etp.y * A.x - etp.x * A.y) / aa);
     a.q[i] = q;

@@ -131,6 +131,7 @@ struct PairJob {
     const double* Lx = nullptr;   // EPI_M / EPI_H: Lhat x
     const double* means = nullptr;// EPI_ADJ: per-component means of x
     const int* done = nullptr;    // skip the whole job if *done != 0
+    int comp = 0;                 // set by run_pairsum: 0 both parts, 1 only Im z, 2 only Re z
 };
 
 // ---------------------------------------------------------------- handle
@@ -182,6 +183,7 @@ struct Boundary {
     void* arena = nullptr;      // the one allocation that holds the buffers above
     int eone_pending = 0;       // Eone, diag(B1), diag(D1), e not yet formed
     int plain = 0;              // 1: diagonals of the form without singularity subtraction
+    int A_real = 0;             // 1: Im A = 0 at every node (then f_B needs only Im E(qx))
     int df_scalar = 0;          // 1: scalar double-float kernel instead of the packed one
     int f32_scalar = 0;         // 1: scalar FP32 kernel instead of the packed one
     double* means = nullptr;    // m1

@@ -293,7 +293,35 @@ __global__ void __launch_bounds__(kThreads32) pairsum32_kernel(Pair32Args a) {
 // instruction serves both lanes.
 constexpr int kPairs32 = kTargets32 / 2;
 
-template <int R, int MODE>
+// z += w / d = w conj(d) / |d|^2 for both lanes, inv = 1/|d|^2 (0 for i = j)
+template <int R, int COMP>
+__device__ __forceinline__ void accumulate32(const float4 (*s_w)[kSrcTile32], int k, float2 dx, float2 dy,
+                                             float2 inv, float2* ax, float2* ay) {
+    if (COMP == 0) {
+        const float2 ar = mul2(dx, inv), ai = mul2(dy, inv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 w = s_w[r][k];
+            const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+            ax[r] = fma2(wx, ar, fma2(wy, ai, ax[r]));
+            ay[r] = fma2(wy, ar, fma2(neg2(wx), ai, ay[r]));
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 w = s_w[r][k];
+            const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+            if (COMP == 1)  // Im(w conj d) = wy dx - wx dy
+                ay[r] = fma2(fma2(neg2(wx), dy, mul2(wy, dx)), inv, ay[r]);
+            else            // Re(w conj d) = wx dx + wy dy
+                ax[r] = fma2(fma2(wy, dy, mul2(wx, dx)), inv, ax[r]);
+        }
+    }
+}
+
+// COMP = 1 (2): only Im z (Re z) is formed, 3 instead of 4 + 2 FP32 operations
+// per pair and right-hand side; the other part of the partial sum is written as 0.
+template <int R, int MODE, int COMP>
 __global__ void __launch_bounds__(kThreads32) pairsum32x2_kernel(Pair32Args a) {
     constexpr int S = kSrcTile32, NT = kThreads32, P = kPairs32;
     static_assert(S == NT, "one source per thread per tile load");
@@ -364,14 +392,7 @@ __global__ void __launch_bounds__(kThreads32) pairsum32x2_kernel(Pair32Args a) {
                     const float2 dx = sub2(ox[u], sx), dy = sub2(oy[u], sy);
                     const float2 r2 = fma2(dy, dy, mul2(dx, dx));
                     const float2 inv = make_float2(recip_f32(r2.x), recip_f32(r2.y));
-                    const float2 ar = mul2(dx, inv), ai = mul2(dy, inv);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float4 w = s_w[r][k];
-                        const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
-                        ax[u][r] = fma2(wx, ar, fma2(wy, ai, ax[u][r]));
-                        ay[u][r] = fma2(wy, ar, fma2(neg2(wx), ai, ay[u][r]));
-                    }
+                    accumulate32<R, COMP>(s_w, k, dx, dy, inv, ax[u], ay[u]);
                 }
             }
         } else {
@@ -387,14 +408,7 @@ __global__ void __launch_bounds__(kThreads32) pairsum32x2_kernel(Pair32Args a) {
                     i0 = (j == idx[2 * u]) ? 0.f : i0;
                     i1 = (j == idx[2 * u + 1]) ? 0.f : i1;
                     const float2 inv = make_float2(i0, i1);
-                    const float2 ar = mul2(dx, inv), ai = mul2(dy, inv);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float4 w = s_w[r][k];
-                        const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
-                        ax[u][r] = fma2(wx, ar, fma2(wy, ai, ax[u][r]));
-                        ay[u][r] = fma2(wy, ar, fma2(neg2(wx), ai, ay[u][r]));
-                    }
+                    accumulate32<R, COMP>(s_w, k, dx, dy, inv, ax[u], ay[u]);
                 }
             }
         }
@@ -543,7 +557,7 @@ __global__ void __launch_bounds__(kThreadsDF) pairsumdf_kernel(PairDFArgs a) {
 // float2 registers; every double-float operation of a pair is one packed
 // instruction for both targets.  Source values are stored duplicated (v, v)
 // in shared memory so that they broadcast to both lanes.
-template <int R, int MODE>
+template <int R, int MODE, int COMP>
 __global__ void __launch_bounds__(kThreadsDF) pairsumdf2_kernel(PairDFArgs a) {
     constexpr int S = kSrcTile32, NT = kThreadsDF;
     static_assert(S == NT, "one source per thread per tile load");
@@ -634,10 +648,14 @@ __global__ void __launch_bounds__(kThreadsDF) pairsumdf2_kernel(PairDFArgs a) {
                 const float4 wa = s_w[r][0][k], wb = s_w[r][1][k];
                 const df2 wx{make_float2(wa.x, wa.y), make_float2(wa.z, wa.w)};
                 const df2 wy{make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
-                df2_acc(are[r], df2_mul(wx, ar));
-                df2_acc(are[r], df2_mul(wy, ai));
-                df2_acc(aim[r], df2_mul(wy, ar));
-                df2_dec(aim[r], df2_mul(wx, ai));
+                if (COMP != 1) {
+                    df2_acc(are[r], df2_mul(wx, ar));
+                    df2_acc(are[r], df2_mul(wy, ai));
+                }
+                if (COMP != 2) {
+                    df2_acc(aim[r], df2_mul(wy, ar));
+                    df2_dec(aim[r], df2_mul(wx, ai));
+                }
             }
         }
     }
@@ -927,15 +945,20 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     }
     dim3 grid(p.tiles_tgt, p.chunks);
     const ProfToken tok = prof_begin(st);
+    const int comp = b.f32_scalar ? 0 : job.comp;
     if (!b.f32_scalar) {
-        if (job.R == 1 && job.mode == W_SCALED)
-            pairsum32x2_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+        if (job.R == 1 && job.mode == W_SCALED && comp == 1)
+            pairsum32x2_kernel<1, W_SCALED, 1><<<grid, kThreads32, 0, st>>>(a);
+        else if (job.R == 1 && job.mode == W_SCALED && comp == 2)
+            pairsum32x2_kernel<1, W_SCALED, 2><<<grid, kThreads32, 0, st>>>(a);
+        else if (job.R == 1 && job.mode == W_SCALED)
+            pairsum32x2_kernel<1, W_SCALED, 0><<<grid, kThreads32, 0, st>>>(a);
         else if (job.R == 1)
-            pairsum32x2_kernel<1, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+            pairsum32x2_kernel<1, W_COMPLEX, 0><<<grid, kThreads32, 0, st>>>(a);
         else if (job.mode == W_SCALED)
-            pairsum32x2_kernel<2, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
+            pairsum32x2_kernel<2, W_SCALED, 0><<<grid, kThreads32, 0, st>>>(a);
         else
-            pairsum32x2_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
+            pairsum32x2_kernel<2, W_COMPLEX, 0><<<grid, kThreads32, 0, st>>>(a);
     } else if (job.R == 1 && job.mode == W_SCALED)
         pairsum32_kernel<1, W_SCALED><<<grid, kThreads32, 0, st>>>(a);
     else if (job.R == 1)
@@ -945,9 +968,10 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsum32_kernel<2, W_COMPLEX><<<grid, kThreads32, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    // FP32 pipe per pair: 6 shared + 4 per right-hand side (plus one MUFU reciprocal)
-    prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st,
-             (6.0 + 4.0 * job.R) * b.N * (b.N - 1.0));
+    // FP32 pipe per pair (plus one MUFU reciprocal): 6 shared + 4 per right-hand
+    // side; one part of z only: 4 shared + 3 per right-hand side
+    const double per_pair = (comp && job.R == 1) ? 4.0 + 3.0 : 6.0 + 4.0 * job.R;
+    prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st, per_pair * b.N * (b.N - 1.0));
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st));
     count_launches(2);
     return GNK_OK;
@@ -971,15 +995,20 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.done = job.done;
     dim3 grid(p.tiles_tgt, p.chunks);
     const ProfToken tok = prof_begin(st);
+    const int comp = b.df_scalar ? 0 : job.comp;
     if (!b.df_scalar) {
-        if (job.R == 1 && job.mode == W_SCALED)
-            pairsumdf2_kernel<1, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+        if (job.R == 1 && job.mode == W_SCALED && comp == 1)
+            pairsumdf2_kernel<1, W_SCALED, 1><<<grid, kThreadsDF, 0, st>>>(a);
+        else if (job.R == 1 && job.mode == W_SCALED && comp == 2)
+            pairsumdf2_kernel<1, W_SCALED, 2><<<grid, kThreadsDF, 0, st>>>(a);
+        else if (job.R == 1 && job.mode == W_SCALED)
+            pairsumdf2_kernel<1, W_SCALED, 0><<<grid, kThreadsDF, 0, st>>>(a);
         else if (job.R == 1)
-            pairsumdf2_kernel<1, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+            pairsumdf2_kernel<1, W_COMPLEX, 0><<<grid, kThreadsDF, 0, st>>>(a);
         else if (job.mode == W_SCALED)
-            pairsumdf2_kernel<2, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
+            pairsumdf2_kernel<2, W_SCALED, 0><<<grid, kThreadsDF, 0, st>>>(a);
         else
-            pairsumdf2_kernel<2, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
+            pairsumdf2_kernel<2, W_COMPLEX, 0><<<grid, kThreadsDF, 0, st>>>(a);
     } else if (job.R == 1 && job.mode == W_SCALED)
         pairsumdf_kernel<1, W_SCALED><<<grid, kThreadsDF, 0, st>>>(a);
     else if (job.R == 1)
@@ -989,9 +1018,10 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     else
         pairsumdf_kernel<2, W_COMPLEX><<<grid, kThreadsDF, 0, st>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    // FP32 pipe per pair: 49 shared (d, |d|^2, reciprocal, 1/d) + 48 per right-hand side
-    prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st,
-             (49.0 + 48.0 * job.R) * b.N * (b.N - 1.0));
+    // FP32 pipe per pair: 49 shared (d, |d|^2, reciprocal, 1/d) + 48 per right-hand
+    // side (two products and two compensated sums per part of z)
+    const double per_pair = (comp && job.R == 1) ? 49.0 + 24.0 : 49.0 + 48.0 * job.R;
+    prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st, per_pair * b.N * (b.N - 1.0));
     GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 2, st));
     count_launches(2);
     return GNK_OK;
@@ -1013,10 +1043,21 @@ int pair_blocks_per_sm(int precision) {
     return nb < 1 ? 1 : nb;
 }
 
+// The part of z = E(q x) an epilogue reads: f_B reads Im(A z) and f_C reads
+// Re(A z), which with Im A = 0 are A Im z and A Re z.
+static int component_needed(const Boundary& b, const PairJob& job) {
+    if (!b.A_real || job.R != 1 || job.mode != W_SCALED || job.s != b.q) return 0;
+    if (job.epi == EPI_IMINUSN || job.epi == EPI_RESID) return 1;
+    if (job.epi == EPI_M) return 2;
+    return 0;
+}
+
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st) {
-    if (precision == GNK_PREC_FP32) return run_pairsum32(b, job, st);
-    if (precision == GNK_PREC_DF32) return run_pairsumdf(b, job, st);
-    return run_pairsum64(b, job, st);
+    PairJob j = job;
+    j.comp = component_needed(b, job);
+    if (precision == GNK_PREC_FP32) return run_pairsum32(b, j, st);
+    if (precision == GNK_PREC_DF32) return run_pairsumdf(b, j, st);
+    return run_pairsum64(b, j, st);
 }
 
 }  // namespace gnk
