@@ -49,14 +49,21 @@ PEAK_INSTR = {
     "pair32": SMS * SM_MAX_MHZ * 1e6 * 128,
     "pair64": SMS * SM_MAX_MHZ * 1e6 * 2,
     "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128,
+    "fmm": SMS * SM_MAX_MHZ * 1e6 * 2,
 }
 PEAK_BASIS = {
     "pair64": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 9 + 4R FP64 instr per pair",
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
+    "fmm": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 4 FP64 instr per complex multiply-add of "
+           "P2M, M2M, M2L, L2L, L2P (order 32) + 9 + 4R per near-field pair",
 }
-KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel"}
-MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3}
+KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
+               "fmm": "FMM product (fmm_leaf_kernel, fmm_m2l_kernel, fmm_p2m_kernel, fmm_m2m_kernel, "
+                      "fmm_l2l_kernel)"}
+PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")
+MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
+FMM_MODES = ("fmm", "mixed_fmm")
 
 
 def parse():
@@ -229,6 +236,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     mode = MODES[args.precision]
     bprec = G.GNK_PREC_DF32 if args.precision in ("mixed_df", "df32") else G.GNK_PREC_FP64
+    if args.precision in FMM_MODES:
+        bprec = G.GNK_PREC_FMM
     opts = G.options(tol=TOL, restart=20, maxit=50, precision=mode, inner_tol=1e-5)
     results = {}
 
@@ -246,7 +255,8 @@ def main():
     torch.cuda.synchronize()
 
     kinds = (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
-             ("reduce", G.PROF_REDUCE), ("circ", G.PROF_CIRC), ("krylov", G.PROF_KRYLOV))
+             ("fmm", G.PROF_FMM), ("reduce", G.PROF_REDUCE), ("circ", G.PROF_CIRC),
+             ("krylov", G.PROF_KRYLOV))
 
     # ---- timed region
     launches0 = G.gnk_kernel_launches()
@@ -281,11 +291,13 @@ def main():
     compare = {}
     kernel_rates = {}
     if not args.no_fp64:
-        for name in ("fp64", "mixed", "mixed_df"):
+        for name in ("fp64", "mixed", "mixed_df", "fmm", "mixed_fmm"):
             if name == args.precision:
                 continue
             o = G.options(tol=TOL, restart=20, maxit=50, precision=MODES[name], inner_tol=1e-5)
             bp = G.GNK_PREC_DF32 if name in ("mixed_df", "df32") else G.GNK_PREC_FP64
+            if name in FMM_MODES:
+                bp = G.GNK_PREC_FMM
             if name != "fp64":
                 step(o, bp)
             flush.zero_()
@@ -305,7 +317,7 @@ def main():
                 "max_rel_diff_mu_vs_headline": float((mu - mu_main).abs().max() / mu_main.abs().max()),
                 "max_abs_diff_hk_vs_headline": float((hk - h_main).abs().max()),
             }
-            for k in ("pair64", "pair32", "pairdf"):
+            for k in PAIR_KINDS:
                 if pk[k][1] > 0 and k not in kernel_rates:
                     kernel_rates[k] = pk[k][2] / (pk[k][1] / 1e3)
         # adjoint equation (I + N* + J) phi = gamma, headline precision
@@ -323,7 +335,7 @@ def main():
         G.gnk_free_boundary(hnd)
         compare["adjoint_" + args.precision] = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3,
                                                 "iterations": ra.iterations, "relres": ra.relres}
-    for k in ("pair64", "pair32", "pairdf"):
+    for k in PAIR_KINDS:
         if prof[k][1] > 0:
             kernel_rates[k] = prof[k][2] / (prof[k][1] / 1e3)
 
@@ -361,12 +373,12 @@ def main():
         return
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
-    dom_kind = max(("pair64", "pair32", "pairdf"), key=lambda k: prof[k][1])
+    dom_kind = max(PAIR_KINDS, key=lambda k: prof[k][1])
     n_l, ms_l, work, instr = prof[dom_kind]
     achieved = instr / (ms_l / 1e3) if ms_l > 0 else 0.0
     peak = PEAK_INSTR[dom_kind]
     total_prof_ms = sum(v[1] for v in prof.values())
-    pair_evals = sum(prof[k][2] for k in ("pair64", "pair32", "pairdf"))
+    pair_evals = sum(prof[k][2] for k in PAIR_KINDS)
     roofline = {
         "bound": "alu", "kernel": KERNEL_NAME[dom_kind],
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
@@ -386,7 +398,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
-                  "fp64": "f64", "df32": "double-float f32 pairs, f64 vectors"}[args.precision],
+                  "fp64": "f64", "df32": "double-float f32 pairs, f64 vectors",
+                  "fmm": "f64 (FMM, order 32)", "mixed_fmm": "f32 pairs + f64 FMM"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
                    "restart": 20, "precision": args.precision,

@@ -60,6 +60,13 @@ extern "C" {
                               accuracy; GB300's FP64 pipe is 1/64 of FP32)     */
 #define GNK_PREC_MIXED_DF 4 /* as GNK_PREC_MIXED, with the refinement residual,
                               right-hand side and h in double-float pair sums  */
+#define GNK_PREC_FMM   5   /* Cauchy sums by the fast multipole method (Sec. 2.5:
+                              the paper's zfmm2dpart route), FP64, expansion
+                              order 32: error below ~1e-12 of
+                              sum_j |w_j / (eta_i - eta_j)|, O(N) work.  The
+                              quadtree is built on the first such call.        */
+#define GNK_PREC_MIXED_FMM 6 /* as GNK_PREC_MIXED, with the refinement residual,
+                              right-hand side and h by the FMM               */
 
 typedef struct gnk_boundary gnk_boundary;
 
@@ -71,7 +78,8 @@ typedef struct gnk_options {
     int restart;       /* inner iterations per cycle (>= 1)                    */
     int maxit;         /* maximum number of cycles (>= 1)                      */
     double tol;        /* relative residual target (> 0)                       */
-    int precision;     /* GNK_PREC_FP64, _DF32, _MIXED or _MIXED_DF            */
+    int precision;     /* GNK_PREC_FP64, _DF32, _FMM, _MIXED, _MIXED_DF or
+                          _MIXED_FMM                                           */
     int max_refine;    /* MIXED: maximum refinement steps                      */
     double inner_tol;  /* MIXED: relative tolerance of each inner solve        */
 } gnk_options;

@@ -90,8 +90,9 @@ int check_handle(const gnk_boundary* h) {
 }
 
 int check_prec(int prec) {
-    if (prec != GNK_PREC_FP64 && prec != GNK_PREC_FP32 && prec != GNK_PREC_DF32) {
-        set_error("precision must be GNK_PREC_FP64, GNK_PREC_FP32 or GNK_PREC_DF32 here, got %d", prec);
+    if (prec != GNK_PREC_FP64 && prec != GNK_PREC_FP32 && prec != GNK_PREC_DF32 && prec != GNK_PREC_FMM) {
+        set_error("precision must be GNK_PREC_FP64, GNK_PREC_FP32, GNK_PREC_DF32 or GNK_PREC_FMM here, "
+                  "got %d", prec);
         return GNK_EINVAL;
     }
     return GNK_OK;
@@ -108,6 +109,7 @@ int dmalloc(T** p, size_t count) {
 }
 
 void release(Boundary& b) {
+    release_fmm(b);
     void* ptrs[] = {b.arena, b.V, b.kry, b.kstate};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -143,10 +145,11 @@ int options_from(const gnk_options* in, gnk_options* o) {
     if (in) *o = *in;
     if (o->restart < 1 || o->restart > 1000 || o->maxit < 1 || !(o->tol > 0.0) ||
         (o->precision != GNK_PREC_FP64 && o->precision != GNK_PREC_MIXED &&
-         o->precision != GNK_PREC_DF32 && o->precision != GNK_PREC_MIXED_DF) ||
+         o->precision != GNK_PREC_DF32 && o->precision != GNK_PREC_MIXED_DF &&
+         o->precision != GNK_PREC_FMM && o->precision != GNK_PREC_MIXED_FMM) ||
         o->max_refine < 0 || !(o->inner_tol > 0.0)) {
         set_error("invalid gnk_options (restart 1..1000, maxit >= 1, tol > 0, precision "
-                  "FP64|MIXED|DF32|MIXED_DF, max_refine >= 0, inner_tol > 0)");
+                  "FP64|MIXED|DF32|MIXED_DF|FMM|MIXED_FMM, max_refine >= 0, inner_tol > 0)");
         return GNK_EINVAL;
     }
     return GNK_OK;
@@ -318,9 +321,9 @@ int gnk_build_boundary_ex(gnk_boundary** out, int m1, int n, const double* et, c
     const int defer = (precision & GNK_BUILD_DEFER) ? 1 : 0;
     const int plain = (precision & GNK_BUILD_PLAIN) ? 1 : 0;
     precision &= ~(GNK_BUILD_DEFER | GNK_BUILD_PLAIN);
-    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
-        set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64 or GNK_PREC_DF32 "
-                  "(optionally | GNK_BUILD_DEFER | GNK_BUILD_PLAIN)");
+    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32 && precision != GNK_PREC_FMM) {
+        set_error("gnk_build_boundary_ex: precision must be GNK_PREC_FP64, GNK_PREC_DF32 or "
+                  "GNK_PREC_FMM (optionally | GNK_BUILD_DEFER | GNK_BUILD_PLAIN)");
         return GNK_EINVAL;
     }
     if (plain && !etpp) {

@@ -1,0 +1,703 @@
+// Fast multipole evaluation of the Cauchy sum z_i = sum_{j != i} w_j / (eta_i - eta_j)
+// (Sec. 2.5, Eqs. fmm-1, fmm-E: the paper forms E w with the FMM of zfmm2dpart,
+// O((m+1)n) operations).  Uniform-depth quadtree over the bounding square of the
+// nodes (levels 2..L, empty boxes pruned), expansions of order P scaled by the box
+// width r (Greengard & Rokhlin's complex-analytic 2-D FMM):
+//   multipole  phi(z) = sum_k a_k r^k / (z - c)^(k+1),  a_k = sum_j w_j ((s_j - c)/r)^k
+//   local      phi(z) = sum_l b_l ((z - c)/r)^l
+//   M2M  a0_m = sum_{k<=m} C(m,k) ((c1-c0)/r0)^(m-k) 2^-k a1_k
+//   M2L  b_l  = (1/r) sum_k (-1)^(k+1) C(k+l,l) delta^-(k+l+1) a_k,  delta = (c1-c0)/r
+//   L2L  b1_m = sum_{l>=m} C(l,m) ((c1-c0)/r0)^(l-m) 2^-m b0_l
+// The near field (a leaf and its eight neighbours) is summed directly with the
+// i = j term excluded.  All translation matrices depend only on the relative box
+// position, so they are tabulated once (4 + 4 + 49 matrices of P x P).  The
+// truncation error is below 0.43^P of sum_j |w_j / (eta_i - eta_j)| (about 2e-12
+// at P = 32 including round-off; checked against direct sums in the tests).
+//
+// The tree is built on the host once per handle (the geometry is fixed for all
+// products): Morton keys of 16-bit box coordinates, a sort of (key, node) pairs,
+// leaf level L = the deepest level whose non-empty boxes hold at least kFmmLeaf
+// nodes on average, interaction and neighbour lists by binary search of the sorted
+// box keys of each level.  Every sum on the device runs in a fixed order, so
+// results are reproducible.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "gnk_internal.h"
+#include "pairmath.cuh"
+
+namespace gnk {
+
+constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
+constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
+constexpr int kFmmNT = 64;    // threads of the leaf (L2P + near field) kernel
+
+struct FmmTree {
+    int L = 0, nbox = 0, nleaf = 0, R = 0;
+    std::vector<int> lvl_off;   // first global box index of level l (index l - 2), size L
+    std::vector<int> lvl_cnt;
+    long long near_pairs = 0, m2l_pairs = 0, m2m_pairs = 0;
+    void* arena = nullptr;
+    int* perm = nullptr;        // sorted position -> node
+    double2* ps = nullptr;      // node positions in sorted order
+    int* leaf_start = nullptr;  // nleaf + 1
+    int* leaf_box = nullptr;    // global box index of each leaf
+    double2* center = nullptr;  // per box
+    double* width = nullptr;    // per box
+    int* child_start = nullptr; // per box: first child (global), level < L
+    int* child_count = nullptr;
+    int* parent = nullptr;      // per box, -1 on level 2
+    int* quad = nullptr;        // quadrant of a box in its parent: 2 qa + qb
+    int* il_start = nullptr;    // interaction lists (nbox + 1), sources, offset codes
+    int* il_src = nullptr;
+    int* il_off = nullptr;
+    int* nl_start = nullptr;    // neighbour leaves of each leaf (nleaf + 1)
+    int* nl_leaf = nullptr;
+    double2* m2m = nullptr;     // [4][k][m]
+    double2* l2l = nullptr;     // [4][l][m]
+    double2* m2l = nullptr;     // [49][k][l]
+    double2* mult = nullptr;    // [R][nbox][P]
+    double2* loc = nullptr;     // [R][nbox][P]
+    double2* ws = nullptr;      // [R][N] weights in sorted order
+};
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+struct FmmArgs {
+    int N, R, P;
+    const int* perm;
+    const double2* ps;
+    const int* leaf_start;
+    const int* leaf_box;
+    const double2* center;
+    const double* width;
+    const int* child_start;
+    const int* child_count;
+    const int* parent;
+    const int* quad;
+    const int* il_start;
+    const int* il_src;
+    const int* il_off;
+    const int* nl_start;
+    const int* nl_leaf;
+    const double2* m2m;
+    const double2* l2l;
+    const double2* m2l;
+    double2* mult;
+    double2* loc;
+    double2* ws;
+    int nbox;
+    // weights
+    int mode;
+    const double2* w0;
+    const double2* w1;
+    const double* x0;
+    const double* x1;
+    const double2* s;
+    double2* out;  // [R][N] in node order
+    const int* done;
+};
+
+__global__ void fmm_gather_kernel(FmmArgs a) {
+    if (a.done != nullptr && *a.done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int j = a.perm[i];
+    for (int r = 0; r < a.R; ++r) {
+        double2 w;
+        if (a.mode == W_COMPLEX) {
+            w = (r == 0) ? a.w0[j] : a.w1[j];
+        } else {
+            const double2 sc = a.s[j];
+            const double x = (r == 0) ? a.x0[j] : a.x1[j];
+            w = make_double2(sc.x * x, sc.y * x);
+        }
+        a.ws[(size_t)r * a.N + i] = w;
+    }
+}
+
+// P2M: one warp per leaf, lane k forms a_k; the powers t^k come from a
+// multiplicative prefix scan across the warp, one node at a time.
+template <int R>
+__global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
+    if (a.done != nullptr && *a.done) return;
+    const int leaf = blockIdx.x, lane = threadIdx.x;
+    const int box = a.leaf_box[leaf];
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    double2 acc[kMaxRHS] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int j = a.leaf_start[leaf]; j < a.leaf_start[leaf + 1]; ++j) {
+        const double2 p = a.ps[j];
+        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
+        double2 v = (lane == 0) ? make_double2(1.0, 0.0) : t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double2 u = make_double2(__shfl_up_sync(0xffffffffu, v.x, off),
+                                           __shfl_up_sync(0xffffffffu, v.y, off));
+            if (lane >= off) v = cmul(u, v);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = cmac(acc[r], a.ws[(size_t)r * a.N + j], v);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = acc[r];
+}
+
+// M2M for the boxes [b0, b0 + gridDim.x) of one level
+__global__ void __launch_bounds__(32) fmm_m2m_kernel(FmmArgs a, int b0) {
+    if (a.done != nullptr && *a.done) return;
+    const int box = b0 + blockIdx.x, lane = threadIdx.x;
+    const int c0 = a.child_start[box], nc = a.child_count[box];
+    for (int r = 0; r < a.R; ++r) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = c0; c < c0 + nc; ++c) {
+            const double2* T = a.m2m + (size_t)a.quad[c] * kFmmP * kFmmP;
+            const double2 mine = a.mult[((size_t)r * a.nbox + c) * kFmmP + lane];
+#pragma unroll 8
+            for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
+        }
+        a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = acc;
+    }
+}
+
+// M2L for every box of levels 2..L (one warp per target box)
+__global__ void __launch_bounds__(32) fmm_m2l_kernel(FmmArgs a) {
+    if (a.done != nullptr && *a.done) return;
+    const int box = blockIdx.x, lane = threadIdx.x;
+    const double ir = 1.0 / a.width[box];
+    const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
+    for (int r = 0; r < a.R; ++r) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int e = e0; e < e1; ++e) {
+            const double2* T = a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP;
+            const double2 mine = a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane];
+#pragma unroll 8
+            for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
+        }
+        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = make_double2(acc.x * ir, acc.y * ir);
+    }
+}
+
+// L2L into the boxes [b0, b0 + gridDim.x) of one level (their M2L part is in place)
+__global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
+    if (a.done != nullptr && *a.done) return;
+    const int box = b0 + blockIdx.x, lane = threadIdx.x;
+    const int par = a.parent[box];
+    const double2* T = a.l2l + (size_t)a.quad[box] * kFmmP * kFmmP;
+    for (int r = 0; r < a.R; ++r) {
+        const double2 mine = a.loc[((size_t)r * a.nbox + par) * kFmmP + lane];
+        double2 acc = a.loc[((size_t)r * a.nbox + box) * kFmmP + lane];
+#pragma unroll 8
+        for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
+        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = acc;
+    }
+}
+
+// L2P and the near field of one leaf per block; writes z in node order
+template <int R>
+__global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
+    if (a.done != nullptr && *a.done) return;
+    __shared__ double2 s_b[kMaxRHS][kFmmP];
+    __shared__ double2 s_p[kFmmNT];
+    __shared__ double2 s_w[kMaxRHS][kFmmNT];
+    const int leaf = blockIdx.x, tid = threadIdx.x;
+    const int box = a.leaf_box[leaf];
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    for (int k = tid; k < R * kFmmP; k += kFmmNT)
+        s_b[k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
+    const int t0 = a.leaf_start[leaf], t1 = a.leaf_start[leaf + 1];
+    const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
+    __syncthreads();
+    for (int base = t0; base < t1; base += kFmmNT) {
+        const int i = base + tid;
+        const bool act = i < t1;
+        const double2 p = a.ps[act ? i : t0];
+        double2 z[kMaxRHS] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+        // local expansion by Horner's rule
+        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            double2 v = s_b[r][kFmmP - 1];
+            for (int l = kFmmP - 2; l >= 0; --l) {
+                const double2 bl = s_b[r][l];
+                v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
+            }
+            z[r] = v;
+        }
+        // near field: the leaf and its neighbours, i = j excluded (Eq. fmm-E)
+        for (int e = n0; e < n1; ++e) {
+            const int nl = a.nl_leaf[e];
+            const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
+            for (int sb = s0; sb < s1; sb += kFmmNT) {
+                __syncthreads();
+                const int j = sb + tid;
+                if (j < s1) {
+                    s_p[tid] = a.ps[j];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) s_w[r][tid] = a.ws[(size_t)r * a.N + j];
+                }
+                __syncthreads();
+                const int cnt = min(kFmmNT, s1 - sb);
+                for (int k = 0; k < cnt; ++k) {
+                    const double dx = p.x - s_p[k].x, dy = p.y - s_p[k].y;
+                    double inv = recip_f64(fma(dx, dx, dy * dy));
+                    inv = (sb + k == i) ? 0.0 : inv;
+                    const double ar = dx * inv, ai = dy * inv;  // 1/d = ar - i ai
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const double2 w = s_w[r][k];
+                        z[r].x = fma(w.x, ar, fma(w.y, ai, z[r].x));
+                        z[r].y = fma(w.y, ar, fma(-w.x, ai, z[r].y));
+                    }
+                }
+            }
+        }
+        if (act) {
+            const int node = a.perm[i];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a.out[(size_t)r * a.N + node] = z[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host: tables
+using cld = std::complex<long double>;
+
+long double binom_ld(int n, int k) {
+    long double v = 1.0L;
+    for (int i = 1; i <= k; ++i) v = v * (long double)(n - k + i) / (long double)i;
+    return v;
+}
+
+void translation_tables(std::vector<double2>* m2m, std::vector<double2>* l2l, std::vector<double2>* m2l) {
+    const int P = kFmmP;
+    m2m->assign(4 * P * P, make_double2(0.0, 0.0));
+    l2l->assign(4 * P * P, make_double2(0.0, 0.0));
+    m2l->assign(49 * P * P, make_double2(0.0, 0.0));
+    for (int q = 0; q < 4; ++q) {
+        const int qa = q >> 1, qb = q & 1;
+        const cld dd((2 * qa - 1) / 4.0L, (2 * qb - 1) / 4.0L);
+        for (int m = 0; m < P; ++m)
+            for (int k = 0; k <= m; ++k) {
+                // M2M: row m, column k; stored [q][k][m]
+                const cld v = binom_ld(m, k) * std::pow(dd, m - k) * std::pow(2.0L, -k);
+                (*m2m)[(size_t)q * P * P + k * P + m] = make_double2((double)v.real(), (double)v.imag());
+            }
+        for (int m = 0; m < P; ++m)
+            for (int l = m; l < P; ++l) {
+                // L2L: row m, column l; stored [q][l][m]
+                const cld v = binom_ld(l, m) * std::pow(dd, l - m) * std::pow(2.0L, -m);
+                (*l2l)[(size_t)q * P * P + l * P + m] = make_double2((double)v.real(), (double)v.imag());
+            }
+    }
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) {
+            if (std::max(std::abs(dx), std::abs(dy)) <= 1) continue;
+            const int o = (dx + 3) * 7 + (dy + 3);
+            const cld inv = 1.0L / cld((long double)dx, (long double)dy);
+            for (int l = 0; l < P; ++l)
+                for (int k = 0; k < P; ++k) {
+                    // M2L: row l, column k; stored [o][k][l]
+                    const long double sgn = ((k + 1) % 2) ? -1.0L : 1.0L;
+                    const cld v = sgn * binom_ld(k + l, l) * std::pow(inv, k + l + 1);
+                    (*m2l)[(size_t)o * P * P + k * P + l] = make_double2((double)v.real(), (double)v.imag());
+                }
+        }
+}
+
+// The translation tables depend only on P: formed once per process.
+const std::vector<double2>& cached_tables(int which) {
+    static std::once_flag once;
+    static std::vector<double2> m2m, l2l, m2l;
+    std::call_once(once, [] { translation_tables(&m2m, &l2l, &m2l); });
+    return which == 0 ? m2m : (which == 1 ? l2l : m2l);
+}
+
+uint32_t spread16(uint32_t v) {
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+}  // namespace
+
+void release_fmm(Boundary& b) {
+    if (b.fmm) {
+        if (b.fmm->arena) cudaFree(b.fmm->arena);
+        delete b.fmm;
+        b.fmm = nullptr;
+    }
+}
+
+// Builds the tree of the handle's nodes (once) with workspace for R right-hand sides.
+int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
+    Boundary& b = const_cast<Boundary&>(bc);
+    (void)R;  // the workspace always holds kMaxRHS right-hand sides
+    if (b.fmm) return GNK_OK;
+    const int N = b.N;
+    std::vector<double2> et(N);
+    GNK_TRY_CUDA(cudaMemcpyAsync(et.data(), b.et, (size_t)N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    double xmin = et[0].x, xmax = et[0].x, ymin = et[0].y, ymax = et[0].y;
+    for (const double2& p : et) {
+        xmin = std::min(xmin, p.x);
+        xmax = std::max(xmax, p.x);
+        ymin = std::min(ymin, p.y);
+        ymax = std::max(ymax, p.y);
+    }
+    const double W = std::max(std::max(xmax - xmin, ymax - ymin) * (1.0 + 1e-9), 1e-300);
+    const double x0 = 0.5 * (xmin + xmax) - 0.5 * W, y0 = 0.5 * (ymin + ymax) - 0.5 * W;
+    std::vector<uint32_t> key0(N), key1(N);
+    std::vector<int> ord0(N), ord1(N);
+    for (int i = 0; i < N; ++i) {
+        const double fx = (et[i].x - x0) / W * 65536.0, fy = (et[i].y - y0) / W * 65536.0;
+        const uint32_t ix = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(fx)));
+        const uint32_t iy = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(fy)));
+        key0[i] = (spread16(ix) << 1) | spread16(iy);
+        ord0[i] = i;
+    }
+    // LSD radix sort, two stable passes of 16 bits: (key, node) in increasing order
+    for (int pass = 0; pass < 2; ++pass) {
+        const int sh = 16 * pass;
+        std::vector<int> cnt(65537, 0);
+        for (int i = 0; i < N; ++i) ++cnt[((key0[i] >> sh) & 0xffffu) + 1];
+        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+        for (int i = 0; i < N; ++i) {
+            const int dst = cnt[(key0[i] >> sh) & 0xffffu]++;
+            key1[dst] = key0[i];
+            ord1[dst] = ord0[i];
+        }
+        key0.swap(key1);
+        ord0.swap(ord1);
+    }
+    auto key_at = [&](int i, int l) { return key0[i] >> (2 * (16 - l)); };
+    // leaf level: deepest level whose non-empty boxes hold >= kFmmLeaf nodes on
+    // average.  Neighbours in key order first differ at level 16 - msb(x)/2.
+    std::vector<long long> first_diff(18, 0);
+    for (int i = 1; i < N; ++i) {
+        const uint32_t x = key0[i] ^ key0[i - 1];
+        if (x == 0) continue;
+        int msb = 31;
+        while (!((x >> msb) & 1u)) --msb;
+        ++first_diff[16 - msb / 2];  // distinct from this level down
+    }
+    int L = 2;
+    long long distinct = 1;
+    for (int l = 1; l <= 16; ++l) {
+        distinct += first_diff[l];
+        if (l < 3) continue;
+        if ((double)N / (double)distinct < kFmmLeaf) break;
+        L = l;
+    }
+    FmmTree* t = new (std::nothrow) FmmTree();
+    if (!t) {
+        set_error("host allocation failed");
+        return GNK_ENOMEM;
+    }
+    t->L = L;
+    t->R = kMaxRHS;
+    // boxes per level (level index l - 2), sorted by key
+    const int nlev = L - 1;
+    std::vector<std::vector<uint32_t>> keys(nlev);
+    std::vector<int> leaf_start;
+    for (int i = 0; i < N; ++i) {
+        const uint32_t k = key_at(i, L);
+        if (i == 0 || k != keys[L - 2].back()) {
+            keys[L - 2].push_back(k);
+            leaf_start.push_back(i);
+        }
+    }
+    leaf_start.push_back(N);
+    for (int l = L - 1; l >= 2; --l)
+        for (uint32_t k : keys[l - 1]) {  // children of level l + 1 are keys[l - 1]
+            const uint32_t pk = k >> 2;
+            if (keys[l - 2].empty() || keys[l - 2].back() != pk) keys[l - 2].push_back(pk);
+        }
+    t->lvl_off.resize(nlev);
+    t->lvl_cnt.resize(nlev);
+    int nbox = 0;
+    for (int l = 2; l <= L; ++l) {
+        t->lvl_off[l - 2] = nbox;
+        t->lvl_cnt[l - 2] = (int)keys[l - 2].size();
+        nbox += (int)keys[l - 2].size();
+    }
+    t->nbox = nbox;
+    t->nleaf = (int)keys[L - 2].size();
+    auto compact = [](uint32_t v) {  // inverse of spread16
+        v &= 0x55555555u;
+        v = (v | (v >> 1)) & 0x33333333u;
+        v = (v | (v >> 2)) & 0x0f0f0f0fu;
+        v = (v | (v >> 4)) & 0x00ff00ffu;
+        v = (v | (v >> 8)) & 0x0000ffffu;
+        return v;
+    };
+    auto decode = [&](uint32_t key, int* ix, int* iy) {
+        *ix = (int)compact(key >> 1);
+        *iy = (int)compact(key);
+    };
+    auto encode = [](int ix, int iy) { return (spread16((uint32_t)ix) << 1) | spread16((uint32_t)iy); };
+    // box lookup: a dense grid per level up to 2^11 x 2^11 boxes, else binary search
+    std::vector<std::vector<int>> grid(nlev);
+    for (int l = 2; l <= L; ++l) {
+        if (l > 11) continue;
+        const int n = 1 << l;
+        grid[l - 2].assign((size_t)n * n, -1);
+        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
+            int ix, iy;
+            decode(keys[l - 2][q], &ix, &iy);
+            grid[l - 2][(size_t)ix * n + iy] = t->lvl_off[l - 2] + q;
+        }
+    }
+    auto find = [&](int l, int ix, int iy) -> int {
+        const int n = 1 << l;
+        if (ix < 0 || iy < 0 || ix >= n || iy >= n) return -1;
+        if (l <= 11) return grid[l - 2][(size_t)ix * n + iy];
+        const std::vector<uint32_t>& v = keys[l - 2];
+        const uint32_t k = encode(ix, iy);
+        auto it = std::lower_bound(v.begin(), v.end(), k);
+        if (it == v.end() || *it != k) return -1;
+        return t->lvl_off[l - 2] + (int)(it - v.begin());
+    };
+    std::vector<double2> center(nbox);
+    std::vector<double> width(nbox);
+    std::vector<int> child_start(nbox, 0), child_count(nbox, 0), parent(nbox, -1), quad(nbox, 0);
+    std::vector<int> il_start(nbox + 1, 0), il_src, il_off;
+    for (int l = 2; l <= L; ++l) {
+        const double r = W / (double)(1 << l);
+        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
+            const int g = t->lvl_off[l - 2] + q;
+            int ix, iy;
+            decode(keys[l - 2][q], &ix, &iy);
+            center[g] = make_double2(x0 + (ix + 0.5) * r, y0 + (iy + 0.5) * r);
+            width[g] = r;
+            quad[g] = ((ix & 1) << 1) | (iy & 1);
+            if (l > 2) parent[g] = find(l - 1, ix >> 1, iy >> 1);
+            if (l < L) {
+                const int c0 = find(l + 1, 2 * ix, 2 * iy);
+                // children of a box are contiguous in key order; the first existing one starts the run
+                int first = -1, cnt = 0;
+                for (int qa = 0; qa < 2; ++qa)
+                    for (int qb = 0; qb < 2; ++qb) {
+                        const int c = find(l + 1, 2 * ix + qa, 2 * iy + qb);
+                        if (c >= 0) {
+                            first = (first < 0) ? c : std::min(first, c);
+                            ++cnt;
+                        }
+                    }
+                (void)c0;
+                child_start[g] = first;
+                child_count[g] = cnt;
+            }
+            // interaction list: children of the parent's neighbours that are not adjacent
+            const int pa = ix >> 1, pb = iy >> 1;
+            for (int sa = 2 * pa - 2; sa <= 2 * pa + 3; ++sa)
+                for (int sb = 2 * pb - 2; sb <= 2 * pb + 3; ++sb) {
+                    const int dx = sa - ix, dy = sb - iy;
+                    if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+                    const int s = find(l, sa, sb);
+                    if (s < 0) continue;
+                    il_src.push_back(s);
+                    il_off.push_back((dx + 3) * 7 + (dy + 3));
+                }
+            il_start[g + 1] = (int)il_src.size();
+        }
+    }
+    // neighbour leaves (3 x 3, the leaf itself included)
+    std::vector<int> nl_start(t->nleaf + 1, 0), nl_leaf, leaf_box(t->nleaf);
+    long long near_pairs = 0;
+    for (int q = 0; q < t->nleaf; ++q) {
+        leaf_box[q] = t->lvl_off[L - 2] + q;
+        int ix, iy;
+        decode(keys[L - 2][q], &ix, &iy);
+        const long long cnt_t = leaf_start[q + 1] - leaf_start[q];
+        for (int sa = ix - 1; sa <= ix + 1; ++sa)
+            for (int sb = iy - 1; sb <= iy + 1; ++sb) {
+                const int g = find(L, sa, sb);
+                if (g < 0) continue;
+                const int lq = g - t->lvl_off[L - 2];
+                nl_leaf.push_back(lq);
+                near_pairs += cnt_t * (leaf_start[lq + 1] - leaf_start[lq]);
+            }
+        nl_start[q + 1] = (int)nl_leaf.size();
+    }
+    t->near_pairs = near_pairs;
+    t->m2l_pairs = (long long)il_src.size();
+    long long m2m_pairs = 0;
+    for (int g = 0; g < nbox; ++g) m2m_pairs += child_count[g];
+    t->m2m_pairs = m2m_pairs;
+    const std::vector<int>& perm = ord0;
+    std::vector<double2> ps(N);
+    for (int i = 0; i < N; ++i) ps[i] = et[perm[i]];
+    const std::vector<double2>& m2m = cached_tables(0);
+    const std::vector<double2>& l2l = cached_tables(1);
+    const std::vector<double2>& m2l = cached_tables(2);
+
+    // one device allocation for the tree and the expansions
+    const size_t P = kFmmP;
+    struct Part {
+        void** p;
+        size_t bytes;
+    };
+    const size_t nil = std::max<size_t>(il_src.size(), 1), nnl = std::max<size_t>(nl_leaf.size(), 1);
+    Part parts[] = {
+        {(void**)&t->perm, N * sizeof(int)},
+        {(void**)&t->ps, N * sizeof(double2)},
+        {(void**)&t->leaf_start, (t->nleaf + 1) * sizeof(int)},
+        {(void**)&t->leaf_box, t->nleaf * sizeof(int)},
+        {(void**)&t->center, nbox * sizeof(double2)},
+        {(void**)&t->width, nbox * sizeof(double)},
+        {(void**)&t->child_start, nbox * sizeof(int)},
+        {(void**)&t->child_count, nbox * sizeof(int)},
+        {(void**)&t->parent, nbox * sizeof(int)},
+        {(void**)&t->quad, nbox * sizeof(int)},
+        {(void**)&t->il_start, (nbox + 1) * sizeof(int)},
+        {(void**)&t->il_src, nil * sizeof(int)},
+        {(void**)&t->il_off, nil * sizeof(int)},
+        {(void**)&t->nl_start, (t->nleaf + 1) * sizeof(int)},
+        {(void**)&t->nl_leaf, nnl * sizeof(int)},
+        {(void**)&t->m2m, 4 * P * P * sizeof(double2)},
+        {(void**)&t->l2l, 4 * P * P * sizeof(double2)},
+        {(void**)&t->m2l, 49 * P * P * sizeof(double2)},
+        {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(double2)},
+        {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(double2)},
+        {(void**)&t->ws, (size_t)t->R * N * sizeof(double2)},
+    };
+    size_t total = 0;
+    for (const Part& p : parts) total += (p.bytes + 255) / 256 * 256;
+    if (cudaMalloc(&t->arena, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        set_error("FMM tree: device allocation of %zu bytes failed", total);
+        return GNK_ENOMEM;
+    }
+    char* cur = static_cast<char*>(t->arena);
+    for (const Part& p : parts) {
+        *p.p = cur;
+        cur += (p.bytes + 255) / 256 * 256;
+    }
+    b.fmm = t;  // owned by the handle from here on (freed by release_fmm)
+    auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (bytes == 0) return GNK_OK;
+        GNK_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+        return GNK_OK;
+    };
+    GNK_TRY(up(t->perm, perm.data(), N * sizeof(int)));
+    GNK_TRY(up(t->ps, ps.data(), N * sizeof(double2)));
+    GNK_TRY(up(t->leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int)));
+    GNK_TRY(up(t->leaf_box, leaf_box.data(), leaf_box.size() * sizeof(int)));
+    GNK_TRY(up(t->center, center.data(), nbox * sizeof(double2)));
+    GNK_TRY(up(t->width, width.data(), nbox * sizeof(double)));
+    GNK_TRY(up(t->child_start, child_start.data(), nbox * sizeof(int)));
+    GNK_TRY(up(t->child_count, child_count.data(), nbox * sizeof(int)));
+    GNK_TRY(up(t->parent, parent.data(), nbox * sizeof(int)));
+    GNK_TRY(up(t->quad, quad.data(), nbox * sizeof(int)));
+    GNK_TRY(up(t->il_start, il_start.data(), il_start.size() * sizeof(int)));
+    GNK_TRY(up(t->il_src, il_src.data(), il_src.size() * sizeof(int)));
+    GNK_TRY(up(t->il_off, il_off.data(), il_off.size() * sizeof(int)));
+    GNK_TRY(up(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int)));
+    GNK_TRY(up(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int)));
+    GNK_TRY(up(t->m2m, m2m.data(), m2m.size() * sizeof(double2)));
+    GNK_TRY(up(t->l2l, l2l.data(), l2l.size() * sizeof(double2)));
+    GNK_TRY(up(t->m2l, m2l.data(), m2l.size() * sizeof(double2)));
+    // the host vectors above are released on return: finish the copies first
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    return GNK_OK;
+}
+
+// FP64-pipe instructions of one FMM product (for the roofline): 4 per complex
+// multiply-add of the translations, P2M scan and L2P; 9 + 4R per near-field pair.
+double fmm_instr(const Boundary& b, int R) {
+    const FmmTree* t = b.fmm;
+    if (!t) return 0.0;
+    const double P = kFmmP;
+    const double trans = (double)(t->m2l_pairs + t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
+    const double p2m = (double)b.N * P * (5.0 + R);
+    const double l2p = (double)b.N * P * R;
+    return 4.0 * (trans * R + p2m + l2p) + (9.0 + 4.0 * R) * (double)t->near_pairs;
+}
+
+int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
+    GNK_TRY(ensure_fmm(b, job.R, st));
+    const FmmTree* t = b.fmm;
+    FmmArgs a;
+    a.N = b.N;
+    a.R = job.R;
+    a.P = kFmmP;
+    a.perm = t->perm;
+    a.ps = t->ps;
+    a.leaf_start = t->leaf_start;
+    a.leaf_box = t->leaf_box;
+    a.center = t->center;
+    a.width = t->width;
+    a.child_start = t->child_start;
+    a.child_count = t->child_count;
+    a.parent = t->parent;
+    a.quad = t->quad;
+    a.il_start = t->il_start;
+    a.il_src = t->il_src;
+    a.il_off = t->il_off;
+    a.nl_start = t->nl_start;
+    a.nl_leaf = t->nl_leaf;
+    a.m2m = t->m2m;
+    a.l2l = t->l2l;
+    a.m2l = t->m2l;
+    a.mult = t->mult;
+    a.loc = t->loc;
+    a.ws = t->ws;
+    a.nbox = t->nbox;
+    a.mode = job.mode;
+    a.w0 = job.w[0];
+    a.w1 = job.w[1];
+    a.x0 = job.x[0];
+    a.x1 = job.x[1];
+    a.s = job.s;
+    a.out = static_cast<double2*>(b.partial);
+    a.done = job.done;
+    const ProfToken tok = prof_begin(st);
+    fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
+    if (job.R == 2)
+        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, st>>>(a);
+    else
+        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, st>>>(a);
+    int launches = 2;
+    for (int l = t->L - 1; l >= 2; --l) {
+        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
+        ++launches;
+    }
+    fmm_m2l_kernel<<<t->nbox, 32, 0, st>>>(a);
+    ++launches;
+    for (int l = 3; l <= t->L; ++l) {
+        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
+        ++launches;
+    }
+    if (job.R == 2)
+        fmm_leaf_kernel<2><<<t->nleaf, kFmmNT, 0, st>>>(a);
+    else
+        fmm_leaf_kernel<1><<<t->nleaf, kFmmNT, 0, st>>>(a);
+    ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R));
+    GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
+    count_launches(launches + 1);
+    return GNK_OK;
+}
+
+}  // namespace gnk

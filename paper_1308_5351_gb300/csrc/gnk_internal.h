@@ -47,6 +47,7 @@ enum ProfKind : int {
     PK_KRYLOV = 4,   // GMRES vector kernels; work = bytes moved
     PK_OTHER = 5,
     PK_PAIRDF = 6,   // double-float pair-sum kernel; work = pair evaluations
+    PK_FMM = 7,      // one FMM product (all its launches); work = the R N (N-1) pairs it replaces
 };
 struct ProfToken {
     void* ev = nullptr;
@@ -134,6 +135,8 @@ struct PairJob {
     int comp = 0;                 // set by run_pairsum: 0 both parts, 1 only Im z, 2 only Re z
 };
 
+struct FmmTree;  // fmm.cu
+
 // ---------------------------------------------------------------- handle
 struct Boundary {
     int m1 = 0, n = 0, N = 0;
@@ -184,6 +187,7 @@ struct Boundary {
     int eone_pending = 0;       // Eone, diag(B1), diag(D1), e not yet formed
     int plain = 0;              // 1: diagonals of the form without singularity subtraction
     int A_real = 0;             // 1: Im A = 0 at every node (then f_B needs only Im E(qx))
+    FmmTree* fmm = nullptr;     // quadtree and expansions, built on the first FMM product
     int df_scalar = 0;          // 1: scalar double-float kernel instead of the packed one
     int f32_scalar = 0;         // 1: scalar FP32 kernel instead of the packed one
     double* means = nullptr;    // m1
@@ -254,6 +258,15 @@ int outer_precision(int solve_precision);
 int fbie_backward(const Boundary& b, const double* mu, const double* gam, const double* gm,
                   const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
                   const gnk_options& opt, gnk_result* info, cudaStream_t st);
+
+// ---------------------------------------------------------------- FMM (fmm.cu)
+int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st);
+int ensure_fmm(const Boundary& b, int R, cudaStream_t st);
+void release_fmm(Boundary& b);
+double fmm_instr(const Boundary& b, int R);
+// the chunk reduction and epilogue of the pair sums, for products formed elsewhere
+cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chunks, int ptype,
+                                 cudaStream_t st);
 
 // ---------------------------------------------------------------- Cauchy formula (cauchy_eval.cu)
 int cauchy_eval(const Boundary& b, int M, const double2* z, const double2* f, double2 finf, double2* out,

@@ -433,8 +433,9 @@ int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
 }  // namespace
 
 int outer_precision(int solve_precision) {
-    return (solve_precision == GNK_PREC_DF32 || solve_precision == GNK_PREC_MIXED_DF) ? GNK_PREC_DF32
-                                                                                     : GNK_PREC_FP64;
+    if (solve_precision == GNK_PREC_DF32 || solve_precision == GNK_PREC_MIXED_DF) return GNK_PREC_DF32;
+    if (solve_precision == GNK_PREC_FMM || solve_precision == GNK_PREC_MIXED_FMM) return GNK_PREC_FMM;
+    return GNK_PREC_FP64;
 }
 
 int solve(const Boundary& bc, int adjoint /* OpId */, const double* rhs, double* x, const gnk_options& opt,
@@ -446,7 +447,7 @@ int solve(const Boundary& bc, int adjoint /* OpId */, const double* rhs, double*
     int status;
     const int outer = outer_precision(opt.precision);
     if (fc_valid) *fc_valid = 0;
-    if (opt.precision == GNK_PREC_FP64 || opt.precision == GNK_PREC_DF32) {
+    if (opt.precision == GNK_PREC_FP64 || opt.precision == GNK_PREC_DF32 || opt.precision == GNK_PREC_FMM) {
         status = gmres(b, adjoint, outer, rhs, x, b.r0, opt.restart, opt.maxit, opt.tol, &res,
                        &relres, st, fc_out, fc_valid);
     } else {

@@ -1052,7 +1052,13 @@ static int component_needed(const Boundary& b, const PairJob& job) {
     return 0;
 }
 
+cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chunks, int ptype,
+                                 cudaStream_t st) {
+    return launch_reduce(b, job, chunks, ptype, st);
+}
+
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st) {
+    if (precision == GNK_PREC_FMM) return run_fmm(b, job, st);
     PairJob j = job;
     j.comp = component_needed(b, job);
     if (precision == GNK_PREC_FP32) return run_pairsum32(b, j, st);

@@ -35,6 +35,8 @@ GNK_PREC_MIXED = 1
 GNK_PREC_FP32 = 2
 GNK_PREC_DF32 = 3
 GNK_PREC_MIXED_DF = 4
+GNK_PREC_FMM = 5
+GNK_PREC_MIXED_FMM = 6
 GNK_BUILD_DEFER = 0x100
 GNK_BUILD_PLAIN = 0x200
 
@@ -49,7 +51,7 @@ EXPORTED = (
     "gnk_cauchy_eval",
 )
 
-PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF = range(7)
+PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM = range(8)
 
 
 class gnk_options(ctypes.Structure):
