@@ -50,18 +50,22 @@ PEAK_INSTR = {
     "pair64": SMS * SM_MAX_MHZ * 1e6 * 2,
     "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm": SMS * SM_MAX_MHZ * 1e6 * 2,
+    "fmm_near": SMS * SM_MAX_MHZ * 1e6 * 128,
 }
 PEAK_BASIS = {
     "pair64": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 9 + 4R FP64 instr per pair",
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
     "fmm": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 4 FP64 instr per complex multiply-add of "
-           "P2M, M2M, M2L, L2L, L2P (order 32) + 9 + 4R per near-field pair",
+           "P2M, M2M, M2L, L2L, L2P (order 32)",
+    "fmm_near": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float "
+                "near-field pair",
 }
 KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
-               "fmm": "FMM product (fmm_leaf_kernel, fmm_m2l_kernel, fmm_p2m_kernel, fmm_m2m_kernel, "
-                      "fmm_l2l_kernel)"}
-PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")
+               "fmm": "FMM far field (fmm_m2l_kernel, fmm_p2m_kernel, fmm_m2m_kernel, fmm_l2l_kernel)",
+               "fmm_near": "fmm_leaf_kernel (L2P + double-float near field)"}
+PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
+ROOF_KINDS = PAIR_KINDS + ("fmm_near",)
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
 FMM_MODES = ("fmm", "mixed_fmm")
 
@@ -255,7 +259,8 @@ def main():
     torch.cuda.synchronize()
 
     kinds = (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
-             ("fmm", G.PROF_FMM), ("reduce", G.PROF_REDUCE), ("circ", G.PROF_CIRC),
+             ("fmm", G.PROF_FMM), ("fmm_near", G.PROF_FMMNEAR), ("reduce", G.PROF_REDUCE),
+             ("circ", G.PROF_CIRC),
              ("krylov", G.PROF_KRYLOV))
 
     # ---- timed region
@@ -373,7 +378,7 @@ def main():
         return
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
-    dom_kind = max(PAIR_KINDS, key=lambda k: prof[k][1])
+    dom_kind = max(ROOF_KINDS, key=lambda k: prof[k][1])
     n_l, ms_l, work, instr = prof[dom_kind]
     achieved = instr / (ms_l / 1e3) if ms_l > 0 else 0.0
     peak = PEAK_INSTR[dom_kind]

@@ -57,6 +57,8 @@ struct FmmTree {
     int* il_off = nullptr;
     int* nl_start = nullptr;    // neighbour leaves of each leaf (nleaf + 1)
     int* nl_leaf = nullptr;
+    int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
+    int nitems = 0;
     double2* m2m = nullptr;     // [4][k][m]
     double2* l2l = nullptr;     // [4][l][m]
     double2* m2l = nullptr;     // [49][k][l]
@@ -110,6 +112,8 @@ struct FmmArgs {
     const double2* s;
     double2* out;  // [R][N] in node order
     const int* done;
+    const int2* items;  // near-field work items: (leaf, first target of a chunk of 32)
+    int nitems;
 };
 
 __global__ void fmm_gather_kernel(FmmArgs a) {
@@ -130,28 +134,43 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
     }
 }
 
-// P2M: one warp per leaf, lane k forms a_k; the powers t^k come from a
-// multiplicative prefix scan across the warp, one node at a time.
+// P2M: one warp per leaf.  Each lane forms the powers t_j^k (k < P) of one
+// node of a chunk of 32 in shared memory; then lane k sums w_j t_j^k over the
+// chunk in node order.
 template <int R>
 __global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
+    __shared__ double2 s_pow[kFmmP][33];
+    __shared__ double2 s_w[R][32];
     if (a.done != nullptr && *a.done) return;
     const int leaf = blockIdx.x, lane = threadIdx.x;
     const int box = a.leaf_box[leaf];
     const double2 c = a.center[box];
     const double ir = 1.0 / a.width[box];
-    double2 acc[kMaxRHS] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-    for (int j = a.leaf_start[leaf]; j < a.leaf_start[leaf + 1]; ++j) {
-        const double2 p = a.ps[j];
-        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
-        double2 v = (lane == 0) ? make_double2(1.0, 0.0) : t;
+    double2 acc[R];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const double2 u = make_double2(__shfl_up_sync(0xffffffffu, v.x, off),
-                                           __shfl_up_sync(0xffffffffu, v.y, off));
-            if (lane >= off) v = cmul(u, v);
+    for (int r = 0; r < R; ++r) acc[r] = make_double2(0.0, 0.0);
+    const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
+    for (int base = j0; base < j1; base += 32) {
+        const int j = base + lane;
+        if (j < j1) {
+            const double2 p = a.ps[j];
+            const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
+            double2 v = make_double2(1.0, 0.0);
+            for (int k = 0; k < kFmmP; ++k) {
+                s_pow[k][lane] = v;
+                v = cmul(v, t);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) s_w[r][lane] = a.ws[(size_t)r * a.N + j];
         }
+        __syncwarp();
+        const int cnt = min(32, j1 - base);
+        for (int q = 0; q < cnt; ++q) {
+            const double2 pw = s_pow[lane][q];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = cmac(acc[r], a.ws[(size_t)r * a.N + j], v);
+            for (int r = 0; r < R; ++r) acc[r] = cmac(acc[r], s_w[r][q], pw);
+        }
+        __syncwarp();
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = acc[r];
@@ -207,71 +226,105 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
     }
 }
 
-// L2P and the near field of one leaf per block; writes z in node order
+// L2P (FP64) and the near field of one chunk of up to 32 targets of a leaf per
+// warp; writes z in node order.  The near field forms d = eta_i - eta_j in FP64
+// (exact for close nodes, whose differences carry the largest terms), splits it
+// into a float pair (2^-48 of |d|), and continues in double-float on the FP32
+// pipe (the FP64 pipe is 1/64 of it): |d|^2 with Dekker products, one Newton
+// step on the reciprocal, compensated accumulation.
+constexpr int kFmmWarps = kFmmNT / 32;
+
 template <int R>
 __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
+    __shared__ double2 s_b[kFmmWarps][R][kFmmP];
+    __shared__ double2 s_p[kFmmWarps][32];
+    __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
     if (a.done != nullptr && *a.done) return;
-    __shared__ double2 s_b[kMaxRHS][kFmmP];
-    __shared__ double2 s_p[kFmmNT];
-    __shared__ double2 s_w[kMaxRHS][kFmmNT];
-    const int leaf = blockIdx.x, tid = threadIdx.x;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kFmmWarps + wid;
+    if (item >= a.nitems) return;  // whole warps only: no block-wide barrier below
+    const int2 it = a.items[item];  // (leaf, first target)
+    const int leaf = it.x;
     const int box = a.leaf_box[leaf];
     const double2 c = a.center[box];
     const double ir = 1.0 / a.width[box];
-    for (int k = tid; k < R * kFmmP; k += kFmmNT)
-        s_b[k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
-    const int t0 = a.leaf_start[leaf], t1 = a.leaf_start[leaf + 1];
+    for (int k = lane; k < R * kFmmP; k += 32)
+        s_b[wid][k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
+    const int t1 = a.leaf_start[leaf + 1];
+    const int i = it.y + lane;
+    const bool act = i < t1;
+    const double2 p = a.ps[act ? i : it.y];
+    __syncwarp();
+    double2 z[R];
+    const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double2 v = s_b[wid][r][kFmmP - 1];
+        for (int l = kFmmP - 2; l >= 0; --l) {
+            const double2 bl = s_b[wid][r][l];
+            v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
+        }
+        z[r] = v;
+    }
+    df are[R], aim[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) are[r] = aim[r] = df{0.f, 0.f};
     const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
-    __syncthreads();
-    for (int base = t0; base < t1; base += kFmmNT) {
-        const int i = base + tid;
-        const bool act = i < t1;
-        const double2 p = a.ps[act ? i : t0];
-        double2 z[kMaxRHS] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-        // local expansion by Horner's rule
-        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
+    for (int e = n0; e < n1; ++e) {
+        const int nl = a.nl_leaf[e];
+        const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
+        for (int sb = s0; sb < s1; sb += 32) {
+            __syncwarp();
+            const int j = sb + lane;
+            if (j < s1) {
+                s_p[wid][lane] = a.ps[j];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            double2 v = s_b[r][kFmmP - 1];
-            for (int l = kFmmP - 2; l >= 0; --l) {
-                const double2 bl = s_b[r][l];
-                v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
-            }
-            z[r] = v;
-        }
-        // near field: the leaf and its neighbours, i = j excluded (Eq. fmm-E)
-        for (int e = n0; e < n1; ++e) {
-            const int nl = a.nl_leaf[e];
-            const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
-            for (int sb = s0; sb < s1; sb += kFmmNT) {
-                __syncthreads();
-                const int j = sb + tid;
-                if (j < s1) {
-                    s_p[tid] = a.ps[j];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) s_w[r][tid] = a.ws[(size_t)r * a.N + j];
-                }
-                __syncthreads();
-                const int cnt = min(kFmmNT, s1 - sb);
-                for (int k = 0; k < cnt; ++k) {
-                    const double dx = p.x - s_p[k].x, dy = p.y - s_p[k].y;
-                    double inv = recip_f64(fma(dx, dx, dy * dy));
-                    inv = (sb + k == i) ? 0.0 : inv;
-                    const double ar = dx * inv, ai = dy * inv;  // 1/d = ar - i ai
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const double2 w = s_w[r][k];
-                        z[r].x = fma(w.x, ar, fma(w.y, ai, z[r].x));
-                        z[r].y = fma(w.y, ar, fma(-w.x, ai, z[r].y));
-                    }
+                for (int r = 0; r < R; ++r) {
+                    const double2 w = a.ws[(size_t)r * a.N + j];
+                    const df wx = df_split(w.x), wy = df_split(w.y);
+                    s_w[wid][r][lane] = make_float4(wx.h, wx.l, wy.h, wy.l);
                 }
             }
-        }
-        if (act) {
-            const int node = a.perm[i];
+            __syncwarp();
+            const int cnt = min(32, s1 - sb);
+            for (int k = 0; k < cnt; ++k) {
+                const double2 q = s_p[wid][k];
+                const df dx = df_split(p.x - q.x), dy = df_split(p.y - q.y);
+                const float px = __fmul_rn(dx.h, dx.h);
+                float ex = fmaf(dx.h, dx.h, -px);
+                ex = fmaf(dx.h, __fadd_rn(dx.l, dx.l), ex);
+                const float py = __fmul_rn(dy.h, dy.h);
+                float ey = fmaf(dy.h, dy.h, -py);
+                ey = fmaf(dy.h, __fadd_rn(dy.l, dy.l), ey);
+                float rh, re;
+                two_sum(px, py, rh, re);
+                const float rl = __fadd_rn(__fadd_rn(ex, ey), re);
+                float y = recip_f32(rh);
+                y = (sb + k == i) ? 0.f : y;  // the i = j term is excluded (Eq. fmm-E)
+                float ee = fmaf(-rh, y, 1.0f);
+                ee = fmaf(-rl, y, ee);
+                const df inv{y, __fmul_rn(y, ee)};
+                const df ar = df_mul(dx, inv), ai = df_mul(dy, inv);  // 1/d = ar - i ai
 #pragma unroll
-            for (int r = 0; r < R; ++r) a.out[(size_t)r * a.N + node] = z[r];
+                for (int r = 0; r < R; ++r) {
+                    const float4 w4 = s_w[wid][r][k];
+                    const df wx{w4.x, w4.y}, wy{w4.z, w4.w};
+                    df_acc(are[r], df_mul(wx, ar));
+                    df_acc(are[r], df_mul(wy, ai));
+                    df_acc(aim[r], df_mul(wy, ar));
+                    const df qq = df_mul(wx, ai);
+                    df_acc(aim[r], df{-qq.h, -qq.l});
+                }
+            }
         }
+    }
+    if (act) {
+        const int node = a.perm[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            a.out[(size_t)r * a.N + node] =
+                make_double2(z[r].x + ((double)are[r].h + (double)are[r].l),
+                             z[r].y + ((double)aim[r].h + (double)aim[r].l));
     }
 }
 
@@ -539,6 +592,14 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         nl_start[q + 1] = (int)nl_leaf.size();
     }
     t->near_pairs = near_pairs;
+    // near-field work items: chunks of 32 targets of a leaf, largest leaves first
+    std::vector<int2> items;
+    for (int q = 0; q < t->nleaf; ++q)
+        for (int i = leaf_start[q]; i < leaf_start[q + 1]; i += 32) items.push_back(make_int2(q, i));
+    std::stable_sort(items.begin(), items.end(), [&](const int2& u, const int2& v) {
+        return (nl_start[u.x + 1] - nl_start[u.x]) > (nl_start[v.x + 1] - nl_start[v.x]);
+    });
+    t->nitems = (int)items.size();
     t->m2l_pairs = (long long)il_src.size();
     long long m2m_pairs = 0;
     for (int g = 0; g < nbox; ++g) m2m_pairs += child_count[g];
@@ -573,6 +634,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         {(void**)&t->il_off, nil * sizeof(int)},
         {(void**)&t->nl_start, (t->nleaf + 1) * sizeof(int)},
         {(void**)&t->nl_leaf, nnl * sizeof(int)},
+        {(void**)&t->items, std::max<size_t>(items.size(), 1) * sizeof(int2)},
         {(void**)&t->m2m, 4 * P * P * sizeof(double2)},
         {(void**)&t->l2l, 4 * P * P * sizeof(double2)},
         {(void**)&t->m2l, 49 * P * P * sizeof(double2)},
@@ -614,6 +676,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     GNK_TRY(up(t->il_off, il_off.data(), il_off.size() * sizeof(int)));
     GNK_TRY(up(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int)));
     GNK_TRY(up(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int)));
+    GNK_TRY(up(t->items, items.data(), items.size() * sizeof(int2)));
     GNK_TRY(up(t->m2m, m2m.data(), m2m.size() * sizeof(double2)));
     GNK_TRY(up(t->l2l, l2l.data(), l2l.size() * sizeof(double2)));
     GNK_TRY(up(t->m2l, m2l.data(), m2l.size() * sizeof(double2)));
@@ -623,15 +686,20 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
 }
 
 // FP64-pipe instructions of one FMM product (for the roofline): 4 per complex
-// multiply-add of the translations, P2M scan and L2P; 9 + 4R per near-field pair.
+// multiply-add of the translations, the P2M powers and sums, and L2P.  (The near
+// field runs on the FP32 pipe, 49 + 48R instructions per pair; see fmm_near_instr.)
 double fmm_instr(const Boundary& b, int R) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
     const double P = kFmmP;
     const double trans = (double)(t->m2l_pairs + t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
-    const double p2m = (double)b.N * P * (5.0 + R);
+    const double p2m = (double)b.N * P * (1.0 + R);
     const double l2p = (double)b.N * P * R;
-    return 4.0 * (trans * R + p2m + l2p) + (9.0 + 4.0 * R) * (double)t->near_pairs;
+    return 4.0 * (trans * R + p2m + l2p);
+}
+
+double fmm_near_instr(const Boundary& b, int R) {
+    return b.fmm ? (49.0 + 48.0 * R) * (double)b.fmm->near_pairs : 0.0;
 }
 
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
@@ -656,6 +724,8 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.il_off = t->il_off;
     a.nl_start = t->nl_start;
     a.nl_leaf = t->nl_leaf;
+    a.items = t->items;
+    a.nitems = t->nitems;
     a.m2m = t->m2m;
     a.l2l = t->l2l;
     a.m2l = t->m2l;
@@ -688,13 +758,18 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
         fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
+    GNK_TRY_CUDA(cudaGetLastError());
+    // the far field stands in for all R N (N - 1) pair evaluations of the product
+    prof_end(tok, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R));
+    const ProfToken tok2 = prof_begin(st);
+    const int grid = (t->nitems + kFmmWarps - 1) / kFmmWarps;
     if (job.R == 2)
-        fmm_leaf_kernel<2><<<t->nleaf, kFmmNT, 0, st>>>(a);
+        fmm_leaf_kernel<2><<<grid, kFmmNT, 0, st>>>(a);
     else
-        fmm_leaf_kernel<1><<<t->nleaf, kFmmNT, 0, st>>>(a);
+        fmm_leaf_kernel<1><<<grid, kFmmNT, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R));
+    prof_end(tok2, PK_FMMNEAR, (double)job.R * t->near_pairs, st, fmm_near_instr(b, job.R));
     GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
     count_launches(launches + 1);
     return GNK_OK;

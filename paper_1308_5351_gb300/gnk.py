@@ -51,7 +51,8 @@ EXPORTED = (
     "gnk_cauchy_eval",
 )
 
-PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM = range(8)
+PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
+    PROF_FMMNEAR = range(9)
 
 
 class gnk_options(ctypes.Structure):
