@@ -34,7 +34,7 @@ namespace gnk {
 
 constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
 constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
-constexpr int kFmmNT = 64;    // threads of the leaf (L2P + near field) kernel
+constexpr int kFmmNT = 256;   // threads of the leaf (L2P + near field) kernel: 8 warps
 
 struct FmmTree {
     int L = 0, nbox = 0, nleaf = 0, R = 0;
@@ -44,6 +44,8 @@ struct FmmTree {
     void* arena = nullptr;
     int* perm = nullptr;        // sorted position -> node
     double2* ps = nullptr;      // node positions in sorted order
+    float4* p3 = nullptr;       // the same split exactly into three floats: (x1, x2, x3, y1)
+    float2* p3b = nullptr;      // (y2, y3)
     int* leaf_start = nullptr;  // nleaf + 1
     int* leaf_box = nullptr;    // global box index of each leaf
     double2* center = nullptr;  // per box
@@ -83,6 +85,8 @@ struct FmmArgs {
     int N, R, P;
     const int* perm;
     const double2* ps;
+    const float4* p3;
+    const float2* p3b;
     const int* leaf_start;
     const int* leaf_box;
     const double2* center;
@@ -234,50 +238,60 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
 // step on the reciprocal, compensated accumulation.
 constexpr int kFmmWarps = kFmmNT / 32;
 
+// d = p - q as a double-float from the exact three-float splits of two FP64
+// coordinates: the TwoSums keep every rounding error, so close nodes (whose
+// FP64 difference is exact) get d to about 2^-47 of |d| itself.
+__device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, float q2, float q3) {
+    float s1, e1, s2, e2, h, l;
+    two_sum(p1, -q1, s1, e1);
+    two_sum(p2, -q2, s2, e2);
+    const float s3 = __fsub_rn(p3, q3);
+    two_sum(s1, s2, h, l);
+    l = __fadd_rn(l, __fadd_rn(__fadd_rn(e1, e2), s3));
+    df r;
+    fast_two_sum(h, l, r.h, r.l);
+    return r;
+}
+
+// One block per chunk of up to 32 targets of a leaf (lane = target); warp w sums
+// the near field of the neighbour leaves w, w + kFmmWarps, ...; the warps'
+// partial sums are added in warp order, then the local expansion (FP64).  The
+// near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
+// of it): d from the exact three-float node coordinates, |d|^2 with Dekker
+// products, one Newton step on the reciprocal, compensated accumulation.
 template <int R>
 __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
-    __shared__ double2 s_b[kFmmWarps][R][kFmmP];
-    __shared__ double2 s_p[kFmmWarps][32];
+    __shared__ float4 s_p[kFmmWarps][32];   // (x1, x2, x3, y1)
+    __shared__ float2 s_q[kFmmWarps][32];   // (y2, y3)
     __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
+    __shared__ double2 s_z[kFmmWarps][R][32];
+    __shared__ double2 s_b[R][kFmmP];
     if (a.done != nullptr && *a.done) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kFmmWarps + wid;
-    if (item >= a.nitems) return;  // whole warps only: no block-wide barrier below
-    const int2 it = a.items[item];  // (leaf, first target)
+    const int2 it = a.items[blockIdx.x];  // (leaf, first target)
     const int leaf = it.x;
     const int box = a.leaf_box[leaf];
-    const double2 c = a.center[box];
-    const double ir = 1.0 / a.width[box];
-    for (int k = lane; k < R * kFmmP; k += 32)
-        s_b[wid][k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
+    for (int k = threadIdx.x; k < R * kFmmP; k += kFmmNT)
+        s_b[k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
     const int t1 = a.leaf_start[leaf + 1];
     const int i = it.y + lane;
     const bool act = i < t1;
     const double2 p = a.ps[act ? i : it.y];
-    __syncwarp();
-    double2 z[R];
-    const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        double2 v = s_b[wid][r][kFmmP - 1];
-        for (int l = kFmmP - 2; l >= 0; --l) {
-            const double2 bl = s_b[wid][r][l];
-            v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
-        }
-        z[r] = v;
-    }
+    const float4 pa = a.p3[act ? i : it.y];
+    const float2 pb = a.p3b[act ? i : it.y];
     df are[R], aim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) are[r] = aim[r] = df{0.f, 0.f};
     const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
-    for (int e = n0; e < n1; ++e) {
+    for (int e = n0 + wid; e < n1; e += kFmmWarps) {
         const int nl = a.nl_leaf[e];
         const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
         for (int sb = s0; sb < s1; sb += 32) {
             __syncwarp();
             const int j = sb + lane;
             if (j < s1) {
-                s_p[wid][lane] = a.ps[j];
+                s_p[wid][lane] = a.p3[j];
+                s_q[wid][lane] = a.p3b[j];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const double2 w = a.ws[(size_t)r * a.N + j];
@@ -288,8 +302,10 @@ __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
             __syncwarp();
             const int cnt = min(32, s1 - sb);
             for (int k = 0; k < cnt; ++k) {
-                const double2 q = s_p[wid][k];
-                const df dx = df_split(p.x - q.x), dy = df_split(p.y - q.y);
+                const float4 qa = s_p[wid][k];
+                const float2 qb = s_q[wid][k];
+                const df dx = diff3(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z);
+                const df dy = diff3(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y);
                 const float px = __fmul_rn(dx.h, dx.h);
                 float ex = fmaf(dx.h, dx.h, -px);
                 ex = fmaf(dx.h, __fadd_rn(dx.l, dx.l), ex);
@@ -318,13 +334,29 @@ __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
             }
         }
     }
-    if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        s_z[wid][r][lane] = make_double2((double)are[r].h + (double)are[r].l,
+                                         (double)aim[r].h + (double)aim[r].l);
+    __syncthreads();
+    if (wid == 0 && act) {
+        const double2 c = a.center[box];
+        const double ir = 1.0 / a.width[box];
+        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
         const int node = a.perm[i];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            a.out[(size_t)r * a.N + node] =
-                make_double2(z[r].x + ((double)are[r].h + (double)are[r].l),
-                             z[r].y + ((double)aim[r].h + (double)aim[r].l));
+        for (int r = 0; r < R; ++r) {
+            double2 v = s_b[r][kFmmP - 1];
+            for (int l = kFmmP - 2; l >= 0; --l) {
+                const double2 bl = s_b[r][l];
+                v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
+            }
+            for (int w = 0; w < kFmmWarps; ++w) {
+                v.x += s_z[w][r][lane].x;
+                v.y += s_z[w][r][lane].y;
+            }
+            a.out[(size_t)r * a.N + node] = v;
+        }
     }
 }
 
@@ -379,6 +411,16 @@ const std::vector<double2>& cached_tables(int which) {
     static std::vector<double2> m2m, l2l, m2l;
     std::call_once(once, [] { translation_tables(&m2m, &l2l, &m2l); });
     return which == 0 ? m2m : (which == 1 ? l2l : m2l);
+}
+
+// v = s[0] + s[1] + s[2] exactly (each float takes the next 24 bits of the
+// double's 53; exact for |v| between 2^-80 and 2^120, which holds for
+// boundary nodes in any sane unit)
+void split3(double v, float* s) {
+    s[0] = (float)v;
+    const double r1 = v - (double)s[0];  // exact
+    s[1] = (float)r1;
+    s[2] = (float)(r1 - (double)s[1]);  // exact: at most 5 bits remain
 }
 
 uint32_t spread16(uint32_t v) {
@@ -621,6 +663,8 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     Part parts[] = {
         {(void**)&t->perm, N * sizeof(int)},
         {(void**)&t->ps, N * sizeof(double2)},
+        {(void**)&t->p3, N * sizeof(float4)},
+        {(void**)&t->p3b, N * sizeof(float2)},
         {(void**)&t->leaf_start, (t->nleaf + 1) * sizeof(int)},
         {(void**)&t->leaf_box, t->nleaf * sizeof(int)},
         {(void**)&t->center, nbox * sizeof(double2)},
@@ -663,6 +707,17 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     };
     GNK_TRY(up(t->perm, perm.data(), N * sizeof(int)));
     GNK_TRY(up(t->ps, ps.data(), N * sizeof(double2)));
+    std::vector<float4> p3(N);
+    std::vector<float2> p3b(N);
+    for (int i = 0; i < N; ++i) {
+        float sx[3], sy[3];
+        split3(ps[i].x, sx);
+        split3(ps[i].y, sy);
+        p3[i] = make_float4(sx[0], sx[1], sx[2], sy[0]);
+        p3b[i] = make_float2(sy[1], sy[2]);
+    }
+    GNK_TRY(up(t->p3, p3.data(), N * sizeof(float4)));
+    GNK_TRY(up(t->p3b, p3b.data(), N * sizeof(float2)));
     GNK_TRY(up(t->leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int)));
     GNK_TRY(up(t->leaf_box, leaf_box.data(), leaf_box.size() * sizeof(int)));
     GNK_TRY(up(t->center, center.data(), nbox * sizeof(double2)));
@@ -711,6 +766,8 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.P = kFmmP;
     a.perm = t->perm;
     a.ps = t->ps;
+    a.p3 = t->p3;
+    a.p3b = t->p3b;
     a.leaf_start = t->leaf_start;
     a.leaf_box = t->leaf_box;
     a.center = t->center;
@@ -762,7 +819,7 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     // the far field stands in for all R N (N - 1) pair evaluations of the product
     prof_end(tok, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R));
     const ProfToken tok2 = prof_begin(st);
-    const int grid = (t->nitems + kFmmWarps - 1) / kFmmWarps;
+    const int grid = t->nitems;
     if (job.R == 2)
         fmm_leaf_kernel<2><<<grid, kFmmNT, 0, st>>>(a);
     else
