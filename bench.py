@@ -49,15 +49,15 @@ PEAK_INSTR = {
     "pair32": SMS * SM_MAX_MHZ * 1e6 * 128,
     "pair64": SMS * SM_MAX_MHZ * 1e6 * 2,
     "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128,
-    "fmm": SMS * SM_MAX_MHZ * 1e6 * 2,
+    "fmm": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm_near": SMS * SM_MAX_MHZ * 1e6 * 128,
 }
 PEAK_BASIS = {
     "pair64": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 9 + 4R FP64 instr per pair",
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
-    "fmm": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 4 FP64 instr per complex multiply-add of "
-           "P2M, M2M, M2L, L2L, L2P (order 32)",
+    "fmm": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 48 FP32 instr per double-float complex "
+           "multiply-add of M2M, M2L, L2L (order 32), 38 + 48R per node and order in P2M",
     "fmm_near": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float "
                 "near-field pair",
 }

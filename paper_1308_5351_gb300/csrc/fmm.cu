@@ -61,25 +61,15 @@ struct FmmTree {
     int* nl_leaf = nullptr;
     int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
     int nitems = 0;
-    double2* m2m = nullptr;     // [4][k][m]
-    double2* l2l = nullptr;     // [4][l][m]
-    double2* m2l = nullptr;     // [49][k][l]
-    double2* mult = nullptr;    // [R][nbox][P]
-    double2* loc = nullptr;     // [R][nbox][P]
+    float4* m2m = nullptr;      // [4][k][m]   double-float complex (re.h, re.l, im.h, im.l)
+    float4* l2l = nullptr;      // [4][l][m]
+    float4* m2l = nullptr;      // [49][k][l]
+    float4* mult = nullptr;     // [R][nbox][P]
+    float4* loc = nullptr;      // [R][nbox][P]
     double2* ws = nullptr;      // [R][N] weights in sorted order
 };
 
 namespace {
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
-}
-__device__ __forceinline__ double2 shfl2(double2 v, int src) {
-    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
 
 struct FmmArgs {
     int N, R, P;
@@ -100,11 +90,11 @@ struct FmmArgs {
     const int* il_off;
     const int* nl_start;
     const int* nl_leaf;
-    const double2* m2m;
-    const double2* l2l;
-    const double2* m2l;
-    double2* mult;
-    double2* loc;
+    const float4* m2m;
+    const float4* l2l;
+    const float4* m2l;
+    float4* mult;
+    float4* loc;
     double2* ws;
     int nbox;
     // weights
@@ -138,46 +128,94 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
     }
 }
 
+// ---- complex double-float arithmetic for the far field (FP32 pipe).  The
+// expansions and translation tables are stored as float4 (re.h, re.l, im.h,
+// im.l); sums keep their rounding errors in the low words (about 2^-46 relative
+// per operation), far below the truncation error of the order-32 expansions.
+struct cdf {
+    df re, im;
+};
+
+__device__ __forceinline__ cdf cdf_of(float4 v) { return cdf{df{v.x, v.y}, df{v.z, v.w}}; }
+__device__ __forceinline__ float4 cdf_pack(cdf c) { return make_float4(c.re.h, c.re.l, c.im.h, c.im.l); }
+__device__ __forceinline__ cdf cdf_zero() { return cdf{df{0.f, 0.f}, df{0.f, 0.f}}; }
+__device__ __forceinline__ cdf cdf_split(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
+__device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
+
+// a + b, renormalised
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    df r;
+    fast_two_sum(s, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
+    return cdf{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))),
+               df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+
+// acc += a b
+__device__ __forceinline__ void cdf_mac(cdf& acc, cdf a, cdf b) {
+    df_acc(acc.re, df_mul(a.re, b.re));
+    df_acc(acc.re, df_neg(df_mul(a.im, b.im)));
+    df_acc(acc.im, df_mul(a.re, b.im));
+    df_acc(acc.im, df_mul(a.im, b.re));
+}
+
+__device__ __forceinline__ cdf cdf_shfl(cdf v, int src) {
+    return cdf{df{__shfl_sync(0xffffffffu, v.re.h, src), __shfl_sync(0xffffffffu, v.re.l, src)},
+               df{__shfl_sync(0xffffffffu, v.im.h, src), __shfl_sync(0xffffffffu, v.im.l, src)}};
+}
+
+// acc_lane += sum_k T[k][lane] x_k, x_k held by lane k (one P x P translation)
+__device__ __forceinline__ void translate(cdf& acc, const float4* __restrict__ T, cdf x, int lane) {
+#pragma unroll 4
+    for (int k = 0; k < kFmmP; ++k) cdf_mac(acc, cdf_of(__ldg(T + k * kFmmP + lane)), cdf_shfl(x, k));
+}
+
 // P2M: one warp per leaf.  Each lane forms the powers t_j^k (k < P) of one
 // node of a chunk of 32 in shared memory; then lane k sums w_j t_j^k over the
 // chunk in node order.
 template <int R>
 __global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
-    __shared__ double2 s_pow[kFmmP][33];
-    __shared__ double2 s_w[R][32];
+    __shared__ float4 s_pow[kFmmP][33];
+    __shared__ float4 s_w[R][32];
     if (a.done != nullptr && *a.done) return;
     const int leaf = blockIdx.x, lane = threadIdx.x;
     const int box = a.leaf_box[leaf];
     const double2 c = a.center[box];
     const double ir = 1.0 / a.width[box];
-    double2 acc[R];
+    cdf acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = make_double2(0.0, 0.0);
+    for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
     const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
     for (int base = j0; base < j1; base += 32) {
         const int j = base + lane;
         if (j < j1) {
             const double2 p = a.ps[j];
-            const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
-            double2 v = make_double2(1.0, 0.0);
+            const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+            cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
             for (int k = 0; k < kFmmP; ++k) {
-                s_pow[k][lane] = v;
-                v = cmul(v, t);
+                s_pow[k][lane] = cdf_pack(v);
+                v = cdf_mul(v, t);
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) s_w[r][lane] = a.ws[(size_t)r * a.N + j];
+            for (int r = 0; r < R; ++r) s_w[r][lane] = cdf_pack(cdf_split(a.ws[(size_t)r * a.N + j]));
         }
         __syncwarp();
         const int cnt = min(32, j1 - base);
         for (int q = 0; q < cnt; ++q) {
-            const double2 pw = s_pow[lane][q];
+            const cdf pw = cdf_of(s_pow[lane][q]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = cmac(acc[r], s_w[r][q], pw);
+            for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(s_w[r][q]), pw);
         }
         __syncwarp();
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = acc[r];
+    for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc[r]);
 }
 
 // M2M for the boxes [b0, b0 + gridDim.x) of one level
@@ -186,32 +224,28 @@ __global__ void __launch_bounds__(32) fmm_m2m_kernel(FmmArgs a, int b0) {
     const int box = b0 + blockIdx.x, lane = threadIdx.x;
     const int c0 = a.child_start[box], nc = a.child_count[box];
     for (int r = 0; r < a.R; ++r) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int c = c0; c < c0 + nc; ++c) {
-            const double2* T = a.m2m + (size_t)a.quad[c] * kFmmP * kFmmP;
-            const double2 mine = a.mult[((size_t)r * a.nbox + c) * kFmmP + lane];
-#pragma unroll 8
-            for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
-        }
-        a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = acc;
+        cdf acc = cdf_zero();
+        for (int c = c0; c < c0 + nc; ++c)
+            translate(acc, a.m2m + (size_t)a.quad[c] * kFmmP * kFmmP,
+                      cdf_of(a.mult[((size_t)r * a.nbox + c) * kFmmP + lane]), lane);
+        a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
     }
 }
 
-// M2L for every box of levels 2..L (one warp per target box)
+// M2L for every box of levels 2..L (one warp per target box); the 1/r factor of
+// the scaled local expansion is applied once at the end
 __global__ void __launch_bounds__(32) fmm_m2l_kernel(FmmArgs a) {
     if (a.done != nullptr && *a.done) return;
     const int box = blockIdx.x, lane = threadIdx.x;
-    const double ir = 1.0 / a.width[box];
     const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
     for (int r = 0; r < a.R; ++r) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int e = e0; e < e1; ++e) {
-            const double2* T = a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP;
-            const double2 mine = a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane];
-#pragma unroll 8
-            for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
-        }
-        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = make_double2(acc.x * ir, acc.y * ir);
+        cdf acc = cdf_zero();
+        for (int e = e0; e < e1; ++e)
+            translate(acc, a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP,
+                      cdf_of(a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane]), lane);
+        const df s = df_split(1.0 / a.width[box]);
+        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] =
+            cdf_pack(cdf{df_mul(acc.re, s), df_mul(acc.im, s)});
     }
 }
 
@@ -220,13 +254,11 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
     if (a.done != nullptr && *a.done) return;
     const int box = b0 + blockIdx.x, lane = threadIdx.x;
     const int par = a.parent[box];
-    const double2* T = a.l2l + (size_t)a.quad[box] * kFmmP * kFmmP;
+    const float4* T = a.l2l + (size_t)a.quad[box] * kFmmP * kFmmP;
     for (int r = 0; r < a.R; ++r) {
-        const double2 mine = a.loc[((size_t)r * a.nbox + par) * kFmmP + lane];
-        double2 acc = a.loc[((size_t)r * a.nbox + box) * kFmmP + lane];
-#pragma unroll 8
-        for (int k = 0; k < kFmmP; ++k) acc = cmac(acc, T[k * kFmmP + lane], shfl2(mine, k));
-        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = acc;
+        cdf acc = cdf_of(a.loc[((size_t)r * a.nbox + box) * kFmmP + lane]);
+        translate(acc, T, cdf_of(a.loc[((size_t)r * a.nbox + par) * kFmmP + lane]), lane);
+        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
     }
 }
 
@@ -272,7 +304,10 @@ __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
     const int leaf = it.x;
     const int box = a.leaf_box[leaf];
     for (int k = threadIdx.x; k < R * kFmmP; k += kFmmNT)
-        s_b[k / kFmmP][k % kFmmP] = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
+    {
+        const float4 v = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
+        s_b[k / kFmmP][k % kFmmP] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
     const int t1 = a.leaf_start[leaf + 1];
     const int i = it.y + lane;
     const bool act = i < t1;
@@ -369,11 +404,17 @@ long double binom_ld(int n, int k) {
     return v;
 }
 
-void translation_tables(std::vector<double2>* m2m, std::vector<double2>* l2l, std::vector<double2>* m2l) {
+// a complex value as a double-float pair per part (hi = nearest float, lo = the rest)
+float4 cdf_host(const cld& v) {
+    const float rh = (float)v.real(), ih = (float)v.imag();
+    return make_float4(rh, (float)(v.real() - (long double)rh), ih, (float)(v.imag() - (long double)ih));
+}
+
+void translation_tables(std::vector<float4>* m2m, std::vector<float4>* l2l, std::vector<float4>* m2l) {
     const int P = kFmmP;
-    m2m->assign(4 * P * P, make_double2(0.0, 0.0));
-    l2l->assign(4 * P * P, make_double2(0.0, 0.0));
-    m2l->assign(49 * P * P, make_double2(0.0, 0.0));
+    m2m->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    l2l->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    m2l->assign(49 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int q = 0; q < 4; ++q) {
         const int qa = q >> 1, qb = q & 1;
         const cld dd((2 * qa - 1) / 4.0L, (2 * qb - 1) / 4.0L);
@@ -381,13 +422,13 @@ void translation_tables(std::vector<double2>* m2m, std::vector<double2>* l2l, st
             for (int k = 0; k <= m; ++k) {
                 // M2M: row m, column k; stored [q][k][m]
                 const cld v = binom_ld(m, k) * std::pow(dd, m - k) * std::pow(2.0L, -k);
-                (*m2m)[(size_t)q * P * P + k * P + m] = make_double2((double)v.real(), (double)v.imag());
+                (*m2m)[(size_t)q * P * P + k * P + m] = cdf_host(v);
             }
         for (int m = 0; m < P; ++m)
             for (int l = m; l < P; ++l) {
                 // L2L: row m, column l; stored [q][l][m]
                 const cld v = binom_ld(l, m) * std::pow(dd, l - m) * std::pow(2.0L, -m);
-                (*l2l)[(size_t)q * P * P + l * P + m] = make_double2((double)v.real(), (double)v.imag());
+                (*l2l)[(size_t)q * P * P + l * P + m] = cdf_host(v);
             }
     }
     for (int dx = -3; dx <= 3; ++dx)
@@ -400,15 +441,15 @@ void translation_tables(std::vector<double2>* m2m, std::vector<double2>* l2l, st
                     // M2L: row l, column k; stored [o][k][l]
                     const long double sgn = ((k + 1) % 2) ? -1.0L : 1.0L;
                     const cld v = sgn * binom_ld(k + l, l) * std::pow(inv, k + l + 1);
-                    (*m2l)[(size_t)o * P * P + k * P + l] = make_double2((double)v.real(), (double)v.imag());
+                    (*m2l)[(size_t)o * P * P + k * P + l] = cdf_host(v);
                 }
         }
 }
 
 // The translation tables depend only on P: formed once per process.
-const std::vector<double2>& cached_tables(int which) {
+const std::vector<float4>& cached_tables(int which) {
     static std::once_flag once;
-    static std::vector<double2> m2m, l2l, m2l;
+    static std::vector<float4> m2m, l2l, m2l;
     std::call_once(once, [] { translation_tables(&m2m, &l2l, &m2l); });
     return which == 0 ? m2m : (which == 1 ? l2l : m2l);
 }
@@ -649,9 +690,9 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     const std::vector<int>& perm = ord0;
     std::vector<double2> ps(N);
     for (int i = 0; i < N; ++i) ps[i] = et[perm[i]];
-    const std::vector<double2>& m2m = cached_tables(0);
-    const std::vector<double2>& l2l = cached_tables(1);
-    const std::vector<double2>& m2l = cached_tables(2);
+    const std::vector<float4>& m2m = cached_tables(0);
+    const std::vector<float4>& l2l = cached_tables(1);
+    const std::vector<float4>& m2l = cached_tables(2);
 
     // one device allocation for the tree and the expansions
     const size_t P = kFmmP;
@@ -679,11 +720,11 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         {(void**)&t->nl_start, (t->nleaf + 1) * sizeof(int)},
         {(void**)&t->nl_leaf, nnl * sizeof(int)},
         {(void**)&t->items, std::max<size_t>(items.size(), 1) * sizeof(int2)},
-        {(void**)&t->m2m, 4 * P * P * sizeof(double2)},
-        {(void**)&t->l2l, 4 * P * P * sizeof(double2)},
-        {(void**)&t->m2l, 49 * P * P * sizeof(double2)},
-        {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(double2)},
-        {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(double2)},
+        {(void**)&t->m2m, 4 * P * P * sizeof(float4)},
+        {(void**)&t->l2l, 4 * P * P * sizeof(float4)},
+        {(void**)&t->m2l, 49 * P * P * sizeof(float4)},
+        {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(float4)},
+        {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->ws, (size_t)t->R * N * sizeof(double2)},
     };
     size_t total = 0;
@@ -732,25 +773,24 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     GNK_TRY(up(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int)));
     GNK_TRY(up(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int)));
     GNK_TRY(up(t->items, items.data(), items.size() * sizeof(int2)));
-    GNK_TRY(up(t->m2m, m2m.data(), m2m.size() * sizeof(double2)));
-    GNK_TRY(up(t->l2l, l2l.data(), l2l.size() * sizeof(double2)));
-    GNK_TRY(up(t->m2l, m2l.data(), m2l.size() * sizeof(double2)));
+    GNK_TRY(up(t->m2m, m2m.data(), m2m.size() * sizeof(float4)));
+    GNK_TRY(up(t->l2l, l2l.data(), l2l.size() * sizeof(float4)));
+    GNK_TRY(up(t->m2l, m2l.data(), m2l.size() * sizeof(float4)));
     // the host vectors above are released on return: finish the copies first
     GNK_TRY_CUDA(cudaStreamSynchronize(st));
     return GNK_OK;
 }
 
-// FP64-pipe instructions of one FMM product (for the roofline): 4 per complex
-// multiply-add of the translations, the P2M powers and sums, and L2P.  (The near
-// field runs on the FP32 pipe, 49 + 48R instructions per pair; see fmm_near_instr.)
+// FP32-pipe instructions of the far field of one FMM product (for the roofline):
+// 48 per double-float complex multiply-add of the translations (4 Dekker products
+// and 4 compensated sums), and per node and order 38 for the power and 48 R for
+// the P2M sums.  (The near field: 49 + 48R per pair, fmm_near_instr.)
 double fmm_instr(const Boundary& b, int R) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
     const double P = kFmmP;
     const double trans = (double)(t->m2l_pairs + t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
-    const double p2m = (double)b.N * P * (1.0 + R);
-    const double l2p = (double)b.N * P * R;
-    return 4.0 * (trans * R + p2m + l2p);
+    return 48.0 * trans * R + (double)b.N * P * (38.0 + 48.0 * R);
 }
 
 double fmm_near_instr(const Boundary& b, int R) {
