@@ -6,11 +6,14 @@ U[0.1,0.4], min gap 0.05) with n = 1024 nodes per boundary (65,536 unknowns),
 gamma = log|eta - alpha| with alpha the centre of the first ellipse.
 
 One step = build the boundary handle from device-resident eta, eta', A (this
-includes Eone = E q and the diagonals), run the fused FBIE computation (right-
-hand side, GMRES to ||b - A mu|| <= 1e-10 ||b||, h and h_k), free the handle.
-The headline form is FP32 pair sums inside GMRES with double-float (FP64-class,
-on the FP32 pipe) refinement residuals; the plain FP64 GPU path, the FP32-inner
-form with native FP64 residuals, and the adjoint equation are timed beside it.
+includes the quadtree, Eone = E q and the diagonals), run the fused FBIE
+computation (right-hand side, GMRES to ||b - A mu|| <= 1e-10 ||b||, h and h_k),
+free the handle.  The headline form evaluates every Cauchy sum by the fast
+multipole method, as the paper does (order-32 expansions, FMM error ~1e-13 of
+sum |w/d|; translations and near field in double-float on the FP32 pipe); the
+final residual is re-checked with direct double-float sums.  The plain FP64
+direct-sum GPU path, FP32 GMRES with FP64 / double-float / FMM refinement and
+the adjoint equation are timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own seeded domain of the same shape
@@ -68,6 +71,10 @@ PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cau
 ROOF_KINDS = PAIR_KINDS + ("fmm_near",)
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
 FMM_MODES = ("fmm", "mixed_fmm")
+DTYPES = {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
+          "fp64": "f64", "df32": "double-float f32 pairs, f64 vectors",
+          "fmm": "f64-class: FMM with double-float f32 translations and near field, f64 vectors",
+          "mixed_fmm": "f32 pairs + f64-class FMM"}
 
 
 def parse():
@@ -81,7 +88,7 @@ def parse():
     ap.add_argument("--count", type=int, default=64, help="ellipses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves")
-    ap.add_argument("--precision", choices=list(MODES), default="mixed_df")
+    ap.add_argument("--precision", choices=list(MODES), default="fmm")
     ap.add_argument("--workload", choices=["ellipses64", "close1024", "batched256", "stars20"],
                     default="ellipses64", help="ellipses64 is the headline; the others are extra lines")
     ap.add_argument("--domains", type=int, default=256, help="batched256: number of domains")
@@ -291,6 +298,14 @@ def main():
     res = results["last"]
     mu_main = mu.clone()
     h_main = hk.clone()
+    # the final relative residual re-checked with direct double-float Cauchy sums
+    hchk = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, None, None, dom.bounded,
+                                   G.GNK_PREC_DF32, stream)
+    yv, kmu = torch.empty_like(gam), torch.empty_like(gam)
+    G.gnk_apply_M(hchk, gam, yv, G.GNK_PREC_DF32, stream)
+    G.gnk_apply_IminusN(hchk, mu, kmu, G.GNK_PREC_DF32, stream)
+    G.gnk_free_boundary(hchk)
+    relres_direct = float((kmu + yv).norm() / yv.norm())
 
     # ---- the same problem in the other forms (one timed run each, after one untimed)
     compare = {}
@@ -402,9 +417,7 @@ def main():
         "metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
-                  "fp64": "f64", "df32": "double-float f32 pairs, f64 vectors",
-                  "fmm": "f64 (FMM, order 32)", "mixed_fmm": "f32 pairs + f64 FMM"}[args.precision],
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
                    "restart": 20, "precision": args.precision,
@@ -414,7 +427,8 @@ def main():
         "pair_evals_per_s_by_kernel": {KERNEL_NAME[k]: v for k, v in kernel_rates.items()},
         "solve": {"precision": args.precision, "iterations": res.iterations,
                   "refinements": res.refinements, "matvecs_fp64_class": res.matvecs_fp64,
-                  "matvecs_fp32": res.matvecs_fp32, "relres": res.relres},
+                  "matvecs_fp32": res.matvecs_fp32, "relres": res.relres,
+                  "relres_direct_df32": relres_direct},
         "compare": compare,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -470,18 +484,22 @@ def run_extra(args, dist, rank, ws, local):
         mu, h = torch.empty_like(gam), torch.empty_like(gam)
         hk = torch.empty(dom.m1, dtype=torch.float64, device=dev)
 
+        main = args.precision
+
         def step(prec):
             o = G.options(tol=TOL, restart=30, maxit=60, precision=MODES[prec], inner_tol=1e-5)
             bp = G.GNK_PREC_DF32 if prec in ("mixed_df", "df32") else G.GNK_PREC_FP64
+            if prec in FMM_MODES:
+                bp = G.GNK_PREC_FMM
             hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, None, None, False, bp, stream)
             r = G.gnk_fbie(hnd, gam, mu, h, hk, o, stream)
             G.gnk_free_boundary(hnd)
             return r
         for _ in range(args.warmup):
-            step("mixed_df")
+            step(main)
         times, res = [], None
         for _ in range(args.steps):
-            res, t = _timed(lambda: step("mixed_df"), stream)
+            res, t = _timed(lambda: step(main), stream)
             times.append(t)
         mu_np, h_np = mu.cpu().numpy(), h.cpu().numpy()
         # rows of the discrete equation (2I + diag(B1) - B) mu = -(D - diag(D1) + Lhat) gamma
@@ -489,10 +507,14 @@ def run_extra(args, dist, rank, ws, local):
         lhs = O.rows_IminusN(dom.et, dom.etp, dom.A, dom.n, mu_np, rows)
         rhs = -O.rows_M(dom.et, dom.etp, dom.A, dom.n, gam_np, rows)
         compare = {}
-        _, t_mixed = _timed(lambda: step("mixed"), stream)
-        compare["mixed"] = {"time_to_solution_s": t_mixed,
-                            "max_rel_diff_mu_vs_headline": float(np.abs(mu.cpu().numpy() - mu_np).max()
-                                                                 / np.abs(mu_np).max())}
+        others = [p for p in ("mixed_df", "mixed_fmm") if p != main]
+        if args.with_fp64:
+            others.append("mixed")
+        for other in others:
+            _, t_o = _timed(lambda: step(other), stream)
+            compare[other] = {"time_to_solution_s": t_o,
+                              "max_rel_diff_mu_vs_headline": float(np.abs(mu.cpu().numpy() - mu_np).max()
+                                                                   / np.abs(mu_np).max())}
         if args.with_fp64:
             _, t64 = _timed(lambda: step("fp64"), stream)
             compare["fp64"] = {"time_to_solution_s": t64,
@@ -501,15 +523,17 @@ def run_extra(args, dist, rank, ws, local):
         # error against the dense oracle on the first 64 boundaries at n = 128
         sub = Dm.build_domain(dom.curves[:64], 128, bounded=False)
         gs = Dm.gamma_log(sub, dom.holes[0])
-        with G.Boundary.from_domain(sub, adjoint=False, device=dev, precision=G.GNK_PREC_DF32) as bs:
-            ms, hs_, hks, rs = bs.fbie(torch.as_tensor(gs, device=dev), tol=TOL, precision=4, restart=30)
+        sub_bp = G.GNK_PREC_FMM if main in FMM_MODES else G.GNK_PREC_DF32
+        with G.Boundary.from_domain(sub, adjoint=False, device=dev, precision=sub_bp) as bs:
+            ms, hs_, hks, rs = bs.fbie(torch.as_tensor(gs, device=dev), tol=TOL, precision=MODES[main],
+                                       restart=30)
         mo, ho, hko = O.fbie(sub.et, sub.etp, sub.A, sub.n, gs)
         line.update({
             "value": statistics.median(times), "ms_per_step": 1e3 * statistics.median(times),
-            "dtype": "f32 + double-float f32 pairs, f64 vectors",
+            "dtype": DTYPES[main],
             "config": {"workload": "1024 close curves (circles, ellipses, 32 graded squares; gaps to "
                                    "1e-3 r), unbounded, n=512 (524,288 unknowns): FBIE solve + h",
-                       "N": dom.N, "tol": TOL, "restart": 30, "precision": "mixed_df",
+                       "N": dom.N, "tol": TOL, "restart": 30, "precision": main,
                        "l2": "working set larger than L2 (basis 130 MB)"},
             "solve": {"iterations": res.iterations, "refinements": res.refinements, "relres": res.relres},
             "sampled_row_residual_rel": float(np.abs(lhs - rhs).max() / np.abs(rhs).max()),
