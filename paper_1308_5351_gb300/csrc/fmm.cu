@@ -24,6 +24,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -446,6 +447,11 @@ void translation_tables(std::vector<float4>* m2m, std::vector<float4>* l2l, std:
         }
 }
 
+// Pinned host staging for the tree upload (grown on demand, kept for the process).
+std::mutex g_stage_mutex;
+void* g_stage = nullptr;
+size_t g_stage_bytes = 0;
+
 // The translation tables depend only on P: formed once per process.
 const std::vector<float4>& cached_tables(int which) {
     static std::once_flag once;
@@ -510,14 +516,14 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         key0[i] = (spread16(ix) << 1) | spread16(iy);
         ord0[i] = i;
     }
-    // LSD radix sort, two stable passes of 16 bits: (key, node) in increasing order
-    for (int pass = 0; pass < 2; ++pass) {
-        const int sh = 16 * pass;
-        std::vector<int> cnt(65537, 0);
-        for (int i = 0; i < N; ++i) ++cnt[((key0[i] >> sh) & 0xffffu) + 1];
-        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+    // LSD radix sort, four stable passes of 8 bits: (key, node) in increasing order
+    for (int pass = 0; pass < 4; ++pass) {
+        const int sh = 8 * pass;
+        int cnt[257] = {0};
+        for (int i = 0; i < N; ++i) ++cnt[((key0[i] >> sh) & 0xffu) + 1];
+        for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
         for (int i = 0; i < N; ++i) {
-            const int dst = cnt[(key0[i] >> sh) & 0xffffu]++;
+            const int dst = cnt[(key0[i] >> sh) & 0xffu]++;
             key1[dst] = key0[i];
             ord1[dst] = ord0[i];
         }
@@ -531,8 +537,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     for (int i = 1; i < N; ++i) {
         const uint32_t x = key0[i] ^ key0[i - 1];
         if (x == 0) continue;
-        int msb = 31;
-        while (!((x >> msb) & 1u)) --msb;
+        const int msb = 31 - __builtin_clz(x);
         ++first_diff[16 - msb / 2];  // distinct from this level down
     }
     int L = 2;
@@ -589,89 +594,82 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         *ix = (int)compact(key >> 1);
         *iy = (int)compact(key);
     };
-    auto encode = [](int ix, int iy) { return (spread16((uint32_t)ix) << 1) | spread16((uint32_t)iy); };
-    // box lookup: a dense grid per level up to 2^11 x 2^11 boxes, else binary search
-    std::vector<std::vector<int>> grid(nlev);
-    for (int l = 2; l <= L; ++l) {
-        if (l > 11) continue;
-        const int n = 1 << l;
-        grid[l - 2].assign((size_t)n * n, -1);
-        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
-            int ix, iy;
-            decode(keys[l - 2][q], &ix, &iy);
-            grid[l - 2][(size_t)ix * n + iy] = t->lvl_off[l - 2] + q;
-        }
-    }
-    auto find = [&](int l, int ix, int iy) -> int {
-        const int n = 1 << l;
-        if (ix < 0 || iy < 0 || ix >= n || iy >= n) return -1;
-        if (l <= 11) return grid[l - 2][(size_t)ix * n + iy];
-        const std::vector<uint32_t>& v = keys[l - 2];
-        const uint32_t k = encode(ix, iy);
-        auto it = std::lower_bound(v.begin(), v.end(), k);
-        if (it == v.end() || *it != k) return -1;
-        return t->lvl_off[l - 2] + (int)(it - v.begin());
-    };
+    // box geometry, parents and children: children of a box are contiguous in
+    // key order, so one pass over each level links it to the level above
+    std::vector<int> bix(nbox), biy(nbox);
+    for (int l = 2; l <= L; ++l)
+        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) decode(keys[l - 2][q], &bix[t->lvl_off[l - 2] + q],
+                                                           &biy[t->lvl_off[l - 2] + q]);
     std::vector<double2> center(nbox);
     std::vector<double> width(nbox);
-    std::vector<int> child_start(nbox, 0), child_count(nbox, 0), parent(nbox, -1), quad(nbox, 0);
-    std::vector<int> il_start(nbox + 1, 0), il_src, il_off;
+    std::vector<int> child_start(nbox, -1), child_count(nbox, 0), parent(nbox, -1), quad(nbox, 0);
     for (int l = 2; l <= L; ++l) {
         const double r = W / (double)(1 << l);
         for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
             const int g = t->lvl_off[l - 2] + q;
-            int ix, iy;
-            decode(keys[l - 2][q], &ix, &iy);
-            center[g] = make_double2(x0 + (ix + 0.5) * r, y0 + (iy + 0.5) * r);
+            center[g] = make_double2(x0 + (bix[g] + 0.5) * r, y0 + (biy[g] + 0.5) * r);
             width[g] = r;
-            quad[g] = ((ix & 1) << 1) | (iy & 1);
-            if (l > 2) parent[g] = find(l - 1, ix >> 1, iy >> 1);
-            if (l < L) {
-                const int c0 = find(l + 1, 2 * ix, 2 * iy);
-                // children of a box are contiguous in key order; the first existing one starts the run
-                int first = -1, cnt = 0;
-                for (int qa = 0; qa < 2; ++qa)
-                    for (int qb = 0; qb < 2; ++qb) {
-                        const int c = find(l + 1, 2 * ix + qa, 2 * iy + qb);
-                        if (c >= 0) {
-                            first = (first < 0) ? c : std::min(first, c);
-                            ++cnt;
-                        }
-                    }
-                (void)c0;
-                child_start[g] = first;
-                child_count[g] = cnt;
+            quad[g] = ((bix[g] & 1) << 1) | (biy[g] & 1);
+        }
+        if (l == 2) continue;
+        int pq = -1;
+        uint32_t last = 0;
+        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
+            const uint32_t pk = keys[l - 2][q] >> 2;
+            if (pq < 0 || pk != last) {
+                ++pq;
+                last = pk;
             }
-            // interaction list: children of the parent's neighbours that are not adjacent
-            const int pa = ix >> 1, pb = iy >> 1;
-            for (int sa = 2 * pa - 2; sa <= 2 * pa + 3; ++sa)
-                for (int sb = 2 * pb - 2; sb <= 2 * pb + 3; ++sb) {
-                    const int dx = sa - ix, dy = sb - iy;
-                    if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
-                    const int s = find(l, sa, sb);
-                    if (s < 0) continue;
-                    il_src.push_back(s);
-                    il_off.push_back((dx + 3) * 7 + (dy + 3));
-                }
-            il_start[g + 1] = (int)il_src.size();
+            const int g = t->lvl_off[l - 2] + q, pg = t->lvl_off[l - 3] + pq;
+            parent[g] = pg;
+            if (child_start[pg] < 0) child_start[pg] = g;
+            ++child_count[pg];
         }
     }
-    // neighbour leaves (3 x 3, the leaf itself included)
+    // neighbour lists (adjacent boxes of the same level, the box itself included)
+    // and interaction lists, level by level from the children of the parent's
+    // neighbours; level 2 compares all pairs
+    std::vector<int> nb_start(nbox + 1, 0), nb;
+    std::vector<int> il_start(nbox + 1, 0), il_src, il_off;
+    nb.reserve((size_t)nbox * 6);
+    il_src.reserve((size_t)nbox * 16);
+    il_off.reserve((size_t)nbox * 16);
+    auto visit = [&](int g, int c) {
+        const int dx = bix[c] - bix[g], dy = biy[c] - biy[g];
+        if (std::abs(dx) <= 1 && std::abs(dy) <= 1) {
+            nb.push_back(c);
+        } else {
+            il_src.push_back(c);
+            il_off.push_back((dx + 3) * 7 + (dy + 3));
+        }
+    };
+    for (int l = 2; l <= L; ++l)
+        for (int q = 0; q < t->lvl_cnt[l - 2]; ++q) {
+            const int g = t->lvl_off[l - 2] + q;
+            if (l == 2) {
+                for (int c = t->lvl_off[0]; c < t->lvl_off[0] + t->lvl_cnt[0]; ++c) visit(g, c);
+            } else {
+                const int pg = parent[g];
+                for (int e = nb_start[pg]; e < nb_start[pg + 1]; ++e) {
+                    const int qn = nb[e];
+                    for (int c = child_start[qn]; c < child_start[qn] + child_count[qn]; ++c) visit(g, c);
+                }
+            }
+            nb_start[g + 1] = (int)nb.size();
+            il_start[g + 1] = (int)il_src.size();
+        }
+    // neighbour leaves of each leaf (the leaf itself included)
     std::vector<int> nl_start(t->nleaf + 1, 0), nl_leaf, leaf_box(t->nleaf);
     long long near_pairs = 0;
+    const int loff = t->lvl_off[L - 2];
     for (int q = 0; q < t->nleaf; ++q) {
-        leaf_box[q] = t->lvl_off[L - 2] + q;
-        int ix, iy;
-        decode(keys[L - 2][q], &ix, &iy);
+        leaf_box[q] = loff + q;
         const long long cnt_t = leaf_start[q + 1] - leaf_start[q];
-        for (int sa = ix - 1; sa <= ix + 1; ++sa)
-            for (int sb = iy - 1; sb <= iy + 1; ++sb) {
-                const int g = find(L, sa, sb);
-                if (g < 0) continue;
-                const int lq = g - t->lvl_off[L - 2];
-                nl_leaf.push_back(lq);
-                near_pairs += cnt_t * (leaf_start[lq + 1] - leaf_start[lq]);
-            }
+        for (int e = nb_start[loff + q]; e < nb_start[loff + q + 1]; ++e) {
+            const int lq = nb[e] - loff;
+            nl_leaf.push_back(lq);
+            near_pairs += cnt_t * (leaf_start[lq + 1] - leaf_start[lq]);
+        }
         nl_start[q + 1] = (int)nl_leaf.size();
     }
     t->near_pairs = near_pairs;
@@ -740,16 +738,32 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         *p.p = cur;
         cur += (p.bytes + 255) / 256 * 256;
     }
-    b.fmm = t;  // owned by the handle from here on (freed by release_fmm)
-    auto up = [&](void* dst, const void* src, size_t bytes) -> int {
-        if (bytes == 0) return GNK_OK;
-        GNK_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
-        return GNK_OK;
+    // everything but the expansions goes up in one copy, staged in a pinned
+    // host buffer laid out like the device arena
+    const size_t upload = (size_t)((char*)t->mult - (char*)t->arena);
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    if (g_stage_bytes < upload) {
+        if (g_stage) cudaFreeHost(g_stage);
+        g_stage = nullptr;
+        g_stage_bytes = 0;
+        if (cudaHostAlloc(&g_stage, upload, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            g_stage = nullptr;
+            cudaFree(t->arena);
+            delete t;
+            set_error("FMM tree: pinned staging allocation of %zu bytes failed", upload);
+            return GNK_ENOMEM;
+        }
+        g_stage_bytes = upload;
+    }
+    char* hb = static_cast<char*>(g_stage);
+    auto put = [&](const void* dst, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(hb + ((const char*)dst - (const char*)t->arena), src, bytes);
     };
-    GNK_TRY(up(t->perm, perm.data(), N * sizeof(int)));
-    GNK_TRY(up(t->ps, ps.data(), N * sizeof(double2)));
-    std::vector<float4> p3(N);
-    std::vector<float2> p3b(N);
+    put(t->perm, perm.data(), N * sizeof(int));
+    put(t->ps, ps.data(), N * sizeof(double2));
+    float4* p3 = reinterpret_cast<float4*>(hb + ((char*)t->p3 - (char*)t->arena));
+    float2* p3b = reinterpret_cast<float2*>(hb + ((char*)t->p3b - (char*)t->arena));
     for (int i = 0; i < N; ++i) {
         float sx[3], sy[3];
         split3(ps[i].x, sx);
@@ -757,27 +771,34 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         p3[i] = make_float4(sx[0], sx[1], sx[2], sy[0]);
         p3b[i] = make_float2(sy[1], sy[2]);
     }
-    GNK_TRY(up(t->p3, p3.data(), N * sizeof(float4)));
-    GNK_TRY(up(t->p3b, p3b.data(), N * sizeof(float2)));
-    GNK_TRY(up(t->leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int)));
-    GNK_TRY(up(t->leaf_box, leaf_box.data(), leaf_box.size() * sizeof(int)));
-    GNK_TRY(up(t->center, center.data(), nbox * sizeof(double2)));
-    GNK_TRY(up(t->width, width.data(), nbox * sizeof(double)));
-    GNK_TRY(up(t->child_start, child_start.data(), nbox * sizeof(int)));
-    GNK_TRY(up(t->child_count, child_count.data(), nbox * sizeof(int)));
-    GNK_TRY(up(t->parent, parent.data(), nbox * sizeof(int)));
-    GNK_TRY(up(t->quad, quad.data(), nbox * sizeof(int)));
-    GNK_TRY(up(t->il_start, il_start.data(), il_start.size() * sizeof(int)));
-    GNK_TRY(up(t->il_src, il_src.data(), il_src.size() * sizeof(int)));
-    GNK_TRY(up(t->il_off, il_off.data(), il_off.size() * sizeof(int)));
-    GNK_TRY(up(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int)));
-    GNK_TRY(up(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int)));
-    GNK_TRY(up(t->items, items.data(), items.size() * sizeof(int2)));
-    GNK_TRY(up(t->m2m, m2m.data(), m2m.size() * sizeof(float4)));
-    GNK_TRY(up(t->l2l, l2l.data(), l2l.size() * sizeof(float4)));
-    GNK_TRY(up(t->m2l, m2l.data(), m2l.size() * sizeof(float4)));
-    // the host vectors above are released on return: finish the copies first
-    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    put(t->leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int));
+    put(t->leaf_box, leaf_box.data(), leaf_box.size() * sizeof(int));
+    put(t->center, center.data(), nbox * sizeof(double2));
+    put(t->width, width.data(), nbox * sizeof(double));
+    put(t->child_start, child_start.data(), nbox * sizeof(int));
+    put(t->child_count, child_count.data(), nbox * sizeof(int));
+    put(t->parent, parent.data(), nbox * sizeof(int));
+    put(t->quad, quad.data(), nbox * sizeof(int));
+    put(t->il_start, il_start.data(), il_start.size() * sizeof(int));
+    put(t->il_src, il_src.data(), il_src.size() * sizeof(int));
+    put(t->il_off, il_off.data(), il_off.size() * sizeof(int));
+    put(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int));
+    put(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int));
+    put(t->items, items.data(), items.size() * sizeof(int2));
+    put(t->m2m, m2m.data(), m2m.size() * sizeof(float4));
+    put(t->l2l, l2l.data(), l2l.size() * sizeof(float4));
+    put(t->m2l, m2l.data(), m2l.size() * sizeof(float4));
+    // the staging buffer is reused by the next build: finish the copy first
+    cudaError_t e = cudaMemcpyAsync(t->arena, hb, upload, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(t->arena);
+        delete t;
+        set_error("FMM tree upload failed: %s", cudaGetErrorString(e));
+        return GNK_ECUDA;
+    }
+    b.fmm = t;  // owned by the handle from here on (freed by release_fmm)
     return GNK_OK;
 }
 

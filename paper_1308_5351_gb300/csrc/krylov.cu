@@ -73,7 +73,7 @@ KPtrs kry_ptrs(double* base, int restart) {
 }
 
 int vec_blocks(int N) {
-    const int b = (N + KT * 4 - 1) / (KT * 4);
+    const int b = (N + KT - 1) / KT;
     return b < 1 ? 1 : (b > KB_MAX ? KB_MAX : b);
 }
 
@@ -87,6 +87,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     if (threadIdx.x == 0)
         for (int w = 0; w < KT / 32; ++w) s += red[w];
     return s;  // valid in thread 0
+}
+
+// sum_{b < nb} part[b * stride] over all threads of the (last) block, in a fixed
+// order: thread t adds b = t, t + KT, ...; then the block tree.  Valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part, size_t stride, int nb, double* red) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += KT) t += part[(size_t)b * stride];
+    return block_sum(t, red);
+}
+
+// The same for one value per warp: lane l adds b = l, l + 32, ...; then shuffles.
+// Valid in lane 0.
+__device__ __forceinline__ double warp_sum_partials(const double* part, size_t stride, int nb) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += part[(size_t)b * stride];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    return t;
 }
 
 // True in every thread of the last block to finish writing its partials.
@@ -108,9 +126,8 @@ __global__ void __launch_bounds__(KT) k_norm(const double* __restrict__ x, int N
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) p.part[blockIdx.x] = acc;
     if (!arrive_last(&s->counter)) return;
+    const double t = sum_partials(p.part, 1, gridDim.x, red);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int b = 0; b < gridDim.x; ++b) t += p.part[b];
         const double nrm = sqrt(t);
         if (mode == 0) {
             s->bnorm = nrm;
@@ -136,24 +153,45 @@ __global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r
     for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) v0[i] = r[i] * inv;
 }
 
-// h[k] = <v_k, w>, k < nv
+// h[k] = <v_k, w>, k < nv: KD dot products per pass over w, reduced per block
+// in a fixed order (warp shuffles, then warps in order), then by the last block
+constexpr int KD = 8;
+
 __global__ void __launch_bounds__(KT) k_dots(const double* __restrict__ V, int N, int nv,
                                              const double* __restrict__ w, KPtrs p, double* hout,
                                              KState* s) {
     if (s->done) return;
-    __shared__ double red[KT / 32];
-    for (int k = 0; k < nv; ++k) {
-        const double* v = V + (size_t)k * N;
-        double acc = 0.0;
-        for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) acc = fma(v[i], w[i], acc);
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) p.part[(size_t)blockIdx.x * p.ld + k] = acc;
+    __shared__ double red[KT / 32][KD];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k0 = 0; k0 < nv; k0 += KD) {
+        const int kn = min(KD, nv - k0);
+        double acc[KD];
+#pragma unroll
+        for (int q = 0; q < KD; ++q) acc[q] = 0.0;
+        for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+            const double wi = w[i];
+#pragma unroll
+            for (int q = 0; q < KD; ++q)
+                if (q < kn) acc[q] = fma(V[(size_t)(k0 + q) * N + i], wi, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < KD; ++q) {
+            double v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[wid][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kn) {
+            double t = 0.0;
+            for (int ww = 0; ww < KT / 32; ++ww) t += red[ww][threadIdx.x];
+            p.part[(size_t)blockIdx.x * p.ld + k0 + threadIdx.x] = t;
+        }
+        __syncthreads();
     }
     if (!arrive_last(&s->counter)) return;
-    for (int k = threadIdx.x; k < nv; k += KT) {
-        double t = 0.0;
-        for (int b = 0; b < gridDim.x; ++b) t += p.part[(size_t)b * p.ld + k];
-        hout[k] = t;
+    for (int k = wid; k < nv; k += KT / 32) {  // one warp per coefficient
+        const double t = warp_sum_partials(p.part + k, p.ld, gridDim.x);
+        if (lane == 0) hout[k] = t;
     }
     if (threadIdx.x == 0) s->counter = 0;
 }
@@ -194,9 +232,8 @@ __global__ void __launch_bounds__(KT) k_update_norm_givens(const double* __restr
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) p.part[blockIdx.x] = acc;
     if (!arrive_last(&s->counter)) return;
+    const double t = sum_partials(p.part, 1, gridDim.x, red);
     if (threadIdx.x != 0) return;
-    double t = 0.0;
-    for (int b = 0; b < gridDim.x; ++b) t += p.part[b];
     const double hn = sqrt(t);
     double* col = p.H + (size_t)j * p.ld;
     for (int k = 0; k < nv; ++k) col[k] = p.h1[k] + p.h2[k];
