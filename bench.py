@@ -54,21 +54,25 @@ PEAK_INSTR = {
     "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm_near": SMS * SM_MAX_MHZ * 1e6 * 128,
+    "fmm_tree": SMS * SM_MAX_MHZ * 1e6 * 128,
 }
 PEAK_BASIS = {
     "pair64": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 9 + 4R FP64 instr per pair",
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
     "fmm": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 48 FP32 instr per double-float complex "
-           "multiply-add of M2M, M2L, L2L (order 32), 38 + 48R per node and order in P2M",
+           "multiply-add of the M2L translations (order 32)",
+    "fmm_tree": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 48 FP32 instr per double-float complex "
+                "multiply-add of M2M and L2L, 38 + 48R per node and order in P2M",
     "fmm_near": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float "
                 "near-field pair",
 }
 KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
-               "fmm": "FMM far field (fmm_m2l_kernel, fmm_p2m_kernel, fmm_m2m_kernel, fmm_l2l_kernel)",
-               "fmm_near": "fmm_leaf_kernel (L2P + double-float near field)"}
+               "fmm": "fmm_m2l_kernel",
+               "fmm_near": "fmm_leaf_kernel (L2P + double-float near field)",
+               "fmm_tree": "fmm_p2m_kernel, fmm_m2m_kernel, fmm_l2l_kernel"}
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
-ROOF_KINDS = PAIR_KINDS + ("fmm_near",)
+ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_tree")
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
 FMM_MODES = ("fmm", "mixed_fmm")
 DTYPES = {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
@@ -266,7 +270,8 @@ def main():
     torch.cuda.synchronize()
 
     kinds = (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
-             ("fmm", G.PROF_FMM), ("fmm_near", G.PROF_FMMNEAR), ("reduce", G.PROF_REDUCE),
+             ("fmm", G.PROF_FMM), ("fmm_near", G.PROF_FMMNEAR), ("fmm_tree", G.PROF_FMMTREE),
+             ("reduce", G.PROF_REDUCE),
              ("circ", G.PROF_CIRC),
              ("krylov", G.PROF_KRYLOV))
 

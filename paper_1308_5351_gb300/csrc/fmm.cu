@@ -68,6 +68,10 @@ struct FmmTree {
     float4* mult = nullptr;     // [R][nbox][P]
     float4* loc = nullptr;      // [R][nbox][P]
     double2* ws = nullptr;      // [R][N] weights in sorted order
+    double2* zn = nullptr;      // [R][N] near-field sums in sorted order
+    int* node_box = nullptr;    // leaf box of each node in sorted order
+    cudaStream_t aux = nullptr; // second stream: the near field runs beside the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -109,6 +113,8 @@ struct FmmArgs {
     const int* done;
     const int2* items;  // near-field work items: (leaf, first target of a chunk of 32)
     int nitems;
+    double2* zn;        // [R][N] near-field sums in sorted order
+    const int* node_box;  // leaf box of each node in sorted order
 };
 
 __global__ void fmm_gather_kernel(FmmArgs a) {
@@ -171,10 +177,18 @@ __device__ __forceinline__ cdf cdf_shfl(cdf v, int src) {
                df{__shfl_sync(0xffffffffu, v.im.h, src), __shfl_sync(0xffffffffu, v.im.l, src)}};
 }
 
-// acc_lane += sum_k T[k][lane] x_k, x_k held by lane k (one P x P translation)
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+
+// acc_lane += sum_k T[k][lane] x_k, x_k held by lane k (one P x P translation);
+// even and odd k go to two accumulators (two independent dependency chains)
 __device__ __forceinline__ void translate(cdf& acc, const float4* __restrict__ T, cdf x, int lane) {
+    cdf odd = cdf_zero();
 #pragma unroll 4
-    for (int k = 0; k < kFmmP; ++k) cdf_mac(acc, cdf_of(__ldg(T + k * kFmmP + lane)), cdf_shfl(x, k));
+    for (int k = 0; k < kFmmP; k += 2) {
+        cdf_mac(acc, cdf_of(__ldg(T + k * kFmmP + lane)), cdf_shfl(x, k));
+        cdf_mac(odd, cdf_of(__ldg(T + (k + 1) * kFmmP + lane)), cdf_shfl(x, k + 1));
+    }
+    acc = cdf_add(acc, odd);
 }
 
 // P2M: one warp per leaf.  Each lane forms the powers t_j^k (k < P) of one
@@ -219,34 +233,54 @@ __global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
     for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc[r]);
 }
 
+// Translation kernels use kFmmTW warps per target box: warp w takes the sources
+// (children, interaction-list entries) w, w + kFmmTW, ...; the warps' sums are
+// added in warp order (reproducible) by warp 0.
+constexpr int kFmmTW = 4;
+
+__device__ __forceinline__ cdf reduce_warps(cdf acc, float4 (*s)[32], int wid, int lane) {
+    s[wid][lane] = cdf_pack(acc);
+    __syncthreads();
+    cdf t = cdf_of(s[0][lane]);
+    if (wid == 0)
+        for (int w = 1; w < kFmmTW; ++w) t = cdf_add(t, cdf_of(s[w][lane]));
+    __syncthreads();
+    return t;  // valid in warp 0
+}
+
 // M2M for the boxes [b0, b0 + gridDim.x) of one level
-__global__ void __launch_bounds__(32) fmm_m2m_kernel(FmmArgs a, int b0) {
+__global__ void __launch_bounds__(32 * kFmmTW) fmm_m2m_kernel(FmmArgs a, int b0) {
+    __shared__ float4 s_acc[kFmmTW][32];
     if (a.done != nullptr && *a.done) return;
-    const int box = b0 + blockIdx.x, lane = threadIdx.x;
+    const int box = b0 + blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = a.child_start[box], nc = a.child_count[box];
     for (int r = 0; r < a.R; ++r) {
         cdf acc = cdf_zero();
-        for (int c = c0; c < c0 + nc; ++c)
+        for (int c = c0 + wid; c < c0 + nc; c += kFmmTW)
             translate(acc, a.m2m + (size_t)a.quad[c] * kFmmP * kFmmP,
                       cdf_of(a.mult[((size_t)r * a.nbox + c) * kFmmP + lane]), lane);
-        a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
+        acc = reduce_warps(acc, s_acc, wid, lane);
+        if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
     }
 }
 
-// M2L for every box of levels 2..L (one warp per target box); the 1/r factor of
-// the scaled local expansion is applied once at the end
-__global__ void __launch_bounds__(32) fmm_m2l_kernel(FmmArgs a) {
+// M2L for every box of levels 2..L; the 1/r factor of the scaled local
+// expansion is applied once at the end
+__global__ void __launch_bounds__(32 * kFmmTW) fmm_m2l_kernel(FmmArgs a) {
+    __shared__ float4 s_acc[kFmmTW][32];
     if (a.done != nullptr && *a.done) return;
-    const int box = blockIdx.x, lane = threadIdx.x;
+    const int box = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
     for (int r = 0; r < a.R; ++r) {
         cdf acc = cdf_zero();
-        for (int e = e0; e < e1; ++e)
+        for (int e = e0 + wid; e < e1; e += kFmmTW)
             translate(acc, a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP,
                       cdf_of(a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane]), lane);
-        const df s = df_split(1.0 / a.width[box]);
-        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] =
-            cdf_pack(cdf{df_mul(acc.re, s), df_mul(acc.im, s)});
+        acc = reduce_warps(acc, s_acc, wid, lane);
+        if (wid == 0) {
+            const df sc = df_split(1.0 / a.width[box]);
+            a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(cdf{df_mul(acc.re, sc), df_mul(acc.im, sc)});
+        }
     }
 }
 
@@ -286,29 +320,23 @@ __device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, floa
     return r;
 }
 
-// One block per chunk of up to 32 targets of a leaf (lane = target); warp w sums
-// the near field of the neighbour leaves w, w + kFmmWarps, ...; the warps'
-// partial sums are added in warp order, then the local expansion (FP64).  The
+// Near field: one block per chunk of up to 32 targets of a leaf (lane = target);
+// warp w sums the neighbour leaves w, w + kFmmWarps, ...; the warps' partial sums
+// are added in warp order and stored in sorted node order (zn).  The
 // near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
 // of it): d from the exact three-float node coordinates, |d|^2 with Dekker
 // products, one Newton step on the reciprocal, compensated accumulation.
 template <int R>
-__global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
+__global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     __shared__ float4 s_p[kFmmWarps][32];   // (x1, x2, x3, y1)
     __shared__ float2 s_q[kFmmWarps][32];   // (y2, y3)
     __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
     __shared__ double2 s_z[kFmmWarps][R][32];
-    __shared__ double2 s_b[R][kFmmP];
     if (a.done != nullptr && *a.done) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = a.items[blockIdx.x];  // (leaf, first target)
     const int leaf = it.x;
     const int box = a.leaf_box[leaf];
-    for (int k = threadIdx.x; k < R * kFmmP; k += kFmmNT)
-    {
-        const float4 v = a.loc[((size_t)(k / kFmmP) * a.nbox + box) * kFmmP + k % kFmmP];
-        s_b[k / kFmmP][k % kFmmP] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
-    }
     const int t1 = a.leaf_start[leaf + 1];
     const int i = it.y + lane;
     const bool act = i < t1;
@@ -376,23 +404,44 @@ __global__ void __launch_bounds__(kFmmNT) fmm_leaf_kernel(FmmArgs a) {
                                          (double)aim[r].h + (double)aim[r].l);
     __syncthreads();
     if (wid == 0 && act) {
-        const double2 c = a.center[box];
-        const double ir = 1.0 / a.width[box];
-        const double2 t = make_double2((p.x - c.x) * ir, (p.y - c.y) * ir);
-        const int node = a.perm[i];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            double2 v = s_b[r][kFmmP - 1];
-            for (int l = kFmmP - 2; l >= 0; --l) {
-                const double2 bl = s_b[r][l];
-                v = make_double2(fma(v.x, t.x, fma(-v.y, t.y, bl.x)), fma(v.x, t.y, fma(v.y, t.x, bl.y)));
-            }
-            for (int w = 0; w < kFmmWarps; ++w) {
+            double2 v = s_z[0][r][lane];
+            for (int w = 1; w < kFmmWarps; ++w) {
                 v.x += s_z[w][r][lane].x;
                 v.y += s_z[w][r][lane].y;
             }
-            a.out[(size_t)r * a.N + node] = v;
+            a.zn[(size_t)r * a.N + i] = v;
         }
+    }
+}
+
+// L2P by Horner's rule in double-float plus the near-field sum; one thread per
+// node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
+// same coefficients); writes z in node order
+template <int R>
+__global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
+    if (a.done != nullptr && *a.done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int box = a.node_box[i];
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    const double2 p = a.ps[i];
+    const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+    const int node = a.perm[i];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
+        cdf u = cdf_of(b[kFmmP - 1]);
+        for (int l = kFmmP - 2; l >= 0; --l) {
+            const cdf m = cdf_mul(u, t);
+            const cdf bl = cdf_of(b[l]);
+            u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+        }
+        const double2 zn = a.zn[(size_t)r * a.N + i];
+        a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
+                                                     ((double)u.im.h + (double)u.im.l) + zn.y);
     }
 }
 
@@ -483,6 +532,12 @@ uint32_t spread16(uint32_t v) {
 
 void release_fmm(Boundary& b) {
     if (b.fmm) {
+        if (b.fmm->aux) {
+            cudaStreamSynchronize(b.fmm->aux);
+            cudaStreamDestroy(b.fmm->aux);
+        }
+        if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
+        if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
         if (b.fmm->arena) cudaFree(b.fmm->arena);
         delete b.fmm;
         b.fmm = nullptr;
@@ -718,12 +773,14 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         {(void**)&t->nl_start, (t->nleaf + 1) * sizeof(int)},
         {(void**)&t->nl_leaf, nnl * sizeof(int)},
         {(void**)&t->items, std::max<size_t>(items.size(), 1) * sizeof(int2)},
+        {(void**)&t->node_box, N * sizeof(int)},
         {(void**)&t->m2m, 4 * P * P * sizeof(float4)},
         {(void**)&t->l2l, 4 * P * P * sizeof(float4)},
         {(void**)&t->m2l, 49 * P * P * sizeof(float4)},
         {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->ws, (size_t)t->R * N * sizeof(double2)},
+        {(void**)&t->zn, (size_t)t->R * N * sizeof(double2)},
     };
     size_t total = 0;
     for (const Part& p : parts) total += (p.bytes + 255) / 256 * 256;
@@ -785,6 +842,9 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     put(t->nl_start, nl_start.data(), nl_start.size() * sizeof(int));
     put(t->nl_leaf, nl_leaf.data(), nl_leaf.size() * sizeof(int));
     put(t->items, items.data(), items.size() * sizeof(int2));
+    int* nbx = reinterpret_cast<int*>(hb + ((char*)t->node_box - (char*)t->arena));
+    for (int q = 0; q < t->nleaf; ++q)
+        for (int i = leaf_start[q]; i < leaf_start[q + 1]; ++i) nbx[i] = leaf_box[q];
     put(t->m2m, m2m.data(), m2m.size() * sizeof(float4));
     put(t->l2l, l2l.data(), l2l.size() * sizeof(float4));
     put(t->m2l, m2l.data(), m2l.size() * sizeof(float4));
@@ -798,20 +858,31 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         set_error("FMM tree upload failed: %s", cudaGetErrorString(e));
         return GNK_ECUDA;
     }
+    if (cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        b.fmm = t;
+        release_fmm(b);
+        set_error("FMM: stream or event creation failed");
+        return GNK_ECUDA;
+    }
     b.fmm = t;  // owned by the handle from here on (freed by release_fmm)
     return GNK_OK;
 }
 
-// FP32-pipe instructions of the far field of one FMM product (for the roofline):
-// 48 per double-float complex multiply-add of the translations (4 Dekker products
-// and 4 compensated sums), and per node and order 38 for the power and 48 R for
-// the P2M sums.  (The near field: 49 + 48R per pair, fmm_near_instr.)
-double fmm_instr(const Boundary& b, int R) {
+// FP32-pipe instructions of one FMM product, for the roofline: 48 per
+// double-float complex multiply-add (4 Dekker products and 4 compensated sums).
+// which = 0: M2L; 1: P2M (38 per node and order for the power, 48 R for the
+// sums), M2M and L2L.  (The near field: fmm_near_instr.)
+double fmm_instr(const Boundary& b, int R, int which) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
     const double P = kFmmP;
-    const double trans = (double)(t->m2l_pairs + t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
-    return 48.0 * trans * R + (double)b.N * P * (38.0 + 48.0 * R);
+    if (which == 0) return 48.0 * R * P * P * (double)t->m2l_pairs;
+    const double trans = (double)(t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
+    // P2M: 38 per node and order for the power, 48 R for the sums; L2P: 38 R
+    return 48.0 * trans * R + (double)b.N * P * (38.0 + 86.0 * R);
 }
 
 double fmm_near_instr(const Boundary& b, int R) {
@@ -844,6 +915,8 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.nl_leaf = t->nl_leaf;
     a.items = t->items;
     a.nitems = t->nitems;
+    a.zn = t->zn;
+    a.node_box = t->node_box;
     a.m2m = t->m2m;
     a.l2l = t->l2l;
     a.m2l = t->m2l;
@@ -859,35 +932,52 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.s = job.s;
     a.out = static_cast<double2*>(b.partial);
     a.done = job.done;
-    const ProfToken tok = prof_begin(st);
+    // gathered weights, then the near field on the second stream beside the far field
     fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
+    GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
+    const ProfToken tokn = prof_begin(t->aux);
+    if (job.R == 2)
+        fmm_near_kernel<2><<<t->nitems, kFmmNT, 0, t->aux>>>(a);
+    else
+        fmm_near_kernel<1><<<t->nitems, kFmmNT, 0, t->aux>>>(a);
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokn, PK_FMMNEAR, (double)job.R * t->near_pairs, t->aux, fmm_near_instr(b, job.R));
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_join, t->aux));
+    int launches = 2;
+    // upward pass
+    const ProfToken tok = prof_begin(st);
     if (job.R == 2)
         fmm_p2m_kernel<2><<<t->nleaf, 32, 0, st>>>(a);
     else
         fmm_p2m_kernel<1><<<t->nleaf, 32, 0, st>>>(a);
-    int launches = 2;
+    ++launches;
     for (int l = t->L - 1; l >= 2; --l) {
-        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
+        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, st>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
-    fmm_m2l_kernel<<<t->nbox, 32, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_FMMTREE, 0.0, st, 0.0);
+    // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
+    const ProfToken tokm = prof_begin(st);
+    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, st>>>(a);
     ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokm, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R, 0));
+    // downward pass, then L2P plus the near field
+    const ProfToken tokd = prof_begin(st);
     for (int l = 3; l <= t->L; ++l) {
         fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
-    GNK_TRY_CUDA(cudaGetLastError());
-    // the far field stands in for all R N (N - 1) pair evaluations of the product
-    prof_end(tok, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R));
-    const ProfToken tok2 = prof_begin(st);
-    const int grid = t->nitems;
+    GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
     if (job.R == 2)
-        fmm_leaf_kernel<2><<<grid, kFmmNT, 0, st>>>(a);
+        fmm_l2p_kernel<2><<<(b.N + 255) / 256, 256, 0, st>>>(a);
     else
-        fmm_leaf_kernel<1><<<grid, kFmmNT, 0, st>>>(a);
+        fmm_l2p_kernel<1><<<(b.N + 255) / 256, 256, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok2, PK_FMMNEAR, (double)job.R * t->near_pairs, st, fmm_near_instr(b, job.R));
+    prof_end(tokd, PK_FMMTREE, 0.0, st, fmm_instr(b, job.R, 1));
     GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
     count_launches(launches + 1);
     return GNK_OK;

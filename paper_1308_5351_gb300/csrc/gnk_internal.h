@@ -47,8 +47,9 @@ enum ProfKind : int {
     PK_KRYLOV = 4,   // GMRES vector kernels; work = bytes moved
     PK_OTHER = 5,
     PK_PAIRDF = 6,   // double-float pair-sum kernel; work = pair evaluations
-    PK_FMM = 7,      // FMM far field (P2M, M2M, M2L, L2L); work = the R N (N-1) pairs of the product
+    PK_FMM = 7,      // FMM M2L; work = the R N (N-1) pairs the product stands for
     PK_FMMNEAR = 8,  // FMM L2P + near field (double-float); work = near-field pair evaluations
+    PK_FMMTREE = 9,  // FMM P2M, M2M (upward) and L2L (downward) passes
 };
 struct ProfToken {
     void* ev = nullptr;
@@ -264,7 +265,7 @@ int fbie_backward(const Boundary& b, const double* mu, const double* gam, const 
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st);
 int ensure_fmm(const Boundary& b, int R, cudaStream_t st);
 void release_fmm(Boundary& b);
-double fmm_instr(const Boundary& b, int R);
+double fmm_instr(const Boundary& b, int R, int which);
 double fmm_near_instr(const Boundary& b, int R);
 // the chunk reduction and epilogue of the pair sums, for products formed elsewhere
 cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chunks, int ptype,

@@ -52,7 +52,7 @@ EXPORTED = (
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
-    PROF_FMMNEAR = range(9)
+    PROF_FMMNEAR, PROF_FMMTREE = range(10)
 
 
 class gnk_options(ctypes.Structure):
