@@ -970,14 +970,17 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
         fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokd, PK_FMMTREE, 0.0, st, fmm_instr(b, job.R, 1));
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
+    const ProfToken tokp = prof_begin(st);
     if (job.R == 2)
         fmm_l2p_kernel<2><<<(b.N + 255) / 256, 256, 0, st>>>(a);
     else
         fmm_l2p_kernel<1><<<(b.N + 255) / 256, 256, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokd, PK_FMMTREE, 0.0, st, fmm_instr(b, job.R, 1));
+    prof_end(tokp, PK_FMMTREE, 0.0, st, 0.0);
     GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
     count_launches(launches + 1);
     return GNK_OK;
