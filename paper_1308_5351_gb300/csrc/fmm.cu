@@ -67,7 +67,7 @@ struct FmmTree {
     float4* m2l = nullptr;      // [49][k][l]
     float4* mult = nullptr;     // [R][nbox][P]
     float4* loc = nullptr;      // [R][nbox][P]
-    double2* ws = nullptr;      // [R][N] weights in sorted order
+    float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
     double2* zn = nullptr;      // [R][N] near-field sums in sorted order
     int* node_box = nullptr;    // leaf box of each node in sorted order
     cudaStream_t aux = nullptr; // second stream: the near field runs beside the far field
@@ -100,7 +100,7 @@ struct FmmArgs {
     const float4* m2l;
     float4* mult;
     float4* loc;
-    double2* ws;
+    float4* ws;
     int nbox;
     // weights
     int mode;
@@ -131,7 +131,8 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
             const double x = (r == 0) ? a.x0[j] : a.x1[j];
             w = make_double2(sc.x * x, sc.y * x);
         }
-        a.ws[(size_t)r * a.N + i] = w;
+        const df wx = df_split(w.x), wy = df_split(w.y);
+        a.ws[(size_t)r * a.N + i] = make_float4(wx.h, wx.l, wy.h, wy.l);
     }
 }
 
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
                 v = cdf_mul(v, t);
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) s_w[r][lane] = cdf_pack(cdf_split(a.ws[(size_t)r * a.N + j]));
+            for (int r = 0; r < R; ++r) s_w[r][lane] = a.ws[(size_t)r * a.N + j];
         }
         __syncwarp();
         const int cnt = min(32, j1 - base);
@@ -321,8 +322,9 @@ __device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, floa
 }
 
 // Near field: one block per chunk of up to 32 targets of a leaf (lane = target);
-// warp w sums the neighbour leaves w, w + kFmmWarps, ...; the warps' partial sums
-// are added in warp order and stored in sorted node order (zn).  The
+// the neighbour leaves' sources, in tiles of 32, are dealt to the warps in turn;
+// the warps' partial sums are added in warp order and stored in sorted node
+// order (zn).  The
 // near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
 // of it): d from the exact three-float node coordinates, |d|^2 with Dekker
 // products, one Newton step on the reciprocal, compensated accumulation.
@@ -336,32 +338,28 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = a.items[blockIdx.x];  // (leaf, first target)
     const int leaf = it.x;
-    const int box = a.leaf_box[leaf];
     const int t1 = a.leaf_start[leaf + 1];
     const int i = it.y + lane;
     const bool act = i < t1;
-    const double2 p = a.ps[act ? i : it.y];
     const float4 pa = a.p3[act ? i : it.y];
     const float2 pb = a.p3b[act ? i : it.y];
     df are[R], aim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) are[r] = aim[r] = df{0.f, 0.f};
     const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
-    for (int e = n0 + wid; e < n1; e += kFmmWarps) {
+    int tile = 0;  // tiles of 32 sources over all neighbour leaves, dealt to the warps in turn
+    for (int e = n0; e < n1; ++e) {
         const int nl = a.nl_leaf[e];
         const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
-        for (int sb = s0; sb < s1; sb += 32) {
+        for (int sb = s0; sb < s1; sb += 32, ++tile) {
+            if (tile % kFmmWarps != wid) continue;
             __syncwarp();
             const int j = sb + lane;
             if (j < s1) {
                 s_p[wid][lane] = a.p3[j];
                 s_q[wid][lane] = a.p3b[j];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const double2 w = a.ws[(size_t)r * a.N + j];
-                    const df wx = df_split(w.x), wy = df_split(w.y);
-                    s_w[wid][r][lane] = make_float4(wx.h, wx.l, wy.h, wy.l);
-                }
+                for (int r = 0; r < R; ++r) s_w[wid][r][lane] = a.ws[(size_t)r * a.N + j];
             }
             __syncwarp();
             const int cnt = min(32, s1 - sb);
@@ -779,7 +777,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         {(void**)&t->m2l, 49 * P * P * sizeof(float4)},
         {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
-        {(void**)&t->ws, (size_t)t->R * N * sizeof(double2)},
+        {(void**)&t->ws, (size_t)t->R * N * sizeof(float4)},
         {(void**)&t->zn, (size_t)t->R * N * sizeof(double2)},
     };
     size_t total = 0;
