@@ -28,51 +28,11 @@
 #include <mutex>
 #include <vector>
 
+#include "fmm_internal.h"
 #include "gnk_internal.h"
 #include "pairmath.cuh"
 
 namespace gnk {
-
-constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
-constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
-constexpr int kFmmNT = 256;   // threads of the leaf (L2P + near field) kernel: 8 warps
-
-struct FmmTree {
-    int L = 0, nbox = 0, nleaf = 0, R = 0;
-    std::vector<int> lvl_off;   // first global box index of level l (index l - 2), size L
-    std::vector<int> lvl_cnt;
-    long long near_pairs = 0, m2l_pairs = 0, m2m_pairs = 0;
-    void* arena = nullptr;
-    int* perm = nullptr;        // sorted position -> node
-    double2* ps = nullptr;      // node positions in sorted order
-    float4* p3 = nullptr;       // the same split exactly into three floats: (x1, x2, x3, y1)
-    float2* p3b = nullptr;      // (y2, y3)
-    int* leaf_start = nullptr;  // nleaf + 1
-    int* leaf_box = nullptr;    // global box index of each leaf
-    double2* center = nullptr;  // per box
-    double* width = nullptr;    // per box
-    int* child_start = nullptr; // per box: first child (global), level < L
-    int* child_count = nullptr;
-    int* parent = nullptr;      // per box, -1 on level 2
-    int* quad = nullptr;        // quadrant of a box in its parent: 2 qa + qb
-    int* il_start = nullptr;    // interaction lists (nbox + 1), sources, offset codes
-    int* il_src = nullptr;
-    int* il_off = nullptr;
-    int* nl_start = nullptr;    // neighbour leaves of each leaf (nleaf + 1)
-    int* nl_leaf = nullptr;
-    int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
-    int nitems = 0;
-    float4* m2m = nullptr;      // [4][k][m]   double-float complex (re.h, re.l, im.h, im.l)
-    float4* l2l = nullptr;      // [4][l][m]
-    float4* m2l = nullptr;      // [49][k][l]
-    float4* mult = nullptr;     // [R][nbox][P]
-    float4* loc = nullptr;      // [R][nbox][P]
-    float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
-    double2* zn = nullptr;      // [R][N] near-field sums in sorted order
-    int* node_box = nullptr;    // leaf box of each node in sorted order
-    cudaStream_t aux = nullptr; // second stream: the near field runs beside the far field
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-};
 
 namespace {
 
@@ -543,10 +503,9 @@ void release_fmm(Boundary& b) {
 }
 
 // Builds the tree of the handle's nodes (once) with workspace for R right-hand sides.
-int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
-    Boundary& b = const_cast<Boundary&>(bc);
-    (void)R;  // the workspace always holds kMaxRHS right-hand sides
-    if (b.fmm) return GNK_OK;
+// The host-side tree builder (used when the tree is too deep for the device
+// builder's lookup grids): fills t and its device arena.
+static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
     const int N = b.N;
     std::vector<double2> et(N);
     GNK_TRY_CUDA(cudaMemcpyAsync(et.data(), b.et, (size_t)N * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -601,13 +560,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         if ((double)N / (double)distinct < kFmmLeaf) break;
         L = l;
     }
-    FmmTree* t = new (std::nothrow) FmmTree();
-    if (!t) {
-        set_error("host allocation failed");
-        return GNK_ENOMEM;
-    }
     t->L = L;
-    t->R = kMaxRHS;
     // boxes per level (level index l - 2), sorted by key
     const int nlev = L - 1;
     std::vector<std::vector<uint32_t>> keys(nlev);
@@ -741,9 +694,6 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     const std::vector<int>& perm = ord0;
     std::vector<double2> ps(N);
     for (int i = 0; i < N; ++i) ps[i] = et[perm[i]];
-    const std::vector<float4>& m2m = cached_tables(0);
-    const std::vector<float4>& l2l = cached_tables(1);
-    const std::vector<float4>& m2l = cached_tables(2);
 
     // one device allocation for the tree and the expansions
     const size_t P = kFmmP;
@@ -772,9 +722,6 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         {(void**)&t->nl_leaf, nnl * sizeof(int)},
         {(void**)&t->items, std::max<size_t>(items.size(), 1) * sizeof(int2)},
         {(void**)&t->node_box, N * sizeof(int)},
-        {(void**)&t->m2m, 4 * P * P * sizeof(float4)},
-        {(void**)&t->l2l, 4 * P * P * sizeof(float4)},
-        {(void**)&t->m2l, 49 * P * P * sizeof(float4)},
         {(void**)&t->mult, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->ws, (size_t)t->R * N * sizeof(float4)},
@@ -784,7 +731,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     for (const Part& p : parts) total += (p.bytes + 255) / 256 * 256;
     if (cudaMalloc(&t->arena, total) != cudaSuccess) {
         cudaGetLastError();
-        delete t;
+        t->arena = nullptr;
         set_error("FMM tree: device allocation of %zu bytes failed", total);
         return GNK_ENOMEM;
     }
@@ -804,8 +751,6 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
         if (cudaHostAlloc(&g_stage, upload, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             g_stage = nullptr;
-            cudaFree(t->arena);
-            delete t;
             set_error("FMM tree: pinned staging allocation of %zu bytes failed", upload);
             return GNK_ENOMEM;
         }
@@ -843,30 +788,82 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     int* nbx = reinterpret_cast<int*>(hb + ((char*)t->node_box - (char*)t->arena));
     for (int q = 0; q < t->nleaf; ++q)
         for (int i = leaf_start[q]; i < leaf_start[q + 1]; ++i) nbx[i] = leaf_box[q];
-    put(t->m2m, m2m.data(), m2m.size() * sizeof(float4));
-    put(t->l2l, l2l.data(), l2l.size() * sizeof(float4));
-    put(t->m2l, m2l.data(), m2l.size() * sizeof(float4));
     // the staging buffer is reused by the next build: finish the copy first
     cudaError_t e = cudaMemcpyAsync(t->arena, hb, upload, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(t->arena);
-        delete t;
         set_error("FMM tree upload failed: %s", cudaGetErrorString(e));
         return GNK_ECUDA;
     }
-    if (cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    return GNK_OK;
+}
+
+int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l, cudaStream_t st) {
+    static std::mutex mu;
+    static std::vector<float4*> per_device;  // indexed by device, never freed
+    int dev = 0;
+    GNK_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)per_device.size() <= dev) per_device.resize(dev + 1, nullptr);
+    const size_t P2 = (size_t)kFmmP * kFmmP;
+    if (!per_device[dev]) {
+        const std::vector<float4>& a = cached_tables(0);
+        const std::vector<float4>& b = cached_tables(1);
+        const std::vector<float4>& c = cached_tables(2);
+        float4* d = nullptr;
+        if (cudaMalloc(&d, (a.size() + b.size() + c.size()) * sizeof(float4)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("FMM: device allocation of the translation tables failed");
+            return GNK_ENOMEM;
+        }
+        cudaError_t e = cudaMemcpyAsync(d, a.data(), a.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + a.size(), b.data(), b.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + a.size() + b.size(), c.data(), c.size() * sizeof(float4),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            set_error("FMM: upload of the translation tables failed");
+            return GNK_ECUDA;
+        }
+        per_device[dev] = d;
+    }
+    *m2m = per_device[dev];
+    *l2l = per_device[dev] + 4 * P2;
+    *m2l = per_device[dev] + 8 * P2;
+    return GNK_OK;
+}
+
+// Builds the tree of the handle's nodes (once) with workspace for kMaxRHS
+// right-hand sides: on the device when the lookup grids fit, else on the host.
+int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
+    Boundary& b = const_cast<Boundary&>(bc);
+    (void)R;
+    if (b.fmm) return GNK_OK;
+    FmmTree* t = new (std::nothrow) FmmTree();
+    if (!t) {
+        set_error("host allocation failed");
+        return GNK_ENOMEM;
+    }
+    t->R = kMaxRHS;
+    int rc = fmm_tree_device(b, t, st);
+    if (rc == kFmmUseHost) rc = fmm_tree_host(b, t, st);
+    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2m, &t->l2l, &t->m2l, st);
+    if (rc == GNK_OK &&
+        (cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
-        b.fmm = t;
-        release_fmm(b);
         set_error("FMM: stream or event creation failed");
-        return GNK_ECUDA;
+        rc = GNK_ECUDA;
     }
     b.fmm = t;  // owned by the handle from here on (freed by release_fmm)
-    return GNK_OK;
+    if (rc != GNK_OK) release_fmm(b);
+    return rc;
 }
 
 // FP32-pipe instructions of one FMM product, for the roofline: 48 per

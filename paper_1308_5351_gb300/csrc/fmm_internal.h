@@ -1,0 +1,65 @@
+// FMM tree shared by the host- and device-side tree builders and the FMM
+// product (fmm.cu, fmm_tree.cu).  Internal header.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "gnk_internal.h"
+
+namespace gnk {
+
+constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
+constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
+constexpr int kFmmNT = 256;   // threads of the leaf (L2P + near field) kernel: 8 warps
+
+struct FmmTree {
+    int L = 0, nbox = 0, nleaf = 0, R = 0;
+    std::vector<int> lvl_off;   // first global box index of level l (index l - 2), size L - 1
+    std::vector<int> lvl_cnt;
+    long long near_pairs = 0, m2l_pairs = 0, m2m_pairs = 0;
+    void* arena = nullptr;
+    int* perm = nullptr;        // sorted position -> node
+    double2* ps = nullptr;      // node positions in sorted order
+    float4* p3 = nullptr;       // the same split exactly into three floats: (x1, x2, x3, y1)
+    float2* p3b = nullptr;      // (y2, y3)
+    int* leaf_start = nullptr;  // nleaf + 1
+    int* leaf_box = nullptr;    // global box index of each leaf
+    double2* center = nullptr;  // per box
+    double* width = nullptr;    // per box
+    int* child_start = nullptr; // per box: first child (global), level < L
+    int* child_count = nullptr;
+    int* parent = nullptr;      // per box, -1 on level 2
+    int* quad = nullptr;        // quadrant of a box in its parent: 2 qa + qb
+    int* il_start = nullptr;    // interaction lists (nbox + 1), sources, offset codes
+    int* il_src = nullptr;
+    int* il_off = nullptr;
+    int* nl_start = nullptr;    // neighbour leaves of each leaf (nleaf + 1)
+    int* nl_leaf = nullptr;
+    int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
+    int nitems = 0;
+    const float4* m2m = nullptr;  // [4][k][m]   double-float complex (re.h, re.l, im.h, im.l),
+    const float4* l2l = nullptr;  // [4][l][m]   in the per-device table cache
+    const float4* m2l = nullptr;  // [49][k][l]
+    float4* mult = nullptr;     // [R][nbox][P]
+    float4* loc = nullptr;      // [R][nbox][P]
+    float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
+    double2* zn = nullptr;      // [R][N] near-field sums in sorted order
+    int* node_box = nullptr;    // leaf box of each node in sorted order
+    cudaStream_t aux = nullptr; // second stream: the near field runs beside the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+
+// Builds the tree on the device (Morton keys, stable radix sort, boxes per level,
+// interaction and neighbour lists) into t, with its device arena.  Returns
+// GNK_OK, an error code, or kFmmUseHost when the tree is too deep for the
+// device lookup grids (then the host builder runs).
+constexpr int kFmmUseHost = 1;
+int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st);
+
+// The double-float translation tables on the current device (formed and
+// uploaded once per device and process): M2M [4][P][P], L2L [4][P][P], M2L [49][P][P].
+int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l, cudaStream_t st);
+
+}  // namespace gnk
