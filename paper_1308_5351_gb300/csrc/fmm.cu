@@ -838,6 +838,16 @@ int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l
     return GNK_OK;
 }
 
+// The highest stream priority of the device (the far-field chain's stream).
+static int fmm_high_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
+}
+
 // Builds the tree of the handle's nodes (once) with workspace for kMaxRHS
 // right-hand sides: on the device when the lookup grids fit, else on the host.
 int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
@@ -854,7 +864,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     if (rc == kFmmUseHost) rc = fmm_tree_host(b, t, st);
     if (rc == GNK_OK) rc = fmm_device_tables(&t->m2m, &t->l2l, &t->m2l, st);
     if (rc == GNK_OK &&
-        (cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        (cudaStreamCreateWithPriority(&t->aux, cudaStreamNonBlocking, fmm_high_priority()) != cudaSuccess ||
          cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
@@ -927,46 +937,51 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.s = job.s;
     a.out = static_cast<double2*>(b.partial);
     a.done = job.done;
-    // gathered weights, then the near field on the second stream beside the far field
+    // gathered weights; then the far field (a chain of short latency-bound
+    // launches) on the handle's high-priority stream while the near field fills
+    // the rest of the GPU on the caller's stream; L2P joins them
     fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
     GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
-    const ProfToken tokn = prof_begin(t->aux);
-    if (job.R == 2)
-        fmm_near_kernel<2><<<t->nitems, kFmmNT, 0, t->aux>>>(a);
-    else
-        fmm_near_kernel<1><<<t->nitems, kFmmNT, 0, t->aux>>>(a);
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokn, PK_FMMNEAR, (double)job.R * t->near_pairs, t->aux, fmm_near_instr(b, job.R));
-    GNK_TRY_CUDA(cudaEventRecord(t->ev_join, t->aux));
-    int launches = 2;
+    cudaStream_t fs = t->aux;
+    int launches = 1;
     // upward pass
-    const ProfToken tok = prof_begin(st);
+    const ProfToken tok = prof_begin(fs);
     if (job.R == 2)
-        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, st>>>(a);
+        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
     else
-        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, st>>>(a);
+        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, fs>>>(a);
     ++launches;
     for (int l = t->L - 1; l >= 2; --l) {
-        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, st>>>(a, t->lvl_off[l - 2]);
+        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, fs>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_FMMTREE, 0.0, st, 0.0);
+    prof_end(tok, PK_FMMTREE, 0.0, fs, 0.0);
     // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
-    const ProfToken tokm = prof_begin(st);
-    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, st>>>(a);
+    const ProfToken tokm = prof_begin(fs);
+    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, fs>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokm, PK_FMM, (double)job.R * b.N * (b.N - 1.0), st, fmm_instr(b, job.R, 0));
-    // downward pass, then L2P plus the near field
-    const ProfToken tokd = prof_begin(st);
+    prof_end(tokm, PK_FMM, (double)job.R * b.N * (b.N - 1.0), fs, fmm_instr(b, job.R, 0));
+    // downward pass
+    const ProfToken tokd = prof_begin(fs);
     for (int l = 3; l <= t->L; ++l) {
-        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, st>>>(a, t->lvl_off[l - 2]);
+        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, fs>>>(a, t->lvl_off[l - 2]);
         ++launches;
     }
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokd, PK_FMMTREE, 0.0, st, fmm_instr(b, job.R, 1));
+    prof_end(tokd, PK_FMMTREE, 0.0, fs, fmm_instr(b, job.R, 1));
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
+    // near field on the caller's stream
+    const ProfToken tokn = prof_begin(st);
+    if (job.R == 2)
+        fmm_near_kernel<2><<<t->nitems, kFmmNT, 0, st>>>(a);
+    else
+        fmm_near_kernel<1><<<t->nitems, kFmmNT, 0, st>>>(a);
+    ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokn, PK_FMMNEAR, (double)job.R * t->near_pairs, st, fmm_near_instr(b, job.R));
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
     const ProfToken tokp = prof_begin(st);
     if (job.R == 2)

@@ -47,7 +47,7 @@ struct FmmTree {
     float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
     double2* zn = nullptr;      // [R][N] near-field sums in sorted order
     int* node_box = nullptr;    // leaf box of each node in sorted order
-    cudaStream_t aux = nullptr; // second stream: the near field runs beside the far field
+    cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
