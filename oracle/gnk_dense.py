@@ -20,6 +20,8 @@ with the generalized Neumann kernel"):
   * variant without singularity subtraction Sec. 7 (Ex. 2), Eqs. (ie-sys), (phi-kp),
                                            (N-tt), (M1-tt)
   * Cauchy integral formula                Sec. 5, Eqs. (cauchy4), (cauchy6)
+  * slit maps by the FBIE route            Sec. 7, Ex. 3 (map formulas of the
+                                           method the paper cites; see slit_map)
 
 Readings of the paper taken here (each is listed with its reason in the design
 notes of the repository):
@@ -435,3 +437,52 @@ def cauchy_formula(et, etp, n, f_nodes, z, bounded, finf=0.0):
         else:
             out[k] = (finf + s1 / (n * 1j)) / (1.0 + s2 / (n * 1j))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 7, Ex. 3: conformal map of a bounded G onto the unit disk with circular
+# slits (theta = pi/2 on a boundary) and radial slits (theta = 0), by the FBIE
+# route: one solve of Eq. (ie) and h of Eq. (h).  The map formulas are the
+# method the paper cites for this example (its references, not restated in the
+# paper):  with A = e^{i(pi/2 - theta)} (eta - alpha) and
+#   gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]   (arg continuous along
+#   each boundary), the function f with boundary values A f = gamma + h + i mu
+# is analytic in G and
+#   w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z))
+# maps G onto the unit disk (|w| = 1 on the outer boundary, w(alpha) = 0,
+# w'(alpha) = e^{-h_0} > 0) with circular slits |w| = e^{h_j - h_0} and radial
+# slits arg w = const.
+# ---------------------------------------------------------------------------
+
+def slit_map_data(et, n, alpha, theta):
+    """A and gamma of the slit map for theta given per boundary component."""
+    et = np.asarray(et, dtype=np.complex128)
+    N, m1 = _sizes(et, n)
+    th = np.repeat(np.asarray(theta, dtype=np.float64), n)
+    rot = np.exp(1j * (math.pi / 2 - th))
+    lg = np.empty(N, dtype=np.complex128)
+    for k in range(m1):
+        d = et[k * n:(k + 1) * n] - alpha
+        lg[k * n:(k + 1) * n] = np.log(np.abs(d)) + 1j * np.unwrap(np.angle(d))
+    A = rot * (et - alpha)
+    gam = -(rot * lg).real
+    return A, gam
+
+
+def slit_map(et, etp, n, alpha, theta, z=None):
+    """Boundary values w(eta) of the slit map, the constant c = e^{-h_0}, the
+    per-component h_k, and (if z is given) w at the points z of G by the Cauchy
+    formula of Eq. (cauchy4) applied to f."""
+    et = np.asarray(et, dtype=np.complex128)
+    N, m1 = _sizes(et, n)
+    A, gam = slit_map_data(et, n, alpha, theta)
+    mu, h, hk = fbie(et, etp, A, n, gam)
+    c = math.exp(-hk[0])
+    fb = (gam + h + 1j * mu) / A
+    w = c * (et - alpha) * np.exp((et - alpha) * fb)
+    wz = None
+    if z is not None:
+        z = np.asarray(z, dtype=np.complex128)
+        fz = cauchy_formula(et, etp, n, fb, z, True)
+        wz = c * (z - alpha) * np.exp((z - alpha) * fz)
+    return w, c, hk, wz
