@@ -664,6 +664,122 @@ int gnk_cauchy_eval(const gnk_boundary* hd, int nz, const double* z, const doubl
     return rc;
 }
 
+// Device views of the arrays of one call (host arrays staged through temporary
+// device buffers); outputs are copied back by finish().
+struct Views {
+    DevArr v[8];
+    int n = 0;
+    int add(const void* p, size_t bytes, bool input, cudaStream_t st, void** dev) {
+        const int rc = dev_view(p, bytes, input, st, &v[n]);
+        if (rc == GNK_OK) *dev = v[n].dev;
+        ++n;
+        return rc;
+    }
+    int finish(int rc, const bool* is_out, cudaStream_t st) {
+        if (rc == GNK_OK)
+            for (int k = 0; k < n; ++k)
+                if (is_out[k] && v[k].tmp &&
+                    cudaMemcpyAsync(v[k].user, v[k].dev, v[k].bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+                    set_error("%s", cudaGetErrorString(cudaGetLastError()));
+                    rc = GNK_ECUDA;
+                }
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == GNK_OK) {
+            set_error("%s", cudaGetErrorString(cudaGetLastError()));
+            rc = GNK_ECUDA;
+        }
+        for (int k = 0; k < n; ++k)
+            if (v[k].tmp) cudaFree(v[k].dev);
+        return rc;
+    }
+};
+
+int gnk_slit_map_data(int m1, int n, const double* et, const double* alpha, const double* theta, double* A,
+                      double* gam, void* stream) {
+    cudaGetLastError();
+    if (!et || !alpha || !theta || !A || !gam || m1 < 1 || n < 4 || (n % 2) != 0 ||
+        (long long)m1 * n > (1LL << 28)) {
+        set_error("gnk_slit_map_data: NULL array or m1, n out of range");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)m1 * n;
+    Views vw;
+    void *det, *dth, *dA, *dg;
+    int rc = vw.add(et, 16 * N, true, st, &det);
+    if (rc == GNK_OK) rc = vw.add(theta, 8 * (size_t)m1, true, st, &dth);
+    if (rc == GNK_OK) rc = vw.add(A, 16 * N, false, st, &dA);
+    if (rc == GNK_OK) rc = vw.add(gam, 8 * N, false, st, &dg);
+    if (rc == GNK_OK)
+        rc = slit_data(m1, n, (const double2*)det, make_double2(alpha[0], alpha[1]), (const double*)dth,
+                       (double2*)dA, (double*)dg, st);
+    const bool out[4] = {false, false, true, true};
+    return vw.finish(rc, out, st);
+}
+
+int gnk_slit_map(const gnk_boundary* hd, const double* alpha, const double* gam, const double* mu,
+                 const double* h, const double* hk, double* w, void* stream) {
+    cudaGetLastError();
+    GNK_TRY(check_handle(hd));
+    const Boundary& b = hd->b;
+    if (!alpha || !gam || !mu || !h || !hk || !w || !b.bounded) {
+        set_error("gnk_slit_map: NULL array or an unbounded handle");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = b.N;
+    Views vw;
+    void *dg, *dmu, *dh, *dhk, *dw;
+    int rc = vw.add(gam, 8 * N, true, st, &dg);
+    if (rc == GNK_OK) rc = vw.add(mu, 8 * N, true, st, &dmu);
+    if (rc == GNK_OK) rc = vw.add(h, 8 * N, true, st, &dh);
+    if (rc == GNK_OK) rc = vw.add(hk, 8 * (size_t)b.m1, true, st, &dhk);
+    if (rc == GNK_OK) rc = vw.add(w, 16 * N, false, st, &dw);
+    if (rc == GNK_OK) rc = slit_nodes_f(b, (const double*)dg, (const double*)dmu, (const double*)dh, b.zbuf, st);
+    if (rc == GNK_OK)
+        rc = slit_w(b.et, b.zbuf, b.N, make_double2(alpha[0], alpha[1]), (const double*)dhk, (double2*)dw, st);
+    const bool out[5] = {false, false, false, false, true};
+    return vw.finish(rc, out, st);
+}
+
+int gnk_slit_map_eval(const gnk_boundary* hd, const double* alpha, const double* gam, const double* mu,
+                      const double* h, const double* hk, int nz, const double* z, double* wz, int precision,
+                      void* stream) {
+    cudaGetLastError();
+    GNK_TRY(check_handle(hd));
+    const Boundary& b = hd->b;
+    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
+        set_error("gnk_slit_map_eval: precision must be GNK_PREC_FP64 or GNK_PREC_DF32, got %d", precision);
+        return GNK_EINVAL;
+    }
+    if (nz < 0 || !b.bounded) {
+        set_error("gnk_slit_map_eval: nz < 0 or an unbounded handle");
+        return GNK_EINVAL;
+    }
+    if (nz == 0) return GNK_OK;
+    if (!alpha || !gam || !mu || !h || !hk || !z || !wz) {
+        set_error("gnk_slit_map_eval: NULL array");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = b.N;
+    Views vw;
+    void *dg, *dmu, *dh, *dhk, *dz, *dw;
+    int rc = vw.add(gam, 8 * N, true, st, &dg);
+    if (rc == GNK_OK) rc = vw.add(mu, 8 * N, true, st, &dmu);
+    if (rc == GNK_OK) rc = vw.add(h, 8 * N, true, st, &dh);
+    if (rc == GNK_OK) rc = vw.add(hk, 8 * (size_t)b.m1, true, st, &dhk);
+    if (rc == GNK_OK) rc = vw.add(z, 16 * (size_t)nz, true, st, &dz);
+    if (rc == GNK_OK) rc = vw.add(wz, 16 * (size_t)nz, false, st, &dw);
+    const double2 al = make_double2(alpha[0], alpha[1]);
+    if (rc == GNK_OK) rc = slit_nodes_f(b, (const double*)dg, (const double*)dmu, (const double*)dh, b.zbuf, st);
+    // f(z) by the Cauchy formula into wz, then w(z) in place
+    if (rc == GNK_OK)
+        rc = cauchy_eval(b, nz, (const double2*)dz, b.zbuf, make_double2(0.0, 0.0), (double2*)dw, precision, st);
+    if (rc == GNK_OK) rc = slit_w((const double2*)dz, (const double2*)dw, nz, al, (const double*)dhk, (double2*)dw, st);
+    const bool out[6] = {false, false, false, false, false, true};
+    return vw.finish(rc, out, st);
+}
+
 int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,
                   void* stream) {
     GNK_TRY(check_handle(h));

@@ -48,7 +48,7 @@ EXPORTED = (
     "gnk_profile_query", "gnk_profile_query_ex", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
-    "gnk_cauchy_eval",
+    "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -129,6 +129,9 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_eval.argtypes = [P, I, P, P, P, P, I, P]
+    lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, P, P, P]
+    lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gnk_slit_map_eval.argtypes = [P, P, P, P, P, P, I, P, P, I, P]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -281,6 +284,57 @@ def gnk_cauchy_eval(h, z, f, fz, finf=None, precision=GNK_PREC_FP64, stream=None
     nz = int(z.numel() if torch is not None and isinstance(z, torch.Tensor) else z.size)
     return _check(load().gnk_cauchy_eval(h, nz, _ptr(z, True), _ptr(f, True), fi, _ptr(fz, True),
                                          int(precision), _stream(stream)))
+
+
+def _c2(alpha):
+    c = complex(alpha)
+    return (ctypes.c_double * 2)(c.real, c.imag)
+
+
+def gnk_slit_map_data(m1, n, et, alpha, theta, A, gam, stream=None):
+    """A = e^{i(pi/2 - theta)} (eta - alpha), gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]."""
+    return _check(load().gnk_slit_map_data(int(m1), int(n), _ptr(et, True), _c2(alpha), _ptr(theta),
+                                           _ptr(A, True), _ptr(gam), _stream(stream)))
+
+
+def gnk_slit_map(h, alpha, gam, mu, hv, hk, w, stream=None):
+    """w at the nodes of the slit map (Sec. 7, Ex. 3)."""
+    return _check(load().gnk_slit_map(h, _c2(alpha), _ptr(gam), _ptr(mu), _ptr(hv), _ptr(hk), _ptr(w, True),
+                                      _stream(stream)))
+
+
+def gnk_slit_map_eval(h, alpha, gam, mu, hv, hk, z, wz, precision=GNK_PREC_FP64, stream=None):
+    """w at points z of G (Cauchy formula for f)."""
+    nz = int(z.numel() if torch is not None and isinstance(z, torch.Tensor) else z.size)
+    return _check(load().gnk_slit_map_eval(h, _c2(alpha), _ptr(gam), _ptr(mu), _ptr(hv), _ptr(hk), nz,
+                                           _ptr(z, True), _ptr(wz, True), int(precision), _stream(stream)))
+
+
+def slit_map(dom, alpha, theta, z=None, device="cuda", precision=GNK_PREC_FMM, tol=1e-12, stream=None):
+    """The slit map of a bounded domain (curves, n of `dom`): returns
+    (w at the nodes, h_k, w at z or None, gnk_result).  theta: one value per
+    boundary (pi/2 circular slit, 0 radial slit).  Cauchy sums by `precision`
+    (GNK_PREC_FMM by default; GNK_PREC_FP64 or _DF32 direct)."""
+    if not dom.bounded:
+        raise ValueError("slit maps are defined here for bounded domains")
+    et = torch.as_tensor(np.ascontiguousarray(dom.et), device=device)
+    etp = torch.as_tensor(np.ascontiguousarray(dom.etp), device=device)
+    th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=device)
+    A = torch.empty_like(et)
+    gam = torch.empty(dom.N, dtype=torch.float64, device=device)
+    gnk_slit_map_data(dom.m1, dom.n, et, alpha, th, A, gam, stream)
+    bprec = GNK_PREC_FMM if precision == GNK_PREC_FMM else GNK_PREC_FP64
+    with Boundary(dom.m1, dom.n, et, etp, A, None, None, True, stream, bprec) as b:
+        mu, h, hk, res = b.fbie(gam, tol=tol, precision=precision, stream=stream)
+        w = torch.empty_like(et)
+        gnk_slit_map(b.handle, alpha, gam, mu, h, hk, w, stream)
+        wz = None
+        if z is not None:
+            zt = torch.as_tensor(np.ascontiguousarray(z, dtype=np.complex128), device=device)
+            wz = torch.empty_like(zt)
+            ep = GNK_PREC_DF32 if precision in (GNK_PREC_DF32, GNK_PREC_MIXED_DF) else GNK_PREC_FP64
+            gnk_slit_map_eval(b.handle, alpha, gam, mu, h, hk, zt, wz, ep, stream)
+    return w, hk, wz, res
 
 
 def gnk_apply_IminusN(h, x, y, precision=GNK_PREC_FP64, stream=None):

@@ -121,3 +121,73 @@ def test_planted_mistakes_are_caught(monkeypatch):
         monkeypatch.setattr(O, "slit_map_data", fn)
         assert not _pins_pass(), fn.__name__
         monkeypatch.undo()
+
+
+# ------------------------------------------------------------------ GPU
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1308_5351_gb300 import build, gnk
+    build.build()
+    gnk.load()
+    return gnk
+
+
+CASES = {
+    "three_circles_circular": (lambda: Dm.three_circles(256), 0.05j, [HALF] * 3),
+    "ex2_mixed": (lambda: Dm.ex2_circles(0.1, 128), 0j, [HALF, 0.0, HALF, 0.0, HALF]),
+    "disk": (lambda: _disk(64, 0.3 + 0.2j), 0.3 + 0.2j, [HALF]),
+}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", list(CASES))
+def test_gpu_slit_map_data(G, case):
+    mk, a, th = CASES[case]
+    d = mk()
+    A_ref, g_ref = O.slit_map_data(d.et, d.n, a, th)
+    et = torch.as_tensor(d.et, device="cuda")
+    A = torch.empty_like(et)
+    g = torch.empty(d.N, dtype=torch.float64, device="cuda")
+    G.gnk_slit_map_data(d.m1, d.n, et, a, torch.as_tensor(np.asarray(th), device="cuda"), A, g)
+    assert np.abs(A.cpu().numpy() - A_ref).max() <= 1e-15 * np.abs(A_ref).max() * 4
+    assert np.abs(g.cpu().numpy() - g_ref).max() <= 1e-13 * max(1.0, np.abs(g_ref).max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fmm", "fp64"])
+def test_gpu_slit_map_matches_oracle(G, case, prec):
+    """w at the nodes and at interior points within 1e-9: mu and h agree with the
+    oracle to 1e-10 relative (solve tolerance 1e-12, condition numbers below
+    100), |mu|, |h| <= 10 here, and w = c (z - alpha) exp(...) with |w| <= 1
+    carries those errors through the exponent."""
+    mk, a, th = CASES[case]
+    d = mk()
+    rng = np.random.default_rng(4)
+    pts = []
+    while len(pts) < 40:
+        z = complex(rng.uniform(-0.9, 0.9), rng.uniform(-0.9, 0.9))
+        if abs(z) < 0.9 and all(abs(z - cv.centre) > cv.radius + 0.05 for cv in d.curves[1:]):
+            pts.append(z)
+    z = np.array(pts)
+    w_ref, c_ref, hk_ref, wz_ref = O.slit_map(d.et, d.etp, d.n, a, th, z=z)
+    p = G.GNK_PREC_FMM if prec == "fmm" else G.GNK_PREC_FP64
+    w, hk, wz, res = G.slit_map(d, a, th, z=z, precision=p)
+    assert res.status == 0
+    assert np.abs(w.cpu().numpy() - w_ref).max() <= 1e-9
+    assert np.abs(wz.cpu().numpy() - wz_ref).max() <= 1e-9
+    assert np.abs(hk.cpu().numpy() - hk_ref).max() <= 1e-10 * max(1.0, np.abs(hk_ref).max())
+
+
+@pytest.mark.gpu
+def test_gpu_slit_map_rejects_unbounded(G):
+    d = Dm.ex4_circles(0.1, 64)
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
+        x = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+        hk = torch.zeros(d.m1, dtype=torch.float64, device="cuda")
+        w = torch.empty(d.N, dtype=torch.complex128, device="cuda")
+        with pytest.raises(G.GnkError):
+            G.gnk_slit_map(b.handle, 0j, x, x, x, hk, w)
