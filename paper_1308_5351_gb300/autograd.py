@@ -24,6 +24,8 @@ class _FBIE(torch.autograd.Function):
     @staticmethod
     def forward(ctx, et, etp, A, gam, m1, n, bounded, precision, tol, restart):
         bprec = G.GNK_PREC_DF32 if precision in (G.GNK_PREC_DF32, G.GNK_PREC_MIXED_DF) else G.GNK_PREC_FP64
+        if precision in (G.GNK_PREC_FMM, G.GNK_PREC_MIXED_FMM):
+            bprec = G.GNK_PREC_FMM
         b = G.Boundary(m1, n, et.detach().contiguous(), etp.detach().contiguous(),
                        A.detach().contiguous(), None, None, bounded, precision=bprec)
         g = gam.detach().contiguous()

@@ -74,6 +74,8 @@ struct FmmArgs {
     const int2* items;  // near-field work items: (leaf, first target of a chunk of 32)
     int nitems;
     double2* zn;        // [R][N] near-field sums in sorted order
+    double2* zf;        // [R][N] near-field sums of w/d^2 in sorted order (EF products)
+    double2* outF;      // [R][N] F sums in node order (EF products)
     const int* node_box;  // leaf box of each node in sorted order
 };
 
@@ -288,12 +290,14 @@ __device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, floa
 // near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
 // of it): d from the exact three-float node coordinates, |d|^2 with Dekker
 // products, one Newton step on the reciprocal, compensated accumulation.
-template <int R>
+// EF: also the sums of w_j / (eta_i - eta_j)^2 (to zf), for the gradient.
+template <int R, bool EF>
 __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
+    constexpr int RS = EF ? 2 * R : R;
     __shared__ float4 s_p[kFmmWarps][32];   // (x1, x2, x3, y1)
     __shared__ float2 s_q[kFmmWarps][32];   // (y2, y3)
     __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
-    __shared__ double2 s_z[kFmmWarps][R][32];
+    __shared__ double2 s_z[kFmmWarps][RS][32];
     if (a.done != nullptr && *a.done) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = a.items[blockIdx.x];  // (leaf, first target)
@@ -303,9 +307,9 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     const bool act = i < t1;
     const float4 pa = a.p3[act ? i : it.y];
     const float2 pb = a.p3b[act ? i : it.y];
-    df are[R], aim[R];
+    df are[RS], aim[RS];
 #pragma unroll
-    for (int r = 0; r < R; ++r) are[r] = aim[r] = df{0.f, 0.f};
+    for (int r = 0; r < RS; ++r) are[r] = aim[r] = df{0.f, 0.f};
     const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
     int tile = 0;  // tiles of 32 sources over all neighbour leaves, dealt to the warps in turn
     for (int e = n0; e < n1; ++e) {
@@ -353,23 +357,40 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
                     const df qq = df_mul(wx, ai);
                     df_acc(aim[r], df{-qq.h, -qq.l});
                 }
+                if (EF) {  // 1/d^2 = (ar - i ai)^2 = gr - i gi
+                    const df a2 = df_mul(ar, ar), b2 = df_mul(ai, ai), ab = df_mul(ar, ai);
+                    const df gr = df_add(a2, df{-b2.h, -b2.l}), gi = df{ab.h + ab.h, ab.l + ab.l};
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float4 w4 = s_w[wid][r][k];
+                        const df wx{w4.x, w4.y}, wy{w4.z, w4.w};
+                        df_acc(are[R + r], df_mul(wx, gr));
+                        df_acc(are[R + r], df_mul(wy, gi));
+                        df_acc(aim[R + r], df_mul(wy, gr));
+                        const df qq = df_mul(wx, gi);
+                        df_acc(aim[R + r], df{-qq.h, -qq.l});
+                    }
+                }
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < RS; ++r)
         s_z[wid][r][lane] = make_double2((double)are[r].h + (double)are[r].l,
                                          (double)aim[r].h + (double)aim[r].l);
     __syncthreads();
     if (wid == 0 && act) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RS; ++r) {
             double2 v = s_z[0][r][lane];
             for (int w = 1; w < kFmmWarps; ++w) {
                 v.x += s_z[w][r][lane].x;
                 v.y += s_z[w][r][lane].y;
             }
-            a.zn[(size_t)r * a.N + i] = v;
+            if (r < R)
+                a.zn[(size_t)r * a.N + i] = v;
+            else
+                a.zf[(size_t)(r - R) * a.N + i] = v;
         }
     }
 }
@@ -377,7 +398,9 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
 // L2P by Horner's rule in double-float plus the near-field sum; one thread per
 // node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
 // same coefficients); writes z in node order
-template <int R>
+// EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
+// plus the near-field sums of w/d^2, written to outF.
+template <int R, bool EF>
 __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
     if (a.done != nullptr && *a.done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,7 +415,9 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
     for (int r = 0; r < R; ++r) {
         const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
         cdf u = cdf_of(b[kFmmP - 1]);
+        cdf du = cdf_zero();
         for (int l = kFmmP - 2; l >= 0; --l) {
+            if (EF) du = cdf_add(cdf_mul(du, t), u);
             const cdf m = cdf_mul(u, t);
             const cdf bl = cdf_of(b[l]);
             u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
@@ -400,17 +425,16 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
         const double2 zn = a.zn[(size_t)r * a.N + i];
         a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
                                                      ((double)u.im.h + (double)u.im.l) + zn.y);
+        if (EF) {
+            const double2 zf = a.zf[(size_t)r * a.N + i];
+            a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
+                                                          -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
+        }
     }
 }
 
 // ---------------------------------------------------------------- host: tables
 using cld = std::complex<long double>;
-
-long double binom_ld(int n, int k) {
-    long double v = 1.0L;
-    for (int i = 1; i <= k; ++i) v = v * (long double)(n - k + i) / (long double)i;
-    return v;
-}
 
 // a complex value as a double-float pair per part (hi = nearest float, lo = the rest)
 float4 cdf_host(const cld& v) {
@@ -418,38 +442,49 @@ float4 cdf_host(const cld& v) {
     return make_float4(rh, (float)(v.real() - (long double)rh), ih, (float)(v.imag() - (long double)ih));
 }
 
+// Binomial coefficients (Pascal's triangle) and powers by repeated products in
+// long double: no library power functions, whose long double forms are slow
+// where long double is emulated in software.
 void translation_tables(std::vector<float4>* m2m, std::vector<float4>* l2l, std::vector<float4>* m2l) {
-    const int P = kFmmP;
+    const int P = kFmmP, PP = 2 * kFmmP + 1;
+    std::vector<long double> C((size_t)PP * PP, 0.0L);  // C[n][k], n < 2P + 1
+    for (int n = 0; n < PP; ++n) {
+        C[(size_t)n * PP] = 1.0L;
+        for (int k = 1; k <= n; ++k) C[(size_t)n * PP + k] = C[(size_t)(n - 1) * PP + k - 1] + C[(size_t)(n - 1) * PP + k];
+    }
+    auto binom = [&](int n, int k) { return C[(size_t)n * PP + k]; };
+    auto powers = [](const cld& z, int count) {
+        std::vector<cld> p(count);
+        p[0] = cld(1.0L, 0.0L);
+        for (int e = 1; e < count; ++e) p[e] = p[e - 1] * z;
+        return p;
+    };
+    std::vector<long double> half(P);  // 2^-k
+    half[0] = 1.0L;
+    for (int k = 1; k < P; ++k) half[k] = half[k - 1] * 0.5L;
     m2m->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
     l2l->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
     m2l->assign(49 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int q = 0; q < 4; ++q) {
         const int qa = q >> 1, qb = q & 1;
-        const cld dd((2 * qa - 1) / 4.0L, (2 * qb - 1) / 4.0L);
+        const std::vector<cld> dp = powers(cld((2 * qa - 1) / 4.0L, (2 * qb - 1) / 4.0L), P);
         for (int m = 0; m < P; ++m)
-            for (int k = 0; k <= m; ++k) {
-                // M2M: row m, column k; stored [q][k][m]
-                const cld v = binom_ld(m, k) * std::pow(dd, m - k) * std::pow(2.0L, -k);
-                (*m2m)[(size_t)q * P * P + k * P + m] = cdf_host(v);
-            }
+            for (int k = 0; k <= m; ++k)  // M2M: row m, column k; stored [q][k][m]
+                (*m2m)[(size_t)q * P * P + k * P + m] = cdf_host(binom(m, k) * half[k] * dp[m - k]);
         for (int m = 0; m < P; ++m)
-            for (int l = m; l < P; ++l) {
-                // L2L: row m, column l; stored [q][l][m]
-                const cld v = binom_ld(l, m) * std::pow(dd, l - m) * std::pow(2.0L, -m);
-                (*l2l)[(size_t)q * P * P + l * P + m] = cdf_host(v);
-            }
+            for (int l = m; l < P; ++l)  // L2L: row m, column l; stored [q][l][m]
+                (*l2l)[(size_t)q * P * P + l * P + m] = cdf_host(binom(l, m) * half[m] * dp[l - m]);
     }
     for (int dx = -3; dx <= 3; ++dx)
         for (int dy = -3; dy <= 3; ++dy) {
             if (std::max(std::abs(dx), std::abs(dy)) <= 1) continue;
             const int o = (dx + 3) * 7 + (dy + 3);
-            const cld inv = 1.0L / cld((long double)dx, (long double)dy);
+            const std::vector<cld> ip = powers(1.0L / cld((long double)dx, (long double)dy), 2 * P);
             for (int l = 0; l < P; ++l)
                 for (int k = 0; k < P; ++k) {
                     // M2L: row l, column k; stored [o][k][l]
                     const long double sgn = ((k + 1) % 2) ? -1.0L : 1.0L;
-                    const cld v = sgn * binom_ld(k + l, l) * std::pow(inv, k + l + 1);
-                    (*m2l)[(size_t)o * P * P + k * P + l] = cdf_host(v);
+                    (*m2l)[(size_t)o * P * P + k * P + l] = cdf_host(sgn * binom(k + l, l) * ip[k + l + 1]);
                 }
         }
 }
@@ -726,6 +761,7 @@ static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
         {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->ws, (size_t)t->R * N * sizeof(float4)},
         {(void**)&t->zn, (size_t)t->R * N * sizeof(double2)},
+        {(void**)&t->zf, (size_t)t->R * N * sizeof(double2)},
     };
     size_t total = 0;
     for (const Part& p : parts) total += (p.bytes + 255) / 256 * 256;
@@ -894,12 +930,78 @@ double fmm_near_instr(const Boundary& b, int R) {
     return b.fmm ? (49.0 + 48.0 * R) * (double)b.fmm->near_pairs : 0.0;
 }
 
-int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
-    GNK_TRY(ensure_fmm(b, job.R, st));
+// One FMM product on the argument block `a` (weights, outputs set by the caller):
+// gather, the far-field chain on the high-priority stream, the near field on
+// `st`, and L2P after they join.  EF: also the sums of w/d^2 (to a.outF).
+static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream_t st, int* nlaunch) {
     const FmmTree* t = b.fmm;
-    FmmArgs a;
+    fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
+    GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
+    cudaStream_t fs = t->aux;
+    int launches = 1;
+    // upward pass
+    const ProfToken tok = prof_begin(fs);
+    if (R == 2)
+        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
+    else
+        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, fs>>>(a);
+    ++launches;
+    for (int l = t->L - 1; l >= 2; --l) {
+        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, fs>>>(a, t->lvl_off[l - 2]);
+        ++launches;
+    }
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_FMMTREE, 0.0, fs, 0.0);
+    // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
+    const ProfToken tokm = prof_begin(fs);
+    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, fs>>>(a);
+    ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokm, PK_FMM, (double)R * b.N * (b.N - 1.0), fs, fmm_instr(b, R, 0));
+    // downward pass
+    const ProfToken tokd = prof_begin(fs);
+    for (int l = 3; l <= t->L; ++l) {
+        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, fs>>>(a, t->lvl_off[l - 2]);
+        ++launches;
+    }
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokd, PK_FMMTREE, 0.0, fs, fmm_instr(b, R, 1));
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
+    // near field on the caller's stream
+    const ProfToken tokn = prof_begin(st);
+    if (R == 2 && EF)
+        fmm_near_kernel<2, true><<<t->nitems, kFmmNT, 0, st>>>(a);
+    else if (R == 2)
+        fmm_near_kernel<2, false><<<t->nitems, kFmmNT, 0, st>>>(a);
+    else if (EF)
+        fmm_near_kernel<1, true><<<t->nitems, kFmmNT, 0, st>>>(a);
+    else
+        fmm_near_kernel<1, false><<<t->nitems, kFmmNT, 0, st>>>(a);
+    ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st, fmm_near_instr(b, R) * (EF ? 2.0 : 1.0));
+    GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
+    const ProfToken tokp = prof_begin(st);
+    const int nb = (b.N + 255) / 256;
+    if (R == 2 && EF)
+        fmm_l2p_kernel<2, true><<<nb, 256, 0, st>>>(a);
+    else if (R == 2)
+        fmm_l2p_kernel<2, false><<<nb, 256, 0, st>>>(a);
+    else if (EF)
+        fmm_l2p_kernel<1, true><<<nb, 256, 0, st>>>(a);
+    else
+        fmm_l2p_kernel<1, false><<<nb, 256, 0, st>>>(a);
+    ++launches;
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tokp, PK_FMMTREE, 0.0, st, 0.0);
+    *nlaunch = launches;
+    return GNK_OK;
+}
+
+static void fmm_args(const Boundary& b, FmmArgs& a) {
+    const FmmTree* t = b.fmm;
     a.N = b.N;
-    a.R = job.R;
     a.P = kFmmP;
     a.perm = t->perm;
     a.ps = t->ps;
@@ -921,6 +1023,7 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.items = t->items;
     a.nitems = t->nitems;
     a.zn = t->zn;
+    a.zf = t->zf;
     a.node_box = t->node_box;
     a.m2m = t->m2m;
     a.l2l = t->l2l;
@@ -929,6 +1032,15 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.loc = t->loc;
     a.ws = t->ws;
     a.nbox = t->nbox;
+    a.outF = nullptr;
+    a.done = nullptr;
+}
+
+int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
+    GNK_TRY(ensure_fmm(b, job.R, st));
+    FmmArgs a;
+    fmm_args(b, a);
+    a.R = job.R;
     a.mode = job.mode;
     a.w0 = job.w[0];
     a.w1 = job.w[1];
@@ -937,62 +1049,32 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.s = job.s;
     a.out = static_cast<double2*>(b.partial);
     a.done = job.done;
-    // gathered weights; then the far field (a chain of short latency-bound
-    // launches) on the handle's high-priority stream while the near field fills
-    // the rest of the GPU on the caller's stream; L2P joins them
-    fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
-    GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
-    GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
-    cudaStream_t fs = t->aux;
-    int launches = 1;
-    // upward pass
-    const ProfToken tok = prof_begin(fs);
-    if (job.R == 2)
-        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
-    else
-        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, fs>>>(a);
-    ++launches;
-    for (int l = t->L - 1; l >= 2; --l) {
-        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, fs>>>(a, t->lvl_off[l - 2]);
-        ++launches;
-    }
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_FMMTREE, 0.0, fs, 0.0);
-    // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
-    const ProfToken tokm = prof_begin(fs);
-    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, fs>>>(a);
-    ++launches;
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokm, PK_FMM, (double)job.R * b.N * (b.N - 1.0), fs, fmm_instr(b, job.R, 0));
-    // downward pass
-    const ProfToken tokd = prof_begin(fs);
-    for (int l = 3; l <= t->L; ++l) {
-        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, fs>>>(a, t->lvl_off[l - 2]);
-        ++launches;
-    }
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokd, PK_FMMTREE, 0.0, fs, fmm_instr(b, job.R, 1));
-    GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
-    // near field on the caller's stream
-    const ProfToken tokn = prof_begin(st);
-    if (job.R == 2)
-        fmm_near_kernel<2><<<t->nitems, kFmmNT, 0, st>>>(a);
-    else
-        fmm_near_kernel<1><<<t->nitems, kFmmNT, 0, st>>>(a);
-    ++launches;
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokn, PK_FMMNEAR, (double)job.R * t->near_pairs, st, fmm_near_instr(b, job.R));
-    GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
-    const ProfToken tokp = prof_begin(st);
-    if (job.R == 2)
-        fmm_l2p_kernel<2><<<(b.N + 255) / 256, 256, 0, st>>>(a);
-    else
-        fmm_l2p_kernel<1><<<(b.N + 255) / 256, 256, 0, st>>>(a);
-    ++launches;
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokp, PK_FMMTREE, 0.0, st, 0.0);
+    int launches = 0;
+    GNK_TRY(fmm_product(b, a, job.R, false, st, &launches));
     GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
     count_launches(launches + 1);
+    return GNK_OK;
+}
+
+// E w and F w (sums of w_j/(eta_i - eta_j) and of w_j/(eta_i - eta_j)^2, i != j)
+// for one or two complex weight vectors (w1 may be null), into E and F
+// (R x N complex each, node order), by one FMM pass.
+int run_fmm_ef(const Boundary& b, const double2* w0, const double2* w1, double2* E, double2* F, cudaStream_t st) {
+    const int R = w1 ? 2 : 1;
+    GNK_TRY(ensure_fmm(b, R, st));
+    FmmArgs a;
+    fmm_args(b, a);
+    a.R = R;
+    a.mode = W_COMPLEX;
+    a.w0 = w0;
+    a.w1 = w1;
+    a.x0 = a.x1 = nullptr;
+    a.s = nullptr;
+    a.out = E;
+    a.outF = F;
+    int launches = 0;
+    GNK_TRY(fmm_product(b, a, R, true, st, &launches));
+    count_launches(launches);
     return GNK_OK;
 }
 

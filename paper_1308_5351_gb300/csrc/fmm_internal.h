@@ -46,6 +46,7 @@ struct FmmTree {
     float4* loc = nullptr;      // [R][nbox][P]
     float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
     double2* zn = nullptr;      // [R][N] near-field sums in sorted order
+    double2* zf = nullptr;      // [R][N] near-field sums of w/d^2 (gradient products)
     int* node_box = nullptr;    // leaf box of each node in sorted order
     cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

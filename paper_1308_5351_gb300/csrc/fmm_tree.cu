@@ -564,6 +564,7 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
         {(void**)&t->loc, (size_t)t->R * nbox * P * sizeof(float4)},
         {(void**)&t->ws, (size_t)t->R * N * sizeof(float4)},
         {(void**)&t->zn, (size_t)t->R * N * sizeof(double2)},
+        {(void**)&t->zf, (size_t)t->R * N * sizeof(double2)},
     };
     size_t total = 0;
     for (const Part& p : parts) total += align256(p.bytes);

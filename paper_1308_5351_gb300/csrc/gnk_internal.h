@@ -263,6 +263,7 @@ int fbie_backward(const Boundary& b, const double* mu, const double* gam, const 
 
 // ---------------------------------------------------------------- FMM (fmm.cu)
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st);
+int run_fmm_ef(const Boundary& b, const double2* w0, const double2* w1, double2* E, double2* F, cudaStream_t st);
 int ensure_fmm(const Boundary& b, int R, cudaStream_t st);
 void release_fmm(Boundary& b);
 double fmm_instr(const Boundary& b, int R, int which);

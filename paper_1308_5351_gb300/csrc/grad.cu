@@ -17,7 +17,9 @@
 // (2/n) conj(dQ/dz).  The derivatives need six Cauchy sums E w and six
 // squared sums (F w)_i = sum_{j != i} w_j/(eta_i - eta_j)^2 of the weights
 //   w = q, q nu, q rho, A a, A lambda, A gh,
-// which one FP64 kernel forms together (both share 1/(eta_i - eta_j)).
+// which one FP64 kernel forms together (both share 1/(eta_i - eta_j)), or, with
+// the FMM precisions, three FMM passes (F from the derivative of the local
+// expansions plus the near field's 1/d^2 sums).
 #include <algorithm>
 #include <cstring>
 
@@ -204,9 +206,10 @@ int fbie_backward(const Boundary& bc, const double* mu, const double* gam, const
     const int tpc = (tiles_src + chunks - 1) / chunks;
     chunks = (tiles_src + tpc - 1) / tpc;
     int st_alloc = GNK_OK;
+    const size_t part_bytes = (outer == GNK_PREC_FMM) ? 0 : (size_t)chunks * 2 * kGR * N * sizeof(double2);
     if (cudaMalloc(&w, (size_t)kGR * N * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&S, (size_t)2 * kGR * N * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&part, (size_t)chunks * 2 * kGR * N * sizeof(double2)) != cudaSuccess) {
+        (part_bytes && cudaMalloc(&part, part_bytes) != cudaSuccess)) {
         cudaGetLastError();
         set_error("gradient workspace allocation failed");
         st_alloc = GNK_ENOMEM;
@@ -214,13 +217,21 @@ int fbie_backward(const Boundary& bc, const double* mu, const double* gam, const
     int rc = st_alloc;
     if (rc == GNK_OK) {
         grad_weights_kernel<<<nb, 256, 0, st>>>(N, b.q, b.A, mu, gam, lam, gh, w);
-        const ProfToken tok = prof_begin(st);
-        gradsum64_kernel<<<dim3(tiles_tgt, chunks), kGThreads, 0, st>>>(b.et, w, N, tiles_src, tpc, part);
-        prof_end(tok, PK_OTHER, (double)N * (N - 1.0), st);
-        gradsum_reduce_kernel<<<nb, 256, 0, st>>>(part, N, chunks, S);
-        count_launches(3);
+        count_launches(1);
+        if (outer == GNK_PREC_FMM) {
+            // the six E and six F sums by three FMM passes of two weights each
+            for (int r = 0; r < kGR && rc == GNK_OK; r += 2)
+                rc = run_fmm_ef(b, w + (size_t)r * N, w + (size_t)(r + 1) * N, S + (size_t)r * N,
+                                S + (size_t)(kGR + r) * N, st);
+        } else {
+            const ProfToken tok = prof_begin(st);
+            gradsum64_kernel<<<dim3(tiles_tgt, chunks), kGThreads, 0, st>>>(b.et, w, N, tiles_src, tpc, part);
+            prof_end(tok, PK_OTHER, (double)N * (N - 1.0), st);
+            gradsum_reduce_kernel<<<nb, 256, 0, st>>>(part, N, chunks, S);
+            count_launches(2);
+        }
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
+        if (rc == GNK_OK && e != cudaSuccess) {
             set_error("gradient kernels: %s", cudaGetErrorString(e));
             rc = GNK_ECUDA;
         }

@@ -84,7 +84,7 @@ def _dev(a):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("which", ["bounded", "unbounded_theta", "graded"])
-@pytest.mark.parametrize("prec", [0, 1, 4])
+@pytest.mark.parametrize("prec", [0, 1, 4, 5, 6])
 def test_backward_matches_oracle(G, which, prec):
     rng = np.random.default_rng(5)
     if which == "bounded":
@@ -101,6 +101,8 @@ def test_backward_matches_oracle(G, which, prec):
     ch = rng.normal(size=d.N)
     ref = O.fbie_gradient(d.et, d.etp, d.A, d.n, gam, cm, ch)
     bprec = G.GNK_PREC_DF32 if prec == 4 else G.GNK_PREC_FP64
+    if prec in (5, 6):  # the six Cauchy and six 1/d^2 sums by three FMM passes
+        bprec = G.GNK_PREC_FMM
     with G.Boundary.from_domain(d, adjoint=False, device="cuda", precision=bprec) as b:
         mu, h, hk, res = b.fbie(_dev(gam), tol=1e-13, precision=prec)
         out = [torch.empty(d.N, dtype=torch.complex128, device="cuda") for _ in range(3)]
