@@ -119,6 +119,10 @@ unsigned long long gnk_kernel_launches(void);
  * 3 circulant, 4 GMRES vector kernels (work = bytes moved).  Launches that
  * a converged GMRES cycle turned into no-ops are not counted. */
 int gnk_profile_enable(int on);
+/* Restricts the recording to the kinds whose bit is set in mask (bit k for
+ * kind k; all kinds by default), so that instrumenting the few launches of
+ * interest does not add event records to every small launch. */
+int gnk_profile_mask(unsigned mask);
 int gnk_profile_query(int kind, long long* launches, double* total_ms,
                       double* work);
 /* As gnk_profile_query, plus the launches' algorithmic instruction count on

@@ -199,7 +199,7 @@ __global__ void prepare_geometry_kernel(PrepArgs a) {
 }  // namespace
 
 int run_circulant(const Boundary& b, const double* x, double* y, cudaStream_t st) {
-    const ProfToken tok = prof_begin(st);
+    const ProfToken tok = prof_begin(st, PK_CIRC);
     if (b.fft_pow2) {
         const int pairs = (b.m1 + 1) / 2;
         const int threads = std::min(512, std::max(32, b.n / 2));
@@ -332,7 +332,7 @@ int run_batch_circulant(const int4* desc, const long long* base, int nblocks, in
                                           2 * 4096 * (int)sizeof(double2)));
         attr_set = true;
     }
-    const ProfToken tok = prof_begin(st);
+    const ProfToken tok = prof_begin(st, PK_CIRC);
     batch_circulant_kernel<<<nblocks, 256, smem, st>>>(desc, base, x, y, tw, col);
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tok, PK_CIRC, 0.0, st);

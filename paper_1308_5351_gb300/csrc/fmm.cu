@@ -941,7 +941,7 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     cudaStream_t fs = t->aux;
     int launches = 1;
     // upward pass
-    const ProfToken tok = prof_begin(fs);
+    const ProfToken tok = prof_begin(fs, PK_FMMTREE);
     if (R == 2)
         fmm_p2m_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
     else
@@ -954,13 +954,13 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tok, PK_FMMTREE, 0.0, fs, 0.0);
     // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
-    const ProfToken tokm = prof_begin(fs);
+    const ProfToken tokm = prof_begin(fs, PK_FMM);
     fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, fs>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokm, PK_FMM, (double)R * b.N * (b.N - 1.0), fs, fmm_instr(b, R, 0));
     // downward pass
-    const ProfToken tokd = prof_begin(fs);
+    const ProfToken tokd = prof_begin(fs, PK_FMMTREE);
     for (int l = 3; l <= t->L; ++l) {
         fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, fs>>>(a, t->lvl_off[l - 2]);
         ++launches;
@@ -969,7 +969,7 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     prof_end(tokd, PK_FMMTREE, 0.0, fs, fmm_instr(b, R, 1));
     GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
     // near field on the caller's stream
-    const ProfToken tokn = prof_begin(st);
+    const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
     if (R == 2 && EF)
         fmm_near_kernel<2, true><<<t->nitems, kFmmNT, 0, st>>>(a);
     else if (R == 2)
@@ -982,7 +982,7 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st, fmm_near_instr(b, R) * (EF ? 2.0 : 1.0));
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
-    const ProfToken tokp = prof_begin(st);
+    const ProfToken tokp = prof_begin(st, PK_FMMTREE);
     const int nb = (b.N + 255) / 256;
     if (R == 2 && EF)
         fmm_l2p_kernel<2, true><<<nb, 256, 0, st>>>(a);

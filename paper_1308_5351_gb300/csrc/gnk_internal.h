@@ -54,7 +54,8 @@ enum ProfKind : int {
 struct ProfToken {
     void* ev = nullptr;
 };
-ProfToken prof_begin(cudaStream_t st);
+// kind >= 0: nothing is recorded while that kind is masked out (gnk_profile_mask)
+ProfToken prof_begin(cudaStream_t st, int kind = -1);
 // `instr`: algorithmic instructions of the launch on its limiting pipe
 // (FP32 pipe for the FP32 and double-float pair kernels, FP64 pipe for the FP64 one).
 long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr = 0.0);

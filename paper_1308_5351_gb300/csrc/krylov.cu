@@ -362,7 +362,7 @@ int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
 // Wraps one vector-kernel launch in a profiling event pair (bytes moved as work).
 #define KLAUNCH(bytes, launch)                                 \
     do {                                                       \
-        const ProfToken t_ = prof_begin(st);                   \
+        const ProfToken t_ = prof_begin(st, PK_KRYLOV);        \
         launch;                                                \
         prof_end(t_, PK_KRYLOV, (double)(bytes), st);          \
     } while (0)
@@ -455,7 +455,7 @@ int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
     KState* ks = static_cast<KState*>(b.kstate);
     KPtrs p = kry_ptrs(b.kry, b.V_cols - 1);
     {
-        const ProfToken t_ = prof_begin(st);
+        const ProfToken t_ = prof_begin(st, PK_KRYLOV);
         k_norm<<<vec_blocks(b.N), KT, 0, st>>>(v, b.N, p, ks, 0);
         prof_end(t_, PK_KRYLOV, 8.0 * b.N, st);
     }

@@ -844,7 +844,7 @@ cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int
     ra.d1w = b.d1;
     ra.job = job;
     const int threads = 256;
-    const ProfToken tok = prof_begin(st);
+    const ProfToken tok = prof_begin(st, PK_REDUCE);
     reduce_epilogue_kernel<<<(b.N + threads - 1) / threads, threads, 0, st>>>(ra);
     const cudaError_t e = cudaGetLastError();
     // bytes: the partials read plus about four N-vectors of operands and output

@@ -20,6 +20,7 @@ struct Rec {
 
 std::mutex g_mu;
 bool g_on = false;
+unsigned g_mask = ~0u;
 thread_local bool t_collect = false;
 thread_local std::vector<long> t_ids;
 std::vector<Rec> g_recs;
@@ -49,10 +50,11 @@ void recycle_all() {
 
 }  // namespace
 
-ProfToken prof_begin(cudaStream_t st) {
+ProfToken prof_begin(cudaStream_t st, int kind) {
     ProfToken t;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return t;
+    if (kind >= 0 && kind < 32 && !((g_mask >> kind) & 1u)) return t;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
         cudaGetLastError();
@@ -108,6 +110,12 @@ int gnk_profile_enable(int on) {
     for (Rec& r : g_recs) cudaEventSynchronize(r.b);
     recycle_all();
     g_on = on != 0;
+    return GNK_OK;
+}
+
+int gnk_profile_mask(unsigned mask) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mask = mask;
     return GNK_OK;
 }
 

@@ -48,7 +48,7 @@ EXPORTED = (
     "gnk_profile_query", "gnk_profile_query_ex", "gnk_cauchy_sum_noalloc", "gnk_build_boundary_ex", "gnk_fbie",
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
-    "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval",
+    "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval", "gnk_profile_mask",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(gnk_result), P]
     lib.gnk_compute_h.argtypes = [P, P, P, P, P, P]
     lib.gnk_profile_enable.argtypes = [I]
+    lib.gnk_profile_mask.argtypes = [ctypes.c_uint]
     lib.gnk_profile_query.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_sum_noalloc.argtypes = [I, P, P, P, P]
@@ -205,6 +206,10 @@ def gnk_kernel_launches() -> int:
 
 def gnk_profile_enable(on: bool):
     return _check(load().gnk_profile_enable(1 if on else 0))
+
+
+def gnk_profile_mask(mask: int):
+    return _check(load().gnk_profile_mask(int(mask) & 0xffffffff))
 
 
 def gnk_profile_query(kind: int):

@@ -155,3 +155,31 @@ def test_fmm_fullsize_ellipses64_sampled_rows(G):
         z = _host(b.cauchy_sum(_dev(w), precision=G.GNK_PREC_FMM))
     err = np.abs(z[rows] - ref)
     assert np.all(err <= 1e-12 * S + (64 + d.N) * U64 * S), (err / S).max()
+
+
+def test_profile_mask_records_only_selected_kinds(G):
+    """gnk_profile_mask: with only the M2L bit set, an FMM product records M2L
+    launches and nothing else; with all bits set, near field and tree kernels too."""
+    d = DOMS["ellipses64_n64"]
+    w = _dev(np.random.default_rng(2).normal(size=d.N) + 0j)
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
+        b.cauchy_sum(w, precision=G.GNK_PREC_FMM)      # tree and tables built
+        torch.cuda.synchronize()
+        try:
+            G.gnk_profile_mask(1 << G.PROF_FMM)
+            G.gnk_profile_enable(True)
+            b.cauchy_sum(w, precision=G.GNK_PREC_FMM)
+            torch.cuda.synchronize()
+            only = {k: G.gnk_profile_query_ex(k) for k in range(10)}
+            G.gnk_profile_mask(0xffffffff)
+            G.gnk_profile_enable(True)                  # clears the records
+            b.cauchy_sum(w, precision=G.GNK_PREC_FMM)
+            torch.cuda.synchronize()
+            every = {k: G.gnk_profile_query_ex(k) for k in range(10)}
+        finally:
+            G.gnk_profile_enable(False)
+            G.gnk_profile_mask(0xffffffff)
+    assert only[G.PROF_FMM][0] >= 1 and only[G.PROF_FMM][3] > 0
+    assert all(only[k][0] == 0 for k in range(10) if k != G.PROF_FMM)
+    assert every[G.PROF_FMM][0] == only[G.PROF_FMM][0]
+    assert every[G.PROF_FMMNEAR][0] >= 1 and every[G.PROF_FMMTREE][0] >= 1
