@@ -55,8 +55,6 @@ struct FmmArgs {
     const int* il_off;
     const int* nl_start;
     const int* nl_leaf;
-    const float4* m2m;
-    const float4* l2l;
     const float4* m2l;
     float4* mult;
     float4* loc;
@@ -77,6 +75,7 @@ struct FmmArgs {
     double2* zf;        // [R][N] near-field sums of w/d^2 in sorted order (EF products)
     double2* outF;      // [R][N] F sums in node order (EF products)
     const int* node_box;  // leaf box of each node in sorted order
+    int* ucnt;            // per box: children counted in the upward pass
 };
 
 __global__ void fmm_gather_kernel(FmmArgs a) {
@@ -154,52 +153,75 @@ __device__ __forceinline__ void translate(cdf& acc, const float4* __restrict__ T
     acc = cdf_add(acc, odd);
 }
 
-// P2M: one warp per leaf.  Each lane forms the powers t_j^k (k < P) of one
-// node of a chunk of 32 in shared memory; then lane k sums w_j t_j^k over the
-// chunk in node order.
-template <int R>
-__global__ void __launch_bounds__(32) fmm_p2m_kernel(FmmArgs a) {
-    __shared__ float4 s_pow[kFmmP][33];
-    __shared__ float4 s_w[R][32];
-    if (a.done != nullptr && *a.done) return;
-    const int leaf = blockIdx.x, lane = threadIdx.x;
-    const int box = a.leaf_box[leaf];
-    const double2 c = a.center[box];
-    const double ir = 1.0 / a.width[box];
-    cdf acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
-    const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
-    for (int base = j0; base < j1; base += 32) {
-        const int j = base + lane;
-        if (j < j1) {
-            const double2 p = a.ps[j];
-            const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
-            cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
-            for (int k = 0; k < kFmmP; ++k) {
-                s_pow[k][lane] = cdf_pack(v);
-                v = cdf_mul(v, t);
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) s_w[r][lane] = a.ws[(size_t)r * a.N + j];
-        }
-        __syncwarp();
-        const int cnt = min(32, j1 - base);
-        for (int q = 0; q < cnt; ++q) {
-            const cdf pw = cdf_of(s_pow[lane][q]);
-#pragma unroll
-            for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(s_w[r][q]), pw);
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc[r]);
+// Translation kernels use kFmmTW warps per target box.
+constexpr int kFmmTW = 4;
+
+// ---- M2M and L2L as binomial transforms.  With delta = (c1 - c0)/r0 =
+// g/4 for a child in quadrant q, g = (2 qa - 1) + i (2 qb - 1):
+//   M2M  a0_m = delta^m sum_{k<=m} C(m,k) [(2 delta)^-k a1_k]
+//   L2L  b1_m = (2 delta)^-m sum_{l>=m} C(l,m) [delta^l b0_l]
+// and (2 delta)^-1 = conj(g).  The scale factors g^e 4^-e and conj(g)^e are
+// Gaussian integers times powers of two, so multiplying by them is exact up
+// to one rounding in each part; the Pascal sums take P - 1 passes of one
+// neighbour addition per lane, with no tables.  Their terms are those of the
+// matrix forms, so the rounding error is of the same size.
+constexpr int kFmmUT = 32 * kFmmTW;  // threads of the upward and downward kernels
+
+// angle of g in units of pi/4 for the quadrant q = 2 qa + qb
+__device__ __forceinline__ int gauss_angle(int q) { return (q == 3) ? 1 : (q == 1) ? 3 : (q == 0) ? 5 : 7; }
+
+// x g^e 2^s for g = sqrt(2) e^{i pi ang / 4} (ang odd): g^e = 2^floor(e/2) (c + i d), c, d in {0, +-1}
+__device__ __forceinline__ cdf cdf_mul_gpow(cdf x, int ang, int e, int s) {
+    const int a8 = (ang * e) & 7;
+    const float m = ldexpf(1.f, (e >> 1) + s);
+    const float gr = (a8 == 0 || a8 == 1 || a8 == 7) ? m : ((a8 >= 3 && a8 <= 5) ? -m : 0.f);
+    const float gi = (a8 >= 1 && a8 <= 3) ? m : ((a8 >= 5) ? -m : 0.f);
+    const df p{__fmul_rn(x.re.h, gr), __fmul_rn(x.re.l, gr)}, q{__fmul_rn(-x.im.h, gi), __fmul_rn(-x.im.l, gi)};
+    const df u{__fmul_rn(x.im.h, gr), __fmul_rn(x.im.l, gr)}, v{__fmul_rn(x.re.h, gi), __fmul_rn(x.re.l, gi)};
+    return cdf{df_add(p, q), df_add(u, v)};
 }
 
-// Translation kernels use kFmmTW warps per target box: warp w takes the sources
-// (children, interaction-list entries) w, w + kFmmTW, ...; the warps' sums are
-// added in warp order (reproducible) by warp 0.
-constexpr int kFmmTW = 4;
+__device__ __forceinline__ cdf cdf_shfl_up1(cdf v) {
+    return cdf{df{__shfl_up_sync(0xffffffffu, v.re.h, 1), __shfl_up_sync(0xffffffffu, v.re.l, 1)},
+               df{__shfl_up_sync(0xffffffffu, v.im.h, 1), __shfl_up_sync(0xffffffffu, v.im.l, 1)}};
+}
+
+__device__ __forceinline__ cdf cdf_shfl_down1(cdf v) {
+    return cdf{df{__shfl_down_sync(0xffffffffu, v.re.h, 1), __shfl_down_sync(0xffffffffu, v.re.l, 1)},
+               df{__shfl_down_sync(0xffffffffu, v.im.h, 1), __shfl_down_sync(0xffffffffu, v.im.l, 1)}};
+}
+
+// lane m: sum_{k<=m} C(m,k) v_k (pass i adds the left neighbour on lanes m >= i)
+__device__ __forceinline__ cdf binom_lower(cdf v, int lane) {
+#pragma unroll 1
+    for (int i = 1; i < kFmmP; ++i) {
+        const cdf u = cdf_shfl_up1(v);
+        if (lane >= i) v = cdf_add(v, u);
+    }
+    return v;
+}
+
+// lane m: sum_{l>=m} C(l,m) v_l (the transposed passes, last first)
+__device__ __forceinline__ cdf binom_upper(cdf v, int lane) {
+#pragma unroll 1
+    for (int i = kFmmP - 1; i >= 1; --i) {
+        const cdf u = cdf_shfl_down1(v);
+        if (lane >= i - 1 && lane <= kFmmP - 2) v = cdf_add(v, u);
+    }
+    return v;
+}
+
+__device__ __forceinline__ cdf m2m_binom(cdf a1, int q, int lane) {
+    const int ang = gauss_angle(q);
+    const cdf c = cdf_mul_gpow(a1, 8 - ang, lane, 0);          // (2 delta)^-k a1_k
+    return cdf_mul_gpow(binom_lower(c, lane), ang, lane, -2 * lane);  // delta^m S_m
+}
+
+__device__ __forceinline__ cdf l2l_binom(cdf b0, int q, int lane) {
+    const int ang = gauss_angle(q);
+    const cdf e = cdf_mul_gpow(b0, ang, lane, -2 * lane);      // delta^l b0_l
+    return cdf_mul_gpow(binom_upper(e, lane), 8 - ang, lane, 0);  // (2 delta)^-m T_m
+}
 
 __device__ __forceinline__ cdf reduce_warps(cdf acc, float4 (*s)[32], int wid, int lane) {
     s[wid][lane] = cdf_pack(acc);
@@ -211,52 +233,113 @@ __device__ __forceinline__ cdf reduce_warps(cdf acc, float4 (*s)[32], int wid, i
     return t;  // valid in warp 0
 }
 
-// M2M for the boxes [b0, b0 + gridDim.x) of one level
-__global__ void __launch_bounds__(32 * kFmmTW) fmm_m2m_kernel(FmmArgs a, int b0) {
+__device__ __forceinline__ cdf cdf_sq(cdf a) { return cdf_mul(a, a); }
+
+// Upward pass, one block per leaf.  P2M: for each chunk of 32 nodes, warp w
+// forms the powers t_j^k of orders 8w .. 8w + 7 (from t^8 by squaring) in
+// shared memory, then sums w_j t_j^k over the chunk's nodes 8w .. 8w + 7 for
+// every k (lane = k); the warps' sums are added in warp order.  Then the
+// multipoles move up the tree without a launch per level: the block that
+// completes the last child of a box (an atomic count per box) forms that box's
+// M2M from its children (warp w takes child w) and goes on to the parent.
+// Nothing waits.
+template <int R>
+__global__ void __launch_bounds__(kFmmUT) fmm_up_kernel(FmmArgs a) {
+    __shared__ float4 s_pow[kFmmP][33];
+    __shared__ float4 s_w[R][32];
     __shared__ float4 s_acc[kFmmTW][32];
+    __shared__ int s_last;
     if (a.done != nullptr && *a.done) return;
-    const int box = b0 + blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = a.child_start[box], nc = a.child_count[box];
-    for (int r = 0; r < a.R; ++r) {
-        cdf acc = cdf_zero();
-        for (int c = c0 + wid; c < c0 + nc; c += kFmmTW)
-            translate(acc, a.m2m + (size_t)a.quad[c] * kFmmP * kFmmP,
-                      cdf_of(a.mult[((size_t)r * a.nbox + c) * kFmmP + lane]), lane);
-        acc = reduce_warps(acc, s_acc, wid, lane);
-        if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
+    const int leaf = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int box = a.leaf_box[leaf];
+    {
+        const double2 c = a.center[box];
+        const double ir = 1.0 / a.width[box];
+        cdf acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
+        const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
+        for (int base = j0; base < j1; base += 32) {
+            const int j = base + lane;
+            if (j < j1) {
+                const double2 p = a.ps[j];
+                const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+                const cdf t8 = cdf_sq(cdf_sq(cdf_sq(t)));
+                cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+                if (wid == 1) v = t8;
+                if (wid >= 2) v = cdf_sq(t8);
+                if (wid == 3) v = cdf_mul(v, t8);
+                for (int k = 8 * wid; k < 8 * wid + 8; ++k) {
+                    s_pow[k][lane] = cdf_pack(v);
+                    v = cdf_mul(v, t);
+                }
+                if (wid < R) s_w[wid][lane] = a.ws[(size_t)wid * a.N + j];
+            }
+            __syncthreads();
+            const int q1 = min(8 * wid + 8, j1 - base);
+            for (int qn = 8 * wid; qn < q1; ++qn) {
+                const cdf pw = cdf_of(s_pow[lane][qn]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(s_w[r][qn]), pw);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cdf s = reduce_warps(acc[r], s_acc, wid, lane);
+            if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(s);
+        }
+    }
+    for (;;) {
+        if (wid == 0) __threadfence();  // the box's multipole (warp 0's stores) before the count
+        __syncthreads();
+        const int par = a.parent[box];
+        if (par < 0) break;  // level 2
+        if (threadIdx.x == 0) {
+            const int last = atomicAdd(&a.ucnt[par], 1) == a.child_count[par] - 1;
+            if (last) {
+                a.ucnt[par] = 0;  // every child has counted: ready for the next product
+                __threadfence();
+            }
+            s_last = last;
+        }
+        __syncthreads();
+        if (!s_last) break;
+        box = par;
+        const int c0 = a.child_start[box], nc = a.child_count[box];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cdf acc = cdf_zero();
+            if (wid < nc) {
+                const int ch = c0 + wid;
+                acc = m2m_binom(cdf_of(__ldcg(a.mult + ((size_t)r * a.nbox + ch) * kFmmP + lane)), a.quad[ch],
+                                lane);
+            }
+            acc = reduce_warps(acc, s_acc, wid, lane);
+            if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
+        }
     }
 }
 
-// M2L for every box of levels 2..L; the 1/r factor of the scaled local
-// expansion is applied once at the end
-__global__ void __launch_bounds__(32 * kFmmTW) fmm_m2l_kernel(FmmArgs a) {
+// M2L for every box of levels 2..L (warp w takes the interaction-list entries
+// w, w + kFmmTW, ...); the 1/r factor of the scaled local expansion is applied
+// once at the end.  loc holds the M2L part of each box's local expansion; the
+// L2L shifts down the tree are applied per leaf in fmm_l2p_kernel.
+template <int R>
+__global__ void __launch_bounds__(kFmmUT) fmm_m2l_kernel(FmmArgs a) {
     __shared__ float4 s_acc[kFmmTW][32];
     if (a.done != nullptr && *a.done) return;
     const int box = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
-    for (int r = 0; r < a.R; ++r) {
+    const df sc = df_split(1.0 / a.width[box]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
         cdf acc = cdf_zero();
         for (int e = e0 + wid; e < e1; e += kFmmTW)
             translate(acc, a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP,
                       cdf_of(a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane]), lane);
         acc = reduce_warps(acc, s_acc, wid, lane);
-        if (wid == 0) {
-            const df sc = df_split(1.0 / a.width[box]);
-            a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(cdf{df_mul(acc.re, sc), df_mul(acc.im, sc)});
-        }
-    }
-}
-
-// L2L into the boxes [b0, b0 + gridDim.x) of one level (their M2L part is in place)
-__global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
-    if (a.done != nullptr && *a.done) return;
-    const int box = b0 + blockIdx.x, lane = threadIdx.x;
-    const int par = a.parent[box];
-    const float4* T = a.l2l + (size_t)a.quad[box] * kFmmP * kFmmP;
-    for (int r = 0; r < a.R; ++r) {
-        cdf acc = cdf_of(a.loc[((size_t)r * a.nbox + box) * kFmmP + lane]);
-        translate(acc, T, cdf_of(a.loc[((size_t)r * a.nbox + par) * kFmmP + lane]), lane);
-        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(acc);
+        if (wid == 0) a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(cdf{df_mul(acc.re, sc), df_mul(acc.im, sc)});
     }
 }
 
@@ -267,6 +350,7 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a, int b0) {
 // pipe (the FP64 pipe is 1/64 of it): |d|^2 with Dekker products, one Newton
 // step on the reciprocal, compensated accumulation.
 constexpr int kFmmWarps = kFmmNT / 32;
+constexpr int kFmmMaxNbr = 9;  // a leaf and its eight neighbours
 
 // d = p - q as a double-float from the exact three-float splits of two FP64
 // coordinates: the TwoSums keep every rounding error, so close nodes (whose
@@ -283,10 +367,11 @@ __device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, floa
     return r;
 }
 
-// Near field: one block per chunk of up to 32 targets of a leaf (lane = target);
-// the neighbour leaves' sources, in tiles of 32, are dealt to the warps in turn;
-// the warps' partial sums are added in warp order and stored in sorted node
-// order (zn).  The
+// Near field: one block per chunk of up to 32 targets of a leaf (lane = target).
+// The sources of the (at most nine) neighbour leaves, taken as one list in
+// neighbour order, are split into kFmmWarps equal ranges, one per warp, which
+// the warp sums in tiles of 32; the warps' partial sums are added in warp
+// order and stored in sorted node order (zn).  The
 // near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
 // of it): d from the exact three-float node coordinates, |d|^2 with Dekker
 // products, one Newton step on the reciprocal, compensated accumulation.
@@ -298,6 +383,9 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     __shared__ float2 s_q[kFmmWarps][32];   // (y2, y3)
     __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
     __shared__ double2 s_z[kFmmWarps][RS][32];
+    __shared__ int s_j[kFmmWarps][32];        // sorted index of each source of the tile
+    __shared__ int s_cum[kFmmMaxNbr + 1];     // prefix sums of the neighbour leaves' sizes
+    __shared__ int s_beg[kFmmMaxNbr];         // first source of each neighbour leaf
     if (a.done != nullptr && *a.done) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = a.items[blockIdx.x];  // (leaf, first target)
@@ -310,23 +398,36 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     df are[RS], aim[RS];
 #pragma unroll
     for (int r = 0; r < RS; ++r) are[r] = aim[r] = df{0.f, 0.f};
-    const int n0 = a.nl_start[leaf], n1 = a.nl_start[leaf + 1];
-    int tile = 0;  // tiles of 32 sources over all neighbour leaves, dealt to the warps in turn
-    for (int e = n0; e < n1; ++e) {
-        const int nl = a.nl_leaf[e];
-        const int s0 = a.leaf_start[nl], s1 = a.leaf_start[nl + 1];
-        for (int sb = s0; sb < s1; sb += 32, ++tile) {
-            if (tile % kFmmWarps != wid) continue;
+    const int n0 = a.nl_start[leaf], nn = min(a.nl_start[leaf + 1] - n0, kFmmMaxNbr);
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int e = 0; e < nn; ++e) {
+            const int nl = a.nl_leaf[n0 + e];
+            s_beg[e] = a.leaf_start[nl];
+            s_cum[e] = c;
+            c += a.leaf_start[nl + 1] - a.leaf_start[nl];
+        }
+        s_cum[nn] = c;
+    }
+    __syncthreads();
+    const int total = s_cum[nn];
+    const int q0 = (int)((long long)total * wid / kFmmWarps), q1 = (int)((long long)total * (wid + 1) / kFmmWarps);
+    for (int qs = q0; qs < q1; qs += 32) {
+        {
             __syncwarp();
-            const int j = sb + lane;
-            if (j < s1) {
+            const int q = qs + lane;
+            if (q < q1) {
+                int e = 0;
+                while (e + 1 < nn && s_cum[e + 1] <= q) ++e;
+                const int j = s_beg[e] + (q - s_cum[e]);
+                s_j[wid][lane] = j;
                 s_p[wid][lane] = a.p3[j];
                 s_q[wid][lane] = a.p3b[j];
 #pragma unroll
                 for (int r = 0; r < R; ++r) s_w[wid][r][lane] = a.ws[(size_t)r * a.N + j];
             }
             __syncwarp();
-            const int cnt = min(32, s1 - sb);
+            const int cnt = min(32, q1 - qs);
             for (int k = 0; k < cnt; ++k) {
                 const float4 qa = s_p[wid][k];
                 const float2 qb = s_q[wid][k];
@@ -342,7 +443,7 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
                 two_sum(px, py, rh, re);
                 const float rl = __fadd_rn(__fadd_rn(ex, ey), re);
                 float y = recip_f32(rh);
-                y = (sb + k == i) ? 0.f : y;  // the i = j term is excluded (Eq. fmm-E)
+                y = (s_j[wid][k] == i) ? 0.f : y;  // the i = j term is excluded (Eq. fmm-E)
                 float ee = fmaf(-rh, y, 1.0f);
                 ee = fmaf(-rl, y, ee);
                 const df inv{y, __fmul_rn(y, ee)};
@@ -395,40 +496,67 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     }
 }
 
-// L2P by Horner's rule in double-float plus the near-field sum; one thread per
-// node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
-// same coefficients); writes z in node order
+// L2L and L2P, one warp per leaf.  The leaf's local expansion is formed from
+// the M2L parts of its ancestors, level 2 first, each shifted to the next
+// level by the binomial L2L (the same operations, in the same order, as a
+// level-by-level downward pass; boxes above the leaf are shifted once per
+// leaf below them, which costs no waiting).  Then Horner's rule in
+// double-float at the leaf's nodes (lane = node), plus the near-field sum;
+// writes z in node order.
 // EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
 // plus the near-field sums of w/d^2, written to outF.
+constexpr int kFmmMaxDepth = 24;
+
 template <int R, bool EF>
-__global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
+__global__ void __launch_bounds__(32) fmm_l2p_kernel(FmmArgs a) {
+    __shared__ float4 s_loc[R][kFmmP];
+    __shared__ int s_path[kFmmMaxDepth];
+    __shared__ int s_depth;
     if (a.done != nullptr && *a.done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
-    const int box = a.node_box[i];
-    const double2 c = a.center[box];
-    const double ir = 1.0 / a.width[box];
-    const double2 p = a.ps[i];
-    const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
-    const int node = a.perm[i];
+    const int leaf = blockIdx.x, lane = threadIdx.x;
+    const int box = a.leaf_box[leaf];
+    if (lane == 0) {
+        int d = 0;
+        for (int bx = box; bx >= 0 && d < kFmmMaxDepth; bx = a.parent[bx]) s_path[d++] = bx;
+        s_depth = d;
+    }
+    __syncwarp();
+    const int D = s_depth;  // s_path[D - 1] is on level 2, s_path[0] is the leaf
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
-        cdf u = cdf_of(b[kFmmP - 1]);
-        cdf du = cdf_zero();
-        for (int l = kFmmP - 2; l >= 0; --l) {
-            if (EF) du = cdf_add(cdf_mul(du, t), u);
-            const cdf m = cdf_mul(u, t);
-            const cdf bl = cdf_of(b[l]);
-            u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+        cdf v = cdf_of(a.loc[((size_t)r * a.nbox + s_path[D - 1]) * kFmmP + lane]);
+        for (int d = D - 2; d >= 0; --d) {
+            const int bx = s_path[d];
+            v = cdf_add(cdf_of(a.loc[((size_t)r * a.nbox + bx) * kFmmP + lane]), l2l_binom(v, a.quad[bx], lane));
         }
-        const double2 zn = a.zn[(size_t)r * a.N + i];
-        a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
-                                                     ((double)u.im.h + (double)u.im.l) + zn.y);
-        if (EF) {
-            const double2 zf = a.zf[(size_t)r * a.N + i];
-            a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
-                                                          -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
+        s_loc[r][lane] = cdf_pack(v);
+    }
+    __syncwarp();
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    const int j1 = a.leaf_start[leaf + 1];
+    for (int i = a.leaf_start[leaf] + lane; i < j1; i += 32) {
+        const double2 p = a.ps[i];
+        const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+        const int node = a.perm[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cdf u = cdf_of(s_loc[r][kFmmP - 1]);
+            cdf du = cdf_zero();
+            for (int l = kFmmP - 2; l >= 0; --l) {
+                if (EF) du = cdf_add(cdf_mul(du, t), u);
+                const cdf m = cdf_mul(u, t);
+                const cdf bl = cdf_of(s_loc[r][l]);
+                u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+            }
+            const double2 zn = a.zn[(size_t)r * a.N + i];
+            a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
+                                                         ((double)u.im.h + (double)u.im.l) + zn.y);
+            if (EF) {
+                const double2 zf = a.zf[(size_t)r * a.N + i];
+                a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
+                                                              -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
+            }
         }
     }
 }
@@ -445,7 +573,7 @@ float4 cdf_host(const cld& v) {
 // Binomial coefficients (Pascal's triangle) and powers by repeated products in
 // long double: no library power functions, whose long double forms are slow
 // where long double is emulated in software.
-void translation_tables(std::vector<float4>* m2m, std::vector<float4>* l2l, std::vector<float4>* m2l) {
+void translation_tables(std::vector<float4>* m2l) {
     const int P = kFmmP, PP = 2 * kFmmP + 1;
     std::vector<long double> C((size_t)PP * PP, 0.0L);  // C[n][k], n < 2P + 1
     for (int n = 0; n < PP; ++n) {
@@ -459,22 +587,7 @@ void translation_tables(std::vector<float4>* m2m, std::vector<float4>* l2l, std:
         for (int e = 1; e < count; ++e) p[e] = p[e - 1] * z;
         return p;
     };
-    std::vector<long double> half(P);  // 2^-k
-    half[0] = 1.0L;
-    for (int k = 1; k < P; ++k) half[k] = half[k - 1] * 0.5L;
-    m2m->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
-    l2l->assign(4 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
     m2l->assign(49 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int q = 0; q < 4; ++q) {
-        const int qa = q >> 1, qb = q & 1;
-        const std::vector<cld> dp = powers(cld((2 * qa - 1) / 4.0L, (2 * qb - 1) / 4.0L), P);
-        for (int m = 0; m < P; ++m)
-            for (int k = 0; k <= m; ++k)  // M2M: row m, column k; stored [q][k][m]
-                (*m2m)[(size_t)q * P * P + k * P + m] = cdf_host(binom(m, k) * half[k] * dp[m - k]);
-        for (int m = 0; m < P; ++m)
-            for (int l = m; l < P; ++l)  // L2L: row m, column l; stored [q][l][m]
-                (*l2l)[(size_t)q * P * P + l * P + m] = cdf_host(binom(l, m) * half[m] * dp[l - m]);
-    }
     for (int dx = -3; dx <= 3; ++dx)
         for (int dy = -3; dy <= 3; ++dy) {
             if (std::max(std::abs(dx), std::abs(dy)) <= 1) continue;
@@ -495,11 +608,11 @@ void* g_stage = nullptr;
 size_t g_stage_bytes = 0;
 
 // The translation tables depend only on P: formed once per process.
-const std::vector<float4>& cached_tables(int which) {
+const std::vector<float4>& cached_tables() {
     static std::once_flag once;
-    static std::vector<float4> m2m, l2l, m2l;
-    std::call_once(once, [] { translation_tables(&m2m, &l2l, &m2l); });
-    return which == 0 ? m2m : (which == 1 ? l2l : m2l);
+    static std::vector<float4> m2l;
+    std::call_once(once, [] { translation_tables(&m2l); });
+    return m2l;
 }
 
 // v = s[0] + s[1] + s[2] exactly (each float takes the next 24 bits of the
@@ -532,6 +645,7 @@ void release_fmm(Boundary& b) {
         if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
         if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
         if (b.fmm->arena) cudaFree(b.fmm->arena);
+        if (b.fmm->sync) cudaFree(b.fmm->sync);
         delete b.fmm;
         b.fmm = nullptr;
     }
@@ -835,30 +949,22 @@ static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
     return GNK_OK;
 }
 
-int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l, cudaStream_t st) {
+int fmm_device_tables(const float4** m2l, cudaStream_t st) {
     static std::mutex mu;
     static std::vector<float4*> per_device;  // indexed by device, never freed
     int dev = 0;
     GNK_TRY_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
     if ((int)per_device.size() <= dev) per_device.resize(dev + 1, nullptr);
-    const size_t P2 = (size_t)kFmmP * kFmmP;
     if (!per_device[dev]) {
-        const std::vector<float4>& a = cached_tables(0);
-        const std::vector<float4>& b = cached_tables(1);
-        const std::vector<float4>& c = cached_tables(2);
+        const std::vector<float4>& c = cached_tables();
         float4* d = nullptr;
-        if (cudaMalloc(&d, (a.size() + b.size() + c.size()) * sizeof(float4)) != cudaSuccess) {
+        if (cudaMalloc(&d, c.size() * sizeof(float4)) != cudaSuccess) {
             cudaGetLastError();
             set_error("FMM: device allocation of the translation tables failed");
             return GNK_ENOMEM;
         }
-        cudaError_t e = cudaMemcpyAsync(d, a.data(), a.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d + a.size(), b.data(), b.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d + a.size() + b.size(), c.data(), c.size() * sizeof(float4),
-                                cudaMemcpyHostToDevice, st);
+        cudaError_t e = cudaMemcpyAsync(d, c.data(), c.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -868,9 +974,7 @@ int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l
         }
         per_device[dev] = d;
     }
-    *m2m = per_device[dev];
-    *l2l = per_device[dev] + 4 * P2;
-    *m2l = per_device[dev] + 8 * P2;
+    *m2l = per_device[dev];
     return GNK_OK;
 }
 
@@ -898,7 +1002,15 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     t->R = kMaxRHS;
     int rc = fmm_tree_device(b, t, st);
     if (rc == kFmmUseHost) rc = fmm_tree_host(b, t, st);
-    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2m, &t->l2l, &t->m2l, st);
+    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2l, st);
+    if (rc == GNK_OK) {  // the upward pass's child counts, all zero
+        if (cudaMalloc(&t->sync, (size_t)t->nbox * sizeof(int)) != cudaSuccess ||
+            cudaMemsetAsync(t->sync, 0, (size_t)t->nbox * sizeof(int), st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("FMM: allocation of the pass counters failed");
+            rc = GNK_ENOMEM;
+        }
+    }
     if (rc == GNK_OK &&
         (cudaStreamCreateWithPriority(&t->aux, cudaStreamNonBlocking, fmm_high_priority()) != cudaSuccess ||
          cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -913,17 +1025,22 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
 }
 
 // FP32-pipe instructions of one FMM product, for the roofline: 48 per
-// double-float complex multiply-add (4 Dekker products and 4 compensated sums).
-// which = 0: M2L; 1: P2M (38 per node and order for the power, 48 R for the
-// sums), M2M and L2L.  (The near field: fmm_near_instr.)
+// double-float complex multiply-add of M2L (4 Dekker products and 4
+// compensated sums); 742 per lane for an M2M or L2L binomial transform (31
+// passes of a double-float complex addition, 22 each, and two exact scalings,
+// 30 each); P2M: 36 per complex double-float power (47 per node: 32 orders,
+// the squarings to t^8 in each warp, t^16 and t^24) and 48 R per node and
+// order for the sums; L2P: 58 R per node and order (a complex product and
+// sum), twice that with the derivative.
+// which = 0: M2L; 1: the upward pass (P2M and M2M); 2: L2L and L2P; 3: the same with the derivative.
+// (The near field: fmm_near_instr.)
 double fmm_instr(const Boundary& b, int R, int which) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
-    const double P = kFmmP;
-    if (which == 0) return 48.0 * R * P * P * (double)t->m2l_pairs;
-    const double trans = (double)(t->m2m_pairs + (t->nbox - t->lvl_cnt[0])) * P * P;
-    // P2M: 38 per node and order for the power, 48 R for the sums; L2P: 38 R
-    return 48.0 * trans * R + (double)b.N * P * (38.0 + 86.0 * R);
+    const double P = kFmmP, binom = 742.0 * P;
+    if (which == 0) return R * 48.0 * P * P * (double)t->m2l_pairs;
+    if (which == 1) return R * binom * (double)t->m2m_pairs + (double)b.N * (36.0 * 47.0 + 48.0 * R * P);
+    return R * (binom * (double)t->nleaf * (t->L - 2) + (double)b.N * P * 58.0 * (which == 3 ? 2.0 : 1.0));
 }
 
 double fmm_near_instr(const Boundary& b, int R) {
@@ -940,33 +1057,24 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
     cudaStream_t fs = t->aux;
     int launches = 1;
-    // upward pass
+    // upward pass (P2M and M2M) in one launch
     const ProfToken tok = prof_begin(fs, PK_FMMTREE);
     if (R == 2)
-        fmm_p2m_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
+        fmm_up_kernel<2><<<t->nleaf, kFmmUT, 0, fs>>>(a);
     else
-        fmm_p2m_kernel<1><<<t->nleaf, 32, 0, fs>>>(a);
+        fmm_up_kernel<1><<<t->nleaf, kFmmUT, 0, fs>>>(a);
     ++launches;
-    for (int l = t->L - 1; l >= 2; --l) {
-        fmm_m2m_kernel<<<t->lvl_cnt[l - 2], 32 * kFmmTW, 0, fs>>>(a, t->lvl_off[l - 2]);
-        ++launches;
-    }
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_FMMTREE, 0.0, fs, 0.0);
+    prof_end(tok, PK_FMMTREE, 0.0, fs, fmm_instr(b, R, 1));
     // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
     const ProfToken tokm = prof_begin(fs, PK_FMM);
-    fmm_m2l_kernel<<<t->nbox, 32 * kFmmTW, 0, fs>>>(a);
+    if (R == 2)
+        fmm_m2l_kernel<2><<<t->nbox, kFmmUT, 0, fs>>>(a);
+    else
+        fmm_m2l_kernel<1><<<t->nbox, kFmmUT, 0, fs>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokm, PK_FMM, (double)R * b.N * (b.N - 1.0), fs, fmm_instr(b, R, 0));
-    // downward pass
-    const ProfToken tokd = prof_begin(fs, PK_FMMTREE);
-    for (int l = 3; l <= t->L; ++l) {
-        fmm_l2l_kernel<<<t->lvl_cnt[l - 2], 32, 0, fs>>>(a, t->lvl_off[l - 2]);
-        ++launches;
-    }
-    GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokd, PK_FMMTREE, 0.0, fs, fmm_instr(b, R, 1));
     GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
     // near field on the caller's stream
     const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
@@ -983,18 +1091,18 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st, fmm_near_instr(b, R) * (EF ? 2.0 : 1.0));
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
     const ProfToken tokp = prof_begin(st, PK_FMMTREE);
-    const int nb = (b.N + 255) / 256;
+    const int nl = t->nleaf;
     if (R == 2 && EF)
-        fmm_l2p_kernel<2, true><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<2, true><<<nl, 32, 0, st>>>(a);
     else if (R == 2)
-        fmm_l2p_kernel<2, false><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<2, false><<<nl, 32, 0, st>>>(a);
     else if (EF)
-        fmm_l2p_kernel<1, true><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<1, true><<<nl, 32, 0, st>>>(a);
     else
-        fmm_l2p_kernel<1, false><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<1, false><<<nl, 32, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokp, PK_FMMTREE, 0.0, st, 0.0);
+    prof_end(tokp, PK_FMMTREE, 0.0, st, fmm_instr(b, R, EF ? 3 : 2));
     *nlaunch = launches;
     return GNK_OK;
 }
@@ -1025,9 +1133,8 @@ static void fmm_args(const Boundary& b, FmmArgs& a) {
     a.zn = t->zn;
     a.zf = t->zf;
     a.node_box = t->node_box;
-    a.m2m = t->m2m;
-    a.l2l = t->l2l;
     a.m2l = t->m2l;
+    a.ucnt = t->sync;
     a.mult = t->mult;
     a.loc = t->loc;
     a.ws = t->ws;

@@ -39,15 +39,14 @@ struct FmmTree {
     int* nl_leaf = nullptr;
     int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
     int nitems = 0;
-    const float4* m2m = nullptr;  // [4][k][m]   double-float complex (re.h, re.l, im.h, im.l),
-    const float4* l2l = nullptr;  // [4][l][m]   in the per-device table cache
-    const float4* m2l = nullptr;  // [49][k][l]
+    const float4* m2l = nullptr;  // [49][k][l] double-float complex (re.h, re.l, im.h, im.l), per-device cache
     float4* mult = nullptr;     // [R][nbox][P]
     float4* loc = nullptr;      // [R][nbox][P]
     float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
     double2* zn = nullptr;      // [R][N] near-field sums in sorted order
     double2* zf = nullptr;      // [R][N] near-field sums of w/d^2 (gradient products)
     int* node_box = nullptr;    // leaf box of each node in sorted order
+    int* sync = nullptr;        // [nbox]: children counted by the upward pass (zero between products)
     cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -59,8 +58,8 @@ struct FmmTree {
 constexpr int kFmmUseHost = 1;
 int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st);
 
-// The double-float translation tables on the current device (formed and
-// uploaded once per device and process): M2M [4][P][P], L2L [4][P][P], M2L [49][P][P].
-int fmm_device_tables(const float4** m2m, const float4** l2l, const float4** m2l, cudaStream_t st);
+// The double-float M2L tables on the current device (formed and uploaded once
+// per device and process): [49][P][P] by the offset code (dx + 3) 7 + (dy + 3).
+int fmm_device_tables(const float4** m2l, cudaStream_t st);
 
 }  // namespace gnk
