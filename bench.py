@@ -54,27 +54,32 @@ PEAK_INSTR = {
     "pairdf": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm": SMS * SM_MAX_MHZ * 1e6 * 128,
     "fmm_near": SMS * SM_MAX_MHZ * 1e6 * 128,
-    "fmm_tree": SMS * SM_MAX_MHZ * 1e6 * 128,
+    "fmm_l2p": SMS * SM_MAX_MHZ * 1e6 * 128,
+    "fmm_up": SMS * SM_MAX_MHZ * 1e6 * 128,
+    "fmm_l2l": SMS * SM_MAX_MHZ * 1e6 * 128,
 }
 PEAK_BASIS = {
     "pair64": "FP64 pipe: 152 SMs x 2 DFMA lanes x 2070 MHz; 9 + 4R FP64 instr per pair",
     "pair32": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 6 + 4R FP32 instr per pair (+1 MUFU)",
     "pairdf": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float pair",
-    "fmm": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 48 FP32 instr per double-float complex "
-           "multiply-add of the M2L translations (order 32)",
-    "fmm_tree": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 48 FP32 instr per double-float complex "
-                "multiply-add of M2M and L2L, 38 + 48R per node and order in P2M",
+    "fmm": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; per M2L pair and lane 24 FP32 instr for each "
+           "of the 32 double-float products of the real Pascal matrix + 98 for the two complex scalings",
+    "fmm_up": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 742 FP32 instr per lane per binomial M2M "
+              "transform, 36 x 47 per node for the powers and 48R per node and order in P2M",
+    "fmm_l2l": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 742 FP32 instr per lane per binomial L2L transform",
+    "fmm_l2p": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 58R FP32 instr per node and order (Horner)",
     "fmm_near": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float "
                 "near-field pair",
 }
 KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
                "fmm": "fmm_m2l_kernel",
-               "fmm_near": "fmm_leaf_kernel (L2P + double-float near field)",
-               "fmm_tree": "fmm_p2m_kernel, fmm_m2m_kernel, fmm_l2l_kernel"}
+               "fmm_near": "fmm_near_kernel (double-float near field)",
+               "fmm_l2p": "fmm_l2p_kernel", "fmm_up": "fmm_up_kernel (P2M and the M2M chain)",
+               "fmm_l2l": "fmm_l2l_kernel"}
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
-ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_tree")
-# instrumented kinds in the timed region: pair sums (0, 1, 6) and the FMM (7, 8, 9)
-PROFILE_MASK = (1 << 0) | (1 << 1) | (1 << 6) | (1 << 7) | (1 << 8) | (1 << 9)
+ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
+# instrumented kinds: pair sums (0, 1, 6) and the FMM kernels (7 to 11)
+PROFILE_MASK = (1 << 0) | (1 << 1) | (1 << 6) | (1 << 7) | (1 << 8) | (1 << 9) | (1 << 10) | (1 << 11)
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
 FMM_MODES = ("fmm", "mixed_fmm")
 DTYPES = {"mixed_df": "f32 + double-float f32 pairs, f64 vectors", "mixed": "f32 + f64",
@@ -157,6 +162,14 @@ class ClockSampler:
                  "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait for the first sample, so that nvidia-smi's start-up (NVML
+        # initialisation) is over before the timed region begins
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -267,7 +280,8 @@ def main():
         return res
 
     kinds = (("pair64", G.PROF_PAIR64), ("pair32", G.PROF_PAIR32), ("pairdf", G.PROF_PAIRDF),
-             ("fmm", G.PROF_FMM), ("fmm_near", G.PROF_FMMNEAR), ("fmm_tree", G.PROF_FMMTREE),
+             ("fmm", G.PROF_FMM), ("fmm_near", G.PROF_FMMNEAR), ("fmm_l2p", G.PROF_FMML2P),
+             ("fmm_up", G.PROF_FMMUP), ("fmm_l2l", G.PROF_FMML2L),
              ("reduce", G.PROF_REDUCE),
              ("circ", G.PROF_CIRC),
              ("krylov", G.PROF_KRYLOV))

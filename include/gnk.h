@@ -114,9 +114,12 @@ unsigned long long gnk_kernel_launches(void);
  * around every kernel launch of the library; gnk_profile_enable(0) stops.
  * gnk_profile_query sums, over the recorded launches of one kind, the number
  * of launches, their device time in ms and their algorithmic work (it waits
- * for the recorded events).  Kinds: 0 FP64 pair-sum kernel and 1 FP32
- * pair-sum kernel (work = pair evaluations R N (N-1)), 2 reduction/epilogue,
- * 3 circulant, 4 GMRES vector kernels (work = bytes moved).  Launches that
+ * for the recorded events).  Kinds: 0 FP64, 1 FP32 and 6 double-float
+ * pair-sum kernels (work = pair evaluations R N (N-1)), 2 reduction/epilogue,
+ * 3 circulant, 4 GMRES vector kernels (work = bytes moved), 5 other, and
+ * the FMM kernels: 7 M2L (work = the R N (N-1) pairs the product stands
+ * for), 8 near field (work = near-field pairs), 9 L2P, 10 the upward pass
+ * (P2M and M2M), 11 L2L.  Launches that
  * a converged GMRES cycle turned into no-ops are not counted. */
 int gnk_profile_enable(int on);
 /* Restricts the recording to the kinds whose bit is set in mask (bit k for
@@ -127,7 +130,8 @@ int gnk_profile_query(int kind, long long* launches, double* total_ms,
                       double* work);
 /* As gnk_profile_query, plus the launches' algorithmic instruction count on
  * their limiting pipe (pair kernels: per pair, FP64 9 + 4R, FP32 6 + 4R,
- * double-float 49 + 48R, R the right-hand sides of the launch). */
+ * double-float 49 + 48R, R the right-hand sides of the launch; the FMM
+ * kernels: FP32-pipe instructions of their double-float arithmetic). */
 int gnk_profile_query_ex(int kind, long long* launches, double* total_ms,
                          double* work, double* instr);
 

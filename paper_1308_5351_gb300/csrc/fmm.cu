@@ -9,17 +9,27 @@
 //   M2L  b_l  = (1/r) sum_k (-1)^(k+1) C(k+l,l) delta^-(k+l+1) a_k,  delta = (c1-c0)/r
 //   L2L  b1_m = sum_{l>=m} C(l,m) ((c1-c0)/r0)^(l-m) 2^-m b0_l
 // The near field (a leaf and its eight neighbours) is summed directly with the
-// i = j term excluded.  All translation matrices depend only on the relative box
-// position, so they are tabulated once (4 + 4 + 49 matrices of P x P).  The
-// truncation error is below 0.43^P of sum_j |w_j / (eta_i - eta_j)| (about 2e-12
-// at P = 32 including round-off; checked against direct sums in the tests).
+// i = j term excluded.  The truncation error is below 0.43^P of
+// sum_j |w_j / (eta_i - eta_j)| (about 2e-12 at P = 32 including round-off;
+// checked against direct sums in the tests).
 //
-// The tree is built on the host once per handle (the geometry is fixed for all
-// products): Morton keys of 16-bit box coordinates, a sort of (key, node) pairs,
-// leaf level L = the deepest level whose non-empty boxes hold at least kFmmLeaf
-// nodes on average, interaction and neighbour lists by binary search of the sorted
-// box keys of each level.  Every sum on the device runs in a fixed order, so
-// results are reproducible.
+// One product is six launches on two streams.  The weights are gathered into
+// tree order; the far field runs on a high-priority stream: the upward pass
+// (P2M, then the M2M chain carried by the block that completes each box's
+// last child, no launch per level), M2L for every box, L2L per leaf down its
+// ancestor path.  The near field runs beside it on the caller's stream; L2P
+// adds the two after they join.  M2M and L2L are
+// binomial transforms between exact Gaussian-integer scalings, M2L a fixed real
+// Pascal matrix between two complex scalings per offset: no P x P table per
+// relative position.  The far field runs in complex double-float on the FP32
+// pipe (GB300's FP64 pipe is 1/64 of it).
+//
+// The tree is built once per handle (the geometry is fixed for all products),
+// on the device when its lookup grids fit (fmm_tree.cu), else on the host:
+// Morton keys of 16-bit box coordinates, a sort of (key, node) pairs, leaf
+// level L = the deepest level whose non-empty boxes hold at least kFmmLeaf
+// nodes on average, interaction and neighbour lists.  Every sum on the device
+// runs in a fixed order, so results are reproducible.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -55,7 +65,8 @@ struct FmmArgs {
     const int* il_off;
     const int* nl_start;
     const int* nl_leaf;
-    const float4* m2l;
+    const float2* m2lH;   // C(k+l, l), [k][l] double-float
+    const float4* m2lS;   // per offset code: (-1)^(k+1) delta^-(k+1), then delta^-l
     float4* mult;
     float4* loc;
     float4* ws;
@@ -134,27 +145,11 @@ __device__ __forceinline__ void cdf_mac(cdf& acc, cdf a, cdf b) {
     df_acc(acc.im, df_mul(a.im, b.re));
 }
 
-__device__ __forceinline__ cdf cdf_shfl(cdf v, int src) {
-    return cdf{df{__shfl_sync(0xffffffffu, v.re.h, src), __shfl_sync(0xffffffffu, v.re.l, src)},
-               df{__shfl_sync(0xffffffffu, v.im.h, src), __shfl_sync(0xffffffffu, v.im.l, src)}};
-}
-
 __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
-
-// acc_lane += sum_k T[k][lane] x_k, x_k held by lane k (one P x P translation);
-// even and odd k go to two accumulators (two independent dependency chains)
-__device__ __forceinline__ void translate(cdf& acc, const float4* __restrict__ T, cdf x, int lane) {
-    cdf odd = cdf_zero();
-#pragma unroll 4
-    for (int k = 0; k < kFmmP; k += 2) {
-        cdf_mac(acc, cdf_of(__ldg(T + k * kFmmP + lane)), cdf_shfl(x, k));
-        cdf_mac(odd, cdf_of(__ldg(T + (k + 1) * kFmmP + lane)), cdf_shfl(x, k + 1));
-    }
-    acc = cdf_add(acc, odd);
-}
 
 // Translation kernels use kFmmTW warps per target box.
 constexpr int kFmmTW = 4;
+constexpr int kFmmMaxDepth = 24;  // ancestors of a leaf, the leaf included
 
 // ---- M2M and L2L as binomial transforms.  With delta = (c1 - c0)/r0 =
 // g/4 for a child in quadrant q, g = (2 qa - 1) + i (2 qb - 1):
@@ -235,14 +230,99 @@ __device__ __forceinline__ cdf reduce_warps(cdf acc, float4 (*s)[32], int wid, i
 
 __device__ __forceinline__ cdf cdf_sq(cdf a) { return cdf_mul(a, a); }
 
-// Upward pass, one block per leaf.  P2M: for each chunk of 32 nodes, warp w
-// forms the powers t_j^k of orders 8w .. 8w + 7 (from t^8 by squaring) in
+// M2L into one box, as a fixed real matrix between two diagonal scalings:
+// with x_k = (-1)^(k+1) delta^-(k+1) a_k (delta the source-to-target centre
+// offset in box widths),
+//   b_l = (1/r) delta^-l sum_k C(k+l, l) x_k.
+// The Pascal matrix C(k+l, l) (double-float, 8 KB) is the same for every
+// pair and stays in L1; the scalings are 2 x 32 double-float complex values
+// per offset code.  The terms are those of the matrix form, so the rounding
+// error is of the same size.  Warp w takes the interaction-list entries w,
+// w + kFmmTW, ...; the warps' sums are added in warp order; the 1/r factor is
+// applied once at the end.  loc then holds the M2L part of the box's local
+// expansion.
+template <int R>
+__device__ __forceinline__ void m2l_box(const FmmArgs& a, int box, int wid, int lane, float4 (*s_acc)[32],
+                                        float4 (*s_x)[32]) {
+    const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
+    const df sc = df_split(1.0 / a.width[box]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        cdf acc = cdf_zero();
+        for (int e = e0 + wid; e < e1; e += kFmmTW) {
+            const float4* S = a.m2lS + (size_t)a.il_off[e] * 2 * kFmmP;
+            const cdf x = cdf_mul(cdf_of(__ldcg(a.mult + ((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane)),
+                                  cdf_of(__ldg(S + lane)));
+            const cdf post = cdf_of(__ldg(S + kFmmP + lane));
+            __syncwarp();
+            s_x[wid][lane] = cdf_pack(x);
+            __syncwarp();
+            df yr{0.f, 0.f}, yi{0.f, 0.f}, zr{0.f, 0.f}, zi{0.f, 0.f};
+#pragma unroll 4
+            for (int k = 0; k < kFmmP; k += 2) {
+                const float2 h0 = __ldg(a.m2lH + k * kFmmP + lane), h1 = __ldg(a.m2lH + (k + 1) * kFmmP + lane);
+                const float4 x0 = s_x[wid][k], x1 = s_x[wid][k + 1];
+                df_acc(yr, df_mul(df{h0.x, h0.y}, df{x0.x, x0.y}));
+                df_acc(yi, df_mul(df{h0.x, h0.y}, df{x0.z, x0.w}));
+                df_acc(zr, df_mul(df{h1.x, h1.y}, df{x1.x, x1.y}));
+                df_acc(zi, df_mul(df{h1.x, h1.y}, df{x1.z, x1.w}));
+            }
+            acc = cdf_add(acc, cdf_mul(cdf{df_add(yr, zr), df_add(yi, zi)}, post));
+        }
+        acc = reduce_warps(acc, s_acc, wid, lane);
+        if (wid == 0) a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(cdf{df_mul(acc.re, sc), df_mul(acc.im, sc)});
+    }
+}
+
+// P2M of one leaf (block of kFmmTW warps): for each chunk of 32 nodes, warp
+// w forms the powers t_j^k of orders 8w .. 8w + 7 (from t^8 by squaring) in
 // shared memory, then sums w_j t_j^k over the chunk's nodes 8w .. 8w + 7 for
-// every k (lane = k); the warps' sums are added in warp order.  Then the
-// multipoles move up the tree without a launch per level: the block that
-// completes the last child of a box (an atomic count per box) forms that box's
-// M2M from its children (warp w takes child w) and goes on to the parent.
-// Nothing waits.
+// every k (lane = k); the warps' sums are added in warp order.
+template <int R>
+__device__ __forceinline__ void p2m_leaf(const FmmArgs& a, int leaf, int box, int wid, int lane,
+                                         float4 (*s_pow)[33], float4 (*s_w)[32], float4 (*s_acc)[32]) {
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    cdf acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
+    const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
+    for (int base = j0; base < j1; base += 32) {
+        const int j = base + lane;
+        if (j < j1) {
+            const double2 p = a.ps[j];
+            const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+            const cdf t8 = cdf_sq(cdf_sq(cdf_sq(t)));
+            cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+            if (wid == 1) v = t8;
+            if (wid >= 2) v = cdf_sq(t8);
+            if (wid == 3) v = cdf_mul(v, t8);
+            for (int k = 8 * wid; k < 8 * wid + 8; ++k) {
+                s_pow[k][lane] = cdf_pack(v);
+                v = cdf_mul(v, t);
+            }
+            if (wid < R) s_w[wid][lane] = a.ws[(size_t)wid * a.N + j];
+        }
+        __syncthreads();
+        const int q1 = min(8 * wid + 8, j1 - base);
+        for (int qn = 8 * wid; qn < q1; ++qn) {
+            const cdf pw = cdf_of(s_pow[lane][qn]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(s_w[r][qn]), pw);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const cdf sm = reduce_warps(acc[r], s_acc, wid, lane);
+        if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(sm);
+    }
+}
+
+// Upward pass, one block per leaf: P2M, then the multipoles move up the tree
+// without a launch per level: the block that completes the last child of a
+// box (an atomic count per box; nothing waits) forms that box's M2M from its
+// children (warp w takes child w) and goes on to the parent.
 template <int R>
 __global__ void __launch_bounds__(kFmmUT) fmm_up_kernel(FmmArgs a) {
     __shared__ float4 s_pow[kFmmP][33];
@@ -252,44 +332,7 @@ __global__ void __launch_bounds__(kFmmUT) fmm_up_kernel(FmmArgs a) {
     if (a.done != nullptr && *a.done) return;
     const int leaf = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int box = a.leaf_box[leaf];
-    {
-        const double2 c = a.center[box];
-        const double ir = 1.0 / a.width[box];
-        cdf acc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
-        const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
-        for (int base = j0; base < j1; base += 32) {
-            const int j = base + lane;
-            if (j < j1) {
-                const double2 p = a.ps[j];
-                const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
-                const cdf t8 = cdf_sq(cdf_sq(cdf_sq(t)));
-                cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
-                if (wid == 1) v = t8;
-                if (wid >= 2) v = cdf_sq(t8);
-                if (wid == 3) v = cdf_mul(v, t8);
-                for (int k = 8 * wid; k < 8 * wid + 8; ++k) {
-                    s_pow[k][lane] = cdf_pack(v);
-                    v = cdf_mul(v, t);
-                }
-                if (wid < R) s_w[wid][lane] = a.ws[(size_t)wid * a.N + j];
-            }
-            __syncthreads();
-            const int q1 = min(8 * wid + 8, j1 - base);
-            for (int qn = 8 * wid; qn < q1; ++qn) {
-                const cdf pw = cdf_of(s_pow[lane][qn]);
-#pragma unroll
-                for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(s_w[r][qn]), pw);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const cdf s = reduce_warps(acc[r], s_acc, wid, lane);
-            if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(s);
-        }
-    }
+    p2m_leaf<R>(a, leaf, box, wid, lane, s_pow, s_w, s_acc);
     for (;;) {
         if (wid == 0) __threadfence();  // the box's multipole (warp 0's stores) before the count
         __syncthreads();
@@ -321,25 +364,43 @@ __global__ void __launch_bounds__(kFmmUT) fmm_up_kernel(FmmArgs a) {
     }
 }
 
-// M2L for every box of levels 2..L (warp w takes the interaction-list entries
-// w, w + kFmmTW, ...); the 1/r factor of the scaled local expansion is applied
-// once at the end.  loc holds the M2L part of each box's local expansion; the
-// L2L shifts down the tree are applied per leaf in fmm_l2p_kernel.
+// M2L for every box of levels 2 .. L (block = box)
 template <int R>
 __global__ void __launch_bounds__(kFmmUT) fmm_m2l_kernel(FmmArgs a) {
     __shared__ float4 s_acc[kFmmTW][32];
+    __shared__ float4 s_x[kFmmTW][32];
     if (a.done != nullptr && *a.done) return;
-    const int box = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int e0 = a.il_start[box], e1 = a.il_start[box + 1];
-    const df sc = df_split(1.0 / a.width[box]);
+    m2l_box<R>(a, blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31, s_acc, s_x);
+}
+
+// L2L, one warp per leaf: the leaf's local expansion is formed from the M2L
+// parts of its ancestors, level 2 first, each shifted to the next level by
+// the binomial L2L (the same operations, in the same order, as a
+// level-by-level downward pass; boxes above the leaf are shifted once per
+// leaf below them, which costs no waiting), and stored over the leaf's M2L part.
+template <int R>
+__global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a) {
+    __shared__ int s_path[kFmmMaxDepth];
+    __shared__ int s_depth;
+    if (a.done != nullptr && *a.done) return;
+    const int leaf = blockIdx.x, lane = threadIdx.x;
+    const int box = a.leaf_box[leaf];
+    if (lane == 0) {
+        int d = 0;
+        for (int bx = box; bx >= 0 && d < kFmmMaxDepth; bx = a.parent[bx]) s_path[d++] = bx;
+        s_depth = d;
+    }
+    __syncwarp();
+    const int D = s_depth;  // s_path[D - 1] is on level 2, s_path[0] is the leaf
+    if (D < 2) return;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        cdf acc = cdf_zero();
-        for (int e = e0 + wid; e < e1; e += kFmmTW)
-            translate(acc, a.m2l + (size_t)a.il_off[e] * kFmmP * kFmmP,
-                      cdf_of(a.mult[((size_t)r * a.nbox + a.il_src[e]) * kFmmP + lane]), lane);
-        acc = reduce_warps(acc, s_acc, wid, lane);
-        if (wid == 0) a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(cdf{df_mul(acc.re, sc), df_mul(acc.im, sc)});
+        cdf v = cdf_of(a.loc[((size_t)r * a.nbox + s_path[D - 1]) * kFmmP + lane]);
+        for (int d = D - 2; d >= 0; --d) {
+            const int bx = s_path[d];
+            v = cdf_add(cdf_of(a.loc[((size_t)r * a.nbox + bx) * kFmmP + lane]), l2l_binom(v, a.quad[bx], lane));
+        }
+        a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(v);
     }
 }
 
@@ -496,67 +557,40 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     }
 }
 
-// L2L and L2P, one warp per leaf.  The leaf's local expansion is formed from
-// the M2L parts of its ancestors, level 2 first, each shifted to the next
-// level by the binomial L2L (the same operations, in the same order, as a
-// level-by-level downward pass; boxes above the leaf are shifted once per
-// leaf below them, which costs no waiting).  Then Horner's rule in
-// double-float at the leaf's nodes (lane = node), plus the near-field sum;
-// writes z in node order.
+// L2P by Horner's rule in double-float plus the near-field sum; one thread per
+// node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
+// same coefficients); writes z in node order
 // EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
 // plus the near-field sums of w/d^2, written to outF.
-constexpr int kFmmMaxDepth = 24;
-
 template <int R, bool EF>
-__global__ void __launch_bounds__(32) fmm_l2p_kernel(FmmArgs a) {
-    __shared__ float4 s_loc[R][kFmmP];
-    __shared__ int s_path[kFmmMaxDepth];
-    __shared__ int s_depth;
+__global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
     if (a.done != nullptr && *a.done) return;
-    const int leaf = blockIdx.x, lane = threadIdx.x;
-    const int box = a.leaf_box[leaf];
-    if (lane == 0) {
-        int d = 0;
-        for (int bx = box; bx >= 0 && d < kFmmMaxDepth; bx = a.parent[bx]) s_path[d++] = bx;
-        s_depth = d;
-    }
-    __syncwarp();
-    const int D = s_depth;  // s_path[D - 1] is on level 2, s_path[0] is the leaf
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        cdf v = cdf_of(a.loc[((size_t)r * a.nbox + s_path[D - 1]) * kFmmP + lane]);
-        for (int d = D - 2; d >= 0; --d) {
-            const int bx = s_path[d];
-            v = cdf_add(cdf_of(a.loc[((size_t)r * a.nbox + bx) * kFmmP + lane]), l2l_binom(v, a.quad[bx], lane));
-        }
-        s_loc[r][lane] = cdf_pack(v);
-    }
-    __syncwarp();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int box = a.node_box[i];
     const double2 c = a.center[box];
     const double ir = 1.0 / a.width[box];
-    const int j1 = a.leaf_start[leaf + 1];
-    for (int i = a.leaf_start[leaf] + lane; i < j1; i += 32) {
-        const double2 p = a.ps[i];
-        const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
-        const int node = a.perm[i];
+    const double2 p = a.ps[i];
+    const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+    const int node = a.perm[i];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            cdf u = cdf_of(s_loc[r][kFmmP - 1]);
-            cdf du = cdf_zero();
-            for (int l = kFmmP - 2; l >= 0; --l) {
-                if (EF) du = cdf_add(cdf_mul(du, t), u);
-                const cdf m = cdf_mul(u, t);
-                const cdf bl = cdf_of(s_loc[r][l]);
-                u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
-            }
-            const double2 zn = a.zn[(size_t)r * a.N + i];
-            a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
-                                                         ((double)u.im.h + (double)u.im.l) + zn.y);
-            if (EF) {
-                const double2 zf = a.zf[(size_t)r * a.N + i];
-                a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
-                                                              -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
-            }
+    for (int r = 0; r < R; ++r) {
+        const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
+        cdf u = cdf_of(b[kFmmP - 1]);
+        cdf du = cdf_zero();
+        for (int l = kFmmP - 2; l >= 0; --l) {
+            if (EF) du = cdf_add(cdf_mul(du, t), u);
+            const cdf m = cdf_mul(u, t);
+            const cdf bl = cdf_of(b[l]);
+            u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+        }
+        const double2 zn = a.zn[(size_t)r * a.N + i];
+        a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
+                                                     ((double)u.im.h + (double)u.im.l) + zn.y);
+        if (EF) {
+            const double2 zf = a.zf[(size_t)r * a.N + i];
+            a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
+                                                          -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
         }
     }
 }
@@ -570,35 +604,42 @@ float4 cdf_host(const cld& v) {
     return make_float4(rh, (float)(v.real() - (long double)rh), ih, (float)(v.imag() - (long double)ih));
 }
 
-// Binomial coefficients (Pascal's triangle) and powers by repeated products in
-// long double: no library power functions, whose long double forms are slow
-// where long double is emulated in software.
-void translation_tables(std::vector<float4>* m2l) {
+// The M2L tables: the Pascal matrix C(k+l, l) as double-float pairs (P x P
+// float2, in kFmmHSlots float4 slots), then per offset code (dx + 3) 7 + (dy + 3)
+// the scalings (-1)^(k+1) delta^-(k+1) and delta^-l, delta = dx + i dy.
+// Binomial coefficients by Pascal's triangle and powers by repeated products
+// in long double: no library power functions, whose long double forms are
+// slow where long double is emulated in software.
+constexpr int kFmmHSlots = kFmmP * kFmmP / 2;
+
+void translation_tables(std::vector<float4>* tab) {
     const int P = kFmmP, PP = 2 * kFmmP + 1;
     std::vector<long double> C((size_t)PP * PP, 0.0L);  // C[n][k], n < 2P + 1
     for (int n = 0; n < PP; ++n) {
         C[(size_t)n * PP] = 1.0L;
         for (int k = 1; k <= n; ++k) C[(size_t)n * PP + k] = C[(size_t)(n - 1) * PP + k - 1] + C[(size_t)(n - 1) * PP + k];
     }
-    auto binom = [&](int n, int k) { return C[(size_t)n * PP + k]; };
-    auto powers = [](const cld& z, int count) {
-        std::vector<cld> p(count);
-        p[0] = cld(1.0L, 0.0L);
-        for (int e = 1; e < count; ++e) p[e] = p[e - 1] * z;
-        return p;
-    };
-    m2l->assign(49 * P * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    tab->assign(kFmmHSlots + 49 * 2 * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    float* H = reinterpret_cast<float*>(tab->data());  // [k][l] (hi, lo)
+    for (int k = 0; k < P; ++k)
+        for (int l = 0; l < P; ++l) {
+            const long double v = C[(size_t)(k + l) * PP + l];
+            const float hi = (float)v;
+            H[2 * (k * P + l)] = hi;
+            H[2 * (k * P + l) + 1] = (float)(v - (long double)hi);
+        }
     for (int dx = -3; dx <= 3; ++dx)
         for (int dy = -3; dy <= 3; ++dy) {
             if (std::max(std::abs(dx), std::abs(dy)) <= 1) continue;
             const int o = (dx + 3) * 7 + (dy + 3);
-            const std::vector<cld> ip = powers(1.0L / cld((long double)dx, (long double)dy), 2 * P);
-            for (int l = 0; l < P; ++l)
-                for (int k = 0; k < P; ++k) {
-                    // M2L: row l, column k; stored [o][k][l]
-                    const long double sgn = ((k + 1) % 2) ? -1.0L : 1.0L;
-                    (*m2l)[(size_t)o * P * P + k * P + l] = cdf_host(sgn * binom(k + l, l) * ip[k + l + 1]);
-                }
+            const cld iz = 1.0L / cld((long double)dx, (long double)dy);
+            float4* S = tab->data() + kFmmHSlots + (size_t)o * 2 * P;
+            cld pw(1.0L, 0.0L);  // delta^-e
+            for (int e = 0; e <= P; ++e) {
+                if (e < P) S[P + e] = cdf_host(pw);                                       // delta^-l, l = e
+                if (e >= 1) S[e - 1] = cdf_host((e % 2 == 1) ? -pw : pw);                // k = e - 1: (-1)^(k+1) = (-1)^e
+                pw *= iz;
+            }
         }
 }
 
@@ -607,12 +648,12 @@ std::mutex g_stage_mutex;
 void* g_stage = nullptr;
 size_t g_stage_bytes = 0;
 
-// The translation tables depend only on P: formed once per process.
+// The M2L tables depend only on P: formed once per process.
 const std::vector<float4>& cached_tables() {
     static std::once_flag once;
-    static std::vector<float4> m2l;
-    std::call_once(once, [] { translation_tables(&m2l); });
-    return m2l;
+    static std::vector<float4> tab;
+    std::call_once(once, [] { translation_tables(&tab); });
+    return tab;
 }
 
 // v = s[0] + s[1] + s[2] exactly (each float takes the next 24 bits of the
@@ -949,7 +990,7 @@ static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
     return GNK_OK;
 }
 
-int fmm_device_tables(const float4** m2l, cudaStream_t st) {
+int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st) {
     static std::mutex mu;
     static std::vector<float4*> per_device;  // indexed by device, never freed
     int dev = 0;
@@ -974,7 +1015,8 @@ int fmm_device_tables(const float4** m2l, cudaStream_t st) {
         }
         per_device[dev] = d;
     }
-    *m2l = per_device[dev];
+    *m2lH = reinterpret_cast<const float2*>(per_device[dev]);
+    *m2lS = per_device[dev] + kFmmHSlots;
     return GNK_OK;
 }
 
@@ -1002,10 +1044,11 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     t->R = kMaxRHS;
     int rc = fmm_tree_device(b, t, st);
     if (rc == kFmmUseHost) rc = fmm_tree_host(b, t, st);
-    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2l, st);
+    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2lH, &t->m2lS, st);
     if (rc == GNK_OK) {  // the upward pass's child counts, all zero
-        if (cudaMalloc(&t->sync, (size_t)t->nbox * sizeof(int)) != cudaSuccess ||
-            cudaMemsetAsync(t->sync, 0, (size_t)t->nbox * sizeof(int), st) != cudaSuccess) {
+        const size_t nsync = (size_t)t->nbox;
+        if (cudaMalloc(&t->sync, nsync * sizeof(int)) != cudaSuccess ||
+            cudaMemsetAsync(t->sync, 0, nsync * sizeof(int), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("FMM: allocation of the pass counters failed");
             rc = GNK_ENOMEM;
@@ -1024,23 +1067,27 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     return rc;
 }
 
-// FP32-pipe instructions of one FMM product, for the roofline: 48 per
-// double-float complex multiply-add of M2L (4 Dekker products and 4
-// compensated sums); 742 per lane for an M2M or L2L binomial transform (31
-// passes of a double-float complex addition, 22 each, and two exact scalings,
-// 30 each); P2M: 36 per complex double-float power (47 per node: 32 orders,
-// the squarings to t^8 in each warp, t^16 and t^24) and 48 R per node and
-// order for the sums; L2P: 58 R per node and order (a complex product and
-// sum), twice that with the derivative.
-// which = 0: M2L; 1: the upward pass (P2M and M2M); 2: L2L and L2P; 3: the same with the derivative.
-// (The near field: fmm_near_instr.)
+// FP32-pipe instructions of one FMM product, for the roofline.  M2L, per pair
+// and lane: 32 (2 Dekker products and 2 compensated sums, 24) for the real
+// Pascal matrix, the two complex scalings (38 each) and the sum (22); 742 per
+// lane for an M2M or L2L binomial transform (31 passes of a double-float
+// complex addition, 22 each, and two exact scalings, 30 each); P2M: 36 per
+// complex double-float power (47 per node: 32 orders, the squarings to t^8 in
+// each warp, t^16 and t^24) and 48 R per node and order for the sums; L2P:
+// 58 R per node and order (a complex product and sum), twice that with the
+// derivative.
+// which = 0: M2L; 1: the upward pass (P2M and M2M); 2: L2L; 3: L2P; 4: L2P
+// with the derivative.  (The near field: fmm_near_instr.)
 double fmm_instr(const Boundary& b, int R, int which) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
-    const double P = kFmmP, binom = 742.0 * P;
-    if (which == 0) return R * 48.0 * P * P * (double)t->m2l_pairs;
-    if (which == 1) return R * binom * (double)t->m2m_pairs + (double)b.N * (36.0 * 47.0 + 48.0 * R * P);
-    return R * (binom * (double)t->nleaf * (t->L - 2) + (double)b.N * P * 58.0 * (which == 3 ? 2.0 : 1.0));
+    const double P = kFmmP, binom = 742.0 * P, m2l = (24.0 * P + 98.0) * P;
+    switch (which) {
+        case 0: return R * m2l * (double)t->m2l_pairs;
+        case 1: return R * binom * (double)t->m2m_pairs + (double)b.N * (36.0 * 47.0 + 48.0 * R * P);
+        case 2: return R * binom * (double)t->nleaf * (t->L - 2);
+        default: return R * (double)b.N * P * 58.0 * (which == 4 ? 2.0 : 1.0);
+    }
 }
 
 double fmm_near_instr(const Boundary& b, int R) {
@@ -1057,24 +1104,34 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
     cudaStream_t fs = t->aux;
     int launches = 1;
-    // upward pass (P2M and M2M) in one launch
-    const ProfToken tok = prof_begin(fs, PK_FMMTREE);
+    // the far field on its stream: the upward pass (P2M and the M2M chain),
+    // M2L for every box, L2L per leaf
+    const ProfToken toku = prof_begin(fs, PK_FMMUP);
     if (R == 2)
         fmm_up_kernel<2><<<t->nleaf, kFmmUT, 0, fs>>>(a);
     else
         fmm_up_kernel<1><<<t->nleaf, kFmmUT, 0, fs>>>(a);
-    ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tok, PK_FMMTREE, 0.0, fs, fmm_instr(b, R, 1));
+    prof_end(toku, PK_FMMUP, 0.0, fs, fmm_instr(b, R, 1));
     // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
     const ProfToken tokm = prof_begin(fs, PK_FMM);
     if (R == 2)
         fmm_m2l_kernel<2><<<t->nbox, kFmmUT, 0, fs>>>(a);
     else
         fmm_m2l_kernel<1><<<t->nbox, kFmmUT, 0, fs>>>(a);
-    ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokm, PK_FMM, (double)R * b.N * (b.N - 1.0), fs, fmm_instr(b, R, 0));
+    launches += 2;
+    if (t->L > 2) {
+        const ProfToken tokd = prof_begin(fs, PK_FMML2L);
+        if (R == 2)
+            fmm_l2l_kernel<2><<<t->nleaf, 32, 0, fs>>>(a);
+        else
+            fmm_l2l_kernel<1><<<t->nleaf, 32, 0, fs>>>(a);
+        GNK_TRY_CUDA(cudaGetLastError());
+        prof_end(tokd, PK_FMML2L, 0.0, fs, fmm_instr(b, R, 2));
+        ++launches;
+    }
     GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
     // near field on the caller's stream
     const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
@@ -1090,19 +1147,19 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st, fmm_near_instr(b, R) * (EF ? 2.0 : 1.0));
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
-    const ProfToken tokp = prof_begin(st, PK_FMMTREE);
-    const int nl = t->nleaf;
+    const ProfToken tokp = prof_begin(st, PK_FMML2P);
+    const int nb = (b.N + 255) / 256;
     if (R == 2 && EF)
-        fmm_l2p_kernel<2, true><<<nl, 32, 0, st>>>(a);
+        fmm_l2p_kernel<2, true><<<nb, 256, 0, st>>>(a);
     else if (R == 2)
-        fmm_l2p_kernel<2, false><<<nl, 32, 0, st>>>(a);
+        fmm_l2p_kernel<2, false><<<nb, 256, 0, st>>>(a);
     else if (EF)
-        fmm_l2p_kernel<1, true><<<nl, 32, 0, st>>>(a);
+        fmm_l2p_kernel<1, true><<<nb, 256, 0, st>>>(a);
     else
-        fmm_l2p_kernel<1, false><<<nl, 32, 0, st>>>(a);
+        fmm_l2p_kernel<1, false><<<nb, 256, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokp, PK_FMMTREE, 0.0, st, fmm_instr(b, R, EF ? 3 : 2));
+    prof_end(tokp, PK_FMML2P, 0.0, st, fmm_instr(b, R, EF ? 4 : 3));
     *nlaunch = launches;
     return GNK_OK;
 }
@@ -1133,7 +1190,8 @@ static void fmm_args(const Boundary& b, FmmArgs& a) {
     a.zn = t->zn;
     a.zf = t->zf;
     a.node_box = t->node_box;
-    a.m2l = t->m2l;
+    a.m2lH = t->m2lH;
+    a.m2lS = t->m2lS;
     a.ucnt = t->sync;
     a.mult = t->mult;
     a.loc = t->loc;

@@ -12,7 +12,7 @@ namespace gnk {
 
 constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
 constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
-constexpr int kFmmNT = 256;   // threads of the leaf (L2P + near field) kernel: 8 warps
+constexpr int kFmmNT = 256;   // threads of the near-field kernel: 8 warps
 
 struct FmmTree {
     int L = 0, nbox = 0, nleaf = 0, R = 0;
@@ -39,7 +39,8 @@ struct FmmTree {
     int* nl_leaf = nullptr;
     int2* items = nullptr;      // (leaf, first target) of every chunk of 32 targets
     int nitems = 0;
-    const float4* m2l = nullptr;  // [49][k][l] double-float complex (re.h, re.l, im.h, im.l), per-device cache
+    const float2* m2lH = nullptr;  // M2L: the Pascal matrix C(k+l, l) [k][l] as double-float,
+    const float4* m2lS = nullptr;  // and per offset code the two complex scalings (per-device cache)
     float4* mult = nullptr;     // [R][nbox][P]
     float4* loc = nullptr;      // [R][nbox][P]
     float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
@@ -59,7 +60,8 @@ constexpr int kFmmUseHost = 1;
 int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st);
 
 // The double-float M2L tables on the current device (formed and uploaded once
-// per device and process): [49][P][P] by the offset code (dx + 3) 7 + (dy + 3).
-int fmm_device_tables(const float4** m2l, cudaStream_t st);
+// per device and process): the Pascal matrix C(k+l, l) [P][P] and, per offset
+// code (dx + 3) 7 + (dy + 3), the scalings (-1)^(k+1) delta^-(k+1) and delta^-l.
+int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st);
 
 }  // namespace gnk

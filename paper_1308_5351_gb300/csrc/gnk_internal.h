@@ -48,8 +48,10 @@ enum ProfKind : int {
     PK_OTHER = 5,
     PK_PAIRDF = 6,   // double-float pair-sum kernel; work = pair evaluations
     PK_FMM = 7,      // FMM M2L; work = the R N (N-1) pairs the product stands for
-    PK_FMMNEAR = 8,  // FMM L2P + near field (double-float); work = near-field pair evaluations
-    PK_FMMTREE = 9,  // FMM P2M, M2M (upward) and L2L (downward) passes
+    PK_FMMNEAR = 8,  // FMM near field (double-float); work = near-field pair evaluations
+    PK_FMML2P = 9,   // FMM L2P and the sum with the near field
+    PK_FMMUP = 10,   // FMM upward pass (P2M and the M2M chain)
+    PK_FMML2L = 11,  // FMM L2L per leaf
 };
 struct ProfToken {
     void* ev = nullptr;

@@ -8,15 +8,19 @@
 // the residual recomputed from x at the start of every cycle.
 //
 // Orthogonalisation is classical Gram-Schmidt applied twice (CGS2): each pass
-// is one multi-dot and one update over the basis, which maps to two
-// bandwidth-bound kernels instead of j dependent passes.  Reductions finish
-// in the last block to arrive (atomic ticket + fence, no spinning) and add
-// the per-block partials in a fixed order, so results are reproducible.
+// is one multi-dot and one update over the basis instead of j dependent
+// passes.  A whole Arnoldi step (both passes, the norm, the Givens update and
+// the scaling of the new basis vector) is one cooperative launch whose blocks
+// meet at two bounded grid barriers (the new norm follows from the second
+// pass by Pythagoras unless it cancels, then a third); the norms at the start of a cycle
+// finish in the last block to arrive (atomic ticket + fence, no spinning).
+// Partial sums are added in a fixed order, so results are reproducible.
 // Inside a cycle every kernel first reads the device flag `done`, so the host
 // enqueues a whole cycle without waiting and synchronises once per cycle.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "gnk_internal.h"
@@ -36,6 +40,8 @@ struct KState {
     int nonfinite;    // a NaN/Inf was met
     int restart;
     unsigned counter; // last-block ticket
+    unsigned bar_count, bar_gen;  // grid barrier of the Arnoldi step: arrivals, generation
+    int bar_err;      // a grid barrier wait gave up
 };
 
 constexpr int KT = 256;       // threads per block of the vector kernels
@@ -55,7 +61,7 @@ struct KPtrs {
 
 size_t kry_doubles(int restart) {
     const size_t ld = restart + 1;
-    return ld * restart + ld + 2 * (size_t)restart + 2 * ld + restart + KB_MAX * ld;
+    return ld * restart + ld + 2 * (size_t)restart + 2 * ld + restart + 2 * KB_MAX * ld;
 }
 
 KPtrs kry_ptrs(double* base, int restart) {
@@ -68,7 +74,7 @@ KPtrs kry_ptrs(double* base, int restart) {
     p.h1 = p.sn + restart;
     p.h2 = p.h1 + p.ld;
     p.y = p.h2 + p.ld;
-    p.part = p.y + restart;
+    p.part = p.y + restart;  // two regions of KB_MAX x ld
     return p;
 }
 
@@ -95,16 +101,6 @@ __device__ __forceinline__ double sum_partials(const double* part, size_t stride
     double t = 0.0;
     for (int b = threadIdx.x; b < nb; b += KT) t += part[(size_t)b * stride];
     return block_sum(t, red);
-}
-
-// The same for one value per warp: lane l adds b = l, l + 32, ...; then shuffles.
-// Valid in lane 0.
-__device__ __forceinline__ double warp_sum_partials(const double* part, size_t stride, int nb) {
-    const int lane = threadIdx.x & 31;
-    double t = 0.0;
-    for (int b = lane; b < nb; b += 32) t += part[(size_t)b * stride];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    return t;
 }
 
 // True in every thread of the last block to finish writing its partials.
@@ -153,26 +149,60 @@ __global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r
     for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) v0[i] = r[i] * inv;
 }
 
-// h[k] = <v_k, w>, k < nv: KD dot products per pass over w, reduced per block
-// in a fixed order (warp shuffles, then warps in order), then by the last block
-constexpr int KD = 8;
+// dot products per pass over w in the Arnoldi step
+constexpr int KD = 12;
 
-__global__ void __launch_bounds__(KT) k_dots(const double* __restrict__ V, int N, int nv,
-                                             const double* __restrict__ w, KPtrs p, double* hout,
-                                             KState* s) {
-    if (s->done) return;
-    __shared__ double red[KT / 32][KD];
+// ---- one Arnoldi step in one cooperative launch.  After the product
+// w = A v_j: the two CGS passes (multi-dot, update), ||w||, the Givens update
+// of column j and v_{j+1} = w / h_{j+1,j}.  Each block takes a contiguous
+// range of the vectors; the partial sums meet at grid barriers, after
+// which every block adds them in the same fixed order (so all blocks hold
+// the same coefficients without another barrier).  Block 0 does the Givens
+// step.  The launch is cooperative, so all blocks are resident and every
+// barrier is reached; the waits are bounded all the same, and one that gives
+// up sets bar_err, which the host reports.
+constexpr int kBarSpin = 1 << 20;
+
+__device__ __forceinline__ void grid_barrier(KState* s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &s->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&s->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&s->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&s->bar_gen, 1u);
+        } else {
+            for (int it = 0; *gen == g; ++it) {
+                if (it >= kBarSpin || *(volatile int*)&s->bar_err) {
+                    atomicExch(&s->bar_err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// dots of w with v_0 .. v_{nv-1} over [i0, i1), block sums to out[0 .. nv);
+// with_norm: also w . w to out[nv]
+__device__ __forceinline__ void range_dots(const double* __restrict__ V, int N, int nv, const double* w,
+                                           int i0, int i1, double* out, double (*red)[KD], bool with_norm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k0 = 0; k0 < nv; k0 += KD) {
-        const int kn = min(KD, nv - k0);
+    const int nt = nv + (with_norm ? 1 : 0);
+    for (int k0 = 0; k0 < nt; k0 += KD) {
+        const int kn = min(KD, nt - k0);
         double acc[KD];
 #pragma unroll
         for (int q = 0; q < KD; ++q) acc[q] = 0.0;
-        for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+        for (int i = i0 + threadIdx.x; i < i1; i += KT) {
             const double wi = w[i];
 #pragma unroll
             for (int q = 0; q < KD; ++q)
-                if (q < kn) acc[q] = fma(V[(size_t)(k0 + q) * N + i], wi, acc[q]);
+                if (q < kn) acc[q] = fma((k0 + q < nv) ? V[(size_t)(k0 + q) * N + i] : wi, wi, acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < KD; ++q) {
@@ -184,101 +214,185 @@ __global__ void __launch_bounds__(KT) k_dots(const double* __restrict__ V, int N
         if (threadIdx.x < kn) {
             double t = 0.0;
             for (int ww = 0; ww < KT / 32; ++ww) t += red[ww][threadIdx.x];
-            p.part[(size_t)blockIdx.x * p.ld + k0 + threadIdx.x] = t;
+            out[k0 + threadIdx.x] = t;
         }
         __syncthreads();
     }
-    if (!arrive_last(&s->counter)) return;
-    for (int k = wid; k < nv; k += KT / 32) {  // one warp per coefficient
-        const double t = warp_sum_partials(p.part + k, p.ld, gridDim.x);
-        if (lane == 0) hout[k] = t;
-    }
-    if (threadIdx.x == 0) s->counter = 0;
 }
 
-// w -= V h (first pass)
-__global__ void __launch_bounds__(KT) k_update(const double* __restrict__ V, int N, int nv,
-                                               double* __restrict__ w, const double* __restrict__ h,
-                                               const KState* s) {
-    if (s->done) return;
-    __shared__ double hs[1024];
-    for (int k = threadIdx.x; k < nv; k += KT) hs[k] = h[k];
+// hs[k] = sum_b part[b * ld + k] over the nb blocks, k < nv: lane = coefficient,
+// warp w adds its eighth of the blocks in order, then the warps' sums are added
+// in warp order; read from L2 (the partials of other blocks)
+__device__ __forceinline__ void reduce_coeffs(const double* part, int ld, int nv, int nb, double* hs,
+                                              double (*red8)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = KT / 32;
+    const int per = (nb + NW - 1) / NW, b0 = min(nb, wid * per), b1 = min(nb, b0 + per);
+    for (int k0 = 0; k0 < nv; k0 += 32) {
+        const int k = k0 + lane;
+        double t = 0.0;
+        if (k < nv) {
+#pragma unroll 4
+            for (int b = b0; b < b1; ++b) t += __ldcg(part + (size_t)b * ld + k);
+        }
+        red8[wid][lane] = t;
+        __syncthreads();
+        if (wid == 0 && k < nv) {
+            double u = red8[0][lane];
+            for (int ww = 1; ww < NW; ++ww) u += red8[ww][lane];
+            hs[k] = u;
+        }
+        __syncthreads();
+    }
+}
+
+// Givens update of column j by block 0: the column h = h1 + h2 (in h1),
+// h_{j+1,j} = hn and the previous rotations are staged in shared memory, one
+// thread applies the rotations, and the column is stored in parallel.  Also
+// the residual estimate and the end-of-cycle test (the triangular solve for y
+// is k_solve_y's, once per cycle).
+__device__ void givens_step(int j, double hn, double* h1, const double* h2, double* scs, double* ssn, KPtrs p,
+                            KState* s) {
+    const int nv = j + 1;
+    for (int k = threadIdx.x; k < j; k += KT) {
+        scs[k] = p.cs[k];
+        ssn[k] = p.sn[k];
+    }
+    for (int k = threadIdx.x; k < nv; k += KT) h1[k] = h1[k] + h2[k];
     __syncthreads();
-    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+    if (threadIdx.x == 0) {
+        double* col = h1;
+        col[j + 1] = hn;
+        s->hnext = hn;
+        for (int k = 0; k < j; ++k) {  // previous rotations
+            const double a = col[k], b = col[k + 1];
+            col[k] = scs[k] * a + ssn[k] * b;
+            col[k + 1] = -ssn[k] * a + scs[k] * b;
+        }
+        const double a = col[j], b = col[j + 1];
+        const double r = hypot(a, b);
+        const double c = (r > 0.0) ? a / r : 1.0;
+        const double sn = (r > 0.0) ? b / r : 0.0;
+        p.cs[j] = c;
+        p.sn[j] = sn;
+        col[j] = r;
+        col[j + 1] = 0.0;
+        const double gj = p.g[j];
+        p.g[j + 1] = -sn * gj;
+        p.g[j] = c * gj;
+        const double est = fabs(sn * gj);
+        s->est = est;
+        s->k = j + 1;
+        const bool bad = !isfinite(est) || !isfinite(hn);
+        if (bad) s->nonfinite = 1;
+        if (bad || est <= s->tol * s->bnorm || j + 1 == s->restart || hn == 0.0) s->done = 1;
+    }
+    __syncthreads();
+    double* colg = p.H + (size_t)j * p.ld;
+    for (int k = threadIdx.x; k < j + 2; k += KT) colg[k] = h1[k];
+}
+
+__global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, int N, int j, double* __restrict__ w,
+                                                KPtrs p, KState* s) {
+    if (s->done) return;  // set before this launch: the same in every block
+    __shared__ double red[KT / 32][KD];
+    __shared__ double red8[KT / 32][32];
+    __shared__ double h1[1025], h2[1025], scs[1024], ssn[1024];
+    __shared__ double s_hn;
+    const int nv = j + 1, nb = gridDim.x;
+    const int per = (N + nb - 1) / nb;
+    const int i0 = min(N, (int)blockIdx.x * per), i1 = min(N, i0 + per);
+    double* part1 = p.part;
+    double* part2 = p.part + (size_t)KB_MAX * p.ld;
+    // first pass: h1 = V^T w
+    range_dots(V, N, nv, w, i0, i1, part1 + (size_t)blockIdx.x * p.ld, red, false);
+    grid_barrier(s);
+    reduce_coeffs(part1, p.ld, nv, nb, h1, red8);
+    // w' = w - V h1 on the block's range, then the second pass h2 = V^T w' with ||w'||^2
+    for (int i = i0 + threadIdx.x; i < i1; i += KT) {
         double acc = w[i];
-        for (int k = 0; k < nv; ++k) acc = fma(-hs[k], V[(size_t)k * N + i], acc);
+        for (int k = 0; k < nv; ++k) acc = fma(-h1[k], V[(size_t)k * N + i], acc);
         w[i] = acc;
     }
-}
-
-// w -= V h2 (second pass), ||w|| -> H(j+1, j); H(:, j) = h1 + h2; Givens
-// rotations; residual estimate; end-of-cycle test and the small triangular
-// solve H y = g when the cycle ends.
-__global__ void __launch_bounds__(KT) k_update_norm_givens(const double* __restrict__ V, int N, int j,
-                                                           double* __restrict__ w, KPtrs p, KState* s) {
-    if (s->done) return;
-    __shared__ double red[KT / 32];
-    __shared__ double hs[1024];
-    const int nv = j + 1;
-    for (int k = threadIdx.x; k < nv; k += KT) hs[k] = p.h2[k];
     __syncthreads();
-    double acc = 0.0;
-    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
-        double wi = w[i];
-        for (int k = 0; k < nv; ++k) wi = fma(-hs[k], V[(size_t)k * N + i], wi);
-        w[i] = wi;
-        acc = fma(wi, wi, acc);
+    range_dots(V, N, nv, w, i0, i1, part2 + (size_t)blockIdx.x * p.ld, red, true);
+    grid_barrier(s);
+    reduce_coeffs(part2, p.ld, nv + 1, nb, h2, red8);
+    // ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 for an orthonormal basis; when more
+    // than half of ||w'||^2 cancels, the norm is summed again after the update
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int k = 0; k < nv; ++k) q = fma(h2[k], h2[k], q);
+        const double d = h2[nv] - q;
+        s_hn = (d > 0.5 * h2[nv]) ? sqrt(d) : -1.0;
     }
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) p.part[blockIdx.x] = acc;
-    if (!arrive_last(&s->counter)) return;
-    const double t = sum_partials(p.part, 1, gridDim.x, red);
-    if (threadIdx.x != 0) return;
-    const double hn = sqrt(t);
-    double* col = p.H + (size_t)j * p.ld;
-    for (int k = 0; k < nv; ++k) col[k] = p.h1[k] + p.h2[k];
-    col[j + 1] = hn;
-    s->hnext = hn;
-    for (int k = 0; k < j; ++k) {  // previous rotations
-        const double a = col[k], b = col[k + 1];
-        col[k] = p.cs[k] * a + p.sn[k] * b;
-        col[k + 1] = -p.sn[k] * a + p.cs[k] * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double r = hypot(a, b);
-    const double c = (r > 0.0) ? a / r : 1.0;
-    const double sn = (r > 0.0) ? b / r : 0.0;
-    p.cs[j] = c;
-    p.sn[j] = sn;
-    col[j] = r;
-    col[j + 1] = 0.0;
-    p.g[j + 1] = -sn * p.g[j];
-    p.g[j] = c * p.g[j];
-    const double est = fabs(p.g[j + 1]);
-    s->est = est;
-    s->k = j + 1;
-    const bool bad = !isfinite(est) || !isfinite(hn);
-    if (bad) s->nonfinite = 1;
-    const bool stop = bad || est <= s->tol * s->bnorm || j + 1 == s->restart || hn == 0.0;
-    if (stop) {
-        // back substitution H(0:k, 0:k) y = g(0:k)
-        const int kk = j + 1;
-        for (int row = kk - 1; row >= 0; --row) {
-            double v = p.g[row];
-            for (int cidx = row + 1; cidx < kk; ++cidx) v -= p.H[(size_t)cidx * p.ld + row] * p.y[cidx];
-            const double d = p.H[(size_t)row * p.ld + row];
-            p.y[row] = (d != 0.0) ? v / d : 0.0;
+    __syncthreads();
+    double hn = s_hn;
+    if (hn < 0.0) {  // the same decision in every block
+        double acc = 0.0;
+        for (int i = i0 + threadIdx.x; i < i1; i += KT) {
+            double wi = w[i];
+            for (int k = 0; k < nv; ++k) wi = fma(-h2[k], V[(size_t)k * N + i], wi);
+            w[i] = wi;
+            acc = fma(wi, wi, acc);
         }
-        s->done = 1;
+        acc = block_sum(acc, &red[0][0]);
+        if (threadIdx.x == 0) part1[(size_t)blockIdx.x * p.ld] = acc;
+        grid_barrier(s);
+        if (threadIdx.x < 32) {
+            double t = 0.0;
+            for (int b = threadIdx.x; b < nb; b += 32) t += __ldcg(part1 + (size_t)b * p.ld);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (threadIdx.x == 0) s_hn = sqrt(t);
+        }
+        __syncthreads();
+        hn = s_hn;
+        if (hn > 0.0 && isfinite(hn)) {
+            const double inv = 1.0 / hn;
+            for (int i = i0 + threadIdx.x; i < i1; i += KT) w[i] *= inv;
+        }
+    } else {  // v_{j+1} = (w' - V h2) / h_{j+1,j} in one pass (unused when the cycle stops here)
+        const double inv = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 1.0;
+        for (int i = i0 + threadIdx.x; i < i1; i += KT) {
+            double wi = w[i];
+            for (int k = 0; k < nv; ++k) wi = fma(-h2[k], V[(size_t)k * N + i], wi);
+            w[i] = wi * inv;
+        }
     }
-    s->counter = 0;
+    if (blockIdx.x == 0) givens_step(j, hn, h1, h2, scs, ssn, p, s);
 }
 
-// v_{j+1} = w / h_{j+1,j} (in place)
-__global__ void __launch_bounds__(KT) k_scale_next(double* __restrict__ w, int N, const KState* s) {
-    if (s->done) return;
-    const double inv = 1.0 / s->hnext;
-    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) w[i] *= inv;
+// y = H(0:k, 0:k)^-1 g(0:k) at the end of a cycle (one block; H staged in
+// shared memory when k <= kSmallH, else read from global memory)
+constexpr int kSmallH = 48;
+
+__global__ void __launch_bounds__(KT) k_solve_y(KPtrs p, const KState* s) {
+    __shared__ double sH[kSmallH * kSmallH], sg[kSmallH];
+    const int kk = s->k;
+    if (kk == 0) return;
+    if (kk <= kSmallH) {
+        for (int e = threadIdx.x; e < kk * kk; e += KT) sH[e] = p.H[(size_t)(e / kk) * p.ld + (e % kk)];
+        for (int e = threadIdx.x; e < kk; e += KT) sg[e] = p.g[e];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int row = kk - 1; row >= 0; --row) {  // sH[c * kk + r] = H(r, c)
+                double v = sg[row];
+                for (int c = row + 1; c < kk; ++c) v -= sH[c * kk + row] * sg[c];
+                const double d = sH[row * kk + row];
+                sg[row] = (d != 0.0) ? v / d : 0.0;  // y overwrites g from the bottom up
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kk; e += KT) p.y[e] = sg[e];
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    for (int row = kk - 1; row >= 0; --row) {
+        double v = p.g[row];
+        for (int c = row + 1; c < kk; ++c) v -= p.H[(size_t)c * p.ld + row] * p.y[c];
+        const double d = p.H[(size_t)row * p.ld + row];
+        p.y[row] = (d != 0.0) ? v / d : 0.0;
+    }
 }
 
 // x += V(:, 0:k) y at the end of a cycle
@@ -313,6 +427,8 @@ __global__ void k_init_state(KState* s, double tol, int restart) {
     s->nonfinite = 0;
     s->restart = restart;
     s->counter = 0;
+    s->bar_count = 0;
+    s->bar_err = 0;
 }
 
 int ensure_krylov(Boundary& b, int restart) {
@@ -359,6 +475,31 @@ int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
     return GNK_OK;
 }
 
+// Blocks of the cooperative Arnoldi launch: one per multiprocessor (all
+// resident at once), at most KB_MAX, at most one per KT entries.
+static int arnoldi_blocks(int N) {
+    static std::mutex mu;
+    static std::vector<int> cap;  // per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cap.size() <= dev) cap.resize(dev + 1, 0);
+    if (cap[dev] == 0) {
+        int occ = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, KT, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+            nsm = 1;
+        }
+        cap[dev] = std::max(1, std::min(occ, 1) * nsm);  // one block per multiprocessor
+    }
+    return std::max(1, std::min(std::min(cap[dev], KB_MAX), (N + KT - 1) / KT));
+}
+
 // Wraps one vector-kernel launch in a profiling event pair (bytes moved as work).
 #define KLAUNCH(bytes, launch)                                 \
     do {                                                       \
@@ -380,6 +521,7 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
     KState* ks = static_cast<KState*>(b.kstate);
     KPtrs p = kry_ptrs(b.kry, restart);
     const int nb = vec_blocks(N);
+    const int ng = arnoldi_blocks(N);
     KState hs;
     k_init_state<<<1, 1, 0, st>>>(ks, tol, restart);
     KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0)));
@@ -403,6 +545,10 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
         count_launches(2);
         GNK_TRY_CUDA(cudaGetLastError());
         GNK_TRY(read_state(b, &hs, st));
+        if (hs.bar_err) {
+            set_error("GMRES: a grid barrier of the Arnoldi step timed out");
+            return GNK_ECUDA;
+        }
         if (cycle > 0) {  // the previous cycle's step count is known only now
             res->iterations += hs.last_k;
             if (prec == GNK_PREC_FP32) res->matvecs_fp32 += hs.last_k; else res->matvecs_fp64 += hs.last_k;
@@ -434,18 +580,21 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
             const double nv = j + 1;
             prof_collect_begin();
             GNK_TRY(apply_op(b, adjoint, vj, w, prec, st, &ks->done));
-            KLAUNCH((nv + 1) * vb, (k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h1, ks)));
-            KLAUNCH((nv + 2) * vb, (k_update<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p.h1, ks)));
-            KLAUNCH((nv + 1) * vb, (k_dots<<<nb, KT, 0, st>>>(b.V, N, j + 1, w, p, p.h2, ks)));
-            KLAUNCH((nv + 2) * vb, (k_update_norm_givens<<<nb, KT, 0, st>>>(b.V, N, j, w, p, ks)));
-            KLAUNCH(2 * vb, (k_scale_next<<<nb, KT, 0, st>>>(w, N, ks)));
+            {
+                const double* Vc = b.V;
+                int Nc = N, jc = j;
+                void* args[] = {(void*)&Vc, (void*)&Nc, (void*)&jc, (void*)&w, (void*)&p, (void*)&ks};
+                KLAUNCH((3 * nv + 6) * vb, GNK_TRY_CUDA(cudaLaunchCooperativeKernel(
+                                               (const void*)k_arnoldi, dim3(ng), dim3(KT), args, 0, st)));
+            }
             prof_collect_end(&step_ids[j]);
             GNK_TRY_CUDA(cudaGetLastError());
-            count_launches(5);
+            count_launches(1);
         }
+        KLAUNCH(0.0, (k_solve_y<<<1, KT, 0, st>>>(p, ks)));
         KLAUNCH((restart + 2) * vb, (k_update_x<<<nb, KT, 0, st>>>(b.V, N, p, x, ks)));
         GNK_TRY_CUDA(cudaGetLastError());
-        count_launches(1);
+        count_launches(2);
         if (fc_valid) *fc_valid = 0;  // x moved
     }
     return status;

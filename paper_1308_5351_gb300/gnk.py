@@ -52,7 +52,7 @@ EXPORTED = (
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
-    PROF_FMMNEAR, PROF_FMMTREE = range(10)
+    PROF_FMMNEAR, PROF_FMML2P, PROF_FMMUP, PROF_FMML2L = range(12)
 
 
 class gnk_options(ctypes.Structure):

@@ -158,8 +158,9 @@ def test_fmm_fullsize_ellipses64_sampled_rows(G):
 
 
 def test_profile_mask_records_only_selected_kinds(G):
-    """gnk_profile_mask: with only the M2L bit set, an FMM product records M2L
-    launches and nothing else; with all bits set, near field and tree kernels too."""
+    """gnk_profile_mask: with only the M2L bit set, an FMM product records the
+    M2L launch and nothing else; with all bits set, the near-field, L2P, upward
+    pass and L2L kernels too."""
     d = DOMS["ellipses64_n64"]
     w = _dev(np.random.default_rng(2).normal(size=d.N) + 0j)
     with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
@@ -170,16 +171,17 @@ def test_profile_mask_records_only_selected_kinds(G):
             G.gnk_profile_enable(True)
             b.cauchy_sum(w, precision=G.GNK_PREC_FMM)
             torch.cuda.synchronize()
-            only = {k: G.gnk_profile_query_ex(k) for k in range(10)}
+            only = {k: G.gnk_profile_query_ex(k) for k in range(12)}
             G.gnk_profile_mask(0xffffffff)
             G.gnk_profile_enable(True)                  # clears the records
             b.cauchy_sum(w, precision=G.GNK_PREC_FMM)
             torch.cuda.synchronize()
-            every = {k: G.gnk_profile_query_ex(k) for k in range(10)}
+            every = {k: G.gnk_profile_query_ex(k) for k in range(12)}
         finally:
             G.gnk_profile_enable(False)
             G.gnk_profile_mask(0xffffffff)
     assert only[G.PROF_FMM][0] >= 1 and only[G.PROF_FMM][3] > 0
-    assert all(only[k][0] == 0 for k in range(10) if k != G.PROF_FMM)
+    assert all(only[k][0] == 0 for k in range(12) if k != G.PROF_FMM)
     assert every[G.PROF_FMM][0] == only[G.PROF_FMM][0]
-    assert every[G.PROF_FMMNEAR][0] >= 1 and every[G.PROF_FMMTREE][0] >= 1
+    assert every[G.PROF_FMMNEAR][0] >= 1 and every[G.PROF_FMML2P][0] >= 1
+    assert every[G.PROF_FMMUP][0] >= 1 and every[G.PROF_FMML2L][0] >= 1
