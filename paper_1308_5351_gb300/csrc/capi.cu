@@ -98,21 +98,22 @@ int check_prec(int prec) {
     return GNK_OK;
 }
 
-template <class T>
-int dmalloc(T** p, size_t count) {
-    if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("device allocation of %zu bytes failed", count * sizeof(T));
-        return GNK_ENOMEM;
-    }
-    return GNK_OK;
-}
-
+// Frees the handle's device memory once every stream's work on it is done
+// (the device synchronisation that cudaFree would imply), back to the pool.
 void release(Boundary& b) {
-    release_fmm(b);
     void* ptrs[] = {b.arena, b.V, b.kry, b.kstate};
+    bool any = b.fmm != nullptr;
+    for (void* p : ptrs) any = any || p != nullptr;
+    if (!any) return;
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    release_fmm(b);
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) pool_free(p, 0);
+    b.arena = nullptr;
+    b.V = nullptr;
+    b.kry = nullptr;
+    b.kstate = nullptr;
 }
 
 // Carves the handle's fixed-size buffers out of one device allocation
@@ -123,10 +124,10 @@ struct Arena {
     void add(T** p, size_t count) {
         parts.emplace_back(reinterpret_cast<void**>(p), count * sizeof(T));
     }
-    int allocate(void** base) {
+    int allocate(void** base, cudaStream_t st) {
         size_t total = 0;
         for (auto& pr : parts) total += (pr.second + 255) / 256 * 256;
-        if (cudaMalloc(base, total + 256) != cudaSuccess) {
+        if (pool_alloc(base, total + 256, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("device allocation of %zu bytes failed", total);
             return GNK_ENOMEM;
@@ -209,7 +210,7 @@ int build(Boundary& b, int m1, int n, const double* et, const double* etp, const
     ar.add(&b.stage, 4 * 2 * N);
     ar.add(reinterpret_cast<char**>(&b.partial), b.partial_bytes);
     ar.add(&b.flag, 1);
-    GNK_TRY(ar.allocate(&b.arena));
+    GNK_TRY(ar.allocate(&b.arena, st));
 
     // geometry copies (host or device sources; cudaMemcpyDefault infers the direction)
     GNK_TRY_CUDA(cudaMemcpyAsync(b.et, et, N * sizeof(double2), cudaMemcpyDefault, st));
@@ -565,7 +566,7 @@ int dev_view(const void* p, size_t bytes, bool input, cudaStream_t st, DevArr* o
         out->dev = const_cast<void*>(p);
         return GNK_OK;
     }
-    if (cudaMalloc(&out->dev, bytes) != cudaSuccess) {
+    if (pool_alloc(&out->dev, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("staging allocation failed");
         return GNK_ENOMEM;
@@ -618,7 +619,7 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
         }
     }
     for (int k = 0; k < 8; ++k)
-        if (v[k].tmp) cudaFree(v[k].dev);
+        if (v[k].tmp) pool_free(v[k].dev, st);
     return s;
 }
 
@@ -660,7 +661,7 @@ int gnk_cauchy_eval(const gnk_boundary* hd, int nz, const double* z, const doubl
     }
     if (rc != GNK_OK) cudaStreamSynchronize(st);
     for (int k = 0; k < 3; ++k)
-        if (v[k].tmp) cudaFree(v[k].dev);
+        if (v[k].tmp) pool_free(v[k].dev, st);
     return rc;
 }
 
@@ -688,7 +689,7 @@ struct Views {
             rc = GNK_ECUDA;
         }
         for (int k = 0; k < n; ++k)
-            if (v[k].tmp) cudaFree(v[k].dev);
+            if (v[k].tmp) pool_free(v[k].dev, st);
         return rc;
     }
 };

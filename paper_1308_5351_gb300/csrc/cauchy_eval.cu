@@ -197,7 +197,7 @@ int cauchy_eval(const Boundary& b, int M, const double2* z, const double2* f, do
     chunks = (tiles_src + tpc - 1) / tpc;
     void* part = nullptr;
     const size_t bytes = (size_t)chunks * 2 * M * (dfp ? sizeof(float4) : sizeof(double2));
-    if (cudaMalloc(&part, bytes) != cudaSuccess) {
+    if (pool_alloc(&part, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("gnk_cauchy_eval: workspace allocation of %zu bytes failed", bytes);
         return GNK_ENOMEM;
@@ -224,7 +224,7 @@ int cauchy_eval(const Boundary& b, int M, const double2* z, const double2* f, do
     count_launches(2);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(part);
+    pool_free(part, st);
     if (e != cudaSuccess) {
         set_error("gnk_cauchy_eval: %s", cudaGetErrorString(e));
         return GNK_ECUDA;

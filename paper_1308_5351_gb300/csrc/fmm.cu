@@ -685,8 +685,12 @@ void release_fmm(Boundary& b) {
         }
         if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
         if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
-        if (b.fmm->arena) cudaFree(b.fmm->arena);
-        if (b.fmm->sync) cudaFree(b.fmm->sync);
+        if (b.fmm->arena || b.fmm->sync) {  // once no stream uses them
+            cudaDeviceSynchronize();
+            cudaGetLastError();
+            pool_free(b.fmm->arena, 0);
+            pool_free(b.fmm->sync, 0);
+        }
         delete b.fmm;
         b.fmm = nullptr;
     }
@@ -920,7 +924,7 @@ static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
     };
     size_t total = 0;
     for (const Part& p : parts) total += (p.bytes + 255) / 256 * 256;
-    if (cudaMalloc(&t->arena, total) != cudaSuccess) {
+    if (pool_alloc(&t->arena, total, st) != cudaSuccess) {
         cudaGetLastError();
         t->arena = nullptr;
         set_error("FMM tree: device allocation of %zu bytes failed", total);
@@ -1047,7 +1051,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     if (rc == GNK_OK) rc = fmm_device_tables(&t->m2lH, &t->m2lS, st);
     if (rc == GNK_OK) {  // the upward pass's child counts, all zero
         const size_t nsync = (size_t)t->nbox;
-        if (cudaMalloc(&t->sync, nsync * sizeof(int)) != cudaSuccess ||
+        if (pool_alloc(reinterpret_cast<void**>(&t->sync), nsync * sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(t->sync, 0, nsync * sizeof(int), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("FMM: allocation of the pass counters failed");

@@ -445,17 +445,18 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     const size_t o_tot = take((size_t)nlev_max * 4);
     const size_t tmp0 = off;
     char* tmp = nullptr;
-    if (cudaMalloc(&tmp, tmp0) != cudaSuccess) {
+    if (pool_alloc(reinterpret_cast<void**>(&tmp), tmp0, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("FMM tree: device allocation of %zu bytes failed", tmp0);
         return GNK_ENOMEM;
     }
-    struct Free {
+    struct Free {  // stream-ordered: no device synchronisation
         char** p;
+        cudaStream_t st;
         ~Free() {
-            if (*p) cudaFree(*p);
+            if (*p) pool_free(*p, st);
         }
-    } free_tmp{&tmp};
+    } free_tmp{&tmp, st};
     double* geom = (double*)(tmp + o_geom);
     uint32_t* k0 = (uint32_t*)(tmp + o_k0);
     uint32_t* k1 = (uint32_t*)(tmp + o_k1);
@@ -498,12 +499,12 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     const size_t o2_boxid = 0;
     const size_t o2_first = align256((size_t)nlev * N * 4);
     const size_t tmp2_bytes = o2_first + align256((size_t)nlev * (N + 1) * 4);
-    if (cudaMalloc(&tmp2, tmp2_bytes) != cudaSuccess) {
+    if (pool_alloc(reinterpret_cast<void**>(&tmp2), tmp2_bytes, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("FMM tree: device allocation of %zu bytes failed", tmp2_bytes);
         return GNK_ENOMEM;
     }
-    Free free_tmp2{&tmp2};
+    Free free_tmp2{&tmp2, st};
     int* boxid = (int*)(tmp2 + o2_boxid);
     int* first = (int*)(tmp2 + o2_first);
     tb_lcount<<<nbl, LV_BLOCK, 0, st>>>(fd, N, L, cnt, nbl);
@@ -568,7 +569,7 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     };
     size_t total = 0;
     for (const Part& p : parts) total += align256(p.bytes);
-    if (cudaMalloc(&t->arena, total) != cudaSuccess) {
+    if (pool_alloc(&t->arena, total, st) != cudaSuccess) {
         cudaGetLastError();
         t->arena = nullptr;
         set_error("FMM tree: device allocation of %zu bytes failed", total);
@@ -595,12 +596,12 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     const size_t o3_go = take3((size_t)nlev * 8);
     const size_t o3_np = take3(8);
     const size_t o3_tot = take3(3 * 4);
-    if (cudaMalloc(&tmp3, o3) != cudaSuccess) {
+    if (pool_alloc(reinterpret_cast<void**>(&tmp3), o3, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("FMM tree: device allocation of %zu bytes failed", o3);
         return GNK_ENOMEM;
     }
-    Free free_tmp3{&tmp3};
+    Free free_tmp3{&tmp3, st};
     GNK_TRY_CUDA(cudaMemsetAsync(tmp3 + o3_grid, 0xff, (size_t)gcells * 4, st));
     GNK_TRY_CUDA(cudaMemsetAsync(tmp3 + o3_np, 0, 8, st));
     GNK_TRY_CUDA(cudaMemcpyAsync(tmp3 + o3_lo, t->lvl_off.data(), nlev * 4, cudaMemcpyHostToDevice, st));

@@ -37,6 +37,12 @@ void count_launches(unsigned long long n);
 // captured into a graph, whose replays are counted instead.
 void count_suppress(bool on);
 
+// ---------------------------------------------------------------- device memory
+// From a per-device stream-ordered pool that keeps freed memory (mem.cu):
+// allocation and free are ordered on st and never synchronise the device.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+cudaError_t pool_free(void* p, cudaStream_t st);
+
 // ---------------------------------------------------------------- profiling
 // Kinds of instrumented launches (gnk_profile_query's `kind`).
 enum ProfKind : int {

@@ -207,9 +207,9 @@ int fbie_backward(const Boundary& bc, const double* mu, const double* gam, const
     chunks = (tiles_src + tpc - 1) / tpc;
     int st_alloc = GNK_OK;
     const size_t part_bytes = (outer == GNK_PREC_FMM) ? 0 : (size_t)chunks * 2 * kGR * N * sizeof(double2);
-    if (cudaMalloc(&w, (size_t)kGR * N * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&S, (size_t)2 * kGR * N * sizeof(double2)) != cudaSuccess ||
-        (part_bytes && cudaMalloc(&part, part_bytes) != cudaSuccess)) {
+    if (pool_alloc(reinterpret_cast<void**>(&w), (size_t)kGR * N * sizeof(double2), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&S), (size_t)2 * kGR * N * sizeof(double2), st) != cudaSuccess ||
+        (part_bytes && pool_alloc(reinterpret_cast<void**>(&part), part_bytes, st) != cudaSuccess)) {
         cudaGetLastError();
         set_error("gradient workspace allocation failed");
         st_alloc = GNK_ENOMEM;
@@ -248,9 +248,9 @@ int fbie_backward(const Boundary& bc, const double* mu, const double* gam, const
             rc = GNK_ECUDA;
         }
     }
-    cudaFree(w);
-    cudaFree(S);
-    cudaFree(part);
+    pool_free(w, st);
+    pool_free(S, st);
+    pool_free(part, st);
     if (rc != GNK_OK) return rc;
     return s;
 }

@@ -431,16 +431,17 @@ __global__ void k_init_state(KState* s, double tol, int restart) {
     s->bar_err = 0;
 }
 
-int ensure_krylov(Boundary& b, int restart) {
+int ensure_krylov(Boundary& b, int restart, cudaStream_t st) {
     if (restart + 1 > 1024) {
         set_error("restart must be below 1024");
         return GNK_EINVAL;
     }
     if (b.V_cols < restart + 1) {
-        if (b.V) cudaFree(b.V);
+        if (b.V) pool_free(b.V, st);
         b.V = nullptr;
         b.V_cols = 0;
-        if (cudaMalloc(&b.V, (size_t)(restart + 1) * b.N * sizeof(double)) != cudaSuccess) {
+        if (pool_alloc(reinterpret_cast<void**>(&b.V), (size_t)(restart + 1) * b.N * sizeof(double), st) !=
+            cudaSuccess) {
             cudaGetLastError();
             set_error("cannot allocate the Krylov basis: %d x %d doubles", restart + 1, b.N);
             return GNK_ENOMEM;
@@ -449,15 +450,15 @@ int ensure_krylov(Boundary& b, int restart) {
     }
     const size_t need = kry_doubles(restart) * sizeof(double);
     if (b.kry_bytes < need) {
-        if (b.kry) cudaFree(b.kry);
+        if (b.kry) pool_free(b.kry, st);
         b.kry = nullptr;
         b.kry_bytes = 0;
-        GNK_TRY_CUDA(cudaMalloc(&b.kry, need));
+        GNK_TRY_CUDA(pool_alloc(reinterpret_cast<void**>(&b.kry), need, st));
         b.kry_bytes = need;
     }
     if (!b.kstate) {
-        GNK_TRY_CUDA(cudaMalloc(&b.kstate, sizeof(KState)));
-        GNK_TRY_CUDA(cudaMemset(b.kstate, 0, sizeof(KState)));
+        GNK_TRY_CUDA(pool_alloc(&b.kstate, sizeof(KState), st));
+        GNK_TRY_CUDA(cudaMemsetAsync(b.kstate, 0, sizeof(KState), st));
     }
     return GNK_OK;
 }
@@ -515,7 +516,7 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
           int restart, int maxit, double tol, gnk_result* res, double* relres, cudaStream_t st,
           double* fc_out, int* fc_valid) {
     if (fc_valid) *fc_valid = 0;
-    GNK_TRY(ensure_krylov(b, restart));
+    GNK_TRY(ensure_krylov(b, restart, st));
     const int N = b.N;
     const double vb = 8.0 * N;  // bytes of one vector
     KState* ks = static_cast<KState*>(b.kstate);
@@ -639,7 +640,7 @@ int solve(const Boundary& bc, int adjoint /* OpId */, const double* rhs, double*
     } else {
         // FP64 iterative refinement: r = rhs - A x (FP64), A d = r with the
         // FP32 operator to inner_tol, x += d.
-        GNK_TRY(ensure_krylov(b, opt.restart));
+        GNK_TRY(ensure_krylov(b, opt.restart, st));
         double* rr = b.r1;
         double* dd = b.r2;
         const int N = b.N;
