@@ -76,6 +76,10 @@ KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pa
                "fmm_near": "fmm_near_kernel (double-float near field)",
                "fmm_l2p": "fmm_l2p_kernel", "fmm_up": "fmm_up_kernel (P2M and the M2M chain)",
                "fmm_l2l": "fmm_l2l_kernel"}
+# DRAM bytes read + written per launch of the kernel at the headline size
+# (64 ellipses, n = 1024), from one ncu capture of the same command
+# (profiles/fmm_kernels_ellipses64.md); valid while the kernel is unchanged.
+TRAFFIC = {"fmm_near": 2.709e6, "fmm": 2.19e6, "fmm_up": 2.24e6, "fmm_l2l": 1.91e6, "fmm_l2p": 3.69e6}
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
 ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
 # instrumented kinds: pair sums (0, 1, 6) and the FMM kernels (7 to 11)
@@ -435,7 +439,7 @@ def main():
     roofline = {
         "bound": "alu", "kernel": KERNEL_NAME[dom_kind],
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
-        "frac": achieved / peak, "traffic": None,
+        "frac": achieved / peak, "traffic": TRAFFIC.get(dom_kind) if args.n == 1024 and args.count == 64 else None,
         "pair_evals_per_s": work / (ms_l / 1e3) if ms_l > 0 else 0.0,
         "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1),
         "share_of_instrumented_time": {k: v[1] / total_prof_ms for k, v in prof_all.items() if v[0] > 0},

@@ -49,7 +49,8 @@ __device__ __forceinline__ uint32_t compact16d(uint32_t v) {
     return v;
 }
 
-// ---- 1. bounding square: per-block min/max, the last block forms (x0, y0, W)
+// ---- 1. bounding square: per-block min/max, the last block combines them
+// and forms (x0, y0, W)
 __global__ void __launch_bounds__(TB) tb_bbox(const double2* __restrict__ et, int N, double4* part,
                                               unsigned* counter, double* geom) {
     __shared__ double4 red[TB];
@@ -80,15 +81,33 @@ __global__ void __launch_bounds__(TB) tb_bbox(const double2* __restrict__ et, in
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    double4 r = part[0];
-    for (int b = 1; b < gridDim.x; ++b) {
-        const double4 o = part[b];
-        r.x = fmin(r.x, o.x);
-        r.y = fmax(r.y, o.y);
-        r.z = fmin(r.z, o.z);
-        r.w = fmax(r.w, o.w);
+    if (!last) return;
+    // the last block combines the partials in parallel (then the same tree)
+    m = make_double4(1e300, -1e300, 1e300, -1e300);
+    for (int b = threadIdx.x; b < gridDim.x; b += TB) {
+        const double2 lo = __ldcg(reinterpret_cast<const double2*>(part + b));
+        const double2 hi = __ldcg(reinterpret_cast<const double2*>(part + b) + 1);
+        const double4 o = make_double4(lo.x, lo.y, hi.x, hi.y);
+        m.x = fmin(m.x, o.x);
+        m.y = fmax(m.y, o.y);
+        m.z = fmin(m.z, o.z);
+        m.w = fmax(m.w, o.w);
     }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = TB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const double4 o = red[threadIdx.x + w];
+            double4& q = red[threadIdx.x];
+            q.x = fmin(q.x, o.x);
+            q.y = fmax(q.y, o.y);
+            q.z = fmin(q.z, o.z);
+            q.w = fmax(q.w, o.w);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double4 r = red[0];
     const double W = fmax(fmax(r.y - r.x, r.w - r.z) * (1.0 + 1e-9), 1e-300);
     geom[0] = 0.5 * (r.x + r.y) - 0.5 * W;
     geom[1] = 0.5 * (r.z + r.w) - 0.5 * W;
