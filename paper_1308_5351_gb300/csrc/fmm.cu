@@ -404,49 +404,60 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a) {
     }
 }
 
-// L2P (FP64) and the near field of one chunk of up to 32 targets of a leaf per
-// warp; writes z in node order.  The near field forms d = eta_i - eta_j in FP64
-// (exact for close nodes, whose differences carry the largest terms), splits it
-// into a float pair (2^-48 of |d|), and continues in double-float on the FP32
-// pipe (the FP64 pipe is 1/64 of it): |d|^2 with Dekker products, one Newton
-// step on the reciprocal, compensated accumulation.
 constexpr int kFmmWarps = kFmmNT / 32;
 constexpr int kFmmMaxNbr = 9;  // a leaf and its eight neighbours
-
-// d = p - q as a double-float from the exact three-float splits of two FP64
-// coordinates: the TwoSums keep every rounding error, so close nodes (whose
-// FP64 difference is exact) get d to about 2^-47 of |d| itself.
-__device__ __forceinline__ df diff3(float p1, float p2, float p3, float q1, float q2, float q3) {
-    float s1, e1, s2, e2, h, l;
-    two_sum(p1, -q1, s1, e1);
-    two_sum(p2, -q2, s2, e2);
-    const float s3 = __fsub_rn(p3, q3);
-    two_sum(s1, s2, h, l);
-    l = __fadd_rn(l, __fadd_rn(__fadd_rn(e1, e2), s3));
-    df r;
-    fast_two_sum(h, l, r.h, r.l);
-    return r;
-}
 
 // Near field: one block per chunk of up to 32 targets of a leaf (lane = target).
 // The sources of the (at most nine) neighbour leaves, taken as one list in
 // neighbour order, are split into kFmmWarps equal ranges, one per warp, which
 // the warp sums in tiles of 32; the warps' partial sums are added in warp
-// order and stored in sorted node order (zn).  The
-// near field runs in double-float on the FP32 pipe (GB300's FP64 pipe is 1/64
-// of it): d from the exact three-float node coordinates, |d|^2 with Dekker
-// products, one Newton step on the reciprocal, compensated accumulation.
+// order and stored in sorted node order (zn).  The near field runs in
+// double-float on the FP32 pipe (GB300's FP64 pipe is 1/64 of it), two
+// sources at a time in the two halves of packed float2 instructions (one
+// issue for both): d from the exact three-float node coordinates, |d|^2 with
+// Dekker products, one Newton step on the reciprocal, compensated
+// accumulation into an even-source and an odd-source sum, added at the end.
 // EF: also the sums of w_j / (eta_i - eta_j)^2 (to zf), for the gradient.
+
+// d = p - q for two sources (one per half) from exact three-float splits: the
+// TwoSums keep every rounding error, so close nodes get d to about 2^-47 |d|.
+__device__ __forceinline__ df2 diff3_2(float2 p1, float2 p2, float2 p3, float2 q1, float2 q2, float2 q3) {
+    float2 s1, e1, s2, e2, h, l;
+    two_diff2(p1, q1, s1, e1);
+    two_diff2(p2, q2, s2, e2);
+    const float2 s3 = sub2(p3, q3);
+    two_sum2(s1, s2, h, l);
+    l = add2(l, add2(add2(e1, e2), s3));
+    df2 r;
+    r.h = add2(h, l);
+    r.l = sub2(l, sub2(r.h, h));
+    return r;
+}
+
+__device__ __forceinline__ df2 df2_neg(df2 a) { return df2{neg2(a.h), neg2(a.l)}; }
+
+// a + b (renormalised), two lanes
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+    float2 s, e;
+    two_sum2(a.h, b.h, s, e);
+    e = add2(e, add2(a.l, b.l));
+    df2 r;
+    r.h = add2(s, e);
+    r.l = sub2(e, sub2(r.h, s));
+    return r;
+}
+
 template <int R, bool EF>
 __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     constexpr int RS = EF ? 2 * R : R;
-    __shared__ float4 s_p[kFmmWarps][32];   // (x1, x2, x3, y1)
-    __shared__ float2 s_q[kFmmWarps][32];   // (y2, y3)
-    __shared__ float4 s_w[kFmmWarps][R][32];   // (wx.h, wx.l, wy.h, wy.l)
+    // one tile of 32 sources per warp, component by component, so that a
+    // float2 read at pair p gives sources 2p and 2p + 1
+    __shared__ float s_c[kFmmWarps][6][32];        // x1, x2, x3, y1, y2, y3
+    __shared__ float s_w[kFmmWarps][R][4][32];     // wx.h, wx.l, wy.h, wy.l
+    __shared__ int s_j[kFmmWarps][32];             // sorted index of each source (-1: padding)
     __shared__ double2 s_z[kFmmWarps][RS][32];
-    __shared__ int s_j[kFmmWarps][32];        // sorted index of each source of the tile
-    __shared__ int s_cum[kFmmMaxNbr + 1];     // prefix sums of the neighbour leaves' sizes
-    __shared__ int s_beg[kFmmMaxNbr];         // first source of each neighbour leaf
+    __shared__ int s_cum[kFmmMaxNbr + 1];          // prefix sums of the neighbour leaves' sizes
+    __shared__ int s_beg[kFmmMaxNbr];              // first source of each neighbour leaf
     if (a.done != nullptr && *a.done) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = a.items[blockIdx.x];  // (leaf, first target)
@@ -456,9 +467,10 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     const bool act = i < t1;
     const float4 pa = a.p3[act ? i : it.y];
     const float2 pb = a.p3b[act ? i : it.y];
-    df are[RS], aim[RS];
+    const float2 tx1 = f2(pa.x), tx2 = f2(pa.y), tx3 = f2(pa.z), ty1 = f2(pa.w), ty2 = f2(pb.x), ty3 = f2(pb.y);
+    df2 are[RS], aim[RS];
 #pragma unroll
-    for (int r = 0; r < RS; ++r) are[r] = aim[r] = df{0.f, 0.f};
+    for (int r = 0; r < RS; ++r) are[r] = aim[r] = df2{f2(0.f), f2(0.f)};
     const int n0 = a.nl_start[leaf], nn = min(a.nl_start[leaf + 1] - n0, kFmmMaxNbr);
     if (threadIdx.x == 0) {
         int c = 0;
@@ -474,72 +486,96 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     const int total = s_cum[nn];
     const int q0 = (int)((long long)total * wid / kFmmWarps), q1 = (int)((long long)total * (wid + 1) / kFmmWarps);
     for (int qs = q0; qs < q1; qs += 32) {
+        __syncwarp();
+        const int cnt = min(32, q1 - qs);
         {
-            __syncwarp();
-            const int q = qs + lane;
-            if (q < q1) {
-                int e = 0;
-                while (e + 1 < nn && s_cum[e + 1] <= q) ++e;
-                const int j = s_beg[e] + (q - s_cum[e]);
-                s_j[wid][lane] = j;
-                s_p[wid][lane] = a.p3[j];
-                s_q[wid][lane] = a.p3b[j];
+            const int q = qs + min(lane, cnt - 1);  // lanes past the end copy the last source, weight 0
+            int e = 0;
+            while (e + 1 < nn && s_cum[e + 1] <= q) ++e;
+            const int j = s_beg[e] + (q - s_cum[e]);
+            const bool pad = lane >= cnt;
+            const float4 c4 = a.p3[j];
+            const float2 c2 = a.p3b[j];
+            s_c[wid][0][lane] = c4.x;
+            s_c[wid][1][lane] = c4.y;
+            s_c[wid][2][lane] = c4.z;
+            s_c[wid][3][lane] = c4.w;
+            s_c[wid][4][lane] = c2.x;
+            s_c[wid][5][lane] = c2.y;
+            s_j[wid][lane] = pad ? -1 : j;
 #pragma unroll
-                for (int r = 0; r < R; ++r) s_w[wid][r][lane] = a.ws[(size_t)r * a.N + j];
+            for (int r = 0; r < R; ++r) {
+                const float4 w4 = pad ? make_float4(0.f, 0.f, 0.f, 0.f) : a.ws[(size_t)r * a.N + j];
+                s_w[wid][r][0][lane] = w4.x;
+                s_w[wid][r][1][lane] = w4.y;
+                s_w[wid][r][2][lane] = w4.z;
+                s_w[wid][r][3][lane] = w4.w;
             }
-            __syncwarp();
-            const int cnt = min(32, q1 - qs);
-            for (int k = 0; k < cnt; ++k) {
-                const float4 qa = s_p[wid][k];
-                const float2 qb = s_q[wid][k];
-                const df dx = diff3(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z);
-                const df dy = diff3(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y);
-                const float px = __fmul_rn(dx.h, dx.h);
-                float ex = fmaf(dx.h, dx.h, -px);
-                ex = fmaf(dx.h, __fadd_rn(dx.l, dx.l), ex);
-                const float py = __fmul_rn(dy.h, dy.h);
-                float ey = fmaf(dy.h, dy.h, -py);
-                ey = fmaf(dy.h, __fadd_rn(dy.l, dy.l), ey);
-                float rh, re;
-                two_sum(px, py, rh, re);
-                const float rl = __fadd_rn(__fadd_rn(ex, ey), re);
-                float y = recip_f32(rh);
-                y = (s_j[wid][k] == i) ? 0.f : y;  // the i = j term is excluded (Eq. fmm-E)
-                float ee = fmaf(-rh, y, 1.0f);
-                ee = fmaf(-rl, y, ee);
-                const df inv{y, __fmul_rn(y, ee)};
-                const df ar = df_mul(dx, inv), ai = df_mul(dy, inv);  // 1/d = ar - i ai
+        }
+        __syncwarp();
+        const int npair = (cnt + 1) >> 1;
+        for (int pp = 0; pp < npair; ++pp) {
+            const float2 qx1 = reinterpret_cast<const float2*>(s_c[wid][0])[pp];
+            const float2 qx2 = reinterpret_cast<const float2*>(s_c[wid][1])[pp];
+            const float2 qx3 = reinterpret_cast<const float2*>(s_c[wid][2])[pp];
+            const float2 qy1 = reinterpret_cast<const float2*>(s_c[wid][3])[pp];
+            const float2 qy2 = reinterpret_cast<const float2*>(s_c[wid][4])[pp];
+            const float2 qy3 = reinterpret_cast<const float2*>(s_c[wid][5])[pp];
+            const int2 jj = reinterpret_cast<const int2*>(s_j[wid])[pp];
+            const df2 dx = diff3_2(tx1, tx2, tx3, qx1, qx2, qx3);
+            const df2 dy = diff3_2(ty1, ty2, ty3, qy1, qy2, qy3);
+            const float2 px = mul2(dx.h, dx.h);
+            float2 ex = fma2(dx.h, dx.h, neg2(px));
+            ex = fma2(dx.h, add2(dx.l, dx.l), ex);
+            const float2 py = mul2(dy.h, dy.h);
+            float2 ey = fma2(dy.h, dy.h, neg2(py));
+            ey = fma2(dy.h, add2(dy.l, dy.l), ey);
+            float2 rh, re;
+            two_sum2(px, py, rh, re);
+            const float2 rl = add2(add2(ex, ey), re);
+            float2 y = make_float2(recip_f32(rh.x), recip_f32(rh.y));
+            // the i = j term is excluded (Eq. fmm-E); padding slots (j < 0) add nothing
+            y.x = (jj.x == i || jj.x < 0) ? 0.f : y.x;
+            y.y = (jj.y == i || jj.y < 0) ? 0.f : y.y;
+            float2 ee = fma2(neg2(rh), y, f2(1.0f));
+            ee = fma2(neg2(rl), y, ee);
+            const df2 inv{y, mul2(y, ee)};
+            const df2 ar = df2_mul(dx, inv), ai = df2_mul(dy, inv);  // 1/d = ar - i ai
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const df2 wx{reinterpret_cast<const float2*>(s_w[wid][r][0])[pp],
+                             reinterpret_cast<const float2*>(s_w[wid][r][1])[pp]};
+                const df2 wy{reinterpret_cast<const float2*>(s_w[wid][r][2])[pp],
+                             reinterpret_cast<const float2*>(s_w[wid][r][3])[pp]};
+                df2_acc(are[r], df2_mul(wx, ar));
+                df2_acc(are[r], df2_mul(wy, ai));
+                df2_acc(aim[r], df2_mul(wy, ar));
+                df2_dec(aim[r], df2_mul(wx, ai));
+            }
+            if (EF) {  // 1/d^2 = (ar - i ai)^2 = gr - i gi
+                const df2 a2 = df2_mul(ar, ar), b2 = df2_mul(ai, ai), ab = df2_mul(ar, ai);
+                const df2 gr = df2_add(a2, df2_neg(b2));
+                const df2 gi{add2(ab.h, ab.h), add2(ab.l, ab.l)};
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float4 w4 = s_w[wid][r][k];
-                    const df wx{w4.x, w4.y}, wy{w4.z, w4.w};
-                    df_acc(are[r], df_mul(wx, ar));
-                    df_acc(are[r], df_mul(wy, ai));
-                    df_acc(aim[r], df_mul(wy, ar));
-                    const df qq = df_mul(wx, ai);
-                    df_acc(aim[r], df{-qq.h, -qq.l});
-                }
-                if (EF) {  // 1/d^2 = (ar - i ai)^2 = gr - i gi
-                    const df a2 = df_mul(ar, ar), b2 = df_mul(ai, ai), ab = df_mul(ar, ai);
-                    const df gr = df_add(a2, df{-b2.h, -b2.l}), gi = df{ab.h + ab.h, ab.l + ab.l};
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float4 w4 = s_w[wid][r][k];
-                        const df wx{w4.x, w4.y}, wy{w4.z, w4.w};
-                        df_acc(are[R + r], df_mul(wx, gr));
-                        df_acc(are[R + r], df_mul(wy, gi));
-                        df_acc(aim[R + r], df_mul(wy, gr));
-                        const df qq = df_mul(wx, gi);
-                        df_acc(aim[R + r], df{-qq.h, -qq.l});
-                    }
+                    const df2 wx{reinterpret_cast<const float2*>(s_w[wid][r][0])[pp],
+                                 reinterpret_cast<const float2*>(s_w[wid][r][1])[pp]};
+                    const df2 wy{reinterpret_cast<const float2*>(s_w[wid][r][2])[pp],
+                                 reinterpret_cast<const float2*>(s_w[wid][r][3])[pp]};
+                    df2_acc(are[R + r], df2_mul(wx, gr));
+                    df2_acc(are[R + r], df2_mul(wy, gi));
+                    df2_acc(aim[R + r], df2_mul(wy, gr));
+                    df2_dec(aim[R + r], df2_mul(wx, gi));
                 }
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < RS; ++r)
-        s_z[wid][r][lane] = make_double2((double)are[r].h + (double)are[r].l,
-                                         (double)aim[r].h + (double)aim[r].l);
+    for (int r = 0; r < RS; ++r) {  // even + odd sums, then to FP64
+        const df sr = df_add(df{are[r].h.x, are[r].l.x}, df{are[r].h.y, are[r].l.y});
+        const df si = df_add(df{aim[r].h.x, aim[r].l.x}, df{aim[r].h.y, aim[r].l.y});
+        s_z[wid][r][lane] = make_double2((double)sr.h + (double)sr.l, (double)si.h + (double)si.l);
+    }
     __syncthreads();
     if (wid == 0 && act) {
 #pragma unroll

@@ -40,8 +40,12 @@ struct KState {
     int nonfinite;    // a NaN/Inf was met
     int restart;
     unsigned counter; // last-block ticket
-    unsigned bar_count, bar_gen;  // grid barrier of the Arnoldi step: arrivals, generation
     int bar_err;      // a grid barrier wait gave up
+    // grid barrier of the Arnoldi step: arrivals and generation on cache lines
+    // of their own, away from the fields above and from each other
+    alignas(128) unsigned bar_count;
+    alignas(128) unsigned bar_gen;
+    char pad_[124];
 };
 
 constexpr int KT = 256;       // threads per block of the vector kernels
