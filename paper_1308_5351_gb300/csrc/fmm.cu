@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "epilogue.cuh"
 #include "gnk_internal.h"
 #include "pairmath.cuh"
 
@@ -595,11 +596,13 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
 
 // L2P by Horner's rule in double-float plus the near-field sum; one thread per
 // node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
-// same coefficients); writes z in node order
+// same coefficients).  EPI: the operator epilogue of the product is applied at
+// once (epilogue_apply: e.g. f_B(x) = 2x + diag(B1) x + (2/n) Im(A z)), so the
+// sums z never go to memory; otherwise z is written in node order.
 // EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
 // plus the near-field sums of w/d^2, written to outF.
-template <int R, bool EF>
-__global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
+template <int R, bool EF, bool EPI>
+__global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a, ReduceArgs e) {
     if (a.done != nullptr && *a.done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
@@ -609,6 +612,7 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
     const double2 p = a.ps[i];
     const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
     const int node = a.perm[i];
+    double zx[kMaxRHS] = {0.0, 0.0}, zy[kMaxRHS] = {0.0, 0.0};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
@@ -621,14 +625,16 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a) {
             u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
         }
         const double2 zn = a.zn[(size_t)r * a.N + i];
-        a.out[(size_t)r * a.N + node] = make_double2(((double)u.re.h + (double)u.re.l) + zn.x,
-                                                     ((double)u.im.h + (double)u.im.l) + zn.y);
+        zx[r] = ((double)u.re.h + (double)u.re.l) + zn.x;
+        zy[r] = ((double)u.im.h + (double)u.im.l) + zn.y;
+        if (!EPI) a.out[(size_t)r * a.N + node] = make_double2(zx[r], zy[r]);
         if (EF) {
             const double2 zf = a.zf[(size_t)r * a.N + i];
             a.outF[(size_t)r * a.N + node] = make_double2(-ir * ((double)du.re.h + (double)du.re.l) + zf.x,
                                                           -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
         }
     }
+    if (EPI) epilogue_apply(e, node, make_double2(zx[0], zy[0]), make_double2(zx[1], zy[1]));
 }
 
 // ---------------------------------------------------------------- host: tables
@@ -1137,7 +1143,8 @@ double fmm_near_instr(const Boundary& b, int R) {
 // One FMM product on the argument block `a` (weights, outputs set by the caller):
 // gather, the far-field chain on the high-priority stream, the near field on
 // `st`, and L2P after they join.  EF: also the sums of w/d^2 (to a.outF).
-static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream_t st, int* nlaunch) {
+static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const ReduceArgs* epi, cudaStream_t st,
+                       int* nlaunch) {
     const FmmTree* t = b.fmm;
     fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
@@ -1189,14 +1196,19 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, cudaStream
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
     const ProfToken tokp = prof_begin(st, PK_FMML2P);
     const int nb = (b.N + 255) / 256;
+    const ReduceArgs e = epi ? *epi : ReduceArgs{};
     if (R == 2 && EF)
-        fmm_l2p_kernel<2, true><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<2, true, false><<<nb, 256, 0, st>>>(a, e);
+    else if (R == 2 && epi)
+        fmm_l2p_kernel<2, false, true><<<nb, 256, 0, st>>>(a, e);
     else if (R == 2)
-        fmm_l2p_kernel<2, false><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<2, false, false><<<nb, 256, 0, st>>>(a, e);
     else if (EF)
-        fmm_l2p_kernel<1, true><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<1, true, false><<<nb, 256, 0, st>>>(a, e);
+    else if (epi)
+        fmm_l2p_kernel<1, false, true><<<nb, 256, 0, st>>>(a, e);
     else
-        fmm_l2p_kernel<1, false><<<nb, 256, 0, st>>>(a);
+        fmm_l2p_kernel<1, false, false><<<nb, 256, 0, st>>>(a, e);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tokp, PK_FMML2P, 0.0, st, fmm_instr(b, R, EF ? 4 : 3));
@@ -1252,12 +1264,12 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.x0 = job.x[0];
     a.x1 = job.x[1];
     a.s = job.s;
-    a.out = static_cast<double2*>(b.partial);
+    a.out = nullptr;
     a.done = job.done;
     int launches = 0;
-    GNK_TRY(fmm_product(b, a, job.R, false, st, &launches));
-    GNK_TRY_CUDA(launch_reduce_public(b, job, 1, 0, st));
-    count_launches(launches + 1);
+    const ReduceArgs e = reduce_args(b, job, 1, 0);  // the epilogue runs inside L2P
+    GNK_TRY(fmm_product(b, a, job.R, false, &e, st, &launches));
+    count_launches(launches);
     return GNK_OK;
 }
 
@@ -1278,7 +1290,7 @@ int run_fmm_ef(const Boundary& b, const double2* w0, const double2* w1, double2*
     a.out = E;
     a.outF = F;
     int launches = 0;
-    GNK_TRY(fmm_product(b, a, R, true, st, &launches));
+    GNK_TRY(fmm_product(b, a, R, true, nullptr, st, &launches));
     count_launches(launches);
     return GNK_OK;
 }
