@@ -79,7 +79,7 @@ KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pa
 # DRAM bytes read + written per launch of the kernel at the headline size
 # (64 ellipses, n = 1024), from one ncu capture of the same command
 # (profiles/fmm_kernels_ellipses64.md); valid while the kernel is unchanged.
-TRAFFIC = {"fmm_near": 2.709e6, "fmm": 2.19e6, "fmm_up": 2.24e6, "fmm_l2l": 1.91e6, "fmm_l2p": 3.69e6}
+TRAFFIC = {"fmm_near": 2.73e6, "fmm": 2.19e6, "fmm_up": 2.24e6, "fmm_l2l": 1.91e6, "fmm_l2p": 5.81e6}
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
 ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
 # instrumented kinds: pair sums (0, 1, 6) and the FMM kernels (7 to 11)
