@@ -110,7 +110,7 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
 }
 
 // ---- complex double-float arithmetic for the far field (FP32 pipe).  The
-// expansions and translation tables are stored as float4 (re.h, re.l, im.h,
+// expansions and the M2L scalings are stored as float4 (re.h, re.l, im.h,
 // im.l); sums keep their rounding errors in the low words (about 2^-46 relative
 // per operation), far below the truncation error of the order-32 expansions.
 struct cdf {
@@ -1048,7 +1048,7 @@ int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st)
         float4* d = nullptr;
         if (cudaMalloc(&d, c.size() * sizeof(float4)) != cudaSuccess) {
             cudaGetLastError();
-            set_error("FMM: device allocation of the translation tables failed");
+            set_error("FMM: device allocation of the M2L tables failed");
             return GNK_ENOMEM;
         }
         cudaError_t e = cudaMemcpyAsync(d, c.data(), c.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
@@ -1056,7 +1056,7 @@ int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st)
         if (e != cudaSuccess) {
             cudaGetLastError();
             cudaFree(d);
-            set_error("FMM: upload of the translation tables failed");
+            set_error("FMM: upload of the M2L tables failed");
             return GNK_ECUDA;
         }
         per_device[dev] = d;
