@@ -192,10 +192,15 @@ __device__ __forceinline__ void grid_barrier(KState* s) {
 }
 
 // dots of w with v_0 .. v_{nv-1} over [i0, i1), block sums to out[0 .. nv);
-// with_norm: also w . w to out[nv]
+// with_norm: also w . w to out[nv].  The block sums take the fewest FP64
+// additions (GB300's FP64 pipe has 2 lanes per SM, so shuffle trees, which
+// add on all 32 lanes at every step, cost 5x more): every thread's partials
+// go to shared memory (buf, KD x KT doubles), kn x 8 threads each add 32 of
+// them (a stride-8 slice), then one thread per dot adds the 8 slices, all in
+// a fixed order.
 __device__ __forceinline__ void range_dots(const double* __restrict__ V, int N, int nv, const double* w,
-                                           int i0, int i1, double* out, double (*red)[KD], bool with_norm) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                                           int i0, int i1, double* out, double (*red)[KD], double* buf,
+                                           bool with_norm) {
     const int nt = nv + (with_norm ? 1 : 0);
     for (int k0 = 0; k0 < nt; k0 += KD) {
         const int kn = min(KD, nt - k0);
@@ -209,15 +214,20 @@ __device__ __forceinline__ void range_dots(const double* __restrict__ V, int N, 
                 if (q < kn) acc[q] = fma((k0 + q < nv) ? V[(size_t)(k0 + q) * N + i] : wi, wi, acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < KD; ++q) {
-            double v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[wid][q] = v;
+        for (int q = 0; q < KD; ++q)
+            if (q < kn) buf[q * KT + threadIdx.x] = acc[q];
+        __syncthreads();
+        if (threadIdx.x < kn * 8) {
+            const int q = threadIdx.x >> 3, part = threadIdx.x & 7;
+            double t = 0.0;
+#pragma unroll 8
+            for (int e = 0; e < KT / 8; ++e) t += buf[q * KT + e * 8 + part];
+            red[part][q] = t;
         }
         __syncthreads();
         if (threadIdx.x < kn) {
             double t = 0.0;
-            for (int ww = 0; ww < KT / 32; ++ww) t += red[ww][threadIdx.x];
+            for (int part = 0; part < 8; ++part) t += red[part][threadIdx.x];
             out[k0 + threadIdx.x] = t;
         }
         __syncthreads();
@@ -299,9 +309,15 @@ __device__ void givens_step(int j, double hn, double* h1, const double* h2, doub
 __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, int N, int j, double* __restrict__ w,
                                                 KPtrs p, KState* s) {
     if (s->done) return;  // set before this launch: the same in every block
-    __shared__ double red[KT / 32][KD];
+    __shared__ double red[8][KD];
     __shared__ double red8[KT / 32][32];
-    __shared__ double h1[1025], h2[1025], scs[1024], ssn[1024];
+    __shared__ double h1[1025];
+    // h2, the Givens staging and, before they are used, the dots' reduction buffer
+    __shared__ double s_pool[1025 + 2 * 1024];
+    static_assert(KD * KT <= 1025 + 2 * 1024, "reduction buffer");
+    double* h2 = s_pool;
+    double* scs = s_pool + 1025;
+    double* ssn = s_pool + 2049;
     __shared__ double s_hn;
     const int nv = j + 1, nb = gridDim.x;
     const int per = (N + nb - 1) / nb;
@@ -309,7 +325,7 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     double* part1 = p.part;
     double* part2 = p.part + (size_t)KB_MAX * p.ld;
     // first pass: h1 = V^T w
-    range_dots(V, N, nv, w, i0, i1, part1 + (size_t)blockIdx.x * p.ld, red, false);
+    range_dots(V, N, nv, w, i0, i1, part1 + (size_t)blockIdx.x * p.ld, red, s_pool, false);
     grid_barrier(s);
     reduce_coeffs(part1, p.ld, nv, nb, h1, red8);
     // w' = w - V h1 on the block's range, then the second pass h2 = V^T w' with ||w'||^2
@@ -319,7 +335,7 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
         w[i] = acc;
     }
     __syncthreads();
-    range_dots(V, N, nv, w, i0, i1, part2 + (size_t)blockIdx.x * p.ld, red, true);
+    range_dots(V, N, nv, w, i0, i1, part2 + (size_t)blockIdx.x * p.ld, red, s_pool, true);
     grid_barrier(s);
     reduce_coeffs(part2, p.ld, nv + 1, nb, h2, red8);
     // ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 for an orthonormal basis; when more
