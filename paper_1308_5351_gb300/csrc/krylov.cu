@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r
 }
 
 // dot products per pass over w in the Arnoldi step
-constexpr int KD = 12;
+constexpr int KD = 16;
 
 // ---- one Arnoldi step in one cooperative launch.  After the product
 // w = A v_j: the two CGS passes (multi-dot, update), ||w||, the Givens update
@@ -261,17 +261,21 @@ __device__ __forceinline__ void reduce_coeffs(const double* part, int ld, int nv
 }
 
 // Givens update of column j by block 0: the column h = h1 + h2 (in h1),
-// h_{j+1,j} = hn and the previous rotations are staged in shared memory, one
-// thread applies the rotations, and the column is stored in parallel.  Also
+// h_{j+1,j} = hn and the previous rotations (staged in shared memory by
+// givens_stage while the grid waits at its second barrier), one thread
+// applies the rotations, and the column is stored in parallel.  Also
 // the residual estimate and the end-of-cycle test (the triangular solve for y
 // is k_solve_y's, once per cycle).
-__device__ void givens_step(int j, double hn, double* h1, const double* h2, double* scs, double* ssn, KPtrs p,
-                            KState* s) {
-    const int nv = j + 1;
+__device__ __forceinline__ void givens_stage(int j, double* scs, double* ssn, KPtrs p) {
     for (int k = threadIdx.x; k < j; k += KT) {
         scs[k] = p.cs[k];
         ssn[k] = p.sn[k];
     }
+}
+
+__device__ void givens_step(int j, double hn, double* h1, const double* h2, const double* scs, const double* ssn,
+                            KPtrs p, KState* s) {
+    const int nv = j + 1;
     for (int k = threadIdx.x; k < nv; k += KT) h1[k] = h1[k] + h2[k];
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -313,8 +317,7 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     __shared__ double red8[KT / 32][32];
     __shared__ double h1[1025];
     // h2, the Givens staging and, before they are used, the dots' reduction buffer
-    __shared__ double s_pool[1025 + 2 * 1024];
-    static_assert(KD * KT <= 1025 + 2 * 1024, "reduction buffer");
+    __shared__ double s_pool[KD * KT > 1025 + 2 * 1024 ? KD * KT : 1025 + 2 * 1024];
     double* h2 = s_pool;
     double* scs = s_pool + 1025;
     double* ssn = s_pool + 2049;
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     }
     __syncthreads();
     range_dots(V, N, nv, w, i0, i1, part2 + (size_t)blockIdx.x * p.ld, red, s_pool, true);
+    if (blockIdx.x == 0) givens_stage(j, scs, ssn, p);  // the reduction buffer is free again
     grid_barrier(s);
     reduce_coeffs(part2, p.ld, nv + 1, nb, h2, red8);
     // ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 for an orthonormal basis; when more
