@@ -185,3 +185,22 @@ def test_profile_mask_records_only_selected_kinds(G):
     assert every[G.PROF_FMM][0] == only[G.PROF_FMM][0]
     assert every[G.PROF_FMMNEAR][0] >= 1 and every[G.PROF_FMML2P][0] >= 1
     assert every[G.PROF_FMMUP][0] >= 1 and every[G.PROF_FMML2L][0] >= 1
+
+
+@pytest.mark.parametrize("count,radius,n", [(64, 1e-4, 1024), (16, 1e-5, 1024)])
+def test_fmm_deep_tree_clustered_circles(G, count, radius, n):
+    """Tiny circles on a coarse grid: the leaf level goes below 11 (14 and 16 here),
+    past the device tree builder's lookup grids, so the host builder makes the tree.
+    Sampled rows against the oracle's direct sums."""
+    side = int(round(count ** 0.5))
+    curves = [Dm.Circle(complex(0.1 * i, 0.1 * j), radius, ccw=False) for i in range(side) for j in range(side)]
+    d = Dm.build_domain(curves, n, bounded=False)
+    rng = np.random.default_rng(17)
+    w = rng.normal(size=d.N) + 1j * rng.normal(size=d.N)
+    rows = np.sort(rng.choice(d.N, 256, replace=False))
+    ref = O.cauchy_rows(d.et, w, rows)
+    S = _S(d, w, rows)
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
+        z = _host(b.cauchy_sum(_dev(w), precision=G.GNK_PREC_FMM))
+    err = np.abs(z[rows] - ref)
+    assert np.all(err <= 1e-12 * S + (64 + d.N) * U64 * S), (err / S).max()
