@@ -64,7 +64,11 @@ extern "C" {
                               the paper's zfmm2dpart route), FP64, expansion
                               order 32: error below ~1e-12 of
                               sum_j |w_j / (eta_i - eta_j)|, O(N) work.  The
-                              quadtree is built on the first such call.        */
+                              quadtree is built on the first such call (on the
+                              device; on the host when it is deeper than 11
+                              levels) and kept with the handle, whose FMM
+                              workspace also serialises its products: one
+                              handle is not used on two streams at once.     */
 #define GNK_PREC_MIXED_FMM 6 /* as GNK_PREC_MIXED, with the refinement residual,
                               right-hand side and h by the FMM               */
 
@@ -190,14 +194,15 @@ int gnk_boundary_size(const gnk_boundary* b, int* m1, int* n);
 /* ---------------------------------------------------------------------------
  * Cauchy sum (Sec. 2.5, Eqs. fmm-1, fmm-E, E-fmm): z = E w,
  *   z_i = sum_{j != i} w_j / (eta_i - eta_j),   i = 1..N,
- * w and z complex (2N doubles).  precision: GNK_PREC_FP64, _FP32 or _DF32.
+ * w and z complex (2N doubles).  precision: GNK_PREC_FP64, _FP32, _DF32 or
+ * _FMM.
  * ------------------------------------------------------------------------- */
 int gnk_cauchy_sum(const gnk_boundary* b, const double* w, double* z,
                    int precision, void* stream);
 
 /* y = (2I + diag(B1) - B) x, the discrete I - N (Eqs. sys, (I-B)x, f_B):
  *   y = 2x - (2/n) Im(A Eone) x + (2/n) Im(A E(q x)).
- * x, y real (N doubles).  precision: GNK_PREC_FP64, _FP32 or _DF32. */
+ * x, y real (N doubles).  precision: GNK_PREC_FP64, _FP32, _DF32 or _FMM. */
 int gnk_apply_IminusN(const gnk_boundary* b, const double* x, double* y,
                       int precision, void* stream);
 
