@@ -36,7 +36,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "time-to-solution at 1e-10 rel. residual and matvec pair-evals/s vs plain FP64 GPU"
-WORKLOAD = "64 ellipses, unbounded, n=1024 (65,536 unknowns): FBIE solve + h"
+def workload(count, n):
+    """The workload name of the ellipse domains (64 ellipses, n = 1024 by default)."""
+    return f"{count} ellipses, unbounded, n={n} ({count * n:,} unknowns): FBIE solve + h"
 TOL = 1e-10
 L2_FLUSH_BYTES = 256 << 20
 SMS, SM_MAX_MHZ = 152, 2070.0
@@ -458,7 +460,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
+        "config": {"workload": workload(dom.m1, dom.n), "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
                    "restart": 20, "precision": args.precision,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -737,7 +739,7 @@ def run_reference(args, dist, rank, ws):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": args.n * args.count, "tol": "direct LU"},
+        "config": {"workload": workload(args.count, args.n), "N": args.n * args.count, "tol": "direct LU"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
