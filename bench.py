@@ -237,6 +237,26 @@ def oracle_sample(dom_full, count_sub=8):
     return est, t_all, sample
 
 
+def oracle_pair_rate(dom, seconds=0.5):
+    """The oracle's direct Cauchy sum (cauchy_rows, as it stands: numpy, one
+    row at a time) on the full domain, for as many rows as take about
+    `seconds`: pair evaluations per second on the host."""
+    import numpy as np
+    from oracle import gnk_dense as O
+    w = np.random.default_rng(0).normal(size=dom.N) + 0j
+    rows, t = 16, 0.0
+    while True:
+        t0 = time.perf_counter()
+        O.cauchy_rows(dom.et, w, np.arange(rows))
+        t = time.perf_counter() - t0
+        if t >= seconds or rows >= dom.N:
+            break
+        rows = min(dom.N, rows * 4)
+    rate = rows * (dom.N - 1) / t
+    return rate, (f"oracle cauchy_rows (numpy, one thread) for {rows} rows of N={dom.N}: "
+                  f"{t:.2f} s")
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -452,8 +472,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         est, t_sample, sample = oracle_sample(dom)
+        rate, pair_sample = oracle_pair_rate(dom)
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
-               "sample_seconds": t_sample}
+               "sample_seconds": t_sample, "pair_evals_per_s": rate, "pair_sample": pair_sample}
     line = {
         "metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
@@ -734,6 +755,7 @@ def run_reference(args, dist, rank, ws):
         vals.append(est)
     wall = time.perf_counter() - t0
     v = statistics.median(vals)
+    rate, pair_sample = oracle_pair_rate(dom, seconds=0.2)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
@@ -741,7 +763,7 @@ def run_reference(args, dist, rank, ws):
         "data": "synthetic",
         "config": {"workload": workload(args.count, args.n), "N": args.n * args.count, "tol": "direct LU"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "pair_evals_per_s": rate, "pair_sample": pair_sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
