@@ -149,19 +149,49 @@ def block_L(n, m1):
     return np.kron(np.eye(m1), circulant_L(n))
 
 
+def _IminusN_from_B(B):
+    """2I + diag(B 1) - B formed in the storage of B (entries as written:
+    -B_ij off the diagonal, 2 + sum_j B_ij on it, since B_ii = 0)."""
+    s = B.sum(axis=1)
+    K = np.negative(B, out=B)
+    idx = np.arange(K.shape[0])
+    K[idx, idx] += 2.0 + s
+    return K
+
+
+def _M_from_D(D, n, m1):
+    """D - diag(D 1) + L-hat formed in the storage of D: L is added on each
+    diagonal block (L-hat is block diagonal), then D 1 is taken off the
+    diagonal (D_ii = L_pp = 0)."""
+    s = D.sum(axis=1)
+    L = circulant_L(n)
+    for k in range(m1):
+        blk = slice(k * n, (k + 1) * n)
+        D[blk, blk] += L
+    idx = np.arange(D.shape[0])
+    D[idx, idx] -= s
+    return D
+
+
 def matrix_IminusN(et, etp, A, n):
     """2I + diag(B 1) - B: the discretisation of I - N with singularity
     subtraction (Eqs. ie-sys2, sys)."""
     B, _ = matrices_BD(et, etp, A, n)
-    N = B.shape[0]
-    return 2.0 * np.eye(N) + np.diag(B.sum(axis=1)) - B
+    return _IminusN_from_B(B)
 
 
 def matrix_M(et, etp, A, n):
     """D - diag(D 1) + L-hat: the discretisation of M (Eq. y, using L-hat 1 = 0)."""
     N, m1 = _sizes(et, n)
     _, D = matrices_BD(et, etp, A, n)
-    return D - np.diag(D.sum(axis=1)) + block_L(n, m1)
+    return _M_from_D(D, n, m1)
+
+
+def matrices_K_M(et, etp, A, n):
+    """(2I + diag(B1) - B, D - diag(D1) + L-hat) from one assembly of B and D."""
+    N, m1 = _sizes(et, n)
+    B, D = matrices_BD(et, etp, A, n)
+    return _IminusN_from_B(B), _M_from_D(D, n, m1)
 
 
 def rhs_y(et, etp, A, n, gam):
@@ -171,9 +201,9 @@ def rhs_y(et, etp, A, n, gam):
 
 def solve_ie(et, etp, A, n, gam):
     """mu solving (2I + diag(B1) - B) mu = -y (Eq. sys), by LU."""
-    Mm = matrix_M(et, etp, A, n)
+    K, Mm = matrices_K_M(et, etp, A, n)
     y = Mm @ np.asarray(gam, dtype=np.float64)
-    return np.linalg.solve(matrix_IminusN(et, etp, A, n), -y)
+    return np.linalg.solve(K, -y)
 
 
 def compute_h(et, etp, A, n, mu, gam):
@@ -181,15 +211,22 @@ def compute_h(et, etp, A, n, mu, gam):
 
     Returns (h at the nodes, h_k = mean of h over component k)."""
     N, m1 = _sizes(et, n)
-    h = (matrix_M(et, etp, A, n) @ mu - matrix_IminusN(et, etp, A, n) @ gam) / 2.0
+    K, Mm = matrices_K_M(et, etp, A, n)
+    h = (Mm @ mu - K @ gam) / 2.0
     return h, h.reshape(m1, n).mean(axis=1)
 
 
 def fbie(et, etp, A, n, gam):
-    """The pair (mu, h, h_k) of Sec. 3 computed densely."""
-    mu = solve_ie(et, etp, A, n, gam)
-    h, hk = compute_h(et, etp, A, n, mu, gam)
-    return mu, h, hk
+    """The triple (mu, h, h_k) of Sec. 3 computed densely, with one assembly
+    of the two matrices and one LU.  gam is one right-hand side (N) or
+    several as the columns of an N x R array; mu and h then have the same
+    shape and h_k is m1 x R."""
+    N, m1 = _sizes(et, n)
+    K, Mm = matrices_K_M(et, etp, A, n)
+    gam = np.asarray(gam, dtype=np.float64)
+    mu = np.linalg.solve(K, -(Mm @ gam))
+    h = (Mm @ mu - K @ gam) / 2.0
+    return mu, h, h.reshape((m1, n) + h.shape[1:]).mean(axis=1)
 
 
 # ---------------------------------------------------------------------------
@@ -239,12 +276,20 @@ def adjoint_e(et, etp, etpp, A, Ap, n, c):
 
 
 def matrix_adjoint(et, etp, etpp, A, Ap, n, c):
-    """diag(e) + B^T + P-hat (Eq. sys*), P-hat = diag(P,...,P), P = (1/n) 1 1^T."""
+    """diag(e) + B^T + P-hat (Eq. sys*), P-hat = diag(P,...,P), P = (1/n) 1 1^T,
+    formed in one N x N array: B^T, then 1/n on each diagonal block (P-hat
+    is block diagonal), then e on the diagonal (B_ii = 0)."""
     N, m1 = _sizes(et, n)
     B, _ = matrices_BD(et, etp, A, n)
     e = adjoint_e(et, etp, etpp, A, Ap, n, c)
-    P = np.kron(np.eye(m1), np.full((n, n), 1.0 / n))
-    return np.diag(e) + B.T + P
+    Ad = np.ascontiguousarray(B.T)
+    del B
+    for k in range(m1):
+        blk = slice(k * n, (k + 1) * n)
+        Ad[blk, blk] += 1.0 / n
+    idx = np.arange(N)
+    Ad[idx, idx] += e
+    return Ad
 
 
 def solve_adjoint_ie(et, etp, etpp, A, Ap, n, c, gam):

@@ -319,7 +319,8 @@ def test_planted_mistakes_are_caught(monkeypatch):
     orig_block = O.nystrom_block
     orig_L = O.circulant_L
     orig_M = O.matrix_M
-    orig_IN = O.matrix_IminusN
+    orig_MD = O._M_from_D
+    orig_KB = O._IminusN_from_B
     assert _pins_pass()
 
     def transposed(et, etp, A, n, rows, cols):
@@ -332,16 +333,21 @@ def test_planted_mistakes_are_caught(monkeypatch):
     def flipped_L(n):
         return -orig_L(n)
 
-    def no_diag_D1(et, etp, A, n):
-        N, m1 = O._sizes(et, n)
-        _, D = O.matrices_BD(et, etp, A, n)
-        return D + O.block_L(n, m1)
+    def no_diag_D1(D, n, m1):
+        s = D.sum(axis=1)
+        out = orig_MD(D, n, m1)
+        idx = np.arange(out.shape[0])
+        out[idx, idx] += s
+        return out
 
-    def identity_not_two(et, etp, A, n):
-        return orig_IN(et, etp, A, n) - np.eye(len(et))
+    def identity_not_two(B):
+        K = orig_KB(B)
+        idx = np.arange(K.shape[0])
+        K[idx, idx] -= 1.0
+        return K
 
     mutants = [("nystrom_block", transposed), ("circulant_L", flipped_L),
-               ("matrix_M", no_diag_D1), ("matrix_IminusN", identity_not_two)]
+               ("_M_from_D", no_diag_D1), ("_IminusN_from_B", identity_not_two)]
     for name, fn in mutants:
         monkeypatch.setattr(O, name, fn)
         assert not _pins_pass(), name
