@@ -1,14 +1,13 @@
 // gnk_cauchy_sum_noalloc: the FP64 Cauchy sum z = E w for callers that must
 // not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured (an allocation there breaks or invalidates the
-// capture), plugins living inside a host framework that owns the device
-// memory pool and forbids allocations of its own, and real-time loops where
-// an allocation's implicit synchronisation or failure is not acceptable.
-// They pass in device buffers for the inputs and the output and get the same
-// sum as gnk_cauchy_sum, with the split-source partial sums kept in a
-// fixed-size array that is part of the library's device image.
+// Some callers cannot call cudaMalloc at all: plugins living inside a host
+// application that owns the device memory and forbids allocations of its
+// own, and real-time loops where an allocation's implicit device
+// synchronisation, or its possible failure, is not acceptable.  They pass in
+// device buffers for the inputs and the output and get the same sum as
+// gnk_cauchy_sum, with the split-source partial sums kept in a fixed-size
+// array that is part of the library's device image.
 //
 // The array below is reserved on every GPU that loads the library and stays
 // there until the process exits.  Its size caps the problem: at most
@@ -19,6 +18,7 @@
 #include <mutex>
 
 #include "gnk_internal.h"
+#include "pairmath.cuh"
 
 namespace gnk {
 namespace {
@@ -35,13 +35,6 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocChunks * kNoA
 
 std::mutex g_na_mu;
 double2* g_na_ptr[kMaxDevices] = {};
-
-__device__ __forceinline__ double na_recip(double x) {
-    double y0;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
-    const double e = fma(-x, y0, 1.0);
-    return fma(y0, fma(e, e, e), y0);  // y0 (1 + e + e^2)
-}
 
 __global__ void __launch_bounds__(kNAThreads) noalloc_pair_kernel(const double2* __restrict__ et,
                                                                   const double2* __restrict__ w,
@@ -78,7 +71,7 @@ __global__ void __launch_bounds__(kNAThreads) noalloc_pair_kernel(const double2*
 #pragma unroll
             for (int t = 0; t < kNATargets; ++t) {
                 const double dx = px[t] - sp.x, dy = py[t] - sp.y;
-                double inv = na_recip(fma(dx, dx, dy * dy));
+                double inv = recip_f64(fma(dx, dx, dy * dy));
                 inv = (j == idx[t]) ? 0.0 : inv;  // no i = j term
                 const double ar = dx * inv, ai = dy * inv;
                 ax[t] = fma(wk.x, ar, fma(wk.y, ai, ax[t]));
@@ -104,13 +97,17 @@ __global__ void noalloc_reduce_kernel(const double2* __restrict__ part, int N, i
     z[i] = make_double2(sx, sy);
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device (kernels launched here dereference
+// it), or managed memory; anything else (host memory, another GPU's memory)
+// is refused.
+bool on_current_device(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -153,8 +150,11 @@ extern "C" int gnk_cauchy_sum_noalloc(int N, const double* et, const double* w, 
         set_error("gnk_cauchy_sum_noalloc: NULL array");
         return GNK_EINVAL;
     }
-    if (!on_device(et) || !on_device(w) || !on_device(z)) {
-        set_error("gnk_cauchy_sum_noalloc: et, w and z must be device memory (nothing is staged)");
+    int dev = 0;
+    GNK_TRY_CUDA(cudaGetDevice(&dev));
+    if (!on_current_device(et, dev) || !on_current_device(w, dev) || !on_current_device(z, dev)) {
+        set_error("gnk_cauchy_sum_noalloc: et, w and z must be device memory of the current device %d "
+                  "(nothing is staged or copied)", dev);
         return GNK_EINVAL;
     }
     double2* part = nullptr;

@@ -68,3 +68,33 @@ def test_binding_refuses_missing_library(tmp_path):
             gnk.load(str(tmp_path / "missing.so"))
     finally:
         gnk._lib = old
+
+
+def test_noalloc_binding_rejects_bad_operands_before_any_call(monkeypatch):
+    """The binding of gnk_cauchy_sum_noalloc refuses arrays that hold fewer
+    than N complex values, wrong dtypes and non-CUDA memory before it touches
+    the library (which cannot see the arrays' lengths)."""
+    torch = pytest.importorskip("torch")
+    from paper_1308_5351_gb300 import gnk
+
+    def no_library(*a, **k):
+        raise AssertionError("the library must not be called")
+    monkeypatch.setattr(gnk, "load", no_library)
+    N = 16
+    full = torch.zeros(N, dtype=torch.complex128)
+    cases = [
+        (torch.zeros(N - 1, dtype=torch.complex128), "fewer than N"),
+        (torch.zeros(2 * N - 2, dtype=torch.float64), "fewer than N"),  # float64 pairs: 15 values
+        (torch.zeros(N, dtype=torch.complex64), "dtype"),
+        (full, "not on the current CUDA device" if torch.cuda.is_available() else "current CUDA device"),
+    ]
+    for bad, msg in cases:
+        for pos in range(3):
+            args = [full, full, full]
+            args[pos] = bad
+            with pytest.raises(gnk.GnkError) as e:
+                gnk.gnk_cauchy_sum_noalloc(N, *args)
+            assert e.value.code == gnk.GNK_EINVAL and msg in str(e.value), (pos, str(e.value))
+    with pytest.raises(gnk.GnkError) as e:
+        gnk.gnk_cauchy_sum_noalloc(N, full.numpy(), full, full)
+    assert "must be a CUDA tensor" in str(e.value)

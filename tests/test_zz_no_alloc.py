@@ -1,8 +1,16 @@
 """gnk_cauchy_sum_noalloc: the Cauchy sum for callers that cannot allocate
-device memory (graph capture, host frameworks that own the memory pool,
-latency-critical loops).  Its output must match gnk_cauchy_sum's on two calls
-in a row, within the tolerance the parity tests use for FP64 Cauchy sums:
+device memory (plugins inside a host application that owns all device
+memory, real-time loops that cannot accept an allocation's implicit
+synchronisation or its possible failure).  It keeps its partial sums in a
+fixed array of the library's device image, shared by every call.
+
+On two calls in a row (the second reads a scratch array that still holds the
+first call's contents) its output must match
+  * the oracle's dense Cauchy matrix times w, element by element, and
+  * gnk_cauchy_sum, the entry point that allocates,
+within the bound the parity tests use for FP64 Cauchy sums:
 |z - z_ref|_i <= (64 + N) u S_i, S_i = sum_j |w_j / (eta_i - eta_j)|.
+The device's free memory must not change across the second call.
 This file is collected last so that a failure here comes after every other
 test has run."""
 import numpy as np
@@ -10,6 +18,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import gnk_dense as O
 from paper_1308_5351_gb300 import domains as Dm
 
 pytestmark = pytest.mark.gpu
@@ -33,29 +42,43 @@ def _case(seed, count, n):
 
 
 @pytest.mark.parametrize("seed,count,n", [(1, 5, 512), (2, 3, 170), (3, 1, 8)])
-def test_noalloc_matches_cauchy_sum_twice(G, seed, count, n):
+def test_noalloc_matches_oracle_and_cauchy_sum_twice(G, seed, count, n):
     d, w = _case(seed, count, n)
-    et = torch.as_tensor(d.et, device="cuda")
-    wd = torch.as_tensor(w, device="cuda")
-    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
-        z_ref = b.cauchy_sum(wd).cpu().numpy()
+    z_oracle = O.cauchy_matrix(d.et) @ w
     S = np.array([np.sum(np.abs(w) / np.where(np.arange(d.N) == i, np.inf,
                                                 np.abs(d.et[i] - d.et))) for i in range(d.N)])
     tol = (64 + d.N) * U64 * S
-    for _ in range(2):  # the shared scratch keeps the previous call's contents
-        z = torch.full_like(wd, complex("nan"))
-        G.gnk_cauchy_sum_noalloc(d.N, et, wd, z)
-        torch.cuda.synchronize()
+    et = torch.as_tensor(d.et, device="cuda")
+    wd = torch.as_tensor(w, device="cuda")
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:
+        z_lib = b.cauchy_sum(wd).cpu().numpy()
+    assert np.all(np.abs(z_lib - z_oracle) <= tol)
+    outs = [torch.full_like(wd, complex("nan")) for _ in range(2)]
+    torch.cuda.synchronize()
+    G.gnk_cauchy_sum_noalloc(d.N, et, wd, outs[0])
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    G.gnk_cauchy_sum_noalloc(d.N, et, wd, outs[1])  # scratch still holds call 1's sums
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    for z in outs:
         got = z.cpu().numpy()
-        assert np.all(np.abs(got - z_ref) <= tol)
+        assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - z_oracle) <= tol)
+        assert np.all(np.abs(got - z_lib) <= tol)
 
 
-def test_noalloc_rejects_oversize_and_host_arrays(G):
+def test_noalloc_rejects_oversize_short_and_host_arrays(G):
     big = 65537
     et = torch.zeros(big, dtype=torch.complex128, device="cuda")
     with pytest.raises(G.GnkError) as e:
         G.gnk_cauchy_sum_noalloc(big, et, et, et)
     assert e.value.code == G.GNK_EINVAL and "65536" in str(e.value)
+    short = torch.zeros(15, dtype=torch.complex128, device="cuda")
+    with pytest.raises(G.GnkError) as e:
+        G.gnk_cauchy_sum_noalloc(16, et, short, et)
+    assert e.value.code == G.GNK_EINVAL and "fewer than N" in str(e.value)
     h = np.zeros(16, dtype=np.complex128)
     with pytest.raises(G.GnkError) as e:
         G.gnk_cauchy_sum_noalloc(16, h, h, h)
