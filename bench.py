@@ -79,11 +79,35 @@ KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pa
                "fmm_l2p": "fmm_l2p_kernel", "fmm_up": "fmm_up_kernel (P2M and the M2M chain)",
                "fmm_l2l": "fmm_l2l_kernel"}
 # DRAM bytes read + written per launch of the kernel at the headline size
-# (64 ellipses, n = 1024), from one ncu capture of the same command
-# (profiles/fmm_kernels_ellipses64.md); valid while the kernel is unchanged.
-TRAFFIC = {"fmm_near": 2.73e6, "fmm": 2.19e6, "fmm_up": 2.24e6, "fmm_l2l": 1.91e6, "fmm_l2p": 5.81e6}
-PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm")   # each stands for whole Cauchy sums
-ROOF_KINDS = PAIR_KINDS + ("fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
+# (64 ellipses, n = 1024), from one ncu capture of the same command, with the
+# SHA-256 prefix of the kernel's source file at the time of the capture: a
+# figure whose source has changed since is reported as null (stale).
+TRAFFIC = {"fmm_near": (2.73e6, "csrc/fmm.cu", None), "fmm": (2.19e6, "csrc/fmm.cu", None),
+           "fmm_up": (2.24e6, "csrc/fmm.cu", None), "fmm_l2l": (1.91e6, "csrc/fmm.cu", None),
+           "fmm_l2p": (5.81e6, "csrc/fmm.cu", None)}
+# kinds whose work is pair evaluations actually performed
+PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm_near")
+ROOF_KINDS = ("pair64", "pair32", "pairdf", "fmm", "fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
+
+
+def source_sha(rel):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1308_5351_gb300", rel)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_of(kind, args):
+    """(bytes per launch or None, note) for the roofline's traffic field."""
+    if kind not in TRAFFIC:
+        return None, "no ncu capture of this kernel"
+    if args.n != 1024 or args.count != 64:
+        return None, "captured at the headline size only"
+    val, rel, sha = TRAFFIC[kind]
+    now = source_sha(rel)
+    if sha is None or sha != now:
+        return None, f"stale: {rel} changed since the ncu capture (now {now})"
+    return val, f"ncu capture of {rel} at {sha}"
 # instrumented kinds: pair sums (0, 1, 6) and the FMM kernels (7 to 11)
 PROFILE_MASK = (1 << 0) | (1 << 1) | (1 << 6) | (1 << 7) | (1 << 8) | (1 << 9) | (1 << 10) | (1 << 11)
 MODES = {"mixed_df": 4, "mixed": 1, "fp64": 0, "df32": 3, "fmm": 5, "mixed_fmm": 6}
@@ -210,51 +234,69 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(dom_full, count_sub=8):
-    """Time the oracle (as it stands) on the sub-domain made of the first
-    `count_sub` boundaries at the same n, and extrapolate to the full domain:
-    assembly and products scale as N^2, the LU as N^3."""
+ORACLE_SUB = 8          # boundaries of the oracle's timed sub-domain (N = 8 n)
+
+
+def oracle_sample(dom_full, count_sub=ORACLE_SUB):
+    """Time the oracle, as it stands, on the sub-domain made of the first
+    `count_sub` boundaries at the same n: the dense assembly of its two
+    matrices, the LU solve of its own system, and h; then extrapolate to the
+    full domain (assembly and h scale as N^2, the LU as N^3).  Returns
+    (extrapolated seconds, measured dict, sample description)."""
     import numpy as np
     from oracle import gnk_dense as O
     from paper_1308_5351_gb300 import domains as Dm
     sub = Dm.build_domain(dom_full.curves[:count_sub], dom_full.n, bounded=dom_full.bounded)
     gam = Dm.gamma_log(sub, dom_full.holes[0])
     t0 = time.perf_counter()
-    O.fbie(sub.et, sub.etp, sub.A, sub.n, gam)
-    t_all = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    Mx = rng.normal(size=(sub.N, sub.N)) + 4 * sub.N ** 0.5 * np.eye(sub.N)
-    bx = rng.normal(size=sub.N)
-    t0 = time.perf_counter()
-    np.linalg.solve(Mx, bx)
-    t_lu = time.perf_counter() - t0
-    t_asm = max(t_all - t_lu, 0.0)
+    K, M = O.matrices_K_M(sub.et, sub.etp, sub.A, sub.n)
+    t1 = time.perf_counter()
+    mu = np.linalg.solve(K, -(M @ gam))
+    t2 = time.perf_counter()
+    h = (M @ mu - K @ gam) / 2.0
+    h.reshape(sub.m1, sub.n).mean(axis=1)
+    t3 = time.perf_counter()
+    t_asm, t_lu, t_h = t1 - t0, t2 - t1, t3 - t2
     r = dom_full.N / sub.N
-    est = t_asm * r ** 2 + t_lu * r ** 3
-    sample = (f"oracle fbie (dense assembly + LU + h) on the first {count_sub} of "
-              f"{dom_full.m1} boundaries (N={sub.N}): {t_all:.2f} s, of which LU {t_lu:.2f} s; "
-              f"extrapolated to N={dom_full.N} as assembly*(N/Ns)^2 + LU*(N/Ns)^3")
-    return est, t_all, sample
+    est = (t_asm + t_h) * r ** 2 + t_lu * r ** 3
+    measured = {"N": sub.N, "boundaries": count_sub, "assembly_s": t_asm, "lu_solve_s": t_lu, "h_s": t_h,
+                "total_s": t3 - t0}
+    sample = (f"oracle (dense K and M assembly, LU solve of its own system, h) on the first {count_sub} of "
+              f"{dom_full.m1} boundaries (N={sub.N}), measured {t3 - t0:.2f} s; full-size figure "
+              f"extrapolated to N={dom_full.N} as (assembly + h)*(N/Ns)^2 + LU*(N/Ns)^3")
+    return est, measured, sample
 
 
-def oracle_pair_rate(dom, seconds=0.5):
-    """The oracle's direct Cauchy sum (cauchy_rows, as it stands: numpy, one
-    row at a time) on the full domain, for as many rows as take about
-    `seconds`: pair evaluations per second on the host."""
+def oracle_pair_rate(dom):
+    """One full direct FP64 Cauchy sum of the oracle's C routine (all host
+    cores, OpenMP) on the whole domain: pair evaluations per second."""
     import numpy as np
-    from oracle import gnk_dense as O
+    from oracle import cauchy_cpu as C
     w = np.random.default_rng(0).normal(size=dom.N) + 0j
-    rows, t = 16, 0.0
-    while True:
-        t0 = time.perf_counter()
-        O.cauchy_rows(dom.et, w, np.arange(rows))
-        t = time.perf_counter() - t0
-        if t >= seconds or rows >= dom.N:
-            break
-        rows = min(dom.N, rows * 4)
-    rate = rows * (dom.N - 1) / t
-    return rate, (f"oracle cauchy_rows (numpy, one thread) for {rows} rows of N={dom.N}: "
-                  f"{t:.2f} s")
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    C.cauchy_sum(dom.et, w, threads=threads)
+    t = time.perf_counter() - t0
+    rate = dom.N * (dom.N - 1) / t
+    return rate, threads, (f"oracle C Cauchy sum (FP64, OpenMP, {threads} threads), one full product "
+                           f"at N={dom.N}: {t:.2f} s")
+
+
+def cpu_baseline_line(dom):
+    """The cpu_baseline object: the oracle timed on the host cores."""
+    est, measured, sample = oracle_sample(dom)
+    rate, threads, pair_sample = oracle_pair_rate(dom)
+    return {"value": est, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample,
+            "value_is": "extrapolated to the full workload from the measured sample",
+            "extrapolated_full_s": est, "measured": measured,
+            "pair_evals_per_s": rate, "pair_sample": pair_sample}
+
+
+def bench_config(args, N, m1, n, ws):
+    """The config dict of both arms (the same workload)."""
+    return {"workload": workload(m1, n), "N": N, "m1": m1, "n": n, "tol": TOL, "restart": 20,
+            "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 
 
 # ------------------------------------------------------------------ main
@@ -446,6 +488,28 @@ def main():
     h2d = 3 * 16 * dom.N + 8 * dom.N
     d2h = 8 * dom.N + 8 * dom.N + 8 * dom.m1
 
+    # ---- FMM products alone: (2I + diag(B1) - B) x by the FMM, back to back
+    fmm_rate = None
+    if args.precision in FMM_MODES:
+        hnd = G.gnk_build_boundary_ex(dom.m1, dom.n, et, etp, A, None, None, dom.bounded, G.GNK_PREC_FMM,
+                                      stream)
+        xv, yv = torch.ones_like(gam), torch.empty_like(gam)
+        for _ in range(3):
+            G.gnk_apply_IminusN(hnd, xv, yv, G.GNK_PREC_FMM, stream)
+        reps = 50
+        G.gnk_profile_enable(True)
+        G.gnk_profile_mask(1 << G.PROF_FMMNEAR)
+        (_, t_f) = _timed(lambda: [G.gnk_apply_IminusN(hnd, xv, yv, G.GNK_PREC_FMM, stream)
+                                   for _ in range(reps)], stream)
+        nf = G.gnk_profile_query_ex(G.PROF_FMMNEAR)
+        G.gnk_profile_enable(False)
+        G.gnk_free_boundary(hnd)
+        fmm_rate = {"products_per_s": reps / t_f, "ms_per_product": 1e3 * t_f / reps,
+                    "near_pairs_per_product": nf[2] / max(nf[0], 1),
+                    "near_pairs_per_s": nf[2] / t_f,
+                    "what": "(2I + diag(B1) - B) x with E(q x) by the FMM, 50 products back to back "
+                            "(one FMM product = one Cauchy sum over all N nodes)"}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -457,11 +521,11 @@ def main():
     achieved = instr / (ms_l / 1e3) if ms_l > 0 else 0.0
     peak = PEAK_INSTR[dom_kind]
     total_prof_ms = sum(v[1] for v in prof_all.values())
-    pair_evals = sum(prof_all[k][2] for k in PAIR_KINDS)
     roofline = {
         "bound": "alu", "kernel": KERNEL_NAME[dom_kind],
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
-        "frac": achieved / peak, "traffic": TRAFFIC.get(dom_kind) if args.n == 1024 and args.count == 64 else None,
+        "frac": achieved / peak, "traffic": traffic_of(dom_kind, args)[0],
+        "traffic_source": traffic_of(dom_kind, args)[1],
         "pair_evals_per_s": work / (ms_l / 1e3) if ms_l > 0 else 0.0,
         "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1),
         "share_of_instrumented_time": {k: v[1] / total_prof_ms for k, v in prof_all.items() if v[0] > 0},
@@ -471,22 +535,19 @@ def main():
     }
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        est, t_sample, sample = oracle_sample(dom)
-        rate, pair_sample = oracle_pair_rate(dom)
-        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
-               "sample_seconds": t_sample, "pair_evals_per_s": rate, "pair_sample": pair_sample}
+        cpu = cpu_baseline_line(dom)
     line = {
         "metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload(dom.m1, dom.n), "N": dom.N, "m1": dom.m1, "n": dom.n, "tol": TOL,
-                   "restart": 20, "precision": args.precision,
-                   "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "pair_evals_per_s": pair_evals / (total_prof_ms / 1e3) if total_prof_ms else None,
+        "config": bench_config(args, dom.N, dom.m1, dom.n, ws),
+        "pair_evals_per_s": roofline["pair_evals_per_s"] if dom_kind in PAIR_KINDS else None,
+        "pair_evals_per_s_note": "pairs actually evaluated by the dominant kernel per second of its live "
+                                 "launch time (the FMM's far field is counted in products, not pairs)",
         "pair_evals_per_s_by_kernel": {KERNEL_NAME[k]: v for k, v in kernel_rates.items()},
+        "fmm_product": fmm_rate,
         "solve": {"precision": args.precision, "iterations": res.iterations,
                   "refinements": res.refinements, "matvecs_fp64_class": res.matvecs_fp64,
                   "matvecs_fp32": res.matvecs_fp32, "relres": res.relres,
@@ -693,9 +754,8 @@ def run_extra(args, dist, rank, ws, local):
                 et = torch.cat(ets + poly_et)
                 etp = torch.cat(etps + poly_etp)
                 gam = torch.log(torch.abs(et - centres[0]))
-                mu, h = AG.fbie(et, etp, torch.ones_like(et), gam, m1, n, bounded=False,
-                                precision=MODES[args.precision], tol=1e-12, restart=30)
-                hk = AG.component_means(h, m1, n)
+                mu, h, hk = AG.fbie(et, etp, torch.ones_like(et), gam, m1, n, bounded=False,
+                                    precision=MODES[args.precision], tol=1e-12, restart=30)
                 return hk[1] - hk[0]
             for _ in range(args.warmup):  # untimed: first-call costs of the process and handles
                 J(params).backward()
@@ -739,7 +799,8 @@ def run_extra(args, dist, rank, ws, local):
 
 def run_reference(args, dist, rank, ws):
     """The oracle, as it stands, on the host cores: each step is the bounded
-    sample of the same workload, extrapolated to the full domain."""
+    sample of the same workload (its first 8 boundaries), timed as measured and
+    extrapolated to the full domain."""
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -747,23 +808,28 @@ def run_reference(args, dist, rank, ws):
     from paper_1308_5351_gb300 import domains as Dm
     dom = Dm.ellipses64(seed=2, n=args.n, count=args.count)
     for _ in range(args.warmup):
-        oracle_sample(dom, count_sub=2)
-    vals, sample = [], ""
+        oracle_sample(dom)
+    vals, meas, sample = [], [], ""
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        est, _, sample = oracle_sample(dom, count_sub=4)
+        est, m, sample = oracle_sample(dom)
         vals.append(est)
+        meas.append(m)
     wall = time.perf_counter() - t0
     v = statistics.median(vals)
-    rate, pair_sample = oracle_pair_rate(dom, seconds=0.2)
+    rate, threads, pair_sample = oracle_pair_rate(dom)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload(args.count, args.n), "N": args.n * args.count, "tol": "direct LU"},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": sample, "pair_evals_per_s": rate, "pair_sample": pair_sample},
+        "config": bench_config(args, dom.N, dom.m1, dom.n, ws),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "value_is": "median over the steps of the full-workload figure extrapolated from "
+                                     "each step's measured sample",
+                         "extrapolated_full_s": v,
+                         "measured": {k: statistics.median(m[k] for m in meas) for k in meas[0]},
+                         "pair_evals_per_s": rate, "pair_sample": pair_sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -14,7 +14,9 @@
  *   (diag(e) + B^T + Phat) mu = gamma.
  * Every product with B, D, B^T and e reduces to the Cauchy sum
  *   (E w)_i = sum_{j != i} w_j / (eta_i - eta_j)              (Eq. fmm-E)
- * which this library evaluates as a direct all-pairs sum on the GPU.
+ * which this library evaluates on the GPU either as a direct all-pairs sum
+ * (FP64, FP32 or double-float) or by the fast multipole method (Sec. 2.5,
+ * the paper's own route), chosen per call by a GNK_PREC_* precision.
  *
  * Conventions for every function below:
  *   - Return value: GNK_OK (0) or a negative GNK_E* code; gnk_last_error()
@@ -86,6 +88,19 @@ typedef struct gnk_options {
                           _MIXED_FMM                                           */
     int max_refine;    /* MIXED: maximum refinement steps                      */
     double inner_tol;  /* MIXED: relative tolerance of each inner solve        */
+    int tile_chunks;   /* tile override of the direct pair-sum kernels (FP64,
+                          FP32, double-float): each target tile's sum over the
+                          N sources is split into this many chunks of whole
+                          source tiles, 1..64 (at most one per tile); 0 = the
+                          handle's plan, chosen at build from the SM count.
+                          The FMM ignores it.                                */
+    int tile_variant;  /* tile override of the batched pair kernels: 1..7
+                          selects the (targets per thread, right-hand sides
+                          per group) shape in the order of gnk_batch_tuning;
+                          0 = the tuned (or default) shape                  */
+    int timing;        /* nonzero: gnk_result receives the phase times
+                          (CUDA events on `stream`; the call then waits for
+                          its last event)                                     */
 } gnk_options;
 
 typedef struct gnk_result {
@@ -96,10 +111,20 @@ typedef struct gnk_result {
     int matvecs_fp64;  /* products with the FP64-class (FP64 or DF32) operator */
     int matvecs_fp32;  /* products with the FP32 operator                      */
     double relres;     /* final true relative residual, evaluated in FP64      */
+    /* Device time of each phase in ms, with gnk_options.timing set (else 0):
+     * setup = deferred precompute (Eone, diagonals) and, for the FMM
+     * precisions, the quadtree; rhs = the right-hand side -y (gnk_fbie: with
+     * f_B(gamma) from the same sum); solve = GMRES with any refinement;
+     * h = h and h_k (gnk_fbie only).  gnk_batch_fbie reports the whole call
+     * as solve. */
+    double setup_ms;
+    double rhs_ms;
+    double solve_ms;
+    double h_ms;
 } gnk_result;
 
 /* Fills `opt` with restart 20, maxit 50, tol 1e-12, FP64, max_refine 10,
- * inner_tol 1e-5. */
+ * inner_tol 1e-5, no tile overrides, timing off. */
 void gnk_default_options(gnk_options* opt);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated
@@ -121,9 +146,9 @@ unsigned long long gnk_kernel_launches(void);
  * for the recorded events).  Kinds: 0 FP64, 1 FP32 and 6 double-float
  * pair-sum kernels (work = pair evaluations R N (N-1)), 2 reduction/epilogue,
  * 3 circulant, 4 GMRES vector kernels (work = bytes moved), 5 other, and
- * the FMM kernels: 7 M2L (work = the R N (N-1) pairs the product stands
- * for), 8 near field (work = near-field pairs), 9 L2P, 10 the upward pass
- * (P2M and M2M), 11 L2L.  Launches that
+ * the FMM kernels: 7 M2L (work = the number of Cauchy sums R, one M2L
+ * launch per FMM product), 8 near field (work = near-field pairs evaluated),
+ * 9 L2P, 10 the upward pass (P2M and M2M), 11 L2L.  Launches that
  * a converged GMRES cycle turned into no-ops are not counted. */
 int gnk_profile_enable(int on);
 /* Restricts the recording to the kinds whose bit is set in mask (bit k for
@@ -274,20 +299,22 @@ int gnk_solve_ie_transpose(const gnk_boundary* b, const double* rhs, double* x,
                            const gnk_options* opt, gnk_result* info,
                            void* stream);
 
-/* Gradient of a loss L(mu, h) of the FBIE outputs with respect to the inputs.
- * Given mu (the solution for gam), gam, grad_mu = dL/dmu and grad_h = dL/dh
- * (N doubles each), writes dL/d eta, dL/d eta', dL/dA (interleaved complex,
- * 2N doubles each: real part = derivative with respect to the real part of
- * the input, imaginary part = derivative with respect to its imaginary part)
- * and dL/dgam (N doubles).  Method: one transposed solve
- * lambda = K^-T (grad_mu + M^T grad_h / 2) with K = 2I + diag(B1) - B and
- * M = D - diag(D1) + Lhat, then one FP64 pass of six Cauchy sums and six sums
- * of the derivative kernel 1/(eta_i - eta_j)^2.  `opt` controls the
- * transposed solve (its precision also sets the arithmetic of M^T).  Host
- * arrays are staged through temporary device buffers.  Returns GNK_OK or
- * GNK_ENOTCONV (gradient from the best iterate). */
+/* Gradient of a loss L(mu, h, h_k) of the FBIE outputs with respect to the
+ * inputs.  Given mu (the solution for gam), gam, grad_mu = dL/dmu and
+ * grad_h = dL/dh (N doubles each) and grad_hk = dL/dh_k (m1 doubles, one per
+ * component mean h_k; NULL when the loss does not use h_k), writes dL/d eta,
+ * dL/d eta', dL/dA (interleaved complex, 2N doubles each: real part =
+ * derivative with respect to the real part of the input, imaginary part =
+ * derivative with respect to its imaginary part) and dL/dgam (N doubles).
+ * Method: grad_h + grad_hk[k]/n on the nodes of component k (h_k is a mean),
+ * one transposed solve lambda = K^-T (grad_mu + M^T grad_h / 2) with
+ * K = 2I + diag(B1) - B and M = D - diag(D1) + Lhat, then one FP64 pass of six
+ * Cauchy sums and six sums of the derivative kernel 1/(eta_i - eta_j)^2.
+ * `opt` controls the transposed solve (its precision also sets the arithmetic
+ * of M^T).  Host arrays are staged through temporary device buffers.  Returns
+ * GNK_OK or GNK_ENOTCONV (gradient from the best iterate). */
 int gnk_fbie_backward(const gnk_boundary* b, const double* mu, const double* gam,
-                      const double* grad_mu, const double* grad_h,
+                      const double* grad_mu, const double* grad_h, const double* grad_hk,
                       double* grad_et, double* grad_etp, double* grad_A,
                       double* grad_gam, const gnk_options* opt,
                       gnk_result* info, void* stream);
@@ -405,12 +432,14 @@ int gnk_batch_fbie(const gnk_batch* b, const double* gam, double* mu,
 /* ---------------------------------------------------------------------------
  * Cauchy sum without any device allocation (no counterpart in the paper).
  *
- * z = E w exactly as gnk_cauchy_sum in FP64, for callers that cannot allocate
- * device memory: code running during CUDA graph capture, plugins whose host
- * framework owns all device memory, and latency-critical loops that cannot
- * afford an allocation.  No handle is needed: et (eta at the N nodes), w and
- * z are interleaved complex arrays of 2N doubles that must already be in
- * device memory (host pointers return GNK_EINVAL; nothing is staged).  The
+ * z = E w exactly as gnk_cauchy_sum computes it in FP64, for callers that
+ * cannot allocate device memory: plugins running inside a host application
+ * that owns all device memory and forbids allocations of its own, and
+ * real-time loops where an allocation's implicit device synchronisation, or
+ * its possible failure, is not acceptable.  No handle is needed: et (eta at
+ * the N nodes), w and z are interleaved complex arrays of 2N doubles that
+ * must already be in device memory of the current device (host pointers and
+ * memory of another GPU return GNK_EINVAL; nothing is staged or copied).  The
  * split-source partial sums go to a fixed 4 MiB array inside the library's
  * device image, which every GPU that loads the library keeps until the
  * process exits; it limits N to 1..65536 (larger N returns GNK_EINVAL before
@@ -420,9 +449,32 @@ int gnk_batch_fbie(const gnk_batch* b, const double* gam, double* mu,
  * can overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Each call overwrites every entry it reads, so no
  * clearing is needed between calls.  Never calls cudaMalloc or cudaFree.
+ * The library cannot check the arrays' lengths: each must hold at least N
+ * complex values.
  * ------------------------------------------------------------------------- */
 int gnk_cauchy_sum_noalloc(int N, const double* et, const double* w,
                            double* z, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics for tests (no counterpart in the paper).
+ *
+ * gnk_debug_recip_f64: y_lib[i] = the FP64 reciprocal that the pair-sum
+ *   kernels use for 1/|d|^2 (the hardware seed refined by the series
+ *   y0 (1 + e + e^2), e = 1 - x y0) and y_div[i] = 1.0 / x[i] by CUDA's IEEE
+ *   division, for n doubles x (device arrays, n >= 0; GNK_EINVAL for host
+ *   pointers).  Asynchronous on `stream`.
+ * gnk_debug_barrier_fault: test hook of the bounded grid-barrier waits inside
+ *   the cooperative Arnoldi step of every later GMRES solve (Sec. 3.5).  With
+ *   skip_block >= 0 that block passes each barrier without arriving, so the
+ *   other blocks' waits run out after spin_limit polls (0 = the default
+ *   limit, 2^20), they set an error flag and return, and the solve returns
+ *   GNK_ECUDA with the message "a grid barrier of the Arnoldi step timed
+ *   out"; no kernel faults and the device stays usable.  (-1, 0) restores
+ *   normal operation.  Process-wide; not for use while solves run on other
+ *   threads.  GNK_EINVAL for skip_block < -1 or spin_limit < 0.
+ * ------------------------------------------------------------------------- */
+int gnk_debug_recip_f64(int n, const double* x, double* y_lib, double* y_div, void* stream);
+int gnk_debug_barrier_fault(int skip_block, int spin_limit);
 
 #ifdef __cplusplus
 }

@@ -615,7 +615,8 @@ struct BatchImpl {
     long long* cbase = nullptr;
     int ncirc = 0;
     // work lists (per kernel variant: targets per thread T, group size RG)
-    int T32 = 2, RG32 = 8, Tdf = 1, RGdf = 4;
+    int T32 = 2, RG32 = 8, Tdf = 1, RGdf = 4;       // shapes of the current work lists
+    int T32t = 2, RG32t = 8, Tdft = 1, RGdft = 4;   // tuned (or default) shapes
     BItem* items32 = nullptr;
     int nitems32 = 0;
     BItem* itemsdf = nullptr;
@@ -732,6 +733,36 @@ int upload_items(const std::vector<BItem>& v, BItem** d, int* n, cudaStream_t st
     if (!v.empty())
         GNK_TRY_CUDA(cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(BItem), cudaMemcpyHostToDevice, st));
     *n = (int)v.size();
+    return GNK_OK;
+}
+
+// The tile shapes of one call: the tuned shapes, or the override of
+// gnk_options.tile_variant (1..4: the FP32 kernel, 5..7: the double-float
+// kernel, in the order of gnk_batch_tuning).  The work lists are rebuilt, and
+// the captured Arnoldi cycle dropped, only when a shape changes.
+int apply_tiles(BatchImpl& B, int variant, cudaStream_t st) {
+    static const int v32[][2] = {{1, 8}, {2, 4}, {2, 8}, {4, 4}};
+    static const int vdf[][2] = {{1, 2}, {1, 4}, {2, 2}};
+    int T32 = B.T32t, RG32 = B.RG32t, Tdf = B.Tdft, RGdf = B.RGdft;
+    if (variant >= 1 && variant <= 4) {
+        T32 = v32[variant - 1][0];
+        RG32 = v32[variant - 1][1];
+    } else if (variant >= 5 && variant <= 7) {
+        Tdf = vdf[variant - 5][0];
+        RGdf = vdf[variant - 5][1];
+    }
+    if (T32 != B.T32 || RG32 != B.RG32) {
+        GNK_TRY(upload_items(make_items(B.hdom, T32, RG32), &B.items32, &B.nitems32, st));
+        B.T32 = T32;
+        B.RG32 = RG32;
+        B.graph_R = -1;
+    }
+    if (Tdf != B.Tdf || RGdf != B.RGdf) {
+        GNK_TRY(upload_items(make_items(B.hdom, Tdf, RGdf), &B.itemsdf, &B.nitemsdf, st));
+        B.Tdf = Tdf;
+        B.RGdf = RGdf;
+        B.graph_R = -1;
+    }
     return GNK_OK;
 }
 
@@ -1161,6 +1192,10 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
         a.epi = BE_EONE;
         TRYB(launchdf(B, a, 1, 1, B.itemsdf1, B.nitemsdf1, st));
     }
+    B.T32t = B.T32;
+    B.RG32t = B.RG32;
+    B.Tdft = B.Tdf;
+    B.RGdft = B.RGdf;
     TRYB(upload_items(make_items(B.hdom, B.T32, B.RG32), &B.items32, &B.nitems32, st));
     TRYB(upload_items(make_items(B.hdom, B.Tdf, B.RGdf), &B.itemsdf, &B.nitemsdf, st));
     if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1242,11 +1277,18 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
     o.precision = GNK_PREC_MIXED_DF;
     if (opt) o = *opt;
     if (o.precision != GNK_PREC_MIXED_DF || o.restart < 1 || o.restart > 1000 || o.maxit < 1 || !(o.tol > 0) ||
-        !(o.inner_tol > 0) || o.max_refine < 0) {
-        set_error("gnk_batch_fbie: options need precision GNK_PREC_MIXED_DF, restart 1..1000, maxit >= 1, tol > 0");
+        !(o.inner_tol > 0) || o.max_refine < 0 || o.tile_variant < 0 || o.tile_variant > 7) {
+        set_error("gnk_batch_fbie: options need precision GNK_PREC_MIXED_DF, restart 1..1000, maxit >= 1, "
+                  "tol > 0, tile_variant 0..7");
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    GNK_TRY(apply_tiles(B, o.tile_variant, st));
+    cudaEvent_t t_ev[2] = {nullptr, nullptr};
+    if (o.timing) {
+        for (auto& e : t_ev) GNK_TRY_CUDA(cudaEventCreate(&e));
+        GNK_TRY_CUDA(cudaEventRecord(t_ev[0], st));
+    }
     const size_t Lb = (size_t)B.L * sizeof(double);
     // gamma (host or device) is copied into the batch's own vector r
     double* g_dev = B.r;
@@ -1334,6 +1376,14 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
     if (relres_per_system) std::memcpy(relres_per_system, rel.data(), ns * sizeof(double));
     res.status = status;
     res.relres = mx;
+    if (o.timing) {
+        float ms = 0.f;
+        if (cudaEventRecord(t_ev[1], st) == cudaSuccess && cudaEventSynchronize(t_ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, t_ev[0], t_ev[1]) == cudaSuccess)
+            res.solve_ms = ms;
+        cudaGetLastError();
+        for (auto& e : t_ev) cudaEventDestroy(e);
+    }
     if (info) *info = res;
     if (status == GNK_ENOTCONV) set_error("batch: some systems did not reach tol");
     return status;

@@ -148,11 +148,65 @@ int options_from(const gnk_options* in, gnk_options* o) {
         (o->precision != GNK_PREC_FP64 && o->precision != GNK_PREC_MIXED &&
          o->precision != GNK_PREC_DF32 && o->precision != GNK_PREC_MIXED_DF &&
          o->precision != GNK_PREC_FMM && o->precision != GNK_PREC_MIXED_FMM) ||
-        o->max_refine < 0 || !(o->inner_tol > 0.0)) {
+        o->max_refine < 0 || !(o->inner_tol > 0.0) || o->tile_chunks < 0 || o->tile_chunks > 64 ||
+        o->tile_variant < 0 || o->tile_variant > 7) {
         set_error("invalid gnk_options (restart 1..1000, maxit >= 1, tol > 0, precision "
-                  "FP64|MIXED|DF32|MIXED_DF|FMM|MIXED_FMM, max_refine >= 0, inner_tol > 0)");
+                  "FP64|MIXED|DF32|MIXED_DF|FMM|MIXED_FMM, max_refine >= 0, inner_tol > 0, "
+                  "tile_chunks 0..64, tile_variant 0..7)");
         return GNK_EINVAL;
     }
+    return GNK_OK;
+}
+
+// The tile override of one call on a handle (calls on one handle never
+// overlap, so the handle carries it for the duration of the call).
+struct TileOverride {
+    const Boundary& b;
+    TileOverride(const Boundary& bb, int chunks) : b(bb) { b.tile_chunks = chunks; }
+    ~TileOverride() { b.tile_chunks = 0; }
+};
+
+// Phase times of one call (gnk_options.timing): an event on the caller's
+// stream at each phase boundary, read once at the end of the call.
+struct Phases {
+    static constexpr int kMax = 5;
+    cudaEvent_t ev[kMax] = {};
+    int n = 0;
+    bool on = false;
+    cudaStream_t st = nullptr;
+    Phases(bool enable, cudaStream_t s) : on(enable), st(s) { mark(); }
+    void mark() {
+        if (!on || n >= kMax) return;
+        if (cudaEventCreate(&ev[n]) != cudaSuccess || cudaEventRecord(ev[n], st) != cudaSuccess) {
+            cudaGetLastError();
+            on = false;
+            return;
+        }
+        ++n;
+    }
+    // Elapsed ms between consecutive marks into out[0..k).
+    void read(double* const* out, int k) {
+        if (!on || n < 2) return;
+        if (cudaEventSynchronize(ev[n - 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        for (int i = 0; i < k && i + 1 < n; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) *out[i] = ms;
+            else cudaGetLastError();
+        }
+    }
+    ~Phases() {
+        for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+    }
+};
+
+// Work of the setup phase that a timed call does up front: the deferred
+// precompute and, for the FMM precisions, the quadtree.
+int timed_setup(const Boundary& b, int outer, cudaStream_t st) {
+    GNK_TRY(ensure_eone(b, st));
+    if (outer == GNK_PREC_FMM) GNK_TRY(ensure_fmm(b, kMaxRHS, st));
     return GNK_OK;
 }
 
@@ -295,6 +349,9 @@ void gnk_default_options(gnk_options* o) {
     o->precision = GNK_PREC_FP64;
     o->max_refine = 10;
     o->inner_tol = 1e-5;
+    o->tile_chunks = 0;
+    o->tile_variant = 0;
+    o->timing = 0;
 }
 
 int gnk_last_error(char* buf, size_t len) {
@@ -456,7 +513,11 @@ static int solve_common(const gnk_boundary* h, const double* gam, double* mu, co
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    const TileOverride tile(b, o.tile_chunks);
+    Phases ph(o.timing != 0, st);
+    if (o.timing) GNK_TRY(timed_setup(b, outer_precision(o.precision), st));
     GNK_TRY(ensure_eone(b, st));
+    ph.mark();
     const double* dg;
     GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
     Out o_mu = stage_out(b, mu, b.N, 1);
@@ -467,8 +528,14 @@ static int solve_common(const gnk_boundary* h, const double* gam, double* mu, co
         GNK_TRY(op_negate(b.r4, b.N, st));
         rhs = b.r4;
     }
+    ph.mark();
     const int s = solve(b, adjoint, rhs, o_mu.dev, o, info, st);
     if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+    ph.mark();
+    if (info) {
+        double* outs[3] = {&info->setup_ms, &info->rhs_ms, &info->solve_ms};
+        ph.read(outs, 3);
+    }
     GNK_TRY(finish_out(o_mu, st));
     if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles");
     if (s == GNK_ENONFINITE) set_error("non-finite value in the GMRES iteration");
@@ -498,6 +565,11 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
     const Boundary& b = hd->b;
     cudaStream_t st = (cudaStream_t)stream;
     const int outer = outer_precision(o.precision);
+    const TileOverride tile(b, o.tile_chunks);
+    Phases ph(o.timing != 0, st);
+    // a timed call forms the deferred precompute and the tree as their own phase
+    if (o.timing) GNK_TRY(timed_setup(b, outer, st));
+    ph.mark();
     const double* dg;
     GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));
     Out o_mu = stage_out(b, mu, b.N, 1);
@@ -509,15 +581,22 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
         GNK_TRY(ensure_eone(b, st));
         GNK_TRY(op_rhs_fb(b, dg, b.r4, b.r5, outer, st));
     }
+    ph.mark();
     int fc_valid = 0;
     const int s = solve(b, 0, b.r4, o_mu.dev, o, info, st, b.r6, &fc_valid);
     if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+    ph.mark();
     if (!fc_valid) GNK_TRY(op_M(b, o_mu.dev, b.r6, outer, st));  // f_C(mu)
     GNK_TRY(op_half_diff(b.r6, b.r5, o_h.dev, b.N, st));
     if (hk) {
         Out o_k = stage_out(b, hk, b.m1, 3);
         GNK_TRY(run_component_means(b, o_h.dev, o_k.dev, st));
         GNK_TRY(finish_out(o_k, st));
+    }
+    ph.mark();
+    if (info) {
+        double* outs[4] = {&info->setup_ms, &info->rhs_ms, &info->solve_ms, &info->h_ms};
+        ph.read(outs, 4);
     }
     GNK_TRY(finish_out(o_mu, st));
     GNK_TRY(finish_out(o_h, st));
@@ -537,6 +616,7 @@ int gnk_solve_ie_transpose(const gnk_boundary* hd, const double* rhs, double* x,
     GNK_TRY(options_from(opt, &o));
     const Boundary& b = hd->b;
     cudaStream_t st = (cudaStream_t)stream;
+    const TileOverride tile(b, o.tile_chunks);
     GNK_TRY(ensure_eone(b, st));
     const double* dr;
     GNK_TRY(stage_in(b, rhs, b.N, 0, st, &dr));
@@ -578,8 +658,9 @@ int dev_view(const void* p, size_t bytes, bool input, cudaStream_t st, DevArr* o
 }  // namespace
 
 int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* gam, const double* grad_mu,
-                      const double* grad_h, double* grad_et, double* grad_etp, double* grad_A,
-                      double* grad_gam, const gnk_options* opt, gnk_result* info, void* stream) {
+                      const double* grad_h, const double* grad_hk, double* grad_et, double* grad_etp,
+                      double* grad_A, double* grad_gam, const gnk_options* opt, gnk_result* info,
+                      void* stream) {
     GNK_TRY(check_handle(hd));
     if (!mu || !gam || !grad_mu || !grad_h || !grad_et || !grad_etp || !grad_A || !grad_gam) {
         set_error("NULL array");
@@ -593,18 +674,22 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
     GNK_TRY(options_from(opt, &o));
     const Boundary& b = hd->b;
     cudaStream_t st = (cudaStream_t)stream;
+    const TileOverride tile(b, o.tile_chunks);
     GNK_TRY(ensure_eone(b, st));
     const size_t rN = (size_t)b.N * sizeof(double), cN = 2 * rN;
-    DevArr v[8];
-    const void* src[8] = {mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam};
-    const size_t sz[8] = {rN, rN, rN, rN, cN, cN, cN, rN};
+    DevArr v[9];
+    const void* src[9] = {mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam, grad_hk};
+    const size_t sz[9] = {rN, rN, rN, rN, cN, cN, cN, rN, (size_t)b.m1 * sizeof(double)};
     int rc = GNK_OK;
-    for (int k = 0; k < 8 && rc == GNK_OK; ++k) rc = dev_view(src[k], sz[k], k < 4, st, &v[k]);
+    for (int k = 0; k < 9 && rc == GNK_OK; ++k) {
+        if (!src[k]) continue;  // grad_hk is optional
+        rc = dev_view(src[k], sz[k], k < 4 || k == 8, st, &v[k]);
+    }
     int s = rc;
     if (rc == GNK_OK) {
         s = fbie_backward(b, (const double*)v[0].dev, (const double*)v[1].dev, (const double*)v[2].dev,
-                          (const double*)v[3].dev, (double2*)v[4].dev, (double2*)v[5].dev,
-                          (double2*)v[6].dev, (double*)v[7].dev, o, info, st);
+                          (const double*)v[3].dev, (const double*)v[8].dev, (double2*)v[4].dev,
+                          (double2*)v[5].dev, (double2*)v[6].dev, (double*)v[7].dev, o, info, st);
         if (s == GNK_OK || s == GNK_ENOTCONV) {
             for (int k = 4; k < 8; ++k)
                 if (v[k].tmp && cudaMemcpyAsync(v[k].user, v[k].dev, v[k].bytes, cudaMemcpyDeviceToHost,
@@ -618,7 +703,7 @@ int gnk_fbie_backward(const gnk_boundary* hd, const double* mu, const double* ga
             }
         }
     }
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 9; ++k)
         if (v[k].tmp) pool_free(v[k].dev, st);
     return s;
 }

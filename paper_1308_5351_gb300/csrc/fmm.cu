@@ -1167,7 +1167,7 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
     else
         fmm_m2l_kernel<1><<<t->nbox, kFmmUT, 0, fs>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokm, PK_FMM, (double)R * b.N * (b.N - 1.0), fs, fmm_instr(b, R, 0));
+    prof_end(tokm, PK_FMM, (double)R, fs, fmm_instr(b, R, 0));  // work: Cauchy sums (products)
     launches += 2;
     if (t->L > 2) {
         const ProfToken tokd = prof_begin(fs, PK_FMML2L);

@@ -184,6 +184,12 @@ struct Boundary {
     // workspace
     void* partial = nullptr;    // split-source partial sums
     size_t partial_bytes = 0;
+    // source-chunk override of the direct pair kernels for the current call
+    // (gnk_options.tile_chunks; 0: the plans below) and the larger partial-sum
+    // workspace it may need (from the memory pool, kept until the handle is freed)
+    mutable int tile_chunks = 0;
+    mutable void* partial_x = nullptr;
+    mutable size_t partial_x_bytes = 0;
     double2* zbuf = nullptr;    // complex scratch, kMaxRHS x N
     double* r0 = nullptr;       // real scratch vectors (N each)
     double* r1 = nullptr;
@@ -264,11 +270,17 @@ int solve(const Boundary& b, int op, const double* rhs, double* x,
           double* fc_out = nullptr, int* fc_valid = nullptr);
 // Arithmetic of the outer (refinement) products for a solve precision.
 int outer_precision(int solve_precision);
+// Test hook behind gnk_debug_barrier_fault.
+int debug_barrier_fault(int skip_block, int spin_limit);
 
 // ---------------------------------------------------------------- gradients (grad.cu)
+// gh: dL/dh at the nodes; ghk (nullable): dL/dh_k of the component means.
 int fbie_backward(const Boundary& b, const double* mu, const double* gam, const double* gm,
-                  const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
-                  const gnk_options& opt, gnk_result* info, cudaStream_t st);
+                  const double* gh, const double* ghk, double2* g_et, double2* g_etp, double2* g_A,
+                  double* g_gam, const gnk_options& opt, gnk_result* info, cudaStream_t st);
+int fbie_backward_nodes(Boundary& b, const double* mu, const double* gam, const double* gm,
+                        const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
+                        const gnk_options& opt, gnk_result* info, cudaStream_t st);
 
 // ---------------------------------------------------------------- FMM (fmm.cu)
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st);

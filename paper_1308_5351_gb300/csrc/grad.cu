@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "gnk_internal.h"
+#include "pairmath.cuh"
 
 namespace gnk {
 namespace {
@@ -31,13 +32,6 @@ namespace {
 constexpr int kGR = 6;         // weight vectors
 constexpr int kGThreads = 128;
 constexpr int kGTile = 64;
-
-__device__ __forceinline__ double grad_recip(double x) {
-    double y0;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
-    const double e = fma(-x, y0, 1.0);
-    return fma(y0, fma(e, e, e), y0);
-}
 
 // partial[chunk][2 kGR][N]: E w_r in slots 0..5, F w_r in slots 6..11
 __global__ void __launch_bounds__(kGThreads) gradsum64_kernel(const double2* __restrict__ et,
@@ -66,7 +60,7 @@ __global__ void __launch_bounds__(kGThreads) gradsum64_kernel(const double2* __r
         for (int k = 0; k < kGTile; ++k) {
             const double2 sp = s_pos[k];
             const double dx = p.x - sp.x, dy = p.y - sp.y;
-            double inv = grad_recip(fma(dx, dx, dy * dy));
+            double inv = recip_f64(fma(dx, dx, dy * dy));
             inv = (j0 + k == i) ? 0.0 : inv;
             const double ar = dx * inv, ai = dy * inv;  // 1/d = ar - i ai
             const double gr = fma(ar, ar, -ai * ai);    // 1/d^2 = gr - i gi
@@ -177,12 +171,45 @@ __global__ void grad_assemble_kernel(int N, int n, const double2* __restrict__ q
     g_gam[i] = -0.5 * ktgh - mtl;
 }
 
+// dL/dh_i + dL/dh_k / n for the nodes i of component k: h_k is the mean of h
+// over its component, so its gradient spreads evenly over the n nodes
+__global__ void fold_hk_kernel(int N, int n, const double* __restrict__ gh, const double* __restrict__ ghk,
+                               double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[i] = gh[i] + ghk[i / n] / n;
+}
+
 }  // namespace
 
 int fbie_backward(const Boundary& bc, const double* mu, const double* gam, const double* gm,
-                  const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
-                  const gnk_options& opt, gnk_result* info, cudaStream_t st) {
+                  const double* gh_nodes, const double* ghk, double2* g_et, double2* g_etp, double2* g_A,
+                  double* g_gam, const gnk_options& opt, gnk_result* info, cudaStream_t st) {
     Boundary& b = const_cast<Boundary&>(bc);
+    const int N = b.N;
+    const int nb = (N + 255) / 256;
+    // the loss's gradient with respect to the node values of h, with that of
+    // the component means h_k folded in
+    const double* gh = gh_nodes;
+    double* gh_fold = nullptr;
+    if (ghk) {
+        if (pool_alloc(reinterpret_cast<void**>(&gh_fold), (size_t)N * sizeof(double), st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("gradient workspace allocation failed");
+            return GNK_ENOMEM;
+        }
+        fold_hk_kernel<<<nb, 256, 0, st>>>(N, b.n, gh_nodes, ghk, gh_fold);
+        GNK_TRY_CUDA(cudaGetLastError());
+        count_launches(1);
+        gh = gh_fold;
+    }
+    const int rc = fbie_backward_nodes(b, mu, gam, gm, gh, g_et, g_etp, g_A, g_gam, opt, info, st);
+    if (gh_fold) pool_free(gh_fold, st);
+    return rc;
+}
+
+int fbie_backward_nodes(Boundary& b, const double* mu, const double* gam, const double* gm,
+                        const double* gh, double2* g_et, double2* g_etp, double2* g_A, double* g_gam,
+                        const gnk_options& opt, gnk_result* info, cudaStream_t st) {
     const int N = b.N;
     const int nb = (N + 255) / 256;
     // rhs_T = gm + (M^T gh)/2  (FP64-class products)

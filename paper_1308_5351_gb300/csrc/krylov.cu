@@ -18,6 +18,7 @@
 // Inside a cycle every kernel first reads the device flag `done`, so the host
 // enqueues a whole cycle without waiting and synchronises once per cycle.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -41,6 +42,8 @@ struct KState {
     int restart;
     unsigned counter; // last-block ticket
     int bar_err;      // a grid barrier wait gave up
+    int bar_limit;    // polls before a grid barrier wait gives up
+    int bar_skip;     // test hook: this block never arrives at a barrier (-1: none)
     // grid barrier of the Arnoldi step: arrivals and generation on cache lines
     // of their own, away from the fields above and from each other
     alignas(128) unsigned bar_count;
@@ -167,11 +170,15 @@ constexpr int KD = 16;
 // up sets bar_err, which the host reports.
 constexpr int kBarSpin = 1 << 20;
 
+// The test hook (bar_skip, set only through gnk_debug_barrier_fault) makes one
+// block pass every barrier without arriving, so that the others' bounded
+// waits run out: the failure path is exercised without a fault.
 __device__ __forceinline__ void grid_barrier(KState* s) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && (int)blockIdx.x != s->bar_skip) {
         volatile unsigned* gen = &s->bar_gen;
         const unsigned g = *gen;
+        const int limit = s->bar_limit;
         __threadfence();
         if (atomicAdd(&s->bar_count, 1u) == gridDim.x - 1) {
             atomicExch(&s->bar_count, 0u);
@@ -179,7 +186,7 @@ __device__ __forceinline__ void grid_barrier(KState* s) {
             atomicAdd(&s->bar_gen, 1u);
         } else {
             for (int it = 0; *gen == g; ++it) {
-                if (it >= kBarSpin || *(volatile int*)&s->bar_err) {
+                if (it >= limit || *(volatile int*)&s->bar_err) {
                     atomicExch(&s->bar_err, 1);
                     break;
                 }
@@ -439,7 +446,7 @@ __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int
     if (i < N) x[i] += d[i];
 }
 
-__global__ void k_init_state(KState* s, double tol, int restart) {
+__global__ void k_init_state(KState* s, double tol, int restart, int bar_limit, int bar_skip) {
     s->bnorm = 0.0;
     s->beta = 0.0;
     s->tol = tol;
@@ -453,7 +460,13 @@ __global__ void k_init_state(KState* s, double tol, int restart) {
     s->counter = 0;
     s->bar_count = 0;
     s->bar_err = 0;
+    s->bar_limit = bar_limit;
+    s->bar_skip = bar_skip;
 }
+
+// Test hook of gnk_debug_barrier_fault, read by every later solve.
+std::atomic<int> g_bar_limit{kBarSpin};
+std::atomic<int> g_bar_skip{-1};
 
 int ensure_krylov(Boundary& b, int restart, cudaStream_t st) {
     if (restart + 1 > 1024) {
@@ -548,7 +561,7 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
     const int nb = vec_blocks(N);
     const int ng = arnoldi_blocks(N);
     KState hs;
-    k_init_state<<<1, 1, 0, st>>>(ks, tol, restart);
+    k_init_state<<<1, 1, 0, st>>>(ks, tol, restart, g_bar_limit.load(), g_bar_skip.load());
     KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0)));
     count_launches(2);
     GNK_TRY_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), st));
@@ -643,6 +656,16 @@ int norm_host(Boundary& b, const double* v, double* out, cudaStream_t st) {
 
 }  // namespace
 
+int debug_barrier_fault(int skip_block, int spin_limit) {
+    if (skip_block < -1 || spin_limit < 0) {
+        set_error("gnk_debug_barrier_fault: skip_block must be >= -1 and spin_limit >= 0");
+        return GNK_EINVAL;
+    }
+    g_bar_skip.store(skip_block);
+    g_bar_limit.store(spin_limit == 0 ? kBarSpin : std::min(spin_limit, kBarSpin));
+    return GNK_OK;
+}
+
 int outer_precision(int solve_precision) {
     if (solve_precision == GNK_PREC_DF32 || solve_precision == GNK_PREC_MIXED_DF) return GNK_PREC_DF32;
     if (solve_precision == GNK_PREC_FMM || solve_precision == GNK_PREC_MIXED_FMM) return GNK_PREC_FMM;
@@ -689,7 +712,10 @@ int solve(const Boundary& bc, int adjoint /* OpId */, const double* rhs, double*
             double inner_rel = 0.0;
             const int s = gmres(b, adjoint, GNK_PREC_FP32, rr, dd, b.r0, opt.restart, opt.maxit,
                                 opt.inner_tol, &res, &inner_rel, st, nullptr, nullptr);
-            if (s == GNK_ENONFINITE) {
+            if (s != GNK_OK && s != GNK_ENOTCONV) {
+                // NaN/Inf, a CUDA failure or a timed-out grid barrier in the
+                // inner solve: its correction is not applied and its status
+                // (and message) is the solve's
                 status = s;
                 break;
             }

@@ -707,8 +707,13 @@ __global__ void reduce_epilogue_kernel(ReduceArgs a) {
 }
 
 cudaError_t launch_reduce(const Boundary& b, const PairJob& job, int chunks, int ptype,
-                          cudaStream_t st) {
-    const ReduceArgs ra = reduce_args(b, job, chunks, ptype);
+                          cudaStream_t st, const void* partial = nullptr) {
+    ReduceArgs ra = reduce_args(b, job, chunks, ptype);
+    if (partial) {
+        ra.pdf = static_cast<const float4*>(partial);
+        ra.p64 = static_cast<const double2*>(partial);
+        ra.p32 = static_cast<const float2*>(partial);
+    }
     const int threads = 256;
     const ProfToken tok = prof_begin(st, PK_REDUCE);
     reduce_epilogue_kernel<<<(b.N + threads - 1) / threads, threads, 0, st>>>(ra);
@@ -756,8 +761,38 @@ int pair_workspace_bytes(const Boundary& b, size_t* bytes) {
     return GNK_OK;
 }
 
+// The plan of one launch: the handle's plan, or, under a source-chunk override
+// (gnk_options.tile_chunks), that many chunks (at most one per source tile)
+// with a partial-sum workspace large enough for them.
+static int launch_plan(const Boundary& b, const PairPlan& base, size_t elem_bytes, PairPlan* p,
+                       void** partial, cudaStream_t st) {
+    *p = base;
+    *partial = b.partial;
+    if (b.tile_chunks <= 0) return GNK_OK;
+    const int want = std::min(b.tile_chunks, p->tiles_src);
+    p->tiles_per_chunk = (p->tiles_src + want - 1) / want;
+    p->chunks = (p->tiles_src + p->tiles_per_chunk - 1) / p->tiles_per_chunk;
+    const size_t need = (size_t)p->chunks * kMaxRHS * b.N * elem_bytes;
+    if (need <= b.partial_bytes) return GNK_OK;
+    if (need > b.partial_x_bytes) {
+        if (b.partial_x) pool_free(b.partial_x, st);
+        b.partial_x = nullptr;
+        b.partial_x_bytes = 0;
+        if (pool_alloc(&b.partial_x, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pair-sum workspace for %d source chunks: allocation failed", p->chunks);
+            return GNK_ENOMEM;
+        }
+        b.partial_x_bytes = need;
+    }
+    *partial = b.partial_x;
+    return GNK_OK;
+}
+
 int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
-    const PairPlan& p = b.plan64;
+    PairPlan p;
+    void* partial = nullptr;
+    GNK_TRY(launch_plan(b, b.plan64, sizeof(double2), &p, &partial, st));
     Pair64Args a;
     a.et = b.et;
     a.N = b.N;
@@ -766,7 +801,7 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.x0 = job.x[0];
     a.x1 = job.x[1];
     a.s = job.s;
-    a.partial = static_cast<double2*>(b.partial);
+    a.partial = static_cast<double2*>(partial);
     a.tiles_src = p.tiles_src;
     a.tiles_per_chunk = p.tiles_per_chunk;
     a.done = job.done;
@@ -784,13 +819,15 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st) {
     // FP64 pipe per pair: 9 shared (d, |d|^2, reciprocal, 1/d) + 4 per right-hand side
     prof_end(tok, PK_PAIR64, (double)job.R * b.N * (b.N - 1.0), st,
              (9.0 + 4.0 * job.R) * b.N * (b.N - 1.0));
-    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 0, st));
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 0, st, partial));
     count_launches(2);
     return GNK_OK;
 }
 
 int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
-    const PairPlan& p = b.plan32;
+    PairPlan p;
+    void* partial = nullptr;
+    GNK_TRY(launch_plan(b, b.plan32, sizeof(float2), &p, &partial, st));
     Pair32Args a;
     a.et32 = b.et32;
     a.ref32 = b.ref32;
@@ -801,7 +838,7 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.x0 = job.x[0];
     a.x1 = job.x[1];
     a.s32 = (job.s == b.q) ? b.q32 : b.A32;
-    a.partial = static_cast<float2*>(b.partial);
+    a.partial = static_cast<float2*>(partial);
     a.tiles_src = p.tiles_src;
     a.tiles_per_chunk = p.tiles_per_chunk;
     a.done = job.done;
@@ -838,13 +875,15 @@ int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st) {
     // side; one part of z only: 4 shared + 3 per right-hand side
     const double per_pair = (comp && job.R == 1) ? 4.0 + 3.0 : 6.0 + 4.0 * job.R;
     prof_end(tok, PK_PAIR32, (double)job.R * b.N * (b.N - 1.0), st, per_pair * b.N * (b.N - 1.0));
-    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st));
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 1, st, partial));
     count_launches(2);
     return GNK_OK;
 }
 
 int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
-    const PairPlan& p = b.plandf;
+    PairPlan p;
+    void* partial = nullptr;
+    GNK_TRY(launch_plan(b, b.plandf, sizeof(float4), &p, &partial, st));
     PairDFArgs a;
     a.et = b.et;
     a.ref64 = b.ref64;
@@ -855,7 +894,7 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.x0 = job.x[0];
     a.x1 = job.x[1];
     a.s = job.s;
-    a.partial = static_cast<float4*>(b.partial);
+    a.partial = static_cast<float4*>(partial);
     a.tiles_src = p.tiles_src;
     a.tiles_per_chunk = p.tiles_per_chunk;
     a.done = job.done;
@@ -888,7 +927,7 @@ int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st) {
     // side (two products and two compensated sums per part of z)
     const double per_pair = (comp && job.R == 1) ? 49.0 + 24.0 : 49.0 + 48.0 * job.R;
     prof_end(tok, PK_PAIRDF, (double)job.R * b.N * (b.N - 1.0), st, per_pair * b.N * (b.N - 1.0));
-    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 2, st));
+    GNK_TRY_CUDA(launch_reduce(b, job, p.chunks, 2, st, partial));
     count_launches(2);
     return GNK_OK;
 }

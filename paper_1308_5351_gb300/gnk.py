@@ -49,6 +49,7 @@ EXPORTED = (
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
     "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval", "gnk_profile_mask",
+    "gnk_debug_recip_f64", "gnk_debug_barrier_fault",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -58,13 +59,16 @@ PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_
 class gnk_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("tile_chunks", ctypes.c_int),
+                ("tile_variant", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class gnk_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("refinements", ctypes.c_int), ("matvecs_fp64", ctypes.c_int),
-                ("matvecs_fp32", ctypes.c_int), ("relres", ctypes.c_double)]
+                ("matvecs_fp32", ctypes.c_int), ("relres", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("rhs_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("h_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,7 +128,7 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(gnk_result), P, P]
     lib.gnk_solve_ie_transpose.argtypes = [P, P, P, ctypes.POINTER(gnk_options),
                                            ctypes.POINTER(gnk_result), P]
-    lib.gnk_fbie_backward.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(gnk_options),
+    lib.gnk_fbie_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(gnk_options),
                                       ctypes.POINTER(gnk_result), P]
     lib.gnk_profile_query_ex.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -133,6 +137,8 @@ def load(path: str = LIB_PATH):
     lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, P, P, P]
     lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
     lib.gnk_slit_map_eval.argtypes = [P, P, P, P, P, P, I, P, P, I, P]
+    lib.gnk_debug_recip_f64.argtypes = [I, P, P, P, P]
+    lib.gnk_debug_barrier_fault.argtypes = [I, I]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
     _lib = lib
@@ -274,10 +280,59 @@ def gnk_cauchy_sum(h, w, z, precision=GNK_PREC_FP64, stream=None):
                                         _stream(stream)))
 
 
+def _noalloc_operand(name, a, N):
+    """Checks one array of gnk_cauchy_sum_noalloc before any launch: a
+    contiguous complex128 (or float64 pairs) CUDA tensor on the current device
+    holding at least N complex values."""
+    if torch is None or not isinstance(a, torch.Tensor):
+        raise GnkError(GNK_EINVAL, f"gnk_cauchy_sum_noalloc: {name} must be a CUDA tensor "
+                                   "(nothing is staged or copied)")
+    if a.dtype == torch.complex128:
+        held = a.numel()
+    elif a.dtype == torch.float64:
+        held = a.numel() // 2
+    else:
+        raise GnkError(GNK_EINVAL, f"gnk_cauchy_sum_noalloc: {name} has dtype {a.dtype}; "
+                                   "expected complex128 or float64 (re, im) pairs")
+    if held < N:
+        raise GnkError(GNK_EINVAL, f"gnk_cauchy_sum_noalloc: {name} holds {held} complex values, "
+                                   f"fewer than N = {N}")
+    if not a.is_contiguous():
+        raise GnkError(GNK_EINVAL, f"gnk_cauchy_sum_noalloc: {name} must be contiguous")
+
+
+def _noalloc_device(name, a):
+    if not a.is_cuda or a.device.index != torch.cuda.current_device():
+        raise GnkError(GNK_EINVAL, f"gnk_cauchy_sum_noalloc: {name} is on {a.device}, not on the "
+                                   "current CUDA device")
+
+
 def gnk_cauchy_sum_noalloc(N, et, w, z, stream=None):
-    """z = E w with no device allocation (device arrays only, N <= 65536)."""
-    return _check(load().gnk_cauchy_sum_noalloc(int(N), _ptr(et, True), _ptr(w, True),
+    """z = E w with no device allocation: et, w, z CUDA tensors on the current
+    device holding at least N complex values each, N <= 65536."""
+    N = int(N)
+    ops = (("et", et), ("w", w), ("z", z))
+    for name, a in ops:
+        _noalloc_operand(name, a, N)
+    for name, a in ops:
+        _noalloc_device(name, a)
+    return _check(load().gnk_cauchy_sum_noalloc(N, _ptr(et, True), _ptr(w, True),
                                                 _ptr(z, True), _stream(stream)))
+
+
+def gnk_debug_recip_f64(x, y_lib, y_div, stream=None):
+    """The pair kernels' FP64 reciprocal and CUDA's 1.0/x of the device array x."""
+    n = int(x.numel())
+    for a in (y_lib, y_div):
+        if a.numel() < n:
+            raise GnkError(GNK_EINVAL, "gnk_debug_recip_f64: output shorter than x")
+    return _check(load().gnk_debug_recip_f64(n, _ptr(x), _ptr(y_lib), _ptr(y_div), _stream(stream)))
+
+
+def gnk_debug_barrier_fault(skip_block: int, spin_limit: int = 0):
+    """Test hook: block `skip_block` of later Arnoldi steps skips its grid-barrier
+    arrivals (-1: none); the other blocks' waits give up after spin_limit polls."""
+    return _check(load().gnk_debug_barrier_fault(int(skip_block), int(spin_limit)))
 
 
 def gnk_cauchy_eval(h, z, f, fz, finf=None, precision=GNK_PREC_FP64, stream=None):
@@ -386,9 +441,10 @@ def gnk_solve_ie_transpose(h, rhs, x, options: Optional[gnk_options] = None, str
 
 
 def gnk_fbie_backward(h, mu, gam, grad_mu, grad_h, grad_et, grad_etp, grad_A, grad_gam,
-                      options: Optional[gnk_options] = None, stream=None):
+                      options: Optional[gnk_options] = None, stream=None, grad_hk=None):
+    """grad_hk (nullable, m1 values): dL/dh_k of the component means."""
     res = gnk_result()
-    code = load().gnk_fbie_backward(h, _ptr(mu), _ptr(gam), _ptr(grad_mu), _ptr(grad_h),
+    code = load().gnk_fbie_backward(h, _ptr(mu), _ptr(gam), _ptr(grad_mu), _ptr(grad_h), _ptr(grad_hk),
                                     _ptr(grad_et, True), _ptr(grad_etp, True), _ptr(grad_A, True),
                                     _ptr(grad_gam),
                                     ctypes.byref(options) if options is not None else None,

@@ -160,8 +160,7 @@ def test_autograd_fourier_coefficients_vs_fd(G):
         et, etp = _star_domain(coeffs, n, centres, r0, polygons)
         A = torch.ones_like(et)
         gam = torch.log(torch.abs(et - centres[0]))
-        mu, h = AG.fbie(et, etp, A, gam, m1, n, bounded=False, tol=1e-13)
-        hk = AG.component_means(h, m1, n)
+        mu, h, hk = AG.fbie(et, etp, A, gam, m1, n, bounded=False, tol=1e-13)
         return hk[1] - hk[0]
 
     params = [(torch.tensor(a, device="cuda", requires_grad=True), torch.tensor(b, device="cuda", requires_grad=True))
@@ -184,3 +183,27 @@ def test_autograd_fourier_coefficients_vs_fd(G):
                 fd = (shifted(eps) - shifted(-eps)) / (2 * eps)
                 an = float(params[s][which].grad[k])
                 assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (s, which, k, fd, an)
+
+
+@pytest.mark.gpu
+def test_autograd_hk_output_and_second_backward(G):
+    """h_k returned by the library's forward pass equals the component means of
+    h; a loss through h_k and the same loss through the means of h give the
+    same gradient; a second backward with retain_graph reuses the handle."""
+    from paper_1308_5351_gb300 import autograd as AG
+    d = Dm.three_circles(64)
+    gam = Dm.gamma_log(d, 0.05j)
+    et = torch.as_tensor(d.et, device="cuda").requires_grad_(True)
+    etp = torch.as_tensor(d.etp, device="cuda")
+    A = torch.as_tensor(d.A, device="cuda")
+    g = torch.as_tensor(gam, device="cuda").requires_grad_(True)
+    w = torch.tensor([0.3, -1.0, 2.0], dtype=torch.float64, device="cuda")
+    mu, h, hk = AG.fbie(et, etp, A, g, d.m1, d.n, bounded=True, tol=1e-13)
+    assert torch.allclose(hk, h.detach().view(d.m1, d.n).mean(dim=1), rtol=0, atol=1e-13)
+    (w * hk).sum().backward(retain_graph=True)
+    ga, gg = et.grad.clone(), g.grad.clone()
+    et.grad = None
+    g.grad = None
+    (w * h.view(d.m1, d.n).mean(dim=1)).sum().backward()
+    assert torch.allclose(et.grad, ga, rtol=0, atol=1e-9 * float(ga.abs().max()))
+    assert torch.allclose(g.grad, gg, rtol=0, atol=1e-9 * float(gg.abs().max()))
