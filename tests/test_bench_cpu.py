@@ -23,6 +23,13 @@ def test_reference_arm_line():
     assert line["config"]["workload"].startswith("8 ellipses, unbounded, n=64 (512 unknowns)")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
-    assert cb["pair_evals_per_s"] > 0 and "cauchy_rows" in cb["pair_sample"]
+    assert cb["pair_evals_per_s"] > 0 and "OpenMP" in cb["pair_sample"]
+    assert cb["measured"]["N"] == 512 and cb["measured"]["lu_solve_s"] > 0
+    # the GPU arm's config dict for the same arguments (same_config)
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(precision="fmm")
+    assert line["config"] == bench.bench_config(args, 512, 8, 64, 1)
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
