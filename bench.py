@@ -68,7 +68,7 @@ PEAK_BASIS = {
            "of the 32 double-float products of the real Pascal matrix + 98 for the two complex scalings",
     "fmm_up": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 742 FP32 instr per lane per binomial M2M "
               "transform, 36 x 47 per node for the powers and 48R per node and order in P2M",
-    "fmm_l2l": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 742 FP32 instr per lane per binomial L2L transform",
+    "fmm_l2l": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 840 FP32 instr per lane per Pascal-matrix L2L transform",
     "fmm_l2p": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 58R FP32 instr per node and order (Horner)",
     "fmm_near": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz; 49 + 48R FP32 instr per double-float "
                 "near-field pair",

@@ -163,6 +163,12 @@ int gnk_profile_query(int kind, long long* launches, double* total_ms,
  * kernels: FP32-pipe instructions of their double-float arithmetic). */
 int gnk_profile_query_ex(int kind, long long* launches, double* total_ms,
                          double* work, double* instr);
+/* As gnk_profile_query_ex, plus the algorithmic bytes the launches read and
+ * wrote where the kernel is bound by memory rather than by a pipe (the FMM
+ * near field from its operator cache: 8 bytes per pair and part of z read);
+ * 0 for the other kernels. */
+int gnk_profile_query_bytes(int kind, long long* launches, double* total_ms,
+                            double* work, double* instr, double* bytes);
 
 /* ---------------------------------------------------------------------------
  * Boundary handle (Sec. 2.1, 2.4; Eqs. eta, A, ti-skp)

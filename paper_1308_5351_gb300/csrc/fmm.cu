@@ -19,9 +19,9 @@
 // last child, no launch per level), M2L for every box, L2L per leaf down its
 // ancestor path.  The near field runs beside it on the caller's stream; L2P
 // adds the two after they join.  M2M and L2L are
-// binomial transforms between exact Gaussian-integer scalings, M2L a fixed real
-// Pascal matrix between two complex scalings per offset: no P x P table per
-// relative position.  The far field runs in complex double-float on the FP32
+// fixed real Pascal matrices between exact Gaussian-integer scalings, M2L a
+// fixed real Pascal matrix between two complex scalings per offset: no P x P
+// table per relative position.  The far field runs in complex double-float on the FP32
 // pipe (GB300's FP64 pipe is 1/64 of it).
 //
 // The tree is built once per handle (the geometry is fixed for all products),
@@ -68,6 +68,7 @@ struct FmmArgs {
     const int* nl_leaf;
     const float2* m2lH;   // C(k+l, l), [k][l] double-float
     const float4* m2lS;   // per offset code: (-1)^(k+1) delta^-(k+1), then delta^-l
+    const float2* bUp;    // C(l, m) at [l][m] (0 for l < m): the L2L Pascal sums
     float4* mult;
     float4* loc;
     float4* ws;
@@ -88,6 +89,8 @@ struct FmmArgs {
     double2* outF;      // [R][N] F sums in node order (EF products)
     const int* node_box;  // leaf box of each node in sorted order
     int* ucnt;            // per box: children counted in the upward pass
+    float2* xs;           // [R][N] x in sorted order as double-float (cached near field), or null
+    const float4* tp;     // [N][P] powers t^k of every node about its leaf centre, or null
 };
 
 __global__ void fmm_gather_kernel(FmmArgs a) {
@@ -106,6 +109,10 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
         }
         const df wx = df_split(w.x), wy = df_split(w.y);
         a.ws[(size_t)r * a.N + i] = make_float4(wx.h, wx.l, wy.h, wy.l);
+        if (a.xs != nullptr) {  // x alone for the cached near field (W_SCALED)
+            const df xv = df_split((r == 0) ? a.x0[j] : a.x1[j]);
+            a.xs[(size_t)r * a.N + i] = make_float2(xv.h, xv.l);
+        }
     }
 }
 
@@ -152,15 +159,18 @@ __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b
 constexpr int kFmmTW = 4;
 constexpr int kFmmMaxDepth = 24;  // ancestors of a leaf, the leaf included
 
-// ---- M2M and L2L as binomial transforms.  With delta = (c1 - c0)/r0 =
-// g/4 for a child in quadrant q, g = (2 qa - 1) + i (2 qb - 1):
+// ---- M2M and L2L between exact scalings.  With delta =
+// (c1 - c0)/r0 = g/4 for a child in quadrant q, g = (2 qa - 1) + i (2 qb - 1):
 //   M2M  a0_m = delta^m sum_{k<=m} C(m,k) [(2 delta)^-k a1_k]
 //   L2L  b1_m = (2 delta)^-m sum_{l>=m} C(l,m) [delta^l b0_l]
 // and (2 delta)^-1 = conj(g).  The scale factors g^e 4^-e and conj(g)^e are
 // Gaussian integers times powers of two, so multiplying by them is exact up
-// to one rounding in each part; the Pascal sums take P - 1 passes of one
-// neighbour addition per lane, with no tables.  Their terms are those of the
-// matrix forms, so the rounding error is of the same size.
+// to one rounding in each part.  The L2L Pascal sum is a product with the
+// fixed real triangular matrix C(l,m) (a double-float table of 8 KB that stays
+// in L1; C(l,m) < 2^29, exact), lane m accumulating its 32 terms (zero beyond
+// the triangle) in two independent compensated sums: one transform has the
+// latency of a 32-term dot product instead of 31 dependent passes.  The M2M
+// sum takes the passes (binom_lower).
 constexpr int kFmmUT = 32 * kFmmTW;  // threads of the upward and downward kernels
 
 // angle of g in units of pi/4 for the quadrant q = 2 qa + qb
@@ -182,12 +192,10 @@ __device__ __forceinline__ cdf cdf_shfl_up1(cdf v) {
                df{__shfl_up_sync(0xffffffffu, v.im.h, 1), __shfl_up_sync(0xffffffffu, v.im.l, 1)}};
 }
 
-__device__ __forceinline__ cdf cdf_shfl_down1(cdf v) {
-    return cdf{df{__shfl_down_sync(0xffffffffu, v.re.h, 1), __shfl_down_sync(0xffffffffu, v.re.l, 1)},
-               df{__shfl_down_sync(0xffffffffu, v.im.h, 1), __shfl_down_sync(0xffffffffu, v.im.l, 1)}};
-}
-
-// lane m: sum_{k<=m} C(m,k) v_k (pass i adds the left neighbour on lanes m >= i)
+// lane m: sum_{k<=m} C(m,k) v_k by P - 1 passes (pass i adds the left
+// neighbour's pre-pass value on lanes m >= i).  The upward pass keeps this
+// form: there the Pascal-table sum below measured slower (more loads while
+// the P2M of other leaves competes for the SM).
 __device__ __forceinline__ cdf binom_lower(cdf v, int lane) {
 #pragma unroll 1
     for (int i = 1; i < kFmmP; ++i) {
@@ -197,26 +205,37 @@ __device__ __forceinline__ cdf binom_lower(cdf v, int lane) {
     return v;
 }
 
-// lane m: sum_{l>=m} C(l,m) v_l (the transposed passes, last first)
-__device__ __forceinline__ cdf binom_upper(cdf v, int lane) {
-#pragma unroll 1
-    for (int i = kFmmP - 1; i >= 1; --i) {
-        const cdf u = cdf_shfl_down1(v);
-        if (lane >= i - 1 && lane <= kFmmP - 2) v = cdf_add(v, u);
+// lane m: sum_k T[k][m] v_k for a real double-float table T (P x P, [k][m])
+// and the complex vector v staged by the warp in sv[0 .. P)
+__device__ __forceinline__ cdf pascal_sum(const float2* __restrict__ T, const float4* sv, int lane) {
+    df yr{0.f, 0.f}, yi{0.f, 0.f}, zr{0.f, 0.f}, zi{0.f, 0.f};
+#pragma unroll 4
+    for (int k = 0; k < kFmmP; k += 2) {
+        const float2 h0 = __ldg(T + k * kFmmP + lane), h1 = __ldg(T + (k + 1) * kFmmP + lane);
+        const float4 x0 = sv[k], x1 = sv[k + 1];
+        df_acc(yr, df_mul(df{h0.x, h0.y}, df{x0.x, x0.y}));
+        df_acc(yi, df_mul(df{h0.x, h0.y}, df{x0.z, x0.w}));
+        df_acc(zr, df_mul(df{h1.x, h1.y}, df{x1.x, x1.y}));
+        df_acc(zi, df_mul(df{h1.x, h1.y}, df{x1.z, x1.w}));
     }
-    return v;
+    return cdf{df_add(yr, zr), df_add(yi, zi)};
 }
 
+// one warp: lane m of a1 (the child's multipole) -> lane m of its contribution
+// to the parent's multipole
 __device__ __forceinline__ cdf m2m_binom(cdf a1, int q, int lane) {
     const int ang = gauss_angle(q);
-    const cdf c = cdf_mul_gpow(a1, 8 - ang, lane, 0);          // (2 delta)^-k a1_k
+    const cdf c = cdf_mul_gpow(a1, 8 - ang, lane, 0);  // (2 delta)^-k a1_k
     return cdf_mul_gpow(binom_lower(c, lane), ang, lane, -2 * lane);  // delta^m S_m
 }
 
-__device__ __forceinline__ cdf l2l_binom(cdf b0, int q, int lane) {
+__device__ __forceinline__ cdf l2l_pascal(cdf b0, int q, int lane, const float2* bUp, float4* sv) {
     const int ang = gauss_angle(q);
-    const cdf e = cdf_mul_gpow(b0, ang, lane, -2 * lane);      // delta^l b0_l
-    return cdf_mul_gpow(binom_upper(e, lane), 8 - ang, lane, 0);  // (2 delta)^-m T_m
+    const cdf e = cdf_mul_gpow(b0, ang, lane, -2 * lane);  // delta^l b0_l
+    __syncwarp();
+    sv[lane] = cdf_pack(e);
+    __syncwarp();
+    return cdf_mul_gpow(pascal_sum(bUp, sv, lane), 8 - ang, lane, 0);  // (2 delta)^-m T_m
 }
 
 __device__ __forceinline__ cdf reduce_warps(cdf acc, float4 (*s)[32], int wid, int lane) {
@@ -320,20 +339,48 @@ __device__ __forceinline__ void p2m_leaf(const FmmArgs& a, int leaf, int box, in
     }
 }
 
-// Upward pass, one block per leaf: P2M, then the multipoles move up the tree
-// without a launch per level: the block that completes the last child of a
-// box (an atomic count per box; nothing waits) forms that box's M2M from its
-// children (warp w takes child w) and goes on to the parent.
+// P2M of one leaf from the cached powers t_j^k (a.tp, [node][k]): warp w
+// sums w_j t_j^k over the leaf's nodes j = j0 + w, j0 + w + kFmmTW, ...
+// (lane = k), with no block barrier until the warps' sums are added in warp
+// order.
 template <int R>
+__device__ __forceinline__ void p2m_leaf_cached(const FmmArgs& a, int leaf, int box, int wid, int lane,
+                                                float4 (*s_acc)[32]) {
+    cdf acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
+    const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
+#pragma unroll 2
+    for (int j = j0 + wid; j < j1; j += kFmmTW) {
+        const cdf pw = cdf_of(__ldcg(a.tp + (size_t)j * kFmmP + lane));
+#pragma unroll
+        for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(__ldcg(a.ws + (size_t)r * a.N + j)), pw);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const cdf sm = reduce_warps(acc[r], s_acc, wid, lane);
+        if (wid == 0) a.mult[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(sm);
+    }
+}
+
+// Upward pass, one block per leaf: P2M (from the cached powers when TP), then
+// the multipoles move up the tree without a launch per level: the block that
+// completes the last child of a box (an atomic count per box; nothing waits)
+// forms that box's M2M from its children (warp w takes child w) and goes on
+// to the parent.
+template <int R, bool TP>
 __global__ void __launch_bounds__(kFmmUT) fmm_up_kernel(FmmArgs a) {
-    __shared__ float4 s_pow[kFmmP][33];
+    __shared__ float4 s_pow[TP ? 1 : kFmmP][33];
     __shared__ float4 s_w[R][32];
     __shared__ float4 s_acc[kFmmTW][32];
     __shared__ int s_last;
     if (a.done != nullptr && *a.done) return;
     const int leaf = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int box = a.leaf_box[leaf];
-    p2m_leaf<R>(a, leaf, box, wid, lane, s_pow, s_w, s_acc);
+    if (TP)
+        p2m_leaf_cached<R>(a, leaf, box, wid, lane, s_acc);
+    else
+        p2m_leaf<R>(a, leaf, box, wid, lane, s_pow, s_w, s_acc);
     for (;;) {
         if (wid == 0) __threadfence();  // the box's multipole (warp 0's stores) before the count
         __syncthreads();
@@ -376,13 +423,14 @@ __global__ void __launch_bounds__(kFmmUT) fmm_m2l_kernel(FmmArgs a) {
 
 // L2L, one warp per leaf: the leaf's local expansion is formed from the M2L
 // parts of its ancestors, level 2 first, each shifted to the next level by
-// the binomial L2L (the same operations, in the same order, as a
+// the Pascal-matrix L2L (the same operations, in the same order, as a
 // level-by-level downward pass; boxes above the leaf are shifted once per
 // leaf below them, which costs no waiting), and stored over the leaf's M2L part.
 template <int R>
 __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a) {
     __shared__ int s_path[kFmmMaxDepth];
     __shared__ int s_depth;
+    __shared__ float4 s_sv[32];
     if (a.done != nullptr && *a.done) return;
     const int leaf = blockIdx.x, lane = threadIdx.x;
     const int box = a.leaf_box[leaf];
@@ -399,7 +447,8 @@ __global__ void __launch_bounds__(32) fmm_l2l_kernel(FmmArgs a) {
         cdf v = cdf_of(a.loc[((size_t)r * a.nbox + s_path[D - 1]) * kFmmP + lane]);
         for (int d = D - 2; d >= 0; --d) {
             const int bx = s_path[d];
-            v = cdf_add(cdf_of(a.loc[((size_t)r * a.nbox + bx) * kFmmP + lane]), l2l_binom(v, a.quad[bx], lane));
+            v = cdf_add(cdf_of(a.loc[((size_t)r * a.nbox + bx) * kFmmP + lane]),
+                        l2l_pascal(v, a.quad[bx], lane, a.bUp, s_sv));
         }
         a.loc[((size_t)r * a.nbox + box) * kFmmP + lane] = cdf_pack(v);
     }
@@ -594,6 +643,321 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_kernel(FmmArgs a) {
     }
 }
 
+// The powers t^k, k < P, of every node about the centre of its leaf in units
+// of the leaf width (t = (s - c)/r), double-float complex, [node][k] in sorted
+// order: formed once per tree, read by every P2M.
+__global__ void fmm_tp_build_kernel(FmmArgs a, float4* __restrict__ tp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int box = a.node_box[i];
+    const double2 c = a.center[box];
+    const double ir = 1.0 / a.width[box];
+    const double2 p = a.ps[i];
+    const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+    cdf v = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+    float4* out = tp + (size_t)i * kFmmP;
+    for (int k = 0; k < kFmmP; ++k) {
+        out[k] = cdf_pack(v);
+        v = cdf_mul(v, t);
+    }
+}
+
+// ---- Near-field operator cache.  The geometry of a handle is fixed for all
+// its products, so the near-field part of z = E(q x), the matrix
+//   Q_ij = q_j / (eta_i - eta_j)   (i = j: 0)
+// over each work item's targets i (a chunk of tn <= 32 nodes of a leaf) and
+// sources j (the nodes of its neighbour leaves, in neighbour order), is
+// formed once, in double-float from the exact three-float coordinates like
+// the near-field kernel above, and each product then only reads it:
+//   z_i = sum_j x_j Q_ij.
+// Layout per item, for source pairs p = (2p, 2p + 1) and targets (lanes):
+//   nq_re[off + p tn + lane] = (Re Q hi of 2p, of 2p+1, Re Q lo of 2p, of 2p+1)
+// and nq_im likewise, so a float4 load gives the packed double-float operand
+// of the two sources.  A product that needs only Im z (f_B with real A)
+// reads nq_im alone: 8 bytes per pair.
+
+// S (near sources) and tn (targets) of work item `it`; s_beg/s_cum (when
+// given) receive the first source and the running count of each neighbour leaf.
+__device__ __forceinline__ void nq_item_shape(const FmmArgs& a, int it, int* S, int* tn, int* s_beg, int* s_cum,
+                                              int* nn_out) {
+    const int2 item = a.items[it];
+    const int leaf = item.x;
+    *tn = min(32, a.leaf_start[leaf + 1] - item.y);
+    const int n0 = a.nl_start[leaf], nn = min(a.nl_start[leaf + 1] - n0, kFmmMaxNbr);
+    int c = 0;
+    for (int e = 0; e < nn; ++e) {
+        const int nl = a.nl_leaf[n0 + e];
+        if (s_beg) {
+            s_beg[e] = a.leaf_start[nl];
+            s_cum[e] = c;
+        }
+        c += a.leaf_start[nl + 1] - a.leaf_start[nl];
+    }
+    if (s_cum) s_cum[nn] = c;
+    *S = c;
+    if (nn_out) *nn_out = nn;
+}
+
+__global__ void fmm_nq_count_kernel(FmmArgs a, long long* cnt, long long* scnt) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nitems) return;
+    int S, tn;
+    nq_item_shape(a, it, &S, &tn, nullptr, nullptr, nullptr);
+    cnt[it] = (long long)((S + 1) / 2) * tn;
+    scnt[it] = S;
+}
+
+// off[i] = cnt[0] + ... + cnt[i - 1] for i <= n (one block of 1024 threads,
+// each a contiguous range, a block scan of the range sums in between).
+__global__ void __launch_bounds__(1024) fmm_nq_scan_kernel(const long long* __restrict__ cnt, int n,
+                                                            long long* __restrict__ off) {
+    __shared__ long long s[1024];
+    const int t = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+    long long sum = 0;
+    for (int i = b0; i < b1; ++i) sum += cnt[i];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const long long v = (t >= o) ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    long long run = (t == 0) ? 0 : s[t - 1];
+    for (int i = b0; i < b1; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (t == 1023) off[n] = s[1023];
+}
+
+// One block per work item, warp w taking its share of the source pairs.
+__global__ void __launch_bounds__(kFmmNT) fmm_nq_build_kernel(FmmArgs a, const double2* __restrict__ q,
+                                                              const long long* __restrict__ off,
+                                                              const long long* __restrict__ soff,
+                                                              float4* __restrict__ nq_re,
+                                                              float4* __restrict__ nq_im,
+                                                              int4* __restrict__ nq_item,
+                                                              int* __restrict__ nq_src) {
+    __shared__ float s_c[kFmmWarps][6][32];   // x1, x2, x3, y1, y2, y3 of the tile's sources
+    __shared__ float s_q[kFmmWarps][4][32];   // q: re.h, re.l, im.h, im.l
+    __shared__ int s_j[kFmmWarps][32];
+    __shared__ int s_cum[kFmmMaxNbr + 1];
+    __shared__ int s_beg[kFmmMaxNbr];
+    __shared__ int s_S, s_tn, s_nn;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int S, tn, nn;
+        nq_item_shape(a, it, &S, &tn, s_beg, s_cum, &nn);
+        s_S = S;
+        s_tn = tn;
+        s_nn = nn;
+    }
+    __syncthreads();
+    const int S = s_S, tn = s_tn, nn = s_nn;
+    const int src0 = (int)soff[it];
+    if (threadIdx.x == 0) nq_item[it] = make_int4(S, tn, src0, 0);
+    for (int qq = threadIdx.x; qq < S; qq += blockDim.x) {  // the item's source list
+        int e = 0;
+        while (e + 1 < nn && s_cum[e + 1] <= qq) ++e;
+        nq_src[src0 + qq] = s_beg[e] + (qq - s_cum[e]);
+    }
+    const int i = a.items[it].y + min(lane, tn - 1);
+    const float4 pa = a.p3[i];
+    const float2 pb = a.p3b[i];
+    const float2 tx1 = f2(pa.x), tx2 = f2(pa.y), tx3 = f2(pa.z), ty1 = f2(pa.w), ty2 = f2(pb.x), ty3 = f2(pb.y);
+    const int npair = (S + 1) >> 1;
+    const int p0 = (int)((long long)npair * wid / kFmmWarps), p1 = (int)((long long)npair * (wid + 1) / kFmmWarps);
+    const long long base = off[it];
+    for (int ps = p0; ps < p1; ps += 16) {
+        __syncwarp();
+        const int np = min(16, p1 - ps);
+        const int cnt = min(2 * np, S - 2 * ps);  // sources of this tile
+        {
+            const int qq = 2 * ps + min(lane, cnt - 1);
+            int e = 0;
+            while (e + 1 < nn && s_cum[e + 1] <= qq) ++e;
+            const int j = s_beg[e] + (qq - s_cum[e]);
+            const float4 c4 = a.p3[j];
+            const float2 c2 = a.p3b[j];
+            s_c[wid][0][lane] = c4.x;
+            s_c[wid][1][lane] = c4.y;
+            s_c[wid][2][lane] = c4.z;
+            s_c[wid][3][lane] = c4.w;
+            s_c[wid][4][lane] = c2.x;
+            s_c[wid][5][lane] = c2.y;
+            s_j[wid][lane] = (lane < cnt) ? j : -1;
+            const double2 qj = q[a.perm[j]];
+            const df qr = df_split(qj.x), qi = df_split(qj.y);
+            s_q[wid][0][lane] = qr.h;
+            s_q[wid][1][lane] = qr.l;
+            s_q[wid][2][lane] = qi.h;
+            s_q[wid][3][lane] = qi.l;
+        }
+        __syncwarp();
+        for (int pp = 0; pp < np; ++pp) {
+            const float2 qx1 = reinterpret_cast<const float2*>(s_c[wid][0])[pp];
+            const float2 qx2 = reinterpret_cast<const float2*>(s_c[wid][1])[pp];
+            const float2 qx3 = reinterpret_cast<const float2*>(s_c[wid][2])[pp];
+            const float2 qy1 = reinterpret_cast<const float2*>(s_c[wid][3])[pp];
+            const float2 qy2 = reinterpret_cast<const float2*>(s_c[wid][4])[pp];
+            const float2 qy3 = reinterpret_cast<const float2*>(s_c[wid][5])[pp];
+            const int2 jj = reinterpret_cast<const int2*>(s_j[wid])[pp];
+            const df2 dx = diff3_2(tx1, tx2, tx3, qx1, qx2, qx3);
+            const df2 dy = diff3_2(ty1, ty2, ty3, qy1, qy2, qy3);
+            const float2 px = mul2(dx.h, dx.h);
+            float2 ex = fma2(dx.h, dx.h, neg2(px));
+            ex = fma2(dx.h, add2(dx.l, dx.l), ex);
+            const float2 py = mul2(dy.h, dy.h);
+            float2 ey = fma2(dy.h, dy.h, neg2(py));
+            ey = fma2(dy.h, add2(dy.l, dy.l), ey);
+            float2 rh, re;
+            two_sum2(px, py, rh, re);
+            const float2 rl = add2(add2(ex, ey), re);
+            float2 y = make_float2(recip_f32(rh.x), recip_f32(rh.y));
+            y.x = (jj.x == i || jj.x < 0) ? 0.f : y.x;  // i = j excluded (Eq. fmm-E); padding
+            y.y = (jj.y == i || jj.y < 0) ? 0.f : y.y;
+            float2 ee = fma2(neg2(rh), y, f2(1.0f));
+            ee = fma2(neg2(rl), y, ee);
+            const df2 inv{y, mul2(y, ee)};
+            const df2 ar = df2_mul(dx, inv), ai = df2_mul(dy, inv);  // 1/d = ar - i ai
+            const df2 qre{reinterpret_cast<const float2*>(s_q[wid][0])[pp], reinterpret_cast<const float2*>(s_q[wid][1])[pp]};
+            const df2 qim{reinterpret_cast<const float2*>(s_q[wid][2])[pp], reinterpret_cast<const float2*>(s_q[wid][3])[pp]};
+            // q (ar - i ai) = (qre ar + qim ai) + i (qim ar - qre ai)
+            df2 Qr = df2_mul(qre, ar), Qi = df2_mul(qim, ar);
+            df2_acc(Qr, df2_mul(qim, ai));
+            df2_dec(Qi, df2_mul(qre, ai));
+            if (lane < tn) {
+                const size_t o = (size_t)(base + (long long)(ps + pp) * tn + lane);
+                nq_re[o] = make_float4(Qr.h.x, Qr.h.y, Qr.l.x, Qr.l.y);
+                nq_im[o] = make_float4(Qi.h.x, Qi.h.y, Qi.l.x, Qi.l.y);
+            }
+        }
+    }
+}
+
+// The near field of z = E(q x) from the cache: one block per work item, warp w
+// taking its share of the source pairs in chunks of up to 32 pairs, lane =
+// target.  Each warp starts from the item's descriptor and source list (no
+// walk over the neighbour leaves) and issues the loads of its first cache
+// entries before it gathers the chunk's x into shared memory, so that the
+// streams of cache entries and of x overlap; even and odd sources in the two
+// halves of packed float2 sums, added at the end, then the warps' sums in
+// warp order.  COMP = 1: Im z only (Re z written as 0).
+constexpr int kNqChunk = 32;   // source pairs per chunk (64 sources)
+constexpr int kNqAhead = 8;    // cache entries loaded before the gather of x
+
+template <int R, int COMP>
+__global__ void __launch_bounds__(kFmmNT) fmm_near_cached_kernel(FmmArgs a, const long long* __restrict__ off,
+                                                                 const int4* __restrict__ nq_item,
+                                                                 const int* __restrict__ nq_src,
+                                                                 const float4* __restrict__ nq_re,
+                                                                 const float4* __restrict__ nq_im) {
+    __shared__ float s_x[kFmmWarps][R][2][2 * kNqChunk];
+    __shared__ double2 s_z[kFmmWarps][R][32];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x;
+    const int4 d = __ldg(nq_item + it);  // (S, tn, first source)
+    const long long o0 = __ldg(off + it);
+    if (a.done != nullptr && *a.done) return;
+    const int S = d.x, tn = d.y;
+    const int npair = (S + 1) >> 1;
+    const int p0 = (int)((long long)npair * wid / kFmmWarps), p1 = (int)((long long)npair * (wid + 1) / kFmmWarps);
+    const bool act = lane < tn;
+    const long long base = o0 + lane;
+    df2 are[R], aim[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) are[r] = aim[r] = df2{f2(0.f), f2(0.f)};
+    for (int ps = p0; ps < p1; ps += kNqChunk) {
+        const int np = min(kNqChunk, p1 - ps);
+        // the first cache entries of the chunk, before the gather of x
+        float4 vi[kNqAhead], vr[kNqAhead];
+#pragma unroll
+        for (int u = 0; u < kNqAhead; ++u) {
+            if (act && u < np) {
+                const size_t o = (size_t)(base + (long long)(ps + u) * tn);
+                vi[u] = __ldcg(nq_im + o);
+                if (COMP == 0) vr[u] = __ldcg(nq_re + o);
+            }
+        }
+        {  // x of the chunk's sources (two per lane)
+            const int cnt = min(2 * np, S - 2 * ps);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = lane + 32 * h;
+                if (q < 2 * np) {
+                    const int j = __ldg(nq_src + d.z + 2 * ps + min(q, cnt - 1));
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float2 xv = (q < cnt) ? a.xs[(size_t)r * a.N + j] : make_float2(0.f, 0.f);
+                        s_x[wid][r][0][q] = xv.x;
+                        s_x[wid][r][1][q] = xv.y;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (act) {
+#pragma unroll
+            for (int u = 0; u < kNqAhead; ++u) {
+                if (u < np) {
+                    const df2 Qi{make_float2(vi[u].x, vi[u].y), make_float2(vi[u].z, vi[u].w)};
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const df2 xv{reinterpret_cast<const float2*>(s_x[wid][r][0])[u],
+                                     reinterpret_cast<const float2*>(s_x[wid][r][1])[u]};
+                        if (COMP == 0)
+                            df2_acc(are[r], df2_mul(xv, df2{make_float2(vr[u].x, vr[u].y),
+                                                            make_float2(vr[u].z, vr[u].w)}));
+                        df2_acc(aim[r], df2_mul(xv, Qi));
+                    }
+                }
+            }
+#pragma unroll 8
+            for (int pp = kNqAhead; pp < np; ++pp) {
+                const size_t o = (size_t)(base + (long long)(ps + pp) * tn);
+                const float4 wi = __ldcg(nq_im + o);
+                const df2 Qi{make_float2(wi.x, wi.y), make_float2(wi.z, wi.w)};
+                df2 Qr{f2(0.f), f2(0.f)};
+                if (COMP == 0) {
+                    const float4 wr = __ldcg(nq_re + o);
+                    Qr = df2{make_float2(wr.x, wr.y), make_float2(wr.z, wr.w)};
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const df2 xv{reinterpret_cast<const float2*>(s_x[wid][r][0])[pp],
+                                 reinterpret_cast<const float2*>(s_x[wid][r][1])[pp]};
+                    if (COMP == 0) df2_acc(are[r], df2_mul(xv, Qr));
+                    df2_acc(aim[r], df2_mul(xv, Qi));
+                }
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const df sr = df_add(df{are[r].h.x, are[r].l.x}, df{are[r].h.y, are[r].l.y});
+        const df si = df_add(df{aim[r].h.x, aim[r].l.x}, df{aim[r].h.y, aim[r].l.y});
+        s_z[wid][r][lane] = make_double2((double)sr.h + (double)sr.l, (double)si.h + (double)si.l);
+    }
+    __syncthreads();
+    if (wid == 0 && act) {
+        const int i = a.items[it].y + lane;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            double2 v = s_z[0][r][lane];
+            for (int w = 1; w < kFmmWarps; ++w) {
+                v.x += s_z[w][r][lane].x;
+                v.y += s_z[w][r][lane].y;
+            }
+            a.zn[(size_t)r * a.N + i] = v;
+        }
+    }
+}
+
 // L2P by Horner's rule in double-float plus the near-field sum; one thread per
 // node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
 // same coefficients).  EPI: the operator epilogue of the product is applied at
@@ -653,6 +1017,9 @@ float4 cdf_host(const cld& v) {
 // in long double: no library power functions, whose long double forms are
 // slow where long double is emulated in software.
 constexpr int kFmmHSlots = kFmmP * kFmmP / 2;
+constexpr int kFmmSSlots = 49 * 2 * kFmmP;
+// then the L2L Pascal table C(l,m) at [l][m] (double-float, zero outside the
+// triangle), kFmmHSlots float4 slots
 
 void translation_tables(std::vector<float4>* tab) {
     const int P = kFmmP, PP = 2 * kFmmP + 1;
@@ -661,7 +1028,14 @@ void translation_tables(std::vector<float4>* tab) {
         C[(size_t)n * PP] = 1.0L;
         for (int k = 1; k <= n; ++k) C[(size_t)n * PP + k] = C[(size_t)(n - 1) * PP + k - 1] + C[(size_t)(n - 1) * PP + k];
     }
-    tab->assign(kFmmHSlots + 49 * 2 * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    tab->assign(2 * kFmmHSlots + kFmmSSlots, make_float4(0.f, 0.f, 0.f, 0.f));
+    float* BU = reinterpret_cast<float*>(tab->data() + kFmmHSlots + kFmmSSlots);  // [l][m] = C(l, m)
+    for (int r = 0; r < P; ++r)
+        for (int c = 0; c < P; ++c) {
+            const long double up = (r >= c) ? C[(size_t)r * PP + c] : 0.0L;  // C(l = r, m = c)
+            BU[2 * (r * P + c)] = (float)up;
+            BU[2 * (r * P + c) + 1] = (float)(up - (long double)(float)up);
+        }
     float* H = reinterpret_cast<float*>(tab->data());  // [k][l] (hi, lo)
     for (int k = 0; k < P; ++k)
         for (int l = 0; l < P; ++l) {
@@ -727,11 +1101,19 @@ void release_fmm(Boundary& b) {
         }
         if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
         if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
-        if (b.fmm->arena || b.fmm->sync) {  // once no stream uses them
+
+        if (b.fmm->arena || b.fmm->sync || b.fmm->nq_re || b.fmm->tp) {  // once no stream uses them
             cudaDeviceSynchronize();
             cudaGetLastError();
             pool_free(b.fmm->arena, 0);
             pool_free(b.fmm->sync, 0);
+            pool_free(b.fmm->nq_off, 0);
+            pool_free(b.fmm->nq_item, 0);
+            pool_free(b.fmm->nq_src, 0);
+            pool_free(b.fmm->nq_re, 0);
+            pool_free(b.fmm->nq_im, 0);
+            pool_free(b.fmm->xs, 0);
+            pool_free(b.fmm->tp, 0);
         }
         delete b.fmm;
         b.fmm = nullptr;
@@ -1036,7 +1418,7 @@ static int fmm_tree_host(const Boundary& b, FmmTree* t, cudaStream_t st) {
     return GNK_OK;
 }
 
-int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st) {
+int fmm_device_tables(const float2** m2lH, const float4** m2lS, const float2** bUp, cudaStream_t st) {
     static std::mutex mu;
     static std::vector<float4*> per_device;  // indexed by device, never freed
     int dev = 0;
@@ -1063,6 +1445,7 @@ int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st)
     }
     *m2lH = reinterpret_cast<const float2*>(per_device[dev]);
     *m2lS = per_device[dev] + kFmmHSlots;
+    *bUp = reinterpret_cast<const float2*>(per_device[dev] + kFmmHSlots + kFmmSSlots);
     return GNK_OK;
 }
 
@@ -1075,6 +1458,10 @@ static int fmm_high_priority() {
     }
     return greatest;
 }
+
+static void fmm_args(const Boundary& b, FmmArgs& a);
+
+constexpr double kTpMaxBytes = 4.0 * (1 << 30);
 
 // Builds the tree of the handle's nodes (once) with workspace for kMaxRHS
 // right-hand sides: on the device when the lookup grids fit, else on the host.
@@ -1090,7 +1477,7 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     t->R = kMaxRHS;
     int rc = fmm_tree_device(b, t, st);
     if (rc == kFmmUseHost) rc = fmm_tree_host(b, t, st);
-    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2lH, &t->m2lS, st);
+    if (rc == GNK_OK) rc = fmm_device_tables(&t->m2lH, &t->m2lS, &t->bUp, st);
     if (rc == GNK_OK) {  // the upward pass's child counts, all zero
         const size_t nsync = (size_t)t->nbox;
         if (pool_alloc(reinterpret_cast<void**>(&t->sync), nsync * sizeof(int), st) != cudaSuccess ||
@@ -1100,6 +1487,21 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
             rc = GNK_ENOMEM;
         }
     }
+    // the powers of the P2M: 512 bytes per node, below kTpMaxBytes (else P2M
+    // forms them itself)
+    if (rc == GNK_OK && (double)b.N * kFmmP * sizeof(float4) <= kTpMaxBytes &&
+        pool_alloc(reinterpret_cast<void**>(&t->tp), (size_t)b.N * kFmmP * sizeof(float4), st) == cudaSuccess) {
+        FmmArgs a;
+        b.fmm = t;
+        fmm_args(b, a);
+        fmm_tp_build_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a, t->tp);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("FMM: launch of the power table failed");
+            rc = GNK_ECUDA;
+        }
+    }
+    cudaGetLastError();
     if (rc == GNK_OK &&
         (cudaStreamCreateWithPriority(&t->aux, cudaStreamNonBlocking, fmm_high_priority()) != cudaSuccess ||
          cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -1115,23 +1517,24 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
 
 // FP32-pipe instructions of one FMM product, for the roofline.  M2L, per pair
 // and lane: 32 (2 Dekker products and 2 compensated sums, 24) for the real
-// Pascal matrix, the two complex scalings (38 each) and the sum (22); 742 per
-// lane for an M2M or L2L binomial transform (31 passes of a double-float
-// complex addition, 22 each, and two exact scalings, 30 each); P2M: 36 per
+// Pascal matrix, the two complex scalings (38 each) and the sum (22); 840 per
+// lane for an L2L transform (32 terms of the Pascal sum at 24 each, two exact
+// scalings at 30 and two double-float additions), 742 for an M2M (31 passes
+// of a double-float complex addition, 22 each, and the two scalings); P2M: 36 per
 // complex double-float power (47 per node: 32 orders, the squarings to t^8 in
 // each warp, t^16 and t^24) and 48 R per node and order for the sums; L2P:
 // 58 R per node and order (a complex product and sum), twice that with the
 // derivative.
-// which = 0: M2L; 1: the upward pass (P2M and M2M); 2: L2L; 3: L2P; 4: L2P
-// with the derivative.  (The near field: fmm_near_instr.)
+// which = 0: M2L; 1: the upward pass (P2M and the M2M climb); 2: L2L; 3: L2P;
+// 4: L2P with the derivative.  (The near field: fmm_near_instr.)
 double fmm_instr(const Boundary& b, int R, int which) {
     const FmmTree* t = b.fmm;
     if (!t) return 0.0;
-    const double P = kFmmP, binom = 742.0 * P, m2l = (24.0 * P + 98.0) * P;
+    const double P = kFmmP, m2m = 742.0 * P, l2l = 840.0 * P, m2l = (24.0 * P + 98.0) * P;
     switch (which) {
         case 0: return R * m2l * (double)t->m2l_pairs;
-        case 1: return R * binom * (double)t->m2m_pairs + (double)b.N * (36.0 * 47.0 + 48.0 * R * P);
-        case 2: return R * binom * (double)t->nleaf * (t->L - 2);
+        case 1: return R * m2m * (double)t->m2m_pairs + (double)b.N * (t->tp ? 48.0 * R * P : 36.0 * 47.0 + 48.0 * R * P);
+        case 2: return R * l2l * (double)t->nleaf * (t->L - 2);
         default: return R * (double)b.N * P * 58.0 * (which == 4 ? 2.0 : 1.0);
     }
 }
@@ -1140,27 +1543,114 @@ double fmm_near_instr(const Boundary& b, int R) {
     return b.fmm ? (49.0 + 48.0 * R) * (double)b.fmm->near_pairs : 0.0;
 }
 
+// The cached near field per pair and right-hand side: a double-float product
+// (4) and a compensated accumulation (8) per part of z; bytes: the cached
+// entries read (8 per part and pair).
+double fmm_near_cached_instr(const Boundary& b, int R, int comp) {
+    return b.fmm ? 12.0 * R * (comp == 1 ? 1.0 : 2.0) * (double)b.fmm->near_pairs : 0.0;
+}
+
+double fmm_near_cached_bytes(const Boundary& b, int R, int comp) {
+    // cached entries, x in (8 bytes) and z out (16 bytes) per node and right-hand side
+    return b.fmm ? 16.0 * (double)b.fmm->nq_slots * (comp == 1 ? 1.0 : 2.0) + 24.0 * R * b.N : 0.0;
+}
+
+// Forms the near-field operator cache of the products z = E(q x) once per
+// handle (count, scan, allocate, build); state -1 when it would exceed
+// kNqMaxBytes or when its allocation fails (the products then compute the
+// near field directly).
+constexpr double kNqMaxBytes = 16.0 * (1 << 30);
+
+static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
+    FmmTree* t = b.fmm;
+    if (t->nq_state != 0) return GNK_OK;
+    t->nq_state = -1;
+    if (t->nitems <= 0) return GNK_OK;
+    FmmArgs a;
+    fmm_args(b, a);
+    const size_t ni = (size_t)t->nitems;
+    long long *cnt = nullptr, *scnt = nullptr, *soff = nullptr;
+    if (pool_alloc(reinterpret_cast<void**>(&cnt), 2 * ni * sizeof(long long), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&soff), (ni + 1) * sizeof(long long), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_off), (ni + 1) * sizeof(long long), st) != cudaSuccess) {
+        cudaGetLastError();
+        pool_free(cnt, st);
+        pool_free(soff, st);
+        return GNK_OK;
+    }
+    scnt = cnt + ni;
+    fmm_nq_count_kernel<<<(t->nitems + 255) / 256, 256, 0, st>>>(a, cnt, scnt);
+    fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(cnt, t->nitems, t->nq_off);
+    fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(scnt, t->nitems, soff);
+    GNK_TRY_CUDA(cudaGetLastError());
+    count_launches(3);
+    long long tot[2] = {0, 0};
+    GNK_TRY_CUDA(cudaMemcpyAsync(&tot[0], t->nq_off + t->nitems, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaMemcpyAsync(&tot[1], soff + t->nitems, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    pool_free(cnt, st);
+    const long long slots = tot[0], nsrc = tot[1];
+    const size_t bytes = (size_t)slots * sizeof(float4);
+    if (slots <= 0 || nsrc <= 0 || nsrc > INT32_MAX || 2.0 * (double)bytes > kNqMaxBytes) {
+        pool_free(soff, st);
+        return GNK_OK;
+    }
+    if (pool_alloc(reinterpret_cast<void**>(&t->nq_re), bytes, st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_im), bytes, st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_item), ni * sizeof(int4), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_src), (size_t)nsrc * sizeof(int), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->xs), (size_t)kMaxRHS * b.N * sizeof(float2), st) != cudaSuccess) {
+        cudaGetLastError();
+        pool_free(soff, st);
+        pool_free(t->nq_re, st);
+        pool_free(t->nq_im, st);
+        pool_free(t->nq_item, st);
+        pool_free(t->nq_src, st);
+        pool_free(t->xs, st);
+        t->nq_re = t->nq_im = nullptr;
+        t->nq_item = nullptr;
+        t->nq_src = nullptr;
+        t->xs = nullptr;
+        return GNK_OK;
+    }
+    t->nq_slots = slots;
+    const ProfToken tok = prof_begin(st, PK_OTHER);
+    fmm_nq_build_kernel<<<t->nitems, kFmmNT, 0, st>>>(a, b.q, t->nq_off, soff, t->nq_re, t->nq_im, t->nq_item,
+                                                      t->nq_src);
+    GNK_TRY_CUDA(cudaGetLastError());
+    prof_end(tok, PK_OTHER, 0.0, st);
+    count_launches(1);
+    pool_free(soff, st);
+    t->nq_state = 1;
+    return GNK_OK;
+}
+
 // One FMM product on the argument block `a` (weights, outputs set by the caller):
 // gather, the far-field chain on the high-priority stream, the near field on
 // `st`, and L2P after they join.  EF: also the sums of w/d^2 (to a.outF).
 static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const ReduceArgs* epi, cudaStream_t st,
-                       int* nlaunch) {
+                       int* nlaunch, int cached = -1) {
     const FmmTree* t = b.fmm;
     fmm_gather_kernel<<<(b.N + 255) / 256, 256, 0, st>>>(a);
     GNK_TRY_CUDA(cudaEventRecord(t->ev_fork, st));
     GNK_TRY_CUDA(cudaStreamWaitEvent(t->aux, t->ev_fork, 0));
     cudaStream_t fs = t->aux;
     int launches = 1;
-    // the far field on its stream: the upward pass (P2M and the M2M chain),
-    // M2L for every box, L2L per leaf
+    // the far field on its stream: the upward pass (P2M and the M2M climb in
+    // one launch), M2L for every box, L2L per leaf.  (Running the finest
+    // level's M2L on a third stream beside the climb measured slower: the two
+    // compete for the same SMs.)
     const ProfToken toku = prof_begin(fs, PK_FMMUP);
-    if (R == 2)
-        fmm_up_kernel<2><<<t->nleaf, kFmmUT, 0, fs>>>(a);
+    if (R == 2 && a.tp)
+        fmm_up_kernel<2, true><<<t->nleaf, kFmmUT, 0, fs>>>(a);
+    else if (R == 2)
+        fmm_up_kernel<2, false><<<t->nleaf, kFmmUT, 0, fs>>>(a);
+    else if (a.tp)
+        fmm_up_kernel<1, true><<<t->nleaf, kFmmUT, 0, fs>>>(a);
     else
-        fmm_up_kernel<1><<<t->nleaf, kFmmUT, 0, fs>>>(a);
+        fmm_up_kernel<1, false><<<t->nleaf, kFmmUT, 0, fs>>>(a);
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(toku, PK_FMMUP, 0.0, fs, fmm_instr(b, R, 1));
-    // M2L: the far field stands in for all R N (N - 1) pair evaluations of the product
     const ProfToken tokm = prof_begin(fs, PK_FMM);
     if (R == 2)
         fmm_m2l_kernel<2><<<t->nbox, kFmmUT, 0, fs>>>(a);
@@ -1180,9 +1670,20 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
         ++launches;
     }
     GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
-    // near field on the caller's stream
+    // near field on the caller's stream (from the operator cache when `cached`
+    // is 0 (both parts of z) or 1 (Im z only))
     const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
-    if (R == 2 && EF)
+    if (cached >= 0) {
+        const long long* off = t->nq_off;
+        if (R == 2 && cached == 1)
+            fmm_near_cached_kernel<2, 1><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+        else if (R == 2)
+            fmm_near_cached_kernel<2, 0><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+        else if (cached == 1)
+            fmm_near_cached_kernel<1, 1><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+        else
+            fmm_near_cached_kernel<1, 0><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+    } else if (R == 2 && EF)
         fmm_near_kernel<2, true><<<t->nitems, kFmmNT, 0, st>>>(a);
     else if (R == 2)
         fmm_near_kernel<2, false><<<t->nitems, kFmmNT, 0, st>>>(a);
@@ -1192,7 +1693,9 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
         fmm_near_kernel<1, false><<<t->nitems, kFmmNT, 0, st>>>(a);
     ++launches;
     GNK_TRY_CUDA(cudaGetLastError());
-    prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st, fmm_near_instr(b, R) * (EF ? 2.0 : 1.0));
+    prof_end(tokn, PK_FMMNEAR, (double)R * t->near_pairs, st,
+             cached >= 0 ? fmm_near_cached_instr(b, R, cached) : fmm_near_instr(b, R) * (EF ? 2.0 : 1.0),
+             cached >= 0 ? fmm_near_cached_bytes(b, R, cached) : 0.0);
     GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
     const ProfToken tokp = prof_begin(st, PK_FMML2P);
     const int nb = (b.N + 255) / 256;
@@ -1244,7 +1747,10 @@ static void fmm_args(const Boundary& b, FmmArgs& a) {
     a.node_box = t->node_box;
     a.m2lH = t->m2lH;
     a.m2lS = t->m2lS;
+    a.bUp = t->bUp;
     a.ucnt = t->sync;
+    a.xs = nullptr;
+    a.tp = t->tp;
     a.mult = t->mult;
     a.loc = t->loc;
     a.ws = t->ws;
@@ -1267,8 +1773,18 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     a.out = nullptr;
     a.done = job.done;
     int launches = 0;
+    // products with the handle's own weights q x read the near field from
+    // the operator cache (formed by the first of them)
+    int cached = -1;
+    if (job.mode == W_SCALED && job.s == b.q && !b.plain) {
+        GNK_TRY(ensure_near_cache(b, st));
+        if (b.fmm->nq_state == 1) {
+            cached = pair_component_needed(b, job) == 1 ? 1 : 0;
+            a.xs = b.fmm->xs;
+        }
+    }
     const ReduceArgs e = reduce_args(b, job, 1, 0);  // the epilogue runs inside L2P
-    GNK_TRY(fmm_product(b, a, job.R, false, &e, st, &launches));
+    GNK_TRY(fmm_product(b, a, job.R, false, &e, st, &launches, cached));
     count_launches(launches);
     return GNK_OK;
 }

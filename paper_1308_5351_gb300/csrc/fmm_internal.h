@@ -11,7 +11,10 @@
 namespace gnk {
 
 constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
-constexpr int kFmmLeaf = 32;  // target mean number of nodes per leaf
+#ifndef GNK_FMM_LEAF
+#define GNK_FMM_LEAF 32
+#endif
+constexpr int kFmmLeaf = GNK_FMM_LEAF;  // target mean number of nodes per leaf
 constexpr int kFmmNT = 256;   // threads of the near-field kernel: 8 warps
 
 struct FmmTree {
@@ -41,6 +44,7 @@ struct FmmTree {
     int nitems = 0;
     const float2* m2lH = nullptr;  // M2L: the Pascal matrix C(k+l, l) [k][l] as double-float,
     const float4* m2lS = nullptr;  // and per offset code the two complex scalings (per-device cache)
+    const float2* bUp = nullptr;   // L2L Pascal table C(l,m) [l][m]
     float4* mult = nullptr;     // [R][nbox][P]
     float4* loc = nullptr;      // [R][nbox][P]
     float4* ws = nullptr;       // [R][N] weights in sorted order, double-float complex
@@ -48,6 +52,18 @@ struct FmmTree {
     double2* zf = nullptr;      // [R][N] near-field sums of w/d^2 (gradient products)
     int* node_box = nullptr;    // leaf box of each node in sorted order
     int* sync = nullptr;        // [nbox]: children counted by the upward pass (zero between products)
+    // near-field operator cache of the products z = E(q x) (fixed geometry):
+    // Q_ij = q_j / (eta_i - eta_j) per work item, double-float, for source
+    // pairs x targets; state 0 not formed, 1 formed, -1 not used (too large)
+    int nq_state = 0;
+    long long nq_slots = 0;     // float4 entries of each of nq_re, nq_im
+    long long* nq_off = nullptr;  // per work item: first entry (nitems + 1)
+    int4* nq_item = nullptr;    // per work item: (S sources, tn targets, first source in nq_src, -)
+    int* nq_src = nullptr;      // the items' sources (sorted node indices), item after item
+    float4* nq_re = nullptr;
+    float4* nq_im = nullptr;
+    float2* xs = nullptr;       // [R][N] x in sorted order, double-float (cached products)
+    float4* tp = nullptr;       // [N][P] powers t^k of each node about its leaf centre (P2M), or null
     cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -59,9 +75,10 @@ struct FmmTree {
 constexpr int kFmmUseHost = 1;
 int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st);
 
-// The double-float M2L tables on the current device (formed and uploaded once
-// per device and process): the Pascal matrix C(k+l, l) [P][P] and, per offset
-// code (dx + 3) 7 + (dy + 3), the scalings (-1)^(k+1) delta^-(k+1) and delta^-l.
-int fmm_device_tables(const float2** m2lH, const float4** m2lS, cudaStream_t st);
+// The double-float translation tables on the current device (formed and
+// uploaded once per device and process): the M2L Pascal matrix C(k+l, l)
+// [P][P] and, per offset code (dx + 3) 7 + (dy + 3), the scalings
+// (-1)^(k+1) delta^-(k+1) and delta^-l; the L2L Pascal matrix C(l, m).
+int fmm_device_tables(const float2** m2lH, const float4** m2lS, const float2** bUp, cudaStream_t st);
 
 }  // namespace gnk

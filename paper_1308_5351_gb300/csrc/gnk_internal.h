@@ -66,7 +66,8 @@ struct ProfToken {
 ProfToken prof_begin(cudaStream_t st, int kind = -1);
 // `instr`: algorithmic instructions of the launch on its limiting pipe
 // (FP32 pipe for the FP32 and double-float pair kernels, FP64 pipe for the FP64 one).
-long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr = 0.0);
+long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr = 0.0,
+              double bytes = 0.0);
 void prof_skip(long idx);
 // Collect the record indices of the launches made between begin and end
 // (calling thread only), to mark launches that a device flag turned into
@@ -227,6 +228,8 @@ int run_pairsum64(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_pairsum32(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_pairsumdf(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st);
+// 0: both parts of z = E(q x) are read by the job's epilogue; 1: only Im z; 2: only Re z
+int pair_component_needed(const Boundary& b, const PairJob& job);
 int pair_blocks_per_sm(int precision);
 
 // ---------------------------------------------------------------- circulant / pointwise

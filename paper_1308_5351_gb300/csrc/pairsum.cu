@@ -950,7 +950,7 @@ int pair_blocks_per_sm(int precision) {
 
 // The part of z = E(q x) an epilogue reads: f_B reads Im(A z) and f_C reads
 // Re(A z), which with Im A = 0 are A Im z and A Re z.
-static int component_needed(const Boundary& b, const PairJob& job) {
+int pair_component_needed(const Boundary& b, const PairJob& job) {
     if (!b.A_real || job.R != 1 || job.mode != W_SCALED || job.s != b.q) return 0;
     if (job.epi == EPI_IMINUSN || job.epi == EPI_RESID) return 1;
     if (job.epi == EPI_M) return 2;
@@ -965,7 +965,7 @@ cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chun
 int run_pairsum(const Boundary& b, const PairJob& job, int precision, cudaStream_t st) {
     if (precision == GNK_PREC_FMM) return run_fmm(b, job, st);
     PairJob j = job;
-    j.comp = component_needed(b, job);
+    j.comp = pair_component_needed(b, job);
     if (precision == GNK_PREC_FP32) return run_pairsum32(b, j, st);
     if (precision == GNK_PREC_DF32) return run_pairsumdf(b, j, st);
     return run_pairsum64(b, j, st);

@@ -15,6 +15,7 @@ struct Rec {
     int kind;
     double work;
     double instr;
+    double bytes;
     bool skipped;
 };
 
@@ -66,7 +67,7 @@ ProfToken prof_begin(cudaStream_t st, int kind) {
     return t;
 }
 
-long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr) {
+long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double instr, double bytes) {
     if (!t.ev) return -1;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) {
@@ -76,7 +77,7 @@ long prof_end(const ProfToken& t, int kind, double work, cudaStream_t st, double
     cudaEvent_t b = take_event();
     if (!b) return -1;
     cudaEventRecord(b, st);
-    g_recs.push_back(Rec{static_cast<cudaEvent_t>(t.ev), b, kind, work, instr, false});
+    g_recs.push_back(Rec{static_cast<cudaEvent_t>(t.ev), b, kind, work, instr, bytes, false});
     const long id = (long)g_recs.size() - 1;
     if (t_collect) t_ids.push_back(id);
     return id;
@@ -124,9 +125,14 @@ int gnk_profile_query(int kind, long long* launches, double* total_ms, double* w
 }
 
 int gnk_profile_query_ex(int kind, long long* launches, double* total_ms, double* work, double* instr) {
+    return gnk_profile_query_bytes(kind, launches, total_ms, work, instr, nullptr);
+}
+
+int gnk_profile_query_bytes(int kind, long long* launches, double* total_ms, double* work, double* instr,
+                            double* bytes) {
     std::lock_guard<std::mutex> lk(g_mu);
     long long n = 0;
-    double ms = 0.0, wk = 0.0, ins = 0.0;
+    double ms = 0.0, wk = 0.0, ins = 0.0, by = 0.0;
     for (const Rec& r : g_recs) {
         if (r.kind != kind || r.skipped) continue;
         if (cudaEventSynchronize(r.b) != cudaSuccess) {
@@ -143,11 +149,13 @@ int gnk_profile_query_ex(int kind, long long* launches, double* total_ms, double
         ms += t;
         wk += r.work;
         ins += r.instr;
+        by += r.bytes;
     }
     if (launches) *launches = n;
     if (total_ms) *total_ms = ms;
     if (work) *work = wk;
     if (instr) *instr = ins;
+    if (bytes) *bytes = by;
     return GNK_OK;
 }
 

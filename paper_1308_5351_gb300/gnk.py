@@ -49,7 +49,7 @@ EXPORTED = (
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
     "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval", "gnk_profile_mask",
-    "gnk_debug_recip_f64", "gnk_debug_barrier_fault",
+    "gnk_debug_recip_f64", "gnk_debug_barrier_fault", "gnk_profile_query_bytes",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -133,6 +133,9 @@ def load(path: str = LIB_PATH):
     lib.gnk_profile_query_ex.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
+    lib.gnk_profile_query_bytes.argtypes = [I, ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_eval.argtypes = [P, I, P, P, P, P, I, P]
     lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, P, P, P]
     lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
@@ -231,6 +234,15 @@ def gnk_profile_query_ex(kind: int):
     _check(load().gnk_profile_query_ex(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk),
                                        ctypes.byref(ins)))
     return n.value, ms.value, wk.value, ins.value
+
+
+def gnk_profile_query_bytes(kind: int):
+    """(launches, total device ms, total work, pipe instructions, algorithmic bytes)."""
+    n, ms, wk, ins, by = (ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double(),
+                          ctypes.c_double())
+    _check(load().gnk_profile_query_bytes(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk),
+                                          ctypes.byref(ins), ctypes.byref(by)))
+    return n.value, ms.value, wk.value, ins.value, by.value
 
 
 def gnk_version() -> str:

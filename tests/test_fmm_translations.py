@@ -7,8 +7,9 @@ complex-analytic 2-D FMM with expansions scaled by the box width r):
 The kernels do not tabulate a P x P matrix per relative box position:
   * M2M and L2L between a box and a child in quadrant q = 2 qa + qb (child
     centre c1 = c0 + delta r0, delta = g/4, g = (2 qa - 1) + i (2 qb - 1)) are
-    binomial transforms between scalings by powers of g and conj(g), taken as
-    P - 1 passes of one neighbour addition per lane;
+    the real Pascal sums C(m,k) (M2M: P - 1 passes of one neighbour addition
+    per lane) and C(l,m) (L2L: a table [l][m], zero outside the triangle,
+    summed by lane m) between scalings by powers of g and conj(g);
   * M2L is the fixed Pascal matrix C(k+l, l) between two complex scalings.
 These tests emulate those steps in numpy (FP64) and compare them with the
 matrix forms and with expansions formed directly from point sources, so a
@@ -41,8 +42,13 @@ def _gpow(ang, e, s):
     return complex(gr, gi)
 
 
+def _table_up():
+    """The kernels' L2L Pascal table: BU[l][m] = C(l, m) for l >= m, zero elsewhere."""
+    return np.array([[math.comb(l, m) if l >= m else 0 for m in range(P)] for l in range(P)], dtype=float)
+
+
 def _binom_lower(v):
-    """lane m: sum_{k<=m} C(m,k) v_k, by the kernels' passes (pass i adds the left
+    """lane m: sum_{k<=m} C(m,k) v_k, by the M2M passes (pass i adds the left
     neighbour's pre-pass value on lanes m >= i)."""
     v = np.array(v, dtype=complex)
     for i in range(1, P):
@@ -53,14 +59,10 @@ def _binom_lower(v):
 
 
 def _binom_upper(v):
-    """lane m: sum_{l>=m} C(l,m) v_l, by the transposed passes, last first."""
-    v = np.array(v, dtype=complex)
-    for i in range(P - 1, 0, -1):
-        u = np.concatenate([v[1:], [0]])
-        m = np.arange(P)
-        lanes = (m >= i - 1) & (m <= P - 2)
-        v = np.where(lanes, v + u, v)
-    return v
+    """lane m: sum_l BU[l][m] v_l, the L2L Pascal-table sum over a staged vector."""
+    T = _table_up()
+    v = np.asarray(v, dtype=complex)
+    return np.array([sum(T[l, m] * v[l] for l in range(P)) for m in range(P)])
 
 
 def _m2m_binom(a1, q):
@@ -86,7 +88,13 @@ def test_gaussian_powers_are_exact():
             assert _gpow(_gauss_angle(q), e, -2 * e) == (g / 4) ** e
 
 
-def test_binomial_passes_are_pascal_sums():
+def test_pascal_table_is_exact_and_triangular():
+    BU = _table_up()
+    assert BU.max() < 2.0 ** 29  # C(31, 15): exact as a double-float pair
+    assert np.array_equal(np.tril(BU), BU)
+
+
+def test_passes_and_table_are_pascal_sums():
     rng = np.random.default_rng(0)
     v = rng.normal(size=P) + 1j * rng.normal(size=P)
     lo = np.array([sum(math.comb(m, k) * v[k] for k in range(m + 1)) for m in range(P)])
@@ -96,7 +104,7 @@ def test_binomial_passes_are_pascal_sums():
 
 
 @pytest.mark.parametrize("q", range(4))
-def test_m2m_binomial_matches_matrix_form_and_direct_multipole(q):
+def test_m2m_pascal_matches_matrix_form_and_direct_multipole(q):
     """M2M of a child's multipole equals the parent multipole formed directly from
     the child's sources (r0 = width of the parent, r1 = r0/2)."""
     rng = np.random.default_rng(10 + q)
@@ -116,7 +124,7 @@ def test_m2m_binomial_matches_matrix_form_and_direct_multipole(q):
 
 
 @pytest.mark.parametrize("q", range(4))
-def test_l2l_binomial_matches_matrix_form_and_direct_local(q):
+def test_l2l_pascal_matches_matrix_form_and_direct_local(q):
     """L2L of a parent's local expansion (of far sources) equals the child's local
     expansion formed directly from those sources."""
     rng = np.random.default_rng(20 + q)
@@ -174,6 +182,10 @@ def test_planted_mistakes_fail():
     ang = _gauss_angle(3)
     c = np.array([a1[k] * _gpow(ang, k, 0) for k in range(P)])  # g^k instead of conj(g)^k
     wrong = np.array([_binom_lower(c)[m] * _gpow(ang, m, -2 * m) for m in range(P)])
+    assert np.abs(wrong - mat).max() > 1e-3 * np.abs(mat).max()
+    # the L2L table in place of the M2M table (a transposed Pascal matrix)
+    c = np.array([a1[k] * _gpow(8 - ang, k, 0) for k in range(P)])
+    wrong = np.array([_binom_upper(c)[m] * _gpow(ang, m, -2 * m) for m in range(P)])
     assert np.abs(wrong - mat).max() > 1e-3 * np.abs(mat).max()
     dd = 2.0 + 1.0j
     pre_wrong = np.array([(-1) ** k * dd ** (-(k + 1)) for k in range(P)])
