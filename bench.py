@@ -75,7 +75,7 @@ PEAK_BASIS = {
 }
 KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
                "fmm": "fmm_m2l_kernel",
-               "fmm_near": "fmm_near_kernel (double-float near field)",
+               "fmm_near": "fmm_near_cached_kernel (near field from the operator cache)",
                "fmm_l2p": "fmm_l2p_kernel", "fmm_up": "fmm_up_kernel (P2M and the M2M chain)",
                "fmm_l2l": "fmm_l2l_kernel"}
 # DRAM bytes read + written per launch of the kernel at the headline size
@@ -88,6 +88,16 @@ TRAFFIC = {"fmm_near": (2.73e6, "csrc/fmm.cu", None), "fmm": (2.19e6, "csrc/fmm.
 # kinds whose work is pair evaluations actually performed
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm_near")
 ROOF_KINDS = ("pair64", "pair32", "pairdf", "fmm", "fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roof: the measured copy bandwidth of this machine's
+    GB300s when MEASURED_PEAKS.json is present, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
 def source_sha(rel):
@@ -363,7 +373,7 @@ def main():
             G.gnk_profile_enable(True)
         step(opts, bprec)
     torch.cuda.synchronize()
-    prof_all = {k: G.gnk_profile_query_ex(i) for k, i in kinds}
+    prof_all = {k: G.gnk_profile_query_bytes(i) for k, i in kinds}
     G.gnk_profile_enable(False)
     dom_kind = max(ROOF_KINDS, key=lambda k: prof_all[k][1])
 
@@ -390,7 +400,7 @@ def main():
     t_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     gpu_launches = G.gnk_kernel_launches() - launches0
-    prof = {k: G.gnk_profile_query_ex(i) for k, i in kinds}
+    prof = {k: G.gnk_profile_query_bytes(i) for k, i in kinds}
     G.gnk_profile_enable(False)
     t_ms = max_over_ranks(dist, t_ms, dev)
     ms_per_step = t_ms / args.steps
@@ -429,7 +439,7 @@ def main():
             r = step(o, bp)
             e1.record(stream)
             torch.cuda.synchronize()
-            pk = {k: G.gnk_profile_query_ex(i) for k, i in kinds}
+            pk = {k: G.gnk_profile_query_bytes(i) for k, i in kinds}
             G.gnk_profile_enable(False)
             compare[name] = {
                 "time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": r.iterations,
@@ -517,21 +527,29 @@ def main():
 
     # ---- roofline of the dominant kernel (largest device time in the last warm-up
     # step), from its launches in the timed region
-    n_l, ms_l, work, instr = prof[dom_kind]
-    achieved = instr / (ms_l / 1e3) if ms_l > 0 else 0.0
-    peak = PEAK_INSTR[dom_kind]
+    n_l, ms_l, work, instr, nbytes = prof[dom_kind]
     total_prof_ms = sum(v[1] for v in prof_all.values())
+    if nbytes > 0:  # a memory-bound kernel (the near field from its operator cache)
+        hbm, hbm_src = hbm_peak()
+        achieved = nbytes / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
+        bound = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                 "bytes_per_launch": nbytes / max(n_l, 1),
+                 "peak_basis": f"HBM copy bandwidth, {hbm_src}; algorithmic bytes: the cached near-field "
+                               "entries read (8 bytes per pair and part of z) + x in and z out per node"}
+    else:
+        achieved = instr / (ms_l / 1e3) if ms_l > 0 else 0.0
+        peak = PEAK_INSTR[dom_kind]
+        bound = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
+                 "frac": achieved / peak, "peak_basis": PEAK_BASIS[dom_kind] + " (derived from unit counts)"}
     roofline = {
-        "bound": "alu", "kernel": KERNEL_NAME[dom_kind],
-        "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
-        "frac": achieved / peak, "traffic": traffic_of(dom_kind, args)[0],
+        "kernel": KERNEL_NAME[dom_kind], **bound,
+        "traffic": traffic_of(dom_kind, args)[0],
         "traffic_source": traffic_of(dom_kind, args)[1],
         "pair_evals_per_s": work / (ms_l / 1e3) if ms_l > 0 else 0.0,
         "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1),
         "share_of_instrumented_time": {k: v[1] / total_prof_ms for k, v in prof_all.items() if v[0] > 0},
         "instrumented": "timed region: the dominant kernel's launches; shares: every kind in the last "
                         "warm-up step",
-        "peak_basis": PEAK_BASIS[dom_kind],
     }
     cpu = None
     if not args.no_cpu_baseline and ws == 1:

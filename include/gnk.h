@@ -348,33 +348,42 @@ int gnk_cauchy_eval(const gnk_boundary* b, int nz, const double* z,
                     int precision, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Conformal maps onto the unit disk with circular and radial slits, by the
- * FBIE route of Sec. 7, Ex. 3 (the method of the paper's references for that
- * example): for a bounded G, a point alpha of G and theta_k = pi/2 (circular
- * slit) or 0 (radial slit) per boundary (theta_0 = pi/2 for the outer one),
- *   A = e^{i(pi/2 - theta)} (eta - alpha),
+ * Conformal maps onto slit domains by the FBIE route of Sec. 7, Ex. 3 (bounded
+ * G) and Ex. 4 (unbounded G), the method of the paper's references for those
+ * examples: for a point alpha of G and theta_k = pi/2 (circular slit) or 0
+ * (radial slit) per boundary (theta_0 = pi/2 for the outer boundary of a
+ * bounded G),
  *   gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]   (arg continuous along
  *           each boundary),
+ *   bounded G:   A = e^{i(pi/2 - theta)} (eta - alpha),
+ *   unbounded G: A = e^{i(pi/2 - theta)}                  (Eq. A),
  * then (mu, h, h_k) of gnk_fbie on a handle built with this A give the analytic
- * f with A f = gamma + h + i mu and the map
- *   w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z)),
- * |w| = 1 on the outer boundary, w(alpha) = 0, w'(alpha) = e^{-h_0} > 0; a
- * circular-slit boundary maps to |w| = e^{h_k - h_0}, a radial-slit one to
- * arg w = const.
+ * f with A f = gamma + h + i mu (f(inf) = 0 for unbounded G) and the map
+ *   bounded G:   w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z)),
+ *                onto the unit disk: |w| = 1 on the outer boundary, w(alpha) = 0,
+ *                w'(alpha) = e^{-h_0} > 0, a circular-slit boundary maps to
+ *                |w| = e^{h_k - h_0};
+ *   unbounded G: w(z) = (z - alpha) exp(f(z)),
+ *                onto the plane with slits: w(alpha) = 0, w(z) = z + O(1) at
+ *                infinity, a circular-slit boundary maps to |w| = e^{h_k};
+ * a radial-slit boundary maps to arg w = const.
  *
  * gnk_slit_map_data: A (2N doubles) and gamma (N) from eta (2N), alpha (2
- *   doubles, read on the host) and theta (m1 doubles, one per boundary).
+ *   doubles, read on the host), theta (m1 doubles, one per boundary) and
+ *   bounded (1: bounded G, 0: unbounded G).
  * gnk_slit_map: w at the nodes (2N doubles) from gamma, mu, h (N each) and h_k
- *   (m1) of the solve; the handle must be bounded and built with that A.
+ *   (m1) of the solve; the handle must be built with that A (its boundedness
+ *   selects the formula).
  * gnk_slit_map_eval: w at nz points z of G (2 nz doubles in, 2 nz out), f from
- *   the Cauchy formula (gnk_cauchy_eval's sums, precision GNK_PREC_FP64 or
- *   GNK_PREC_DF32).
+ *   the Cauchy formula (gnk_cauchy_eval's sums with f(inf) = 0, precision
+ *   GNK_PREC_FP64 or GNK_PREC_DF32).
  * Arrays may be host or device pointers (host arrays are staged); the calls
- * synchronise `stream`.  GNK_EINVAL for NULL arrays, an unbounded handle, nz < 0
- * or m1, n out of range.
+ * synchronise `stream`.  GNK_EINVAL for NULL arrays, nz < 0 or m1, n out of
+ * range.
  * ------------------------------------------------------------------------- */
 int gnk_slit_map_data(int m1, int n, const double* et, const double* alpha,
-                      const double* theta, double* A, double* gam, void* stream);
+                      const double* theta, int bounded, double* A, double* gam,
+                      void* stream);
 int gnk_slit_map(const gnk_boundary* b, const double* alpha, const double* gam,
                  const double* mu, const double* h, const double* hk, double* w,
                  void* stream);

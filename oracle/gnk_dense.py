@@ -485,21 +485,24 @@ def cauchy_formula(et, etp, n, f_nodes, z, bounded, finf=0.0):
 
 
 # ---------------------------------------------------------------------------
-# Sec. 7, Ex. 3: conformal map of a bounded G onto the unit disk with circular
-# slits (theta = pi/2 on a boundary) and radial slits (theta = 0), by the FBIE
-# route: one solve of Eq. (ie) and h of Eq. (h).  The map formulas are the
-# method the paper cites for this example (its references, not restated in the
-# paper):  with A = e^{i(pi/2 - theta)} (eta - alpha) and
-#   gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]   (arg continuous along
-#   each boundary), the function f with boundary values A f = gamma + h + i mu
-# is analytic in G and
-#   w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z))
-# maps G onto the unit disk (|w| = 1 on the outer boundary, w(alpha) = 0,
-# w'(alpha) = e^{-h_0} > 0) with circular slits |w| = e^{h_j - h_0} and radial
-# slits arg w = const.
+# Sec. 7, Ex. 3 and Ex. 4: conformal maps onto slit domains by the FBIE route:
+# one solve of Eq. (ie) and h of Eq. (h), with theta = pi/2 on a boundary that
+# becomes a circular slit and theta = 0 on one that becomes a radial slit.
+# The map formulas are the method the paper cites for these examples (its
+# references, not restated in the paper); with gamma =
+# -Re[e^{i(pi/2 - theta)} log(eta - alpha)] (arg continuous along each
+# boundary) and the analytic f with boundary values A f = gamma + h + i mu:
+#   bounded G (Ex. 3), A = e^{i(pi/2 - theta)} (eta - alpha), alpha in G:
+#     w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z))
+#     onto the unit disk (|w| = 1 on the outer boundary) with circular slits
+#     |w| = e^{h_j - h_0} and radial slits, w(alpha) = 0, w'(alpha) > 0;
+#   unbounded G (Ex. 4), A = e^{i(pi/2 - theta)} (Eq. A), f(inf) = 0, alpha in G:
+#     w(z) = (z - alpha) exp(f(z))
+#     onto the plane with circular slits |w| = e^{h_j} and radial slits
+#     arg w = -h_j, w(alpha) = 0 and w(z) = z + O(1) at infinity.
 # ---------------------------------------------------------------------------
 
-def slit_map_data(et, n, alpha, theta):
+def slit_map_data(et, n, alpha, theta, bounded=True):
     """A and gamma of the slit map for theta given per boundary component."""
     et = np.asarray(et, dtype=np.complex128)
     N, m1 = _sizes(et, n)
@@ -509,25 +512,30 @@ def slit_map_data(et, n, alpha, theta):
     for k in range(m1):
         d = et[k * n:(k + 1) * n] - alpha
         lg[k * n:(k + 1) * n] = np.log(np.abs(d)) + 1j * np.unwrap(np.angle(d))
-    A = rot * (et - alpha)
+    A = rot * (et - alpha) if bounded else rot.astype(np.complex128)
     gam = -(rot * lg).real
     return A, gam
 
 
-def slit_map(et, etp, n, alpha, theta, z=None):
-    """Boundary values w(eta) of the slit map, the constant c = e^{-h_0}, the
-    per-component h_k, and (if z is given) w at the points z of G by the Cauchy
-    formula of Eq. (cauchy4) applied to f."""
+def slit_map(et, etp, n, alpha, theta, z=None, bounded=True):
+    """Boundary values w(eta) of the slit map, the constant c (e^{-h_0} for
+    bounded G, 1 for unbounded G), the per-component h_k, and (if z is given)
+    w at the points z of G by the Cauchy formula of Eq. (cauchy4) applied to f
+    (with f(inf) = 0 for unbounded G)."""
     et = np.asarray(et, dtype=np.complex128)
     N, m1 = _sizes(et, n)
-    A, gam = slit_map_data(et, n, alpha, theta)
+    A, gam = slit_map_data(et, n, alpha, theta, bounded)
     mu, h, hk = fbie(et, etp, A, n, gam)
-    c = math.exp(-hk[0])
     fb = (gam + h + 1j * mu) / A
-    w = c * (et - alpha) * np.exp((et - alpha) * fb)
     wz = None
+    if bounded:
+        c = math.exp(-hk[0])
+        w = c * (et - alpha) * np.exp((et - alpha) * fb)
+    else:
+        c = 1.0
+        w = (et - alpha) * np.exp(fb)
     if z is not None:
         z = np.asarray(z, dtype=np.complex128)
-        fz = cauchy_formula(et, etp, n, fb, z, True)
-        wz = c * (z - alpha) * np.exp((z - alpha) * fz)
+        fz = cauchy_formula(et, etp, n, fb, z, bounded)
+        wz = c * (z - alpha) * np.exp((z - alpha) * fz) if bounded else (z - alpha) * np.exp(fz)
     return w, c, hk, wz

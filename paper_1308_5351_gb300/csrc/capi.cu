@@ -779,8 +779,8 @@ struct Views {
     }
 };
 
-int gnk_slit_map_data(int m1, int n, const double* et, const double* alpha, const double* theta, double* A,
-                      double* gam, void* stream) {
+int gnk_slit_map_data(int m1, int n, const double* et, const double* alpha, const double* theta, int bounded,
+                      double* A, double* gam, void* stream) {
     cudaGetLastError();
     if (!et || !alpha || !theta || !A || !gam || m1 < 1 || n < 4 || (n % 2) != 0 ||
         (long long)m1 * n > (1LL << 28)) {
@@ -796,7 +796,7 @@ int gnk_slit_map_data(int m1, int n, const double* et, const double* alpha, cons
     if (rc == GNK_OK) rc = vw.add(A, 16 * N, false, st, &dA);
     if (rc == GNK_OK) rc = vw.add(gam, 8 * N, false, st, &dg);
     if (rc == GNK_OK)
-        rc = slit_data(m1, n, (const double2*)det, make_double2(alpha[0], alpha[1]), (const double*)dth,
+        rc = slit_data(m1, n, (const double2*)det, make_double2(alpha[0], alpha[1]), (const double*)dth, bounded,
                        (double2*)dA, (double*)dg, st);
     const bool out[4] = {false, false, true, true};
     return vw.finish(rc, out, st);
@@ -807,8 +807,8 @@ int gnk_slit_map(const gnk_boundary* hd, const double* alpha, const double* gam,
     cudaGetLastError();
     GNK_TRY(check_handle(hd));
     const Boundary& b = hd->b;
-    if (!alpha || !gam || !mu || !h || !hk || !w || !b.bounded) {
-        set_error("gnk_slit_map: NULL array or an unbounded handle");
+    if (!alpha || !gam || !mu || !h || !hk || !w) {
+        set_error("gnk_slit_map: NULL array");
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -822,7 +822,8 @@ int gnk_slit_map(const gnk_boundary* hd, const double* alpha, const double* gam,
     if (rc == GNK_OK) rc = vw.add(w, 16 * N, false, st, &dw);
     if (rc == GNK_OK) rc = slit_nodes_f(b, (const double*)dg, (const double*)dmu, (const double*)dh, b.zbuf, st);
     if (rc == GNK_OK)
-        rc = slit_w(b.et, b.zbuf, b.N, make_double2(alpha[0], alpha[1]), (const double*)dhk, (double2*)dw, st);
+        rc = slit_w(b.et, b.zbuf, b.N, make_double2(alpha[0], alpha[1]), (const double*)dhk, b.bounded,
+                    (double2*)dw, st);
     const bool out[5] = {false, false, false, false, true};
     return vw.finish(rc, out, st);
 }
@@ -837,8 +838,8 @@ int gnk_slit_map_eval(const gnk_boundary* hd, const double* alpha, const double*
         set_error("gnk_slit_map_eval: precision must be GNK_PREC_FP64 or GNK_PREC_DF32, got %d", precision);
         return GNK_EINVAL;
     }
-    if (nz < 0 || !b.bounded) {
-        set_error("gnk_slit_map_eval: nz < 0 or an unbounded handle");
+    if (nz < 0) {
+        set_error("gnk_slit_map_eval: nz < 0");
         return GNK_EINVAL;
     }
     if (nz == 0) return GNK_OK;
@@ -861,7 +862,8 @@ int gnk_slit_map_eval(const gnk_boundary* hd, const double* alpha, const double*
     // f(z) by the Cauchy formula into wz, then w(z) in place
     if (rc == GNK_OK)
         rc = cauchy_eval(b, nz, (const double2*)dz, b.zbuf, make_double2(0.0, 0.0), (double2*)dw, precision, st);
-    if (rc == GNK_OK) rc = slit_w((const double2*)dz, (const double2*)dw, nz, al, (const double*)dhk, (double2*)dw, st);
+    if (rc == GNK_OK)
+        rc = slit_w((const double2*)dz, (const double2*)dw, nz, al, (const double*)dhk, b.bounded, (double2*)dw, st);
     const bool out[6] = {false, false, false, false, false, true};
     return vw.finish(rc, out, st);
 }

@@ -297,11 +297,11 @@ cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chun
                                  cudaStream_t st);
 
 // ---------------------------------------------------------------- slit maps (slitmap.cu)
-int slit_data(int m1, int n, const double2* et, double2 alpha, const double* theta, double2* A, double* gam,
-              cudaStream_t st);
+int slit_data(int m1, int n, const double2* et, double2 alpha, const double* theta, int bounded, double2* A,
+              double* gam, cudaStream_t st);
 int slit_nodes_f(const Boundary& b, const double* gam, const double* mu, const double* h, double2* f,
                  cudaStream_t st);
-int slit_w(const double2* z, const double2* f, int M, double2 alpha, const double* hk, double2* w,
+int slit_w(const double2* z, const double2* f, int M, double2 alpha, const double* hk, int bounded, double2* w,
            cudaStream_t st);
 
 // ---------------------------------------------------------------- Cauchy formula (cauchy_eval.cu)

@@ -1,10 +1,12 @@
-// Conformal maps of a bounded G onto the unit disk with circular slits
-// (theta = pi/2 on a boundary) and radial slits (theta = 0) by the FBIE route
-// (Sec. 7, Ex. 3): with A = e^{i(pi/2 - theta)} (eta - alpha) and
-// gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)] (arg continuous along each
-// boundary), the solution mu and h of Eqs. (ie), (h) give the boundary values
-// A f = gamma + h + i mu of an analytic f, and
-//   w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z)),
+// Conformal maps onto slit domains by the FBIE route (Sec. 7, Ex. 3 and Ex. 4):
+// theta = pi/2 on a boundary that becomes a circular slit, theta = 0 on one that
+// becomes a radial slit, gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)] (arg
+// continuous along each boundary), and the solution mu and h of Eqs. (ie), (h)
+// give the boundary values A f = gamma + h + i mu of an analytic f:
+//   bounded G, A = e^{i(pi/2 - theta)} (eta - alpha):
+//     w(z) = e^{-h_0} (z - alpha) exp((z - alpha) f(z))  (onto the unit disk);
+//   unbounded G, A = e^{i(pi/2 - theta)} (Eq. A), f(inf) = 0:
+//     w(z) = (z - alpha) exp(f(z))                        (w = z + O(1) at infinity);
 // with f inside G from the Cauchy formula (Eq. cauchy4).
 #include <cmath>
 
@@ -30,8 +32,8 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
 // component by a block scan of the wrapped increments (in node order), then
 // A = e^{i(pi/2 - theta)} (eta - alpha) and gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)].
 __global__ void __launch_bounds__(SM_T) slit_data_kernel(const double2* __restrict__ et, int n, double2 alpha,
-                                                         const double* __restrict__ theta, double2* A,
-                                                         double* gam) {
+                                                         const double* __restrict__ theta, int bounded,
+                                                         double2* A, double* gam) {
     __shared__ double s[SM_T];
     __shared__ double carry, phi0;
     const int k = blockIdx.x;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(SM_T) slit_data_kernel(const double2* __restri
             const double arg = phi0 + carry + s[threadIdx.x];
             const double lr = 0.5 * log(d.x * d.x + d.y * d.y);
             const size_t i = (size_t)k * n + p;
-            A[i] = make_double2(cr * d.x - sr * d.y, cr * d.y + sr * d.x);
+            A[i] = bounded ? make_double2(cr * d.x - sr * d.y, cr * d.y + sr * d.x) : make_double2(cr, sr);
             gam[i] = -(cr * lr - sr * arg);
         }
         __syncthreads();
@@ -90,23 +92,27 @@ __global__ void slit_f_kernel(const double2* __restrict__ A, const double* __res
     f[i] = make_double2((re * a.x + im * a.y) / aa, (im * a.x - re * a.y) / aa);
 }
 
-// w = e^{-h_0} (z - alpha) exp((z - alpha) f) for points z with values f (h_0 = hk[0])
+// w at points z with values f: bounded G, e^{-h_0} (z - alpha) exp((z - alpha) f)
+// (h_0 = hk[0]); unbounded G, (z - alpha) exp(f)
 __global__ void slit_w_kernel(const double2* __restrict__ z, const double2* __restrict__ f, int M, double2 alpha,
-                              const double* __restrict__ hk, double2* w) {
+                              const double* __restrict__ hk, int bounded, double2* w) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const double c = exp(-hk[0]);
     const double2 d = make_double2(z[i].x - alpha.x, z[i].y - alpha.y);
-    const double2 ex = cexp2(cmul2(d, f[i]));
-    const double2 v = cmul2(d, ex);
-    w[i] = make_double2(c * v.x, c * v.y);
+    if (bounded) {
+        const double c = exp(-hk[0]);
+        const double2 v = cmul2(d, cexp2(cmul2(d, f[i])));
+        w[i] = make_double2(c * v.x, c * v.y);
+    } else {
+        w[i] = cmul2(d, cexp2(f[i]));
+    }
 }
 
 }  // namespace
 
-int slit_data(int m1, int n, const double2* et, double2 alpha, const double* theta, double2* A, double* gam,
-              cudaStream_t st) {
-    slit_data_kernel<<<m1, SM_T, 0, st>>>(et, n, alpha, theta, A, gam);
+int slit_data(int m1, int n, const double2* et, double2 alpha, const double* theta, int bounded, double2* A,
+              double* gam, cudaStream_t st) {
+    slit_data_kernel<<<m1, SM_T, 0, st>>>(et, n, alpha, theta, bounded ? 1 : 0, A, gam);
     GNK_TRY_CUDA(cudaGetLastError());
     count_launches(1);
     return GNK_OK;
@@ -120,9 +126,9 @@ int slit_nodes_f(const Boundary& b, const double* gam, const double* mu, const d
     return GNK_OK;
 }
 
-int slit_w(const double2* z, const double2* f, int M, double2 alpha, const double* hk, double2* w,
+int slit_w(const double2* z, const double2* f, int M, double2 alpha, const double* hk, int bounded, double2* w,
            cudaStream_t st) {
-    slit_w_kernel<<<(M + 255) / 256, 256, 0, st>>>(z, f, M, alpha, hk, w);
+    slit_w_kernel<<<(M + 255) / 256, 256, 0, st>>>(z, f, M, alpha, hk, bounded ? 1 : 0, w);
     GNK_TRY_CUDA(cudaGetLastError());
     count_launches(1);
     return GNK_OK;

@@ -137,7 +137,7 @@ def load(path: str = LIB_PATH):
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.gnk_cauchy_eval.argtypes = [P, I, P, P, P, P, I, P]
-    lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, P, P, P]
+    lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, I, P, P, P]
     lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
     lib.gnk_slit_map_eval.argtypes = [P, P, P, P, P, P, I, P, P, I, P]
     lib.gnk_debug_recip_f64.argtypes = [I, P, P, P, P]
@@ -363,10 +363,11 @@ def _c2(alpha):
     return (ctypes.c_double * 2)(c.real, c.imag)
 
 
-def gnk_slit_map_data(m1, n, et, alpha, theta, A, gam, stream=None):
-    """A = e^{i(pi/2 - theta)} (eta - alpha), gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]."""
+def gnk_slit_map_data(m1, n, et, alpha, theta, A, gam, stream=None, bounded=True):
+    """A = e^{i(pi/2 - theta)} (eta - alpha) (bounded G) or e^{i(pi/2 - theta)}
+    (unbounded G), gamma = -Re[e^{i(pi/2 - theta)} log(eta - alpha)]."""
     return _check(load().gnk_slit_map_data(int(m1), int(n), _ptr(et, True), _c2(alpha), _ptr(theta),
-                                           _ptr(A, True), _ptr(gam), _stream(stream)))
+                                           1 if bounded else 0, _ptr(A, True), _ptr(gam), _stream(stream)))
 
 
 def gnk_slit_map(h, alpha, gam, mu, hv, hk, w, stream=None):
@@ -383,20 +384,18 @@ def gnk_slit_map_eval(h, alpha, gam, mu, hv, hk, z, wz, precision=GNK_PREC_FP64,
 
 
 def slit_map(dom, alpha, theta, z=None, device="cuda", precision=GNK_PREC_FMM, tol=1e-12, stream=None):
-    """The slit map of a bounded domain (curves, n of `dom`): returns
+    """The slit map of a domain (curves, n and boundedness of `dom`): returns
     (w at the nodes, h_k, w at z or None, gnk_result).  theta: one value per
     boundary (pi/2 circular slit, 0 radial slit).  Cauchy sums by `precision`
     (GNK_PREC_FMM by default; GNK_PREC_FP64 or _DF32 direct)."""
-    if not dom.bounded:
-        raise ValueError("slit maps are defined here for bounded domains")
     et = torch.as_tensor(np.ascontiguousarray(dom.et), device=device)
     etp = torch.as_tensor(np.ascontiguousarray(dom.etp), device=device)
     th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=device)
     A = torch.empty_like(et)
     gam = torch.empty(dom.N, dtype=torch.float64, device=device)
-    gnk_slit_map_data(dom.m1, dom.n, et, alpha, th, A, gam, stream)
+    gnk_slit_map_data(dom.m1, dom.n, et, alpha, th, A, gam, stream, bounded=dom.bounded)
     bprec = GNK_PREC_FMM if precision == GNK_PREC_FMM else GNK_PREC_FP64
-    with Boundary(dom.m1, dom.n, et, etp, A, None, None, True, stream, bprec) as b:
+    with Boundary(dom.m1, dom.n, et, etp, A, None, None, dom.bounded, stream, bprec) as b:
         mu, h, hk, res = b.fbie(gam, tol=tol, precision=precision, stream=stream)
         w = torch.empty_like(et)
         gnk_slit_map(b.handle, alpha, gam, mu, h, hk, w, stream)
