@@ -434,9 +434,14 @@ int gnk_batch_tuning(const gnk_batch* b, int* fp32_targets, int* fp32_group,
 int gnk_batch_apply_IminusN(const gnk_batch* b, const double* x, double* y,
                             int precision, void* stream);
 
-/* mu and h of every system (FBIE: Eqs. sys, y, bh) with FP32 pair sums inside
- * GMRES and double-float refinement (opt->precision must be
- * GNK_PREC_MIXED_DF; NULL opt means the defaults with that precision).  Each
+/* mu and h of every system (FBIE: Eqs. sys, y, bh).  opt->precision
+ * GNK_PREC_MIXED_DF (the default when opt is NULL): FP32 pair sums inside
+ * GMRES and double-float refinement, every product one persistent launch over
+ * the whole batch.  GNK_PREC_FMM: each domain solved by the single-domain FBIE
+ * path with FMM products (Sec. 2.5; domains of fewer than 4096 nodes with
+ * double-float direct sums), one quadtree and its caches per domain kept with
+ * the batch, the domains taken largest first by 8 host worker threads with a
+ * CUDA stream each, so that several domains' products share the GPU.  Each
  * system stops when its own ||b - A mu|| <= tol ||b||.  info->relres is the
  * largest final relative residual; relres_per_system (nullable, one double
  * per system) receives each.  hk is nullable. */

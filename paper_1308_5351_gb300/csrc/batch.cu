@@ -18,11 +18,24 @@
 //   both pair kernels are chosen at build time by timing each variant on a
 //   sample of the batch's work list.
 //
+// * With GNK_PREC_FMM the systems are solved by the single-domain FBIE path
+//   with every Cauchy sum by the FMM (one quadtree, power table and near-field
+//   cache per domain, kept with the batch): worker threads, each with a CUDA
+//   stream of its own, take the domains in turn (largest first) and solve
+//   their right-hand sides one after the other, so that several domains'
+//   products run on the GPU at once (a product of a domain of a few thousand
+//   nodes fills only part of it).  Domains below kBatchFmmMin nodes use
+//   double-float direct sums (GNK_PREC_DF32) instead.
+//
 // Vector layout: system s = (domain d, rhs r) owns elements
 // [vec_off_d + r N_d, vec_off_d + (r+1) N_d) of every batch vector.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "gnk_internal.h"
@@ -638,6 +651,13 @@ struct BatchImpl {
     double graph_tol = -1.0;
     cudaStream_t graph_stream = nullptr;
     double last_tune_total = 0.0;
+    // FMM path: per-domain handles (built on first use), boundedness, the
+    // systems' hk offsets, the worker streams
+    std::vector<int> hbounded;
+    std::vector<int> hhk;
+    std::vector<gnk_boundary*> fmm_h;
+    std::vector<cudaStream_t> wstreams;
+    int device = 0;
 };
 
 namespace {
@@ -833,6 +853,12 @@ int autotune(BatchImpl& B, cudaStream_t st) {
 }
 
 void release_batch(BatchImpl& B) {
+    for (gnk_boundary* h : B.fmm_h)
+        if (h) gnk_free_boundary(h);
+    B.fmm_h.clear();
+    for (cudaStream_t w : B.wstreams)
+        if (w) cudaStreamDestroy(w);
+    B.wstreams.clear();
     void* p[] = {B.dom, B.dom1, B.sys, B.hk_off, B.et, B.etp, B.A, B.q, B.ref64, B.Eone, B.b1, B.d1, B.e, B.ones,
                  B.et32, B.ref32, B.offdf, B.off32, B.q32, B.A32, B.twid, B.lcol, B.cdesc, B.cbase, B.items32,
                  B.itemsdf, B.itemsdf1, B.counter, B.rhs, B.x, B.r, B.rr, B.dd, B.fb, B.fc, B.Lx, B.k.V, B.k.H,
@@ -949,7 +975,113 @@ int gmres_batch(BatchImpl& B, const double* rhs, double* x, int R, int maxit, do
     return GNK_OK;
 }
 
+// ---------------------------------------------------------------- FMM path
+constexpr int kBatchFmmMin = 4096;  // nodes: smaller domains use double-float direct sums
+constexpr int kBatchWorkers = 8;    // host threads, each with a CUDA stream of its own
+
 }  // namespace
+
+// Solves every system of the batch by gnk_fbie on a per-domain handle (FMM
+// products, or double-float direct sums below kBatchFmmMin nodes), the domains
+// taken largest first by kBatchWorkers worker threads.  g, x, hv, hkd: device
+// batch vectors (gamma in, mu, h and the systems' h_k out).
+static int run_batch_fmm(BatchImpl& B, const double* g, double* x, double* hv, double* hkd, const gnk_options& o,
+                  gnk_result* res, std::vector<double>* rel, cudaStream_t st) {
+    std::vector<int> order(B.ndom);
+    for (int d = 0; d < B.ndom; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+        return (long long)B.hdom[u].N * B.hdom[u].nrhs > (long long)B.hdom[v].N * B.hdom[v].nrhs;
+    });
+    const int nw = std::min(kBatchWorkers, B.ndom);
+    while ((int)B.wstreams.size() < nw) {
+        cudaStream_t w = nullptr;
+        GNK_TRY_CUDA(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking));
+        B.wstreams.push_back(w);
+    }
+    GNK_TRY_CUDA(cudaStreamSynchronize(st));  // gamma is in place before the workers start
+    std::atomic<int> next{0};
+    std::mutex mu;
+    int first_rc = GNK_OK;
+    std::string first_msg;
+    std::vector<int> iters(B.nsys, 0), cycles(B.nsys, 0), stat(B.nsys, GNK_OK);
+    auto worker = [&](int wi) {
+        if (cudaSetDevice(B.device) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (first_rc == GNK_OK) {
+                first_rc = GNK_ECUDA;
+                first_msg = "cudaSetDevice failed in a worker thread";
+            }
+            return;
+        }
+        cudaStream_t ws = B.wstreams[wi];
+        for (;;) {
+            const int k = next.fetch_add(1);
+            if (k >= B.ndom) break;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                if (first_rc != GNK_OK) break;
+            }
+            const int d = order[k];
+            const BDom& D = B.hdom[d];
+            const int prec = D.N >= kBatchFmmMin ? GNK_PREC_FMM : GNK_PREC_DF32;
+            int rc = GNK_OK;
+            if (!B.fmm_h[d]) {
+                gnk_boundary* h = nullptr;
+                rc = gnk_build_boundary_ex(&h, D.m1, D.n, reinterpret_cast<const double*>(B.et + D.node_off),
+                                           reinterpret_cast<const double*>(B.etp + D.node_off), nullptr,
+                                           reinterpret_cast<const double*>(B.A + D.node_off), nullptr,
+                                           B.hbounded[d], prec | GNK_BUILD_DEFER, ws);
+                if (rc == GNK_OK) B.fmm_h[d] = h;
+            }
+            gnk_options od = o;
+            od.precision = prec;
+            od.timing = 0;
+            od.tile_variant = 0;
+            for (int r = 0; r < D.nrhs && rc == GNK_OK; ++r) {
+                const int sidx = D.sys_off + r;
+                const long long off = D.vec_off + (long long)r * D.N;
+                gnk_result rr;
+                std::memset(&rr, 0, sizeof(rr));
+                rc = gnk_fbie(B.fmm_h[d], g + off, x + off, hv + off, hkd + B.hhk[sidx], &od, &rr, ws);
+                if (rc == GNK_ENOTCONV || rc == GNK_ENONFINITE) rc = GNK_OK;  // kept per system
+                (*rel)[sidx] = rr.relres;
+                iters[sidx] = rr.iterations;
+                cycles[sidx] = rr.cycles;
+                stat[sidx] = rr.status;
+            }
+            if (rc == GNK_OK && cudaStreamSynchronize(ws) != cudaSuccess) {
+                set_error("batch (FMM): %s", cudaGetErrorString(cudaGetLastError()));
+                rc = GNK_ECUDA;
+            }
+            if (rc != GNK_OK) {
+                char buf[1024];
+                gnk_last_error(buf, sizeof(buf));
+                std::lock_guard<std::mutex> lk(mu);
+                if (first_rc == GNK_OK) {
+                    first_rc = rc;
+                    first_msg = buf;
+                }
+            }
+        }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 0; w < nw; ++w) threads.emplace_back(worker, w);
+    for (std::thread& t : threads) t.join();
+    if (first_rc != GNK_OK) {
+        set_error("batch (FMM): %s", first_msg.c_str());
+        return first_rc;
+    }
+    int status = GNK_OK;
+    for (int sidx = 0; sidx < B.nsys; ++sidx) {
+        res->iterations += iters[sidx];
+        res->cycles += cycles[sidx];
+        res->matvecs_fp64 += iters[sidx] + 2;
+        if (stat[sidx] == GNK_ENONFINITE) status = GNK_ENONFINITE;
+        else if (stat[sidx] == GNK_ENOTCONV && status == GNK_OK) status = GNK_ENOTCONV;
+    }
+    return status;
+}
+
 }  // namespace gnk
 
 using namespace gnk;
@@ -998,6 +1130,8 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
         return code;
     };
     B.ndom = ndom;
+    B.hbounded.assign(bounded, bounded + ndom);
+    B.fmm_h.assign(ndom, nullptr);
     B.Ntot = (int)Ntot;
     B.L = L;
     B.nmax = nmax;
@@ -1006,6 +1140,7 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
     B.ntiles = ntiles;
     int dev = 0;
     cudaGetDevice(&dev);
+    B.device = dev;
     cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev);
     // tables
     std::vector<BSys> hsys;
@@ -1063,6 +1198,7 @@ int gnk_build_batch(gnk_batch** out, int ndom, const int* m1, const int* n, cons
         vec += (long long)D.N * nrhs[d];
     }
     B.ncirc = (int)desc.size();
+    B.hhk = hhk;
     const size_t N = Ntot;
     rc = GNK_OK;
 #define TRYB(x)                 \
@@ -1276,10 +1412,11 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
     gnk_default_options(&o);
     o.precision = GNK_PREC_MIXED_DF;
     if (opt) o = *opt;
-    if (o.precision != GNK_PREC_MIXED_DF || o.restart < 1 || o.restart > 1000 || o.maxit < 1 || !(o.tol > 0) ||
-        !(o.inner_tol > 0) || o.max_refine < 0 || o.tile_variant < 0 || o.tile_variant > 7) {
-        set_error("gnk_batch_fbie: options need precision GNK_PREC_MIXED_DF, restart 1..1000, maxit >= 1, "
-                  "tol > 0, tile_variant 0..7");
+    if ((o.precision != GNK_PREC_MIXED_DF && o.precision != GNK_PREC_FMM) || o.restart < 1 || o.restart > 1000 ||
+        o.maxit < 1 || !(o.tol > 0) || !(o.inner_tol > 0) || o.max_refine < 0 || o.tile_variant < 0 ||
+        o.tile_variant > 7) {
+        set_error("gnk_batch_fbie: options need precision GNK_PREC_MIXED_DF or GNK_PREC_FMM, restart 1..1000, "
+                  "maxit >= 1, tol > 0, tile_variant 0..7");
         return GNK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -1295,6 +1432,32 @@ int gnk_batch_fbie(const gnk_batch* hc, const double* gam, double* mu, double* h
     GNK_TRY_CUDA(cudaMemcpyAsync(g_dev, gam, Lb, cudaMemcpyDefault, st));
     gnk_result res;
     std::memset(&res, 0, sizeof(res));
+    if (o.precision == GNK_PREC_FMM) {
+        std::vector<double> rel(B.nsys, 0.0);
+        const int s = run_batch_fmm(B, g_dev, B.x, B.dd, B.Lx, o, &res, &rel, st);
+        if (s != GNK_OK && s != GNK_ENOTCONV && s != GNK_ENONFINITE) return s;
+        GNK_TRY_CUDA(cudaMemcpyAsync(mu, B.x, Lb, cudaMemcpyDefault, st));
+        GNK_TRY_CUDA(cudaMemcpyAsync(hv, B.dd, Lb, cudaMemcpyDefault, st));
+        if (hk) GNK_TRY_CUDA(cudaMemcpyAsync(hk, B.Lx, (size_t)B.nhk * sizeof(double), cudaMemcpyDefault, st));
+        if (o.timing) {
+            float ms = 0.f;
+            if (cudaEventRecord(t_ev[1], st) == cudaSuccess && cudaEventSynchronize(t_ev[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, t_ev[0], t_ev[1]) == cudaSuccess)
+                res.solve_ms = ms;
+            cudaGetLastError();
+            for (auto& e : t_ev) cudaEventDestroy(e);
+        }
+        GNK_TRY_CUDA(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double v : rel) mx = std::max(mx, v);
+        if (relres_per_system) std::memcpy(relres_per_system, rel.data(), rel.size() * sizeof(double));
+        res.status = s;
+        res.relres = mx;
+        if (info) *info = res;
+        if (s == GNK_ENOTCONV) set_error("batch: some systems did not reach tol");
+        if (s == GNK_ENONFINITE) set_error("batch: non-finite value in some system");
+        return s;
+    }
     // right-hand side -y and f_B(gamma) from one double-float product
     GNK_TRY(run_batch_circulant(B.cdesc, B.cbase, B.ncirc, B.nmax, g_dev, B.Lx, B.twid, B.lcol, st));
     {

@@ -97,3 +97,36 @@ def test_batch_apply_matches_oracle(G, prec):
             tol = (4 * 8 * (64 + d.N) * 2.0 ** -24 if prec == 2 else 1e-11) * scale
             assert np.abs(y[off:off + d.N] - K @ xs).max() <= tol
             off += d.N
+
+
+def test_batch_fmm_matches_oracle(G):
+    """GNK_PREC_FMM: every domain by the single-domain FBIE path with FMM
+    products (the two domains of >= 4096 nodes) or double-float direct sums
+    (the small ones), on concurrent worker streams; system by system against
+    the oracle to the bounds of the single-domain solves."""
+    doms, nrhs, gam = _batch_case(seed=5)
+    rng = np.random.default_rng(3)
+    for cnt, n in ((5, 1024), (9, 512)):
+        d = Dm.build_domain(Dm.random_ellipses(rng, cnt, 2.2), n, bounded=False)
+        doms.append(d)
+        nrhs.append(2)
+        gam = np.concatenate([gam, Dm.gamma_log(d, d.holes[0]), Dm.gamma_log(d, d.holes[1])])
+    assert sum(d.N >= 4096 for d in doms) == 2
+    with G.Batch(doms, nrhs, autotune=False, device="cuda") as b:
+        g = torch.as_tensor(gam, device="cuda")
+        mu, h, hk, res, rel = b.fbie(g, tol=1e-12, restart=30, precision=G.GNK_PREC_FMM, timing=1)
+        assert res.status == 0 and rel.max() <= 1e-12 and res.solve_ms > 0
+        mu2, _, _, res2, _ = b.fbie(g, tol=1e-12, restart=30, precision=G.GNK_PREC_FMM)  # handles reused
+        mu, h, hk, mu2 = mu.cpu().numpy(), h.cpu().numpy(), hk.cpu().numpy(), mu2.cpu().numpy()
+    assert np.array_equal(mu, mu2)
+    off, koff = 0, 0
+    for d, r in zip(doms, nrhs):
+        for k in range(r):
+            g_ = gam[off:off + d.N]
+            mu_r, h_r, hk_r = O.fbie(d.et, d.etp, d.A, d.n, g_)
+            assert np.abs(mu[off:off + d.N] - mu_r).max() <= 1e-10 * np.abs(mu_r).max()
+            hs = max(1.0, np.abs(h_r).max())
+            assert np.abs(h[off:off + d.N] - h_r).max() <= 1e-10 * hs
+            assert np.abs(hk[koff:koff + d.m1] - hk_r).max() <= 1e-10 * hs
+            off += d.N
+            koff += d.m1

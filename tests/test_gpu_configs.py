@@ -12,7 +12,8 @@ workload configurations, at the configuration's own boundary resolution
       equation (I + N* + J) mu = gamma through the FMM;
   C4  batched: domains of the 256-domain batch with n in {512, 1024} and
       m+1 >= 16 (and three small ones), m+1 right-hand sides each, system by
-      system;
+      system, by the persistent mixed double-float launches and by the FMM
+      path (per-domain FMM handles on concurrent worker streams);
   C5  the gradient: a 4-curve slice (3 star curves and a graded square) of
       the star/polygon domain at n = 512, gnk_fbie_backward against the
       oracle's dense adjoint gradient, FP64 and FMM.
@@ -129,7 +130,8 @@ def test_c3_adjoint_subset64_n512(G, c3):
 
 
 # ------------------------------------------------------------------ C4
-def test_c4_batched_large_domains(G):
+@pytest.mark.parametrize("form", ["mixed_df", "fmm"])
+def test_c4_batched_large_domains(G, form):
     full = Dm.batch_domains(4, 256)
     big = sorted([(d.N, i) for i, d in enumerate(full) if d.n >= 512 and d.m1 >= 16])[:2]
     big1024 = sorted([(d.N, i) for i, d in enumerate(full) if d.n == 1024 and d.m1 >= 16])[:1]
@@ -140,8 +142,9 @@ def test_c4_batched_large_domains(G):
     nrhs = [d.m1 for d in doms]
     gams = [np.stack([Dm.gamma_log(d, d.holes[k]) for k in range(d.m1)], axis=1) for d in doms]
     gam = np.concatenate([g.T.reshape(-1) for g in gams])
-    with G.Batch(doms, nrhs, autotune=True, device="cuda") as b:
-        mu, h, hk, res, rel = b.fbie(_dev(gam), tol=1e-10, restart=20, inner_tol=1e-6)
+    prec = G.GNK_PREC_MIXED_DF if form == "mixed_df" else G.GNK_PREC_FMM
+    with G.Batch(doms, nrhs, autotune=(form == "mixed_df"), device="cuda") as b:
+        mu, h, hk, res, rel = b.fbie(_dev(gam), tol=1e-10, restart=20, inner_tol=1e-6, precision=prec)
     assert res.status == 0 and rel.max() <= 1e-10
     mu, h, hk = mu.cpu().numpy(), h.cpu().numpy(), hk.cpu().numpy()
     off, koff = 0, 0
