@@ -202,10 +202,10 @@ struct Phases {
     }
 };
 
-// Work of the setup phase that a timed call does up front: the deferred
-// precompute and, for the FMM precisions, the quadtree.
+// Work of the setup phase that a timed call does up front: for the FMM
+// precisions the quadtree and its power table (the work an untimed call does
+// at its first product; a deferred Eone stays fused with the right-hand side).
 int timed_setup(const Boundary& b, int outer, cudaStream_t st) {
-    GNK_TRY(ensure_eone(b, st));
     if (outer == GNK_PREC_FMM) GNK_TRY(ensure_fmm(b, kMaxRHS, st));
     return GNK_OK;
 }

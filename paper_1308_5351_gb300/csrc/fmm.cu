@@ -352,7 +352,7 @@ __device__ __forceinline__ void p2m_leaf_cached(const FmmArgs& a, int leaf, int 
     const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
 #pragma unroll 2
     for (int j = j0 + wid; j < j1; j += kFmmTW) {
-        const cdf pw = cdf_of(__ldcg(a.tp + (size_t)j * kFmmP + lane));
+        const cdf pw = cdf_of(__ldcs(a.tp + (size_t)j * kFmmP + lane));
 #pragma unroll
         for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(__ldcg(a.ws + (size_t)r * a.N + j)), pw);
     }
@@ -879,8 +879,8 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_cached_kernel(FmmArgs a, cons
         for (int u = 0; u < kNqAhead; ++u) {
             if (act && u < np) {
                 const size_t o = (size_t)(base + (long long)(ps + u) * tn);
-                vi[u] = __ldcg(nq_im + o);
-                if (COMP == 0) vr[u] = __ldcg(nq_re + o);
+                vi[u] = __ldcs(nq_im + o);
+                if (COMP == 0) vr[u] = __ldcs(nq_re + o);
             }
         }
         {  // x of the chunk's sources (two per lane)
@@ -919,11 +919,11 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_cached_kernel(FmmArgs a, cons
 #pragma unroll 8
             for (int pp = kNqAhead; pp < np; ++pp) {
                 const size_t o = (size_t)(base + (long long)(ps + pp) * tn);
-                const float4 wi = __ldcg(nq_im + o);
+                const float4 wi = __ldcs(nq_im + o);
                 const df2 Qi{make_float2(wi.x, wi.y), make_float2(wi.z, wi.w)};
                 df2 Qr{f2(0.f), f2(0.f)};
                 if (COMP == 0) {
-                    const float4 wr = __ldcg(nq_re + o);
+                    const float4 wr = __ldcs(nq_re + o);
                     Qr = df2{make_float2(wr.x, wr.y), make_float2(wr.z, wr.w)};
                 }
 #pragma unroll
@@ -1551,8 +1551,9 @@ double fmm_near_cached_instr(const Boundary& b, int R, int comp) {
 }
 
 double fmm_near_cached_bytes(const Boundary& b, int R, int comp) {
-    // cached entries, x in (8 bytes) and z out (16 bytes) per node and right-hand side
-    return b.fmm ? 16.0 * (double)b.fmm->nq_slots * (comp == 1 ? 1.0 : 2.0) + 24.0 * R * b.N : 0.0;
+    // 8 bytes per near pair and part of z read from the cache, x in (8 bytes)
+    // and z out (16 bytes) per node and right-hand side
+    return b.fmm ? 8.0 * (double)b.fmm->near_pairs * (comp == 1 ? 1.0 : 2.0) + 24.0 * R * b.N : 0.0;
 }
 
 // Forms the near-field operator cache of the products z = E(q x) once per
@@ -1568,14 +1569,36 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
     if (t->nitems <= 0) return GNK_OK;
     FmmArgs a;
     fmm_args(b, a);
+    // sizes from bounds the tree already gives, so that nothing waits for the
+    // device: sum_items ceil(S/2) tn <= (near pairs + N)/2 entries, and
+    // sum_items S <= near pairs sources (each source meets at least one target)
     const size_t ni = (size_t)t->nitems;
+    const long long slots = (t->near_pairs + b.N) / 2 + 1, nsrc = t->near_pairs + 1;
+    const size_t bytes = (size_t)slots * sizeof(float4);
+    if (nsrc > INT32_MAX || 2.0 * (double)bytes > kNqMaxBytes) return GNK_OK;
     long long *cnt = nullptr, *scnt = nullptr, *soff = nullptr;
     if (pool_alloc(reinterpret_cast<void**>(&cnt), 2 * ni * sizeof(long long), st) != cudaSuccess ||
         pool_alloc(reinterpret_cast<void**>(&soff), (ni + 1) * sizeof(long long), st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->nq_off), (ni + 1) * sizeof(long long), st) != cudaSuccess) {
+        pool_alloc(reinterpret_cast<void**>(&t->nq_off), (ni + 1) * sizeof(long long), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_re), bytes, st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_im), bytes, st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_item), ni * sizeof(int4), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->nq_src), (size_t)nsrc * sizeof(int), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->xs), (size_t)kMaxRHS * b.N * sizeof(float2), st) != cudaSuccess) {
         cudaGetLastError();
         pool_free(cnt, st);
         pool_free(soff, st);
+        pool_free(t->nq_off, st);
+        pool_free(t->nq_re, st);
+        pool_free(t->nq_im, st);
+        pool_free(t->nq_item, st);
+        pool_free(t->nq_src, st);
+        pool_free(t->xs, st);
+        t->nq_off = nullptr;
+        t->nq_re = t->nq_im = nullptr;
+        t->nq_item = nullptr;
+        t->nq_src = nullptr;
+        t->xs = nullptr;
         return GNK_OK;
     }
     scnt = cnt + ni;
@@ -1584,35 +1607,7 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
     fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(scnt, t->nitems, soff);
     GNK_TRY_CUDA(cudaGetLastError());
     count_launches(3);
-    long long tot[2] = {0, 0};
-    GNK_TRY_CUDA(cudaMemcpyAsync(&tot[0], t->nq_off + t->nitems, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    GNK_TRY_CUDA(cudaMemcpyAsync(&tot[1], soff + t->nitems, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    GNK_TRY_CUDA(cudaStreamSynchronize(st));
     pool_free(cnt, st);
-    const long long slots = tot[0], nsrc = tot[1];
-    const size_t bytes = (size_t)slots * sizeof(float4);
-    if (slots <= 0 || nsrc <= 0 || nsrc > INT32_MAX || 2.0 * (double)bytes > kNqMaxBytes) {
-        pool_free(soff, st);
-        return GNK_OK;
-    }
-    if (pool_alloc(reinterpret_cast<void**>(&t->nq_re), bytes, st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->nq_im), bytes, st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->nq_item), ni * sizeof(int4), st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->nq_src), (size_t)nsrc * sizeof(int), st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->xs), (size_t)kMaxRHS * b.N * sizeof(float2), st) != cudaSuccess) {
-        cudaGetLastError();
-        pool_free(soff, st);
-        pool_free(t->nq_re, st);
-        pool_free(t->nq_im, st);
-        pool_free(t->nq_item, st);
-        pool_free(t->nq_src, st);
-        pool_free(t->xs, st);
-        t->nq_re = t->nq_im = nullptr;
-        t->nq_item = nullptr;
-        t->nq_src = nullptr;
-        t->xs = nullptr;
-        return GNK_OK;
-    }
     t->nq_slots = slots;
     const ProfToken tok = prof_begin(st, PK_OTHER);
     fmm_nq_build_kernel<<<t->nitems, kFmmNT, 0, st>>>(a, b.q, t->nq_off, soff, t->nq_re, t->nq_im, t->nq_item,

@@ -267,6 +267,42 @@ __device__ __forceinline__ void reduce_coeffs(const double* part, int ld, int nv
     }
 }
 
+// As reduce_coeffs, with every partial loaded at once (one round of
+// independent L2 loads instead of a chain per warp) into `stage` (at least
+// nb * nv doubles of shared memory), then summed per coefficient in a fixed
+// order: 8 threads per coefficient each add a contiguous eighth of the blocks,
+// then the eighths are added in order.  The result is the same in every block.
+constexpr int kStage = 4096;  // doubles of the staging area
+constexpr int kPool = KD * KT > 1025 + 2 * 1024 ? KD * KT : 1025 + 2 * 1024;
+constexpr size_t kArnoldiDyn = (size_t)(kPool + kStage) * sizeof(double);  // dynamic shared bytes
+
+__device__ __forceinline__ void reduce_coeffs_staged(const double* part, int ld, int nv, int nb, double* hs,
+                                                     double* stage, double (*red8)[32]) {
+    const int tot = nv * nb;
+    for (int e = threadIdx.x; e < tot; e += KT) {  // e = b * nv + k
+        const int b = e / nv, k = e - b * nv;
+        stage[e] = __ldcg(part + (size_t)b * ld + k);
+    }
+    __syncthreads();
+    const int per = (nb + 7) / 8;
+    for (int k0 = 0; k0 < nv; k0 += KT / 8) {
+        const int k = k0 + (threadIdx.x >> 3), slice = threadIdx.x & 7;
+        double t = 0.0;
+        if (k < nv) {
+            const int b0 = min(nb, slice * per), b1 = min(nb, b0 + per);
+            for (int b = b0; b < b1; ++b) t += stage[b * nv + k];
+        }
+        red8[slice][threadIdx.x >> 3] = t;  // red8 is [8][32]: slices x coefficients of this round
+        __syncthreads();
+        if (threadIdx.x < KT / 8 && k0 + (int)threadIdx.x < nv) {
+            double u = red8[0][threadIdx.x];
+            for (int sl = 1; sl < 8; ++sl) u += red8[sl][threadIdx.x];
+            hs[k0 + threadIdx.x] = u;
+        }
+        __syncthreads();
+    }
+}
+
 // Givens update of column j by block 0: the column h = h1 + h2 (in h1),
 // h_{j+1,j} = hn and the previous rotations (staged in shared memory by
 // givens_stage while the grid waits at its second barrier), one thread
@@ -278,6 +314,7 @@ __device__ __forceinline__ void givens_stage(int j, double* scs, double* ssn, KP
         scs[k] = p.cs[k];
         ssn[k] = p.sn[k];
     }
+    if (threadIdx.x == 0) scs[1023] = p.g[j];  // g_j (scs holds at most j <= 1023 rotations before it)
 }
 
 __device__ void givens_step(int j, double hn, double* h1, const double* h2, const double* scs, const double* ssn,
@@ -317,19 +354,100 @@ __device__ void givens_step(int j, double hn, double* h1, const double* h2, cons
     for (int k = threadIdx.x; k < j + 2; k += KT) colg[k] = h1[k];
 }
 
+// givens_step by warp 0 alone (no block barrier), so that the other warps of
+// block 0 can update the block's range of the new basis vector meanwhile.  The
+// previous rotations applied to the column x = h1 + h2 form the first-order
+// recurrence z_0 = x_0, z_{k+1} = -s_k z_k + c_k x_{k+1} with outputs
+// y_k = c_k z_k + s_k x_{k+1}: for j <= 32 it is evaluated as an inclusive scan
+// of the affine maps z -> a z + b over the lanes (5 shuffle steps instead of
+// j dependent steps of one thread on GB300's 2-lane FP64 pipe); longer cycles
+// take the serial loop.  gj: g_j staged in shared memory.
+__device__ void givens_step_warp0(int j, double hn, double* h1, const double* h2, const double* scs,
+                                  const double* ssn, double gj, KPtrs p, KState* s) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;  // warp 0
+    const int nv = j + 1;
+    for (int k = lane; k < nv; k += 32) h1[k] = h1[k] + h2[k];
+    __syncwarp();
+    double zj;
+    if (j <= 32) {
+        const double x0 = h1[0];
+        double a = 1.0, b = 0.0, ck = 1.0, sk = 0.0, xk1 = 0.0;
+        if (lane < j) {
+            ck = scs[lane];
+            sk = ssn[lane];
+            xk1 = h1[lane + 1];
+            a = -sk;
+            b = ck * xk1;
+        }
+        for (int o = 1; o < 32; o <<= 1) {  // (a, b) <- (a, b) o (ap, bp)
+            const double ap = __shfl_up_sync(full, a, o), bp = __shfl_up_sync(full, b, o);
+            if (lane >= o) {
+                b = fma(a, bp, b);
+                a *= ap;
+            }
+        }
+        const double znext = fma(a, x0, b);                       // z_{lane+1}
+        const double zprev = __shfl_up_sync(full, znext, 1);
+        const double zcur = (lane == 0) ? x0 : zprev;             // z_lane
+        __syncwarp();
+        if (lane < j) h1[lane] = fma(ck, zcur, sk * xk1);         // y_lane
+        zj = (j == 0) ? x0 : __shfl_sync(full, znext, j - 1);
+    } else {
+        if (lane == 0) {
+            double* col = h1;
+            for (int k = 0; k < j; ++k) {
+                const double a = col[k], b = col[k + 1];
+                col[k] = scs[k] * a + ssn[k] * b;
+                col[k + 1] = -ssn[k] * a + scs[k] * b;
+            }
+        }
+        __syncwarp();
+        zj = h1[j];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double* col = h1;
+        s->hnext = hn;
+        const double r = sqrt(fma(zj, zj, hn * hn));
+        const double inv = (r > 0.0) ? 1.0 / r : 0.0;
+        const double c = (r > 0.0) ? zj * inv : 1.0;
+        const double sn = (r > 0.0) ? hn * inv : 0.0;
+        p.cs[j] = c;
+        p.sn[j] = sn;
+        col[j] = r;
+        col[j + 1] = 0.0;
+        p.g[j + 1] = -sn * gj;
+        p.g[j] = c * gj;
+        const double est = fabs(sn * gj);
+        s->est = est;
+        s->k = j + 1;
+        const bool bad = !isfinite(est) || !isfinite(hn);
+        if (bad) s->nonfinite = 1;
+        if (bad || est <= s->tol * s->bnorm || j + 1 == s->restart || hn == 0.0) s->done = 1;
+    }
+    __syncwarp();
+    double* colg = p.H + (size_t)j * p.ld;
+    for (int k = lane; k < j + 2; k += 32) colg[k] = h1[k];
+}
+
 __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, int N, int j, double* __restrict__ w,
                                                 KPtrs p, KState* s) {
     if (s->done) return;  // set before this launch: the same in every block
     __shared__ double red[8][KD];
     __shared__ double red8[KT / 32][32];
     __shared__ double h1[1025];
-    // h2, the Givens staging and, before they are used, the dots' reduction buffer
-    __shared__ double s_pool[KD * KT > 1025 + 2 * 1024 ? KD * KT : 1025 + 2 * 1024];
+    // dynamic: s_pool (h2, the Givens staging and, before they are used, the
+    // dots' reduction buffer), then the staging area of the coefficient sums
+    extern __shared__ double s_dyn[];
+    double* s_pool = s_dyn;
+    double* s_stage = s_dyn + kPool;
     double* h2 = s_pool;
     double* scs = s_pool + 1025;
     double* ssn = s_pool + 2049;
     __shared__ double s_hn;
     const int nv = j + 1, nb = gridDim.x;
+    const bool staged = nb * (nv + 1) <= kStage;
     const int per = (N + nb - 1) / nb;
     const int i0 = min(N, (int)blockIdx.x * per), i1 = min(N, i0 + per);
     double* part1 = p.part;
@@ -337,7 +455,10 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     // first pass: h1 = V^T w
     range_dots(V, N, nv, w, i0, i1, part1 + (size_t)blockIdx.x * p.ld, red, s_pool, false);
     grid_barrier(s);
-    reduce_coeffs(part1, p.ld, nv, nb, h1, red8);
+    if (staged)
+        reduce_coeffs_staged(part1, p.ld, nv, nb, h1, s_stage, red8);
+    else
+        reduce_coeffs(part1, p.ld, nv, nb, h1, red8);
     // w' = w - V h1 on the block's range, then the second pass h2 = V^T w' with ||w'||^2
     for (int i = i0 + threadIdx.x; i < i1; i += KT) {
         double acc = w[i];
@@ -348,14 +469,20 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     range_dots(V, N, nv, w, i0, i1, part2 + (size_t)blockIdx.x * p.ld, red, s_pool, true);
     if (blockIdx.x == 0) givens_stage(j, scs, ssn, p);  // the reduction buffer is free again
     grid_barrier(s);
-    reduce_coeffs(part2, p.ld, nv + 1, nb, h2, red8);
+    if (staged)
+        reduce_coeffs_staged(part2, p.ld, nv + 1, nb, h2, s_stage, red8);
+    else
+        reduce_coeffs(part2, p.ld, nv + 1, nb, h2, red8);
     // ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 for an orthonormal basis; when more
     // than half of ||w'||^2 cancels, the norm is summed again after the update
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // ||h2||^2 by warp 0 (a butterfly: every lane gets the same sum)
         double q = 0.0;
-        for (int k = 0; k < nv; ++k) q = fma(h2[k], h2[k], q);
-        const double d = h2[nv] - q;
-        s_hn = (d > 0.5 * h2[nv]) ? sqrt(d) : -1.0;
+        for (int k = threadIdx.x; k < nv; k += 32) q = fma(h2[k], h2[k], q);
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (threadIdx.x == 0) {
+            const double d = h2[nv] - q;
+            s_hn = (d > 0.5 * h2[nv]) ? sqrt(d) : -1.0;
+        }
     }
     __syncthreads();
     double hn = s_hn;
@@ -382,15 +509,19 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
             const double inv = 1.0 / hn;
             for (int i = i0 + threadIdx.x; i < i1; i += KT) w[i] *= inv;
         }
+        if (blockIdx.x == 0) givens_step(j, hn, h1, h2, scs, ssn, p, s);
     } else {  // v_{j+1} = (w' - V h2) / h_{j+1,j} in one pass (unused when the cycle stops here)
         const double inv = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 1.0;
-        for (int i = i0 + threadIdx.x; i < i1; i += KT) {
+        // block 0: warp 0 does the Givens update while the other warps update the range
+        const int t0 = (blockIdx.x == 0) ? 32 : 0;
+        if (blockIdx.x == 0 && threadIdx.x < 32) givens_step_warp0(j, hn, h1, h2, scs, ssn, scs[1023], p, s);
+        for (int i = i0 + (int)threadIdx.x - t0; i < i1; i += KT - t0) {
+            if ((int)threadIdx.x < t0) break;
             double wi = w[i];
             for (int k = 0; k < nv; ++k) wi = fma(-h2[k], V[(size_t)k * N + i], wi);
             w[i] = wi * inv;
         }
     }
-    if (blockIdx.x == 0) givens_step(j, hn, h1, h2, scs, ssn, p, s);
 }
 
 // y = H(0:k, 0:k)^-1 g(0:k) at the end of a cycle (one block; H staged in
@@ -527,7 +658,9 @@ static int arnoldi_blocks(int N) {
     if ((int)cap.size() <= dev) cap.resize(dev + 1, 0);
     if (cap[dev] == 0) {
         int occ = 0, nsm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, KT, 0) != cudaSuccess ||
+        if (cudaFuncSetAttribute((const void*)k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kArnoldiDyn) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, KT, kArnoldiDyn) != cudaSuccess ||
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             occ = 1;
@@ -623,7 +756,8 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
                 int Nc = N, jc = j;
                 void* args[] = {(void*)&Vc, (void*)&Nc, (void*)&jc, (void*)&w, (void*)&p, (void*)&ks};
                 KLAUNCH((3 * nv + 6) * vb, GNK_TRY_CUDA(cudaLaunchCooperativeKernel(
-                                               (const void*)k_arnoldi, dim3(ng), dim3(KT), args, 0, st)));
+                                               (const void*)k_arnoldi, dim3(ng), dim3(KT), args, kArnoldiDyn,
+                                               st)));
             }
             prof_collect_end(&step_ids[j]);
             GNK_TRY_CUDA(cudaGetLastError());
