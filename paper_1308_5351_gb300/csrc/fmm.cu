@@ -350,11 +350,26 @@ __device__ __forceinline__ void p2m_leaf_cached(const FmmArgs& a, int leaf, int 
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = cdf_zero();
     const int j0 = a.leaf_start[leaf], j1 = a.leaf_start[leaf + 1];
-#pragma unroll 2
-    for (int j = j0 + wid; j < j1; j += kFmmTW) {
-        const cdf pw = cdf_of(__ldcs(a.tp + (size_t)j * kFmmP + lane));
+    constexpr int U = 8;  // rows loaded before they are used: 8 loads in flight per warp
+    for (int j = j0 + wid; j < j1; j += kFmmTW * U) {
+        float4 tv[U], wv[R][U];
 #pragma unroll
-        for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(__ldcg(a.ws + (size_t)r * a.N + j)), pw);
+        for (int u = 0; u < U; ++u) {
+            const int jj = j + u * kFmmTW;
+            if (jj < j1) {
+                tv[u] = __ldcs(a.tp + (size_t)jj * kFmmP + lane);
+#pragma unroll
+                for (int r = 0; r < R; ++r) wv[r][u] = __ldcg(a.ws + (size_t)r * a.N + jj);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j + u * kFmmTW < j1) {
+                const cdf pw = cdf_of(tv[u]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) cdf_mac(acc[r], cdf_of(wv[r][u]), pw);
+            }
+        }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {

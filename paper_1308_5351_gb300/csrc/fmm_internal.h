@@ -12,7 +12,7 @@ namespace gnk {
 
 constexpr int kFmmP = 32;     // expansion order (one warp lane per coefficient)
 #ifndef GNK_FMM_LEAF
-#define GNK_FMM_LEAF 32
+#define GNK_FMM_LEAF 64
 #endif
 constexpr int kFmmLeaf = GNK_FMM_LEAF;  // target mean number of nodes per leaf
 constexpr int kFmmNT = 256;   // threads of the near-field kernel: 8 warps

@@ -460,6 +460,8 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     else
         reduce_coeffs(part1, p.ld, nv, nb, h1, red8);
     // w' = w - V h1 on the block's range, then the second pass h2 = V^T w' with ||w'||^2
+    // (fusing this update with the second pass's dots, the basis entries kept in
+    // registers, measured slower: 168 registers per thread)
     for (int i = i0 + threadIdx.x; i < i1; i += KT) {
         double acc = w[i];
         for (int k = 0; k < nv; ++k) acc = fma(-h1[k], V[(size_t)k * N + i], acc);
