@@ -1122,6 +1122,8 @@ void release_fmm(Boundary& b) {
             cudaGetLastError();
             pool_free(b.fmm->arena, 0);
             pool_free(b.fmm->sync, 0);
+            pool_free(b.fmm->nq_cnt, 0);
+            pool_free(b.fmm->nq_soff, 0);
             pool_free(b.fmm->nq_off, 0);
             pool_free(b.fmm->nq_item, 0);
             pool_free(b.fmm->nq_src, 0);
@@ -1582,8 +1584,6 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
     if (t->nq_state != 0) return GNK_OK;
     t->nq_state = -1;
     if (t->nitems <= 0) return GNK_OK;
-    FmmArgs a;
-    fmm_args(b, a);
     // sizes from bounds the tree already gives, so that nothing waits for the
     // device: sum_items ceil(S/2) tn <= (near pairs + N)/2 entries, and
     // sum_items S <= near pairs sources (each source meets at least one target)
@@ -1591,7 +1591,7 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
     const long long slots = (t->near_pairs + b.N) / 2 + 1, nsrc = t->near_pairs + 1;
     const size_t bytes = (size_t)slots * sizeof(float4);
     if (nsrc > INT32_MAX || 2.0 * (double)bytes > kNqMaxBytes) return GNK_OK;
-    long long *cnt = nullptr, *scnt = nullptr, *soff = nullptr;
+    long long *cnt = nullptr, *soff = nullptr;
     if (pool_alloc(reinterpret_cast<void**>(&cnt), 2 * ni * sizeof(long long), st) != cudaSuccess ||
         pool_alloc(reinterpret_cast<void**>(&soff), (ni + 1) * sizeof(long long), st) != cudaSuccess ||
         pool_alloc(reinterpret_cast<void**>(&t->nq_off), (ni + 1) * sizeof(long long), st) != cudaSuccess ||
@@ -1616,21 +1616,39 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
         t->xs = nullptr;
         return GNK_OK;
     }
-    scnt = cnt + ni;
+    t->nq_slots = slots;
+    t->nq_cnt = cnt;
+    t->nq_soff = soff;
+    t->nq_state = 2;  // allocated; formed by near_cache_build before the first cached near field
+    return GNK_OK;
+}
+
+// The launches that form the cache (count, scans, entries), on `st` after the
+// product has forked its far field, so that they overlap it.
+static int near_cache_build(const Boundary& b, cudaStream_t st) {
+    FmmTree* t = b.fmm;
+    if (t->nq_state != 2) return GNK_OK;
+    FmmArgs a;
+    fmm_args(b, a);
+    const size_t ni = (size_t)t->nitems;
+    long long* cnt = t->nq_cnt;
+    long long* scnt = cnt + ni;
+    long long* soff = t->nq_soff;
     fmm_nq_count_kernel<<<(t->nitems + 255) / 256, 256, 0, st>>>(a, cnt, scnt);
     fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(cnt, t->nitems, t->nq_off);
     fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(scnt, t->nitems, soff);
     GNK_TRY_CUDA(cudaGetLastError());
     count_launches(3);
-    pool_free(cnt, st);
-    t->nq_slots = slots;
     const ProfToken tok = prof_begin(st, PK_OTHER);
     fmm_nq_build_kernel<<<t->nitems, kFmmNT, 0, st>>>(a, b.q, t->nq_off, soff, t->nq_re, t->nq_im, t->nq_item,
                                                       t->nq_src);
     GNK_TRY_CUDA(cudaGetLastError());
     prof_end(tok, PK_OTHER, 0.0, st);
     count_launches(1);
+    pool_free(cnt, st);
     pool_free(soff, st);
+    t->nq_cnt = nullptr;
+    t->nq_soff = nullptr;
     t->nq_state = 1;
     return GNK_OK;
 }
@@ -1681,7 +1699,9 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
     }
     GNK_TRY_CUDA(cudaEventRecord(t->ev_join, fs));
     // near field on the caller's stream (from the operator cache when `cached`
-    // is 0 (both parts of z) or 1 (Im z only))
+    // is 0 (both parts of z) or 1 (Im z only)); the first cached product forms
+    // the cache here, beside its far field
+    if (cached >= 0) GNK_TRY(near_cache_build(b, st));
     const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
     if (cached >= 0) {
         const long long* off = t->nq_off;
@@ -1788,7 +1808,7 @@ int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {
     int cached = -1;
     if (job.mode == W_SCALED && job.s == b.q && !b.plain) {
         GNK_TRY(ensure_near_cache(b, st));
-        if (b.fmm->nq_state == 1) {
+        if (b.fmm->nq_state >= 1) {
             cached = pair_component_needed(b, job) == 1 ? 1 : 0;
             a.xs = b.fmm->xs;
         }

@@ -54,8 +54,11 @@ struct FmmTree {
     int* sync = nullptr;        // [nbox]: children counted by the upward pass (zero between products)
     // near-field operator cache of the products z = E(q x) (fixed geometry):
     // Q_ij = q_j / (eta_i - eta_j) per work item, double-float, for source
-    // pairs x targets; state 0 not formed, 1 formed, -1 not used (too large)
+    // pairs x targets; state 0 not formed, 2 allocated (formed by the first
+    // cached product), 1 formed, -1 not used (too large)
     int nq_state = 0;
+    long long* nq_cnt = nullptr;   // build temporaries while state is 2
+    long long* nq_soff = nullptr;
     long long nq_slots = 0;     // float4 entries of each of nq_re, nq_im
     long long* nq_off = nullptr;  // per work item: first entry (nitems + 1)
     int4* nq_item = nullptr;    // per work item: (S sources, tn targets, first source in nq_src, -)
