@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "gnk_internal.h"
+#include "pairmath.cuh"
 
 namespace gnk {
 namespace {
@@ -148,12 +149,19 @@ __global__ void __launch_bounds__(KT) k_norm(const double* __restrict__ x, int N
     }
 }
 
-// v0 = r / beta
+// v0 = r / beta (and its double-float copy when vd0 is given)
 __global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r, double* __restrict__ v0,
-                                                    int N, const KState* s) {
+                                                    float2* __restrict__ vd0, int N, const KState* s) {
     if (s->done) return;
     const double inv = 1.0 / s->beta;
-    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) v0[i] = r[i] * inv;
+    for (int i = blockIdx.x * KT + threadIdx.x; i < N; i += gridDim.x * KT) {
+        const double v = r[i] * inv;
+        v0[i] = v;
+        if (vd0) {
+            const df d = df_split(v);
+            vd0[i] = make_float2(d.h, d.l);
+        }
+    }
 }
 
 // dot products per pass over w in the Arnoldi step
@@ -310,7 +318,7 @@ __device__ __forceinline__ void reduce_coeffs_staged(const double* part, int ld,
 // the residual estimate and the end-of-cycle test (the triangular solve for y
 // is k_solve_y's, once per cycle).
 __device__ __forceinline__ void givens_stage(int j, double* scs, double* ssn, KPtrs p) {
-    for (int k = threadIdx.x; k < j; k += KT) {
+    for (int k = threadIdx.x; k < j; k += blockDim.x) {
         scs[k] = p.cs[k];
         ssn[k] = p.sn[k];
     }
@@ -320,7 +328,7 @@ __device__ __forceinline__ void givens_stage(int j, double* scs, double* ssn, KP
 __device__ void givens_step(int j, double hn, double* h1, const double* h2, const double* scs, const double* ssn,
                             KPtrs p, KState* s) {
     const int nv = j + 1;
-    for (int k = threadIdx.x; k < nv; k += KT) h1[k] = h1[k] + h2[k];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) h1[k] = h1[k] + h2[k];
     __syncthreads();
     if (threadIdx.x == 0) {
         double* col = h1;
@@ -351,7 +359,7 @@ __device__ void givens_step(int j, double hn, double* h1, const double* h2, cons
     }
     __syncthreads();
     double* colg = p.H + (size_t)j * p.ld;
-    for (int k = threadIdx.x; k < j + 2; k += KT) colg[k] = h1[k];
+    for (int k = threadIdx.x; k < j + 2; k += blockDim.x) colg[k] = h1[k];
 }
 
 // givens_step by warp 0 alone (no block barrier), so that the other warps of
@@ -526,37 +534,527 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, in
     }
 }
 
-// y = H(0:k, 0:k)^-1 g(0:k) at the end of a cycle (one block; H staged in
-// shared memory when k <= kSmallH, else read from global memory)
-constexpr int kSmallH = 48;
+// ---- the same Arnoldi step with the Gram-Schmidt arithmetic in double-float
+// on the FP32 pipe (GB300's FP64 pipe has 2 lanes per SM against 128 FP32
+// lanes, and each pass is nv multiply-adds per entry), shaped for latency:
+// each pass is a handful of dependent memory round trips, so the step is
+// built to take as few as possible.
+//  * The basis is kept in FP64 (the operator's input and the update of x read
+//    it) and as a double-float copy Vd (hi, lo per entry).  At the start, one
+//    thread issues bulk asynchronous copies (cp.async.bulk, completion on an
+//    mbarrier) of the block's range of Vd_0 .. Vd_j and of w = A v_j into
+//    shared memory; every pass then reads shared memory.  (Ranges too long
+//    for shared memory read global memory through the same code.)
+//  * Dots: warp per basis vector, lanes over the range, a fixed shuffle tree.
+//  * Grid barriers: one relaxed-cost arrival (red.release) on a counter that
+//    only grows during a solve, and polls (ld.acquire) for the barrier's target
+//    count; the target follows from the count seen at the kernel's start.
+// Block and grid sums are compensated double-float sums in a fixed order;
+// the coefficients stay double-float for the updates and are rounded to FP64
+// for the Givens step.  With about 48 significant bits the basis is
+// orthonormal to ~1e-14, far below the solver's tolerances; GNK_PREC_FP64
+// keeps the FP64 step above.
+__device__ __forceinline__ df df_renorm(df a) {
+    df r;
+    fast_two_sum(a.h, a.l, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ float2 f2_of(df v) { return make_float2(v.h, v.l); }
+__device__ __forceinline__ double df_dbl(df v) { return (double)v.h + (double)v.l; }
+__device__ __forceinline__ df df_minus(df a, df b) { return df_sub(a.h, a.l, b.h, b.l); }
+__device__ __forceinline__ df df_plus(df a, df b) { return df_sub(a.h, a.l, -b.h, -b.l); }
+__device__ __forceinline__ df df_prod(df a, df b) { return df_renorm(df_mul(a, b)); }
+
+// sqrt(a), a > 0: one Newton step from the rounded FP32 root (the residual
+// a.h - y^2 is exact by the FMA), about 46 significant bits
+__device__ __forceinline__ df df_sqrt(df a) {
+    const float y = __fsqrt_rn(a.h);
+    const float e = __fadd_rn(fmaf(-y, y, a.h), a.l);
+    df r;
+    fast_two_sum(y, __fmul_rn(e, __fdiv_rn(0.5f, y)), r.h, r.l);
+    return r;
+}
+
+// 1 / a: one Newton step from the rounded FP32 reciprocal (1 - a.h y exact by the FMA)
+__device__ __forceinline__ df df_rcp(df a) {
+    const float y = __frcp_rn(a.h);
+    const float e = __fsub_rn(fmaf(-a.h, y, 1.0f), __fmul_rn(a.l, y));
+    df r;
+    fast_two_sum(y, __fmul_rn(y, e), r.h, r.l);
+    return r;
+}
+
+// shared memory of the range (bytes) beyond the pool and the staging area
+constexpr int kSliceBytes = 128 * 1024;
+constexpr size_t kArnoldiDfDyn = kArnoldiDyn + kSliceBytes;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on the growing counter: arrive, then wait until the count
+// reaches `target` (bounded; a wait that gives up sets bar_err).  The test hook
+// block bar_skip passes without arriving.
+__device__ __forceinline__ void grid_barrier_count(KState* s, unsigned target) {
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x != s->bar_skip) {
+        red_release_add(&s->bar_count, 1u);
+        const int limit = s->bar_limit;
+        for (int it = 0; (int)(ld_acquire(&s->bar_count) - target) < 0; ++it) {
+            if (it >= limit || *(volatile int*)&s->bar_err) {
+                atomicExch(&s->bar_err, 1);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared memory
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(unsigned long long* bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `phase` of the mbarrier with a limit; on a timeout sets
+// bar_err and waits once more (also bounded) for the copies in flight.
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsigned phase, KState* s) {
+    const int limit = s->bar_limit;
+    int it = 0;
+    while (!mbar_done(bar, phase)) {
+        if (++it >= limit) {
+            atomicExch(&s->bar_err, 1);
+            for (int k = 0; k < limit && !mbar_done(bar, phase); ++k) {
+            }
+            return;
+        }
+    }
+}
+
+// Threads of the double-float step: one block per multiprocessor, so that the
+// block's few hundred entries and short dependent chains have 32 warps to hide
+// their latencies.
+constexpr int KTD = 1024;
+
+// Block partials of the dots of the range's w (ws, len entries) with the
+// rows Vr + k ld, k < nv (and ws . ws when with_norm), to out[0 .. nv(+1)):
+// warp w takes k = w, w + 32, ...; lane l the entries l, l + 32, ... in two
+// interleaved compensated sums, then a shuffle tree in a fixed order.
+__device__ __forceinline__ void slice_dots(const float2* Vr, size_t ld, const float2* ws, int len, int nv,
+                                           bool with_norm, float2* out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nt = nv + (with_norm ? 1 : 0);
+    for (int k = wid; k < nt; k += KTD / 32) {
+        const float2* row = (k < nv) ? Vr + (size_t)k * ld : ws;
+        df a0{0.f, 0.f}, a1{0.f, 0.f};
+        int e = lane;
+        for (; e + 32 < len; e += 64) {
+            df_acc(a0, df_mul(df_of(row[e]), df_of(ws[e])));
+            df_acc(a1, df_mul(df_of(row[e + 32]), df_of(ws[e + 32])));
+        }
+        if (e < len) df_acc(a0, df_mul(df_of(row[e]), df_of(ws[e])));
+        df_acc(a0, a1);
+        for (int o = 16; o > 0; o >>= 1) {
+            const df t{__shfl_down_sync(full, a0.h, o), __shfl_down_sync(full, a0.l, o)};
+            df_acc(a0, t);
+        }
+        if (lane == 0) out[k] = f2_of(df_renorm(a0));
+    }
+}
+
+// hs[k] = sum_b part[b * ld + k] over the nb blocks, k < nv, in double-float:
+// staged (the partials loaded at once, up to kStageLoads independent loads per
+// thread, into `stage`, at least nb * nv entries) when it fits, else read in
+// place; 8 threads per coefficient each add a contiguous eighth of the blocks,
+// then the eighths in order.  The result is the same in every block.
+constexpr int kStageLoads = 4;
+
+__device__ __forceinline__ void reduce_coeffs_df(const float2* part, int ld, int nv, int nb, float2* hs,
+                                                 float2* stage, bool staged, float2 (*red8)[KTD / 8]) {
+    if (staged) {
+        const int tot = nv * nb;
+        for (int e0 = 0; e0 < tot; e0 += kStageLoads * KTD) {
+            float2 v[kStageLoads];
+#pragma unroll
+            for (int u = 0; u < kStageLoads; ++u) {
+                const int e = e0 + u * KTD + threadIdx.x;  // e = b * nv + k
+                if (e < tot) {
+                    const int b = e / nv, k = e - b * nv;
+                    v[u] = __ldcg(part + (size_t)b * ld + k);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kStageLoads; ++u) {
+                const int e = e0 + u * KTD + threadIdx.x;
+                if (e < tot) stage[e] = v[u];
+            }
+        }
+        __syncthreads();
+    }
+    const int per = (nb + 7) / 8;
+    for (int k0 = 0; k0 < nv; k0 += KTD / 8) {
+        const int k = k0 + (threadIdx.x >> 3), slice = threadIdx.x & 7;
+        df t{0.f, 0.f};
+        if (k < nv) {
+            const int b0 = min(nb, slice * per), b1 = min(nb, b0 + per);
+            for (int b = b0; b < b1; ++b)
+                df_acc(t, df_of(staged ? stage[b * nv + k] : __ldcg(part + (size_t)b * ld + k)));
+        }
+        red8[slice][threadIdx.x >> 3] = f2_of(t);
+        __syncthreads();
+        if (threadIdx.x < KTD / 8 && k0 + (int)threadIdx.x < nv) {
+            df u = df_of(red8[0][threadIdx.x]);
+            for (int sl = 1; sl < 8; ++sl) df_acc(u, df_of(red8[sl][threadIdx.x]));
+            hs[k0 + threadIdx.x] = f2_of(df_renorm(u));
+        }
+        __syncthreads();
+    }
+}
+
+// sum_k Vr[k ld + e] c_k for k < nv (two interleaved compensated sums)
+__device__ __forceinline__ df slice_combo(const float2* Vr, size_t ld, int nv, int e, const float2* c) {
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
+    int k = 0;
+    for (; k + 1 < nv; k += 2) {
+        df_acc(s0, df_mul(df_of(Vr[(size_t)k * ld + e]), df_of(c[k])));
+        df_acc(s1, df_mul(df_of(Vr[(size_t)(k + 1) * ld + e]), df_of(c[k + 1])));
+    }
+    if (k < nv) df_acc(s0, df_mul(df_of(Vr[(size_t)k * ld + e]), df_of(c[k])));
+    df_acc(s0, s1);
+    return s0;
+}
+
+// givens_step_warp0 for the double-float step: the column x = hcol (h1 + h2,
+// FP64, k <= j) and h_{j+1,j} = hn in double-float.  The previous rotations
+// by the same scan; the new rotation (a square root and a reciprocal, each a
+// chain of hundreds of cycles on GB300's FP64 pipe) in double-float on the
+// FP32 pipe, rounded to FP64 where it is stored.
+__device__ void givens_df_warp0(int j, df hn, double* hcol, const double* scs, const double* ssn, double gj,
+                                KPtrs p, KState* s) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;  // warp 0
+    double zj;
+    if (j <= 32) {
+        const double x0 = hcol[0];
+        double a = 1.0, b = 0.0, ck = 1.0, sk = 0.0, xk1 = 0.0;
+        if (lane < j) {
+            ck = scs[lane];
+            sk = ssn[lane];
+            xk1 = hcol[lane + 1];
+            a = -sk;
+            b = ck * xk1;
+        }
+        for (int o = 1; o < 32; o <<= 1) {  // (a, b) <- (a, b) o (ap, bp)
+            const double ap = __shfl_up_sync(full, a, o), bp = __shfl_up_sync(full, b, o);
+            if (lane >= o) {
+                b = fma(a, bp, b);
+                a *= ap;
+            }
+        }
+        const double znext = fma(a, x0, b);                       // z_{lane+1}
+        const double zprev = __shfl_up_sync(full, znext, 1);
+        const double zcur = (lane == 0) ? x0 : zprev;             // z_lane
+        __syncwarp();
+        if (lane < j) hcol[lane] = fma(ck, zcur, sk * xk1);       // y_lane
+        zj = (j == 0) ? x0 : __shfl_sync(full, znext, j - 1);
+    } else {
+        if (lane == 0) {
+            for (int k = 0; k < j; ++k) {
+                const double a = hcol[k], b = hcol[k + 1];
+                hcol[k] = scs[k] * a + ssn[k] * b;
+                hcol[k + 1] = -ssn[k] * a + scs[k] * b;
+            }
+        }
+        __syncwarp();
+        zj = hcol[j];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const double hnd = df_dbl(hn);
+        s->hnext = hnd;
+        const df z = df_split(zj);
+        const df g = df_split(gj);
+        const df r2 = df_plus(df_prod(z, z), df_prod(hn, hn));
+        df r{0.f, 0.f}, c{1.f, 0.f}, sn{0.f, 0.f};
+        if (r2.h > 0.f) {
+            r = df_sqrt(r2);
+            const df inv = df_rcp(r);
+            c = df_prod(z, inv);
+            sn = df_prod(hn, inv);
+        }
+        const df gn = df_prod(sn, g);
+        p.cs[j] = df_dbl(c);
+        p.sn[j] = df_dbl(sn);
+        hcol[j] = df_dbl(r);
+        hcol[j + 1] = 0.0;
+        p.g[j + 1] = -df_dbl(gn);
+        p.g[j] = df_dbl(df_prod(c, g));
+        const double est = fabs(df_dbl(gn));
+        s->est = est;
+        s->k = j + 1;
+        const bool bad = !isfinite(est) || !isfinite(hnd) || !isfinite(zj);
+        if (bad) s->nonfinite = 1;
+        if (bad || est <= s->tol * s->bnorm || j + 1 == s->restart || hnd == 0.0) s->done = 1;
+    }
+    __syncwarp();
+    double* colg = p.H + (size_t)j * p.ld;
+    for (int k = lane; k < j + 2; k += 32) colg[k] = hcol[k];
+}
+
+// Entries per block of the double-float step: even, so that every block's
+// range starts on a 16-byte boundary of the (even-length) vectors.
+__host__ __device__ __forceinline__ int arnoldi_df_per(int N, int nb) {
+    const int per = (N + nb - 1) / nb;
+    return per + (per & 1);
+}
+
+__global__ void __launch_bounds__(KTD) k_arnoldi_df(double* __restrict__ V, float2* __restrict__ Vd, int N,
+                                                    int j, float2* __restrict__ wd, KPtrs p, KState* s) {
+    if (s->done) return;  // set before this launch: the same in every block
+    __shared__ float2 red8[8][KTD / 8];
+    __shared__ float2 h1f[1025];
+    __shared__ float2 h2f[1025];
+    __shared__ double h1[1025];
+    __shared__ float2 s_hnf, s_inv;
+    __shared__ __align__(8) unsigned long long s_bar;
+    // dynamic: pool (h2 and the Givens staging), the staging area of the
+    // coefficient sums, then the range of Vd_0 .. Vd_j and w
+    extern __shared__ __align__(16) double s_dyn[];
+    double* h2 = s_dyn;
+    double* scs = s_dyn + 1025;
+    double* ssn = s_dyn + 2049;
+    float2* s_stage = reinterpret_cast<float2*>(s_dyn + kPool);
+    float2* s_slice = reinterpret_cast<float2*>(s_dyn + kPool + kStage);
+    const int nv = j + 1, nb = gridDim.x;
+    const bool staged = nb * (nv + 1) <= kStage;
+    const int per = arnoldi_df_per(N, nb);
+    const int i0 = min(N, (int)blockIdx.x * per), i1 = min(N, i0 + per);
+    const int len = i1 - i0;
+    const bool in_smem = (size_t)(nv + 1) * per * sizeof(float2) <= (size_t)kSliceBytes;
+    float2* part1 = reinterpret_cast<float2*>(p.part);
+    float2* part2 = reinterpret_cast<float2*>(p.part + (size_t)KB_MAX * p.ld);
+    double* w = V + (size_t)(j + 1) * N;  // the product A v_j, overwritten by v_{j+1}
+    // the rows of the range: Vr + k ld (k < nv), and w' at ws
+    const float2* Vr;
+    size_t ld;
+    float2* ws;
+    unsigned bar_base = 0;
+    if (threadIdx.x == 0) {
+        const unsigned c = *(volatile unsigned*)&s->bar_count;
+        bar_base = c - c % (unsigned)nb;  // no block of this launch has passed a barrier yet
+    }
+    if (in_smem) {
+        Vr = s_slice;
+        ld = per;
+        ws = s_slice + (size_t)nv * per;
+        if (threadIdx.x == 0) {
+            mbar_init(&s_bar);
+            if (len > 0) {
+                const unsigned row = (unsigned)len * sizeof(float2);
+                mbar_expect_tx(&s_bar, row * (nv + 1));
+                bulk_load(ws, w + i0, row, &s_bar);  // FP64 w, split in place below
+                for (int k = 0; k < nv; ++k) bulk_load(s_slice + (size_t)k * per, Vd + (size_t)k * N + i0, row, &s_bar);
+            } else {
+                mbar_expect_tx(&s_bar, 0);
+            }
+        }
+        __syncthreads();
+        mbar_wait_bounded(&s_bar, 0, s);
+        const double* wsrc = reinterpret_cast<const double*>(ws);
+        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split(wsrc[e]));
+    } else {
+        Vr = Vd + i0;
+        ld = N;
+        ws = wd + i0;
+        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split(w[i0 + e]));
+    }
+    __syncthreads();
+    // first pass: h1 = V^T w
+    slice_dots(Vr, ld, ws, len, nv, false, part1 + (size_t)blockIdx.x * p.ld);
+    grid_barrier_count(s, bar_base + (unsigned)nb);
+    reduce_coeffs_df(part1, p.ld, nv, nb, h1f, s_stage, staged, red8);
+    // w' = w - V h1 on the range, then the second pass h2 = V^T w' with ||w'||^2
+    for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_minus(df_of(ws[e]), slice_combo(Vr, ld, nv, e, h1f)));
+    __syncthreads();
+    slice_dots(Vr, ld, ws, len, nv, true, part2 + (size_t)blockIdx.x * p.ld);
+    if (blockIdx.x == 0) givens_stage(j, scs, ssn, p);
+    grid_barrier_count(s, bar_base + 2u * (unsigned)nb);
+    reduce_coeffs_df(part2, p.ld, nv + 1, nb, h2f, s_stage, staged, red8);
+    // warp 0: ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 (an orthonormal basis) in
+    // double-float, its root and reciprocal; when more than half of ||w'||^2
+    // cancels, the norm is summed again after the update
+    if (threadIdx.x < 32) {
+        df q{0.f, 0.f};
+        for (int k = threadIdx.x; k < nv; k += 32) {
+            const df v = df_of(h2f[k]);
+            df_acc(q, df_mul(v, v));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const df t{__shfl_down_sync(0xffffffffu, q.h, o), __shfl_down_sync(0xffffffffu, q.l, o)};
+            df_acc(q, t);
+        }
+        if (threadIdx.x == 0) {
+            const df n2 = df_of(h2f[nv]);
+            const df d = df_minus(n2, df_renorm(q));
+            const df hn = (d.h > 0.5f * n2.h) ? df_sqrt(d) : df{-1.f, 0.f};
+            s_hnf = f2_of(hn);
+            s_inv = f2_of((hn.h > 0.f && isfinite(hn.h)) ? df_rcp(hn) : df{1.f, 0.f});
+        }
+    }
+    __syncthreads();
+    df hn = df_of(s_hnf);
+    float2* vnext = Vd + (size_t)(j + 1) * N + i0;
+    double* wout = w + i0;
+    if (hn.h < 0.f) {  // the same decision in every block
+        df acc{0.f, 0.f};
+        for (int e = threadIdx.x; e < len; e += KTD) {
+            const df wi = df_minus(df_of(ws[e]), slice_combo(Vr, ld, nv, e, h2f));
+            ws[e] = f2_of(wi);
+            df_acc(acc, df_mul(wi, wi));
+        }
+        s_stage[threadIdx.x] = f2_of(acc);  // the staging area is free again
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            df t{0.f, 0.f};
+            for (int e = 0; e < KTD; ++e) df_acc(t, df_of(s_stage[e]));
+            part1[(size_t)blockIdx.x * p.ld] = f2_of(df_renorm(t));
+        }
+        grid_barrier_count(s, bar_base + 3u * (unsigned)nb);
+        if (threadIdx.x == 0) {
+            df t{0.f, 0.f};
+            for (int b = 0; b < nb; ++b) df_acc(t, df_of(__ldcg(part1 + (size_t)b * p.ld)));
+            t = df_renorm(t);
+            const df h = (t.h > 0.f) ? df_sqrt(t) : df{0.f, 0.f};
+            s_hnf = f2_of(h);
+            s_inv = f2_of((h.h > 0.f && isfinite(h.h)) ? df_rcp(h) : df{1.f, 0.f});
+        }
+        __syncthreads();
+        hn = df_of(s_hnf);
+        const df inv = df_of(s_inv);
+        for (int e = threadIdx.x; e < len; e += KTD) {
+            const df v = df_renorm(df_mul(df_of(ws[e]), inv));
+            vnext[e] = f2_of(v);
+            wout[e] = df_dbl(v);
+        }
+        if (blockIdx.x == 0) {
+            for (int k = threadIdx.x; k <= nv; k += KTD) {
+                h1[k] = df_dbl(df_of(h1f[k]));
+                h2[k] = df_dbl(df_of(h2f[k]));
+            }
+            __syncthreads();
+            givens_step(j, df_dbl(hn), h1, h2, scs, ssn, p, s);
+        }
+    } else {  // v_{j+1} = (w' - V h2) / h_{j+1,j} in one pass (unused when the cycle stops here)
+        const df inv = df_of(s_inv);
+        // block 0: warp 0 does the Givens update while the other warps update the range
+        const int t0 = (blockIdx.x == 0) ? 32 : 0;
+        if (blockIdx.x == 0 && threadIdx.x < 32) {
+            for (int k = threadIdx.x; k < nv; k += 32) h1[k] = df_dbl(df_plus(df_of(h1f[k]), df_of(h2f[k])));
+            __syncwarp();
+            givens_df_warp0(j, hn, h1, scs, ssn, scs[1023], p, s);
+        }
+        if ((int)threadIdx.x >= t0) {
+            for (int e = (int)threadIdx.x - t0; e < len; e += KTD - t0) {
+                const df wi = df_minus(df_of(ws[e]), slice_combo(Vr, ld, nv, e, h2f));
+                const df v = df_renorm(df_mul(wi, inv));
+                vnext[e] = f2_of(v);
+                wout[e] = df_dbl(v);
+            }
+        }
+    }
+}
+
+// y = H(0:k, 0:k)^-1 g(0:k) at the end of a cycle (one block), by columns:
+// once y_c is known, every row r < c takes its term H(r, c) y_c at once, so
+// the dependent chain is one multiply and one multiply-add per column (on
+// GB300's 2-lane FP64 pipe a row-by-row loop of one thread costs k^2/2
+// dependent steps).  The diagonal's reciprocals are formed first, in
+// parallel.  k <= kSmallH: warp 0, H staged in shared memory, two rows per
+// lane in registers; longer cycles: the whole block, H read in place.
+constexpr int kSmallH = 64;
 
 __global__ void __launch_bounds__(KT) k_solve_y(KPtrs p, const KState* s) {
-    __shared__ double sH[kSmallH * kSmallH], sg[kSmallH];
+    __shared__ double sH[kSmallH * kSmallH];  // k > kSmallH: the rows' values and reciprocals instead
+    double* sv = sH;
+    double* sinv = sH + 1024;
     const int kk = s->k;
     if (kk == 0) return;
     if (kk <= kSmallH) {
         for (int e = threadIdx.x; e < kk * kk; e += KT) sH[e] = p.H[(size_t)(e / kk) * p.ld + (e % kk)];
-        for (int e = threadIdx.x; e < kk; e += KT) sg[e] = p.g[e];
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int row = kk - 1; row >= 0; --row) {  // sH[c * kk + r] = H(r, c)
-                double v = sg[row];
-                for (int c = row + 1; c < kk; ++c) v -= sH[c * kk + row] * sg[c];
-                const double d = sH[row * kk + row];
-                sg[row] = (d != 0.0) ? v / d : 0.0;  // y overwrites g from the bottom up
+        if (threadIdx.x >= 32) return;
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x;
+        // rows lane and lane + 32: right-hand side and 1 / H(r, r) (0 where H(r, r) = 0)
+        double g0 = (lane < kk) ? p.g[lane] : 0.0, g1 = (lane + 32 < kk) ? p.g[lane + 32] : 0.0;
+        const double d0 = (lane < kk) ? sH[lane * kk + lane] : 1.0;
+        const double d1 = (lane + 32 < kk) ? sH[(lane + 32) * kk + lane + 32] : 1.0;
+        const double i0 = (d0 != 0.0) ? 1.0 / d0 : 0.0, i1 = (d1 != 0.0) ? 1.0 / d1 : 0.0;
+        for (int c = kk - 1; c >= 0; --c) {  // sH[c * kk + r] = H(r, c)
+            const double own = (c < 32) ? g0 * i0 : g1 * i1;
+            const double yc = __shfl_sync(full, own, c & 31);
+            if (lane == (c & 31)) {
+                if (c < 32) g0 = yc; else g1 = yc;
             }
+            if (lane < c) g0 = fma(-sH[c * kk + lane], yc, g0);
+            if (lane + 32 < c) g1 = fma(-sH[c * kk + lane + 32], yc, g1);
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kk; e += KT) p.y[e] = sg[e];
+        if (lane < kk) p.y[lane] = g0;
+        if (lane + 32 < kk) p.y[lane + 32] = g1;
         return;
     }
-    if (threadIdx.x != 0) return;
-    for (int row = kk - 1; row >= 0; --row) {
-        double v = p.g[row];
-        for (int c = row + 1; c < kk; ++c) v -= p.H[(size_t)c * p.ld + row] * p.y[c];
-        const double d = p.H[(size_t)row * p.ld + row];
-        p.y[row] = (d != 0.0) ? v / d : 0.0;
+    for (int r = threadIdx.x; r < kk; r += KT) {
+        sv[r] = p.g[r];
+        const double d = p.H[(size_t)r * p.ld + r];
+        sinv[r] = (d != 0.0) ? 1.0 / d : 0.0;
     }
+    __syncthreads();
+    for (int c = kk - 1; c >= 0; --c) {
+        const double yc = sv[c] * sinv[c];
+        __syncthreads();  // every thread has read sv[c]
+        if (threadIdx.x == 0) sv[c] = yc;
+        for (int r = threadIdx.x; r < c; r += KT) sv[r] = fma(-p.H[(size_t)c * p.ld + r], yc, sv[r]);
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < kk; r += KT) p.y[r] = sv[r];
 }
 
 // x += V(:, 0:k) y at the end of a cycle
@@ -601,6 +1099,18 @@ __global__ void k_init_state(KState* s, double tol, int restart, int bar_limit, 
 std::atomic<int> g_bar_limit{kBarSpin};
 std::atomic<int> g_bar_skip{-1};
 
+size_t krylov_basis_bytes(int restart, int N) {
+    return (size_t)(restart + 1) * N * (sizeof(double) + sizeof(float2)) + (size_t)N * sizeof(float2);
+}
+
+float2* basis_df(const Boundary& b) {
+    return reinterpret_cast<float2*>(b.V + (size_t)b.V_cols * b.N);
+}
+
+float2* basis_df_scratch(const Boundary& b) {
+    return basis_df(b) + (size_t)b.V_cols * b.N;
+}
+
 int ensure_krylov(Boundary& b, int restart, cudaStream_t st) {
     if (restart + 1 > 1024) {
         set_error("restart must be below 1024");
@@ -610,8 +1120,9 @@ int ensure_krylov(Boundary& b, int restart, cudaStream_t st) {
         if (b.V) pool_free(b.V, st);
         b.V = nullptr;
         b.V_cols = 0;
-        if (pool_alloc(reinterpret_cast<void**>(&b.V), (size_t)(restart + 1) * b.N * sizeof(double), st) !=
-            cudaSuccess) {
+        // V (FP64), its double-float copy Vd and the scratch wd of the
+        // double-float Arnoldi step, in one allocation
+        if (pool_alloc(reinterpret_cast<void**>(&b.V), krylov_basis_bytes(restart, b.N), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("cannot allocate the Krylov basis: %d x %d doubles", restart + 1, b.N);
             return GNK_ENOMEM;
@@ -659,16 +1170,20 @@ static int arnoldi_blocks(int N) {
     std::lock_guard<std::mutex> lock(mu);
     if ((int)cap.size() <= dev) cap.resize(dev + 1, 0);
     if (cap[dev] == 0) {
-        int occ = 0, nsm = 0;
+        int occ = 0, occ_df = 0, nsm = 0;
         if (cudaFuncSetAttribute((const void*)k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kArnoldiDyn) != cudaSuccess ||
+            cudaFuncSetAttribute((const void*)k_arnoldi_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kArnoldiDfDyn) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, KT, kArnoldiDyn) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_df, k_arnoldi_df, KTD, kArnoldiDfDyn) !=
+                cudaSuccess ||
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
-            occ = 1;
+            occ = occ_df = 1;
             nsm = 1;
         }
-        cap[dev] = std::max(1, std::min(occ, 1) * nsm);  // one block per multiprocessor
+        cap[dev] = std::max(1, std::min(std::min(occ, occ_df), 1) * nsm);  // one block per multiprocessor
     }
     return std::max(1, std::min(std::min(cap[dev], KB_MAX), (N + KT - 1) / KT));
 }
@@ -695,6 +1210,8 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
     KPtrs p = kry_ptrs(b.kry, restart);
     const int nb = vec_blocks(N);
     const int ng = arnoldi_blocks(N);
+    // Gram-Schmidt in double-float for every operator precision but plain FP64
+    const bool dfa = prec != GNK_PREC_FP64;
     KState hs;
     k_init_state<<<1, 1, 0, st>>>(ks, tol, restart, g_bar_limit.load(), g_bar_skip.load());
     KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(rhs, N, p, ks, 0)));
@@ -714,7 +1231,7 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
             if (fc_valid && fc_out) *fc_valid = 1;  // f_C of the current x
         }
         KLAUNCH(vb, (k_norm<<<nb, KT, 0, st>>>(r, N, p, ks, 1)));
-        KLAUNCH(2 * vb, (k_scale_first<<<nb, KT, 0, st>>>(r, b.V, N, ks)));
+        KLAUNCH((dfa ? 3 : 2) * vb, (k_scale_first<<<nb, KT, 0, st>>>(r, b.V, dfa ? basis_df(b) : nullptr, N, ks)));
         count_launches(2);
         GNK_TRY_CUDA(cudaGetLastError());
         GNK_TRY(read_state(b, &hs, st));
@@ -753,7 +1270,17 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
             const double nv = j + 1;
             prof_collect_begin();
             GNK_TRY(apply_op(b, adjoint, vj, w, prec, st, &ks->done));
-            {
+            if (dfa) {
+                double* Vc = b.V;
+                float2* Vdc = basis_df(b);
+                float2* wdc = basis_df_scratch(b);
+                int Nc = N, jc = j;
+                void* args[] = {(void*)&Vc, (void*)&Vdc, (void*)&Nc, (void*)&jc, (void*)&wdc, (void*)&p,
+                                (void*)&ks};
+                KLAUNCH((3 * nv + 9) * vb, GNK_TRY_CUDA(cudaLaunchCooperativeKernel(
+                                               (const void*)k_arnoldi_df, dim3(ng), dim3(KTD), args,
+                                               kArnoldiDfDyn, st)));
+            } else {
                 const double* Vc = b.V;
                 int Nc = N, jc = j;
                 void* args[] = {(void*)&Vc, (void*)&Nc, (void*)&jc, (void*)&w, (void*)&p, (void*)&ks};
