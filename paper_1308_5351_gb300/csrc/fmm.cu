@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "tma.cuh"
 #include "epilogue.cuh"
 #include "gnk_internal.h"
 #include "pairmath.cuh"
@@ -91,6 +92,7 @@ struct FmmArgs {
     int* ucnt;            // per box: children counted in the upward pass
     float2* xs;           // [R][N] x in sorted order as double-float (cached near field), or null
     const float4* tp;     // [N][P] powers t^k of every node about its leaf centre, or null
+    int* fault;           // set by a bounded wait that gave up
 };
 
 __global__ void fmm_gather_kernel(FmmArgs a) {
@@ -719,7 +721,7 @@ __global__ void fmm_nq_count_kernel(FmmArgs a, long long* cnt, long long* scnt) 
     int S, tn;
     nq_item_shape(a, it, &S, &tn, nullptr, nullptr, nullptr);
     cnt[it] = (long long)((S + 1) / 2) * tn;
-    scnt[it] = S;
+    scnt[it] = S + (S & 1);  // lists padded to even length (16-byte aligned chunks of x)
 }
 
 // off[i] = cnt[0] + ... + cnt[i - 1] for i <= n (one block of 1024 threads,
@@ -854,103 +856,126 @@ __global__ void __launch_bounds__(kFmmNT) fmm_nq_build_kernel(FmmArgs a, const d
     }
 }
 
-// The near field of z = E(q x) from the cache: one block per work item, warp w
-// taking its share of the source pairs in chunks of up to 32 pairs, lane =
-// target.  Each warp starts from the item's descriptor and source list (no
-// walk over the neighbour leaves) and issues the loads of its first cache
-// entries before it gathers the chunk's x into shared memory, so that the
-// streams of cache entries and of x overlap; even and odd sources in the two
-// halves of packed float2 sums, added at the end, then the warps' sums in
-// warp order.  COMP = 1: Im z only (Re z written as 0).
-constexpr int kNqChunk = 32;   // source pairs per chunk (64 sources)
-constexpr int kNqAhead = 8;    // cache entries loaded before the gather of x
+// x in the items' source-list order for the cached near field:
+// xl[r][q] = xs[r][nq_src[q]] (0 at the lists' padding), so that each chunk of
+// a work item's sources is one contiguous, 16-byte aligned run.
+__global__ void fmm_nq_xlist_kernel(const int* __restrict__ src, long long qb, int R, int N,
+                                    const float2* __restrict__ xs, float2* __restrict__ xl, const int* done) {
+    if (done != nullptr && *done) return;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= qb) return;
+    const int j = src[q];
+    for (int r = 0; r < R; ++r) xl[(size_t)r * qb + q] = (j >= 0) ? xs[(size_t)r * N + j] : make_float2(0.f, 0.f);
+}
+
+// The near field of z = E(q x) from the cache, streamed into shared memory by
+// the Tensor Memory Accelerator: one block per work item; a producer warp
+// issues bulk copies of the item's cache entries (contiguous, pair-major) and
+// of its sources' x (list order) in chunks of kNbPairs source pairs through a
+// ring of kNbStages buffers (full/empty mbarriers); 8 consumer warps, lane =
+// target, warp w taking pairs w, w + 8, ... of each chunk.  Even and odd
+// sources go to the two halves of packed float2 sums, added at the end, then
+// the warps' sums in warp order.  COMP = 1: Im z only (Re z written as 0).
+// Every wait is bounded (kNbSpin polls); one that gives up sets a.fault, and
+// the producer still waits (bounded) for its copies in flight before leaving.
+constexpr int kNbPairs = 32;                 // source pairs per chunk
+constexpr int kNbStages = 3;
+constexpr int kNbThreads = kFmmNT + 32;      // 8 consumer warps and the producer warp
+constexpr int kNbSpin = 1 << 22;
 
 template <int R, int COMP>
-__global__ void __launch_bounds__(kFmmNT) fmm_near_cached_kernel(FmmArgs a, const long long* __restrict__ off,
-                                                                 const int4* __restrict__ nq_item,
-                                                                 const int* __restrict__ nq_src,
-                                                                 const float4* __restrict__ nq_re,
-                                                                 const float4* __restrict__ nq_im) {
-    __shared__ float s_x[kFmmWarps][R][2][2 * kNqChunk];
+struct NbLayout {
+    static constexpr int kParts = COMP == 0 ? 2 : 1;
+    static constexpr int kQ = kNbPairs * 32;                  // float4 entries of one part (tn <= 32)
+    static constexpr int kX = kNbPairs;                       // float4 of x per right-hand side (a pair each)
+    static constexpr int kStage = kParts * kQ + R * kX;       // float4 per stage
+    static constexpr int kBytes = kNbStages * kStage * 16;    // dynamic shared memory
+};
+
+template <int R, int COMP>
+__global__ void __launch_bounds__(kNbThreads) fmm_near_bulk_kernel(FmmArgs a, const long long* __restrict__ off,
+                                                                   const int4* __restrict__ nq_item,
+                                                                   const float4* __restrict__ nq_re,
+                                                                   const float4* __restrict__ nq_im,
+                                                                   const float2* __restrict__ xl, long long qb) {
+    using L = NbLayout<R, COMP>;
+    extern __shared__ __align__(16) float4 nb_buf[];
+    __shared__ __align__(8) unsigned long long full[kNbStages], empty[kNbStages];
     __shared__ double2 s_z[kFmmWarps][R][32];
+    if (a.done != nullptr && *a.done) return;  // set before this launch: the same in every thread
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x;
     const int4 d = __ldg(nq_item + it);  // (S, tn, first source)
     const long long o0 = __ldg(off + it);
-    if (a.done != nullptr && *a.done) return;
-    const int S = d.x, tn = d.y;
+    const int S = d.x, tn = d.y, src0 = d.z;
     const int npair = (S + 1) >> 1;
-    const int p0 = (int)((long long)npair * wid / kFmmWarps), p1 = (int)((long long)npair * (wid + 1) / kFmmWarps);
-    const bool act = lane < tn;
-    const long long base = o0 + lane;
+    const int nch = (npair + kNbPairs - 1) / kNbPairs;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kNbStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kFmmWarps);
+        }
+    }
+    __syncthreads();
+    if (wid == kFmmWarps) {  // the producer
+        if (lane == 0) {
+            int c = 0;
+            for (; c < nch; ++c) {
+                const int st = c % kNbStages;
+                if (c >= kNbStages && !mbar_wait(&empty[st], (unsigned)((c / kNbStages - 1) & 1), kNbSpin)) {
+                    atomicExch(a.fault, 1);
+                    break;
+                }
+                const int p0 = c * kNbPairs, np = min(kNbPairs, npair - p0);
+                const unsigned qbytes = (unsigned)(np * tn) * 16u, xbytes = (unsigned)np * 16u;
+                float4* stage = nb_buf + (size_t)st * L::kStage;
+                mbar_expect_tx(&full[st], L::kParts * qbytes + R * xbytes);
+                bulk_load(stage, nq_im + o0 + (long long)p0 * tn, qbytes, &full[st]);
+                if (COMP == 0) bulk_load(stage + L::kQ, nq_re + o0 + (long long)p0 * tn, qbytes, &full[st]);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    bulk_load(stage + L::kParts * L::kQ + r * L::kX, xl + (size_t)r * qb + src0 + 2 * p0, xbytes,
+                              &full[st]);
+            }
+            // the copies still in flight land before the warp leaves
+            for (int k = max(0, c - kNbStages); k < c; ++k)
+                mbar_wait(&full[k % kNbStages], (unsigned)((k / kNbStages) & 1), kNbSpin);
+        }
+        return;
+    }
     df2 are[R], aim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) are[r] = aim[r] = df2{f2(0.f), f2(0.f)};
-    for (int ps = p0; ps < p1; ps += kNqChunk) {
-        const int np = min(kNqChunk, p1 - ps);
-        // the first cache entries of the chunk, before the gather of x
-        float4 vi[kNqAhead], vr[kNqAhead];
-#pragma unroll
-        for (int u = 0; u < kNqAhead; ++u) {
-            if (act && u < np) {
-                const size_t o = (size_t)(base + (long long)(ps + u) * tn);
-                vi[u] = __ldcs(nq_im + o);
-                if (COMP == 0) vr[u] = __ldcs(nq_re + o);
-            }
+    for (int c = 0; c < nch; ++c) {
+        const int st = c % kNbStages;
+        if (!mbar_wait(&full[st], (unsigned)((c / kNbStages) & 1), kNbSpin)) {
+            atomicExch(a.fault, 1);
+            break;
         }
-        {  // x of the chunk's sources (two per lane)
-            const int cnt = min(2 * np, S - 2 * ps);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int q = lane + 32 * h;
-                if (q < 2 * np) {
-                    const int j = __ldg(nq_src + d.z + 2 * ps + min(q, cnt - 1));
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 xv = (q < cnt) ? a.xs[(size_t)r * a.N + j] : make_float2(0.f, 0.f);
-                        s_x[wid][r][0][q] = xv.x;
-                        s_x[wid][r][1][q] = xv.y;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (act) {
-#pragma unroll
-            for (int u = 0; u < kNqAhead; ++u) {
-                if (u < np) {
-                    const df2 Qi{make_float2(vi[u].x, vi[u].y), make_float2(vi[u].z, vi[u].w)};
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const df2 xv{reinterpret_cast<const float2*>(s_x[wid][r][0])[u],
-                                     reinterpret_cast<const float2*>(s_x[wid][r][1])[u]};
-                        if (COMP == 0)
-                            df2_acc(are[r], df2_mul(xv, df2{make_float2(vr[u].x, vr[u].y),
-                                                            make_float2(vr[u].z, vr[u].w)}));
-                        df2_acc(aim[r], df2_mul(xv, Qi));
-                    }
-                }
-            }
-#pragma unroll 8
-            for (int pp = kNqAhead; pp < np; ++pp) {
-                const size_t o = (size_t)(base + (long long)(ps + pp) * tn);
-                const float4 wi = __ldcs(nq_im + o);
+        const float4* qi = nb_buf + (size_t)st * L::kStage;
+        const float4* qr = qi + L::kQ;
+        const float4* xv4 = qi + L::kParts * L::kQ;
+        const int np = min(kNbPairs, npair - c * kNbPairs);
+        if (lane < tn) {
+            for (int pp = wid; pp < np; pp += kFmmWarps) {
+                const float4 wi = qi[pp * tn + lane];
                 const df2 Qi{make_float2(wi.x, wi.y), make_float2(wi.z, wi.w)};
                 df2 Qr{f2(0.f), f2(0.f)};
                 if (COMP == 0) {
-                    const float4 wr = __ldcs(nq_re + o);
+                    const float4 wr = qr[pp * tn + lane];
                     Qr = df2{make_float2(wr.x, wr.y), make_float2(wr.z, wr.w)};
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const df2 xv{reinterpret_cast<const float2*>(s_x[wid][r][0])[pp],
-                                 reinterpret_cast<const float2*>(s_x[wid][r][1])[pp]};
+                    const float4 v = xv4[r * L::kX + pp];  // (hi, lo) of sources 2pp and 2pp + 1
+                    const df2 xv{make_float2(v.x, v.z), make_float2(v.y, v.w)};
                     if (COMP == 0) df2_acc(are[r], df2_mul(xv, Qr));
                     df2_acc(aim[r], df2_mul(xv, Qi));
                 }
             }
         }
         __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -958,8 +983,8 @@ __global__ void __launch_bounds__(kFmmNT) fmm_near_cached_kernel(FmmArgs a, cons
         const df si = df_add(df{aim[r].h.x, aim[r].l.x}, df{aim[r].h.y, aim[r].l.y});
         s_z[wid][r][lane] = make_double2((double)sr.h + (double)sr.l, (double)si.h + (double)si.l);
     }
-    __syncthreads();
-    if (wid == 0 && act) {
+    asm volatile("bar.sync 1, %0;" ::"r"(kFmmNT) : "memory");  // the consumer warps only
+    if (wid == 0 && lane < tn) {
         const int i = a.items[it].y + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -1117,7 +1142,7 @@ void release_fmm(Boundary& b) {
         if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
         if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
 
-        if (b.fmm->arena || b.fmm->sync || b.fmm->nq_re || b.fmm->tp) {  // once no stream uses them
+        if (b.fmm->arena || b.fmm->sync || b.fmm->nq_re || b.fmm->tp || b.fmm->fault) {  // once no stream uses them
             cudaDeviceSynchronize();
             cudaGetLastError();
             pool_free(b.fmm->arena, 0);
@@ -1130,6 +1155,8 @@ void release_fmm(Boundary& b) {
             pool_free(b.fmm->nq_re, 0);
             pool_free(b.fmm->nq_im, 0);
             pool_free(b.fmm->xs, 0);
+            pool_free(b.fmm->xl, 0);
+            pool_free(b.fmm->fault, 0);
             pool_free(b.fmm->tp, 0);
         }
         delete b.fmm;
@@ -1498,7 +1525,9 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     if (rc == GNK_OK) {  // the upward pass's child counts, all zero
         const size_t nsync = (size_t)t->nbox;
         if (pool_alloc(reinterpret_cast<void**>(&t->sync), nsync * sizeof(int), st) != cudaSuccess ||
-            cudaMemsetAsync(t->sync, 0, nsync * sizeof(int), st) != cudaSuccess) {
+            cudaMemsetAsync(t->sync, 0, nsync * sizeof(int), st) != cudaSuccess ||
+            pool_alloc(reinterpret_cast<void**>(&t->fault), sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(t->fault, 0, sizeof(int), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("FMM: allocation of the pass counters failed");
             rc = GNK_ENOMEM;
@@ -1568,9 +1597,16 @@ double fmm_near_cached_instr(const Boundary& b, int R, int comp) {
 }
 
 double fmm_near_cached_bytes(const Boundary& b, int R, int comp) {
-    // 8 bytes per near pair and part of z read from the cache, x in (8 bytes)
-    // and z out (16 bytes) per node and right-hand side
-    return b.fmm ? 8.0 * (double)b.fmm->near_pairs * (comp == 1 ? 1.0 : 2.0) + 24.0 * R * b.N : 0.0;
+    // 8 bytes per near pair and part of z read from the cache, x in list order
+    // (8 bytes per list entry, counted at the lists' bound) and z out (16 bytes
+    // per node) per right-hand side
+    return b.fmm ? 8.0 * (double)b.fmm->near_pairs * (comp == 1 ? 1.0 : 2.0) +
+                       8.0 * R * (double)b.fmm->nq_qb + 16.0 * R * b.N
+                 : 0.0;
+}
+
+const int* fmm_fault_word(const Boundary& b) {
+    return b.fmm ? b.fmm->fault : nullptr;
 }
 
 // Forms the near-field operator cache of the products z = E(q x) once per
@@ -1588,7 +1624,12 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
     // device: sum_items ceil(S/2) tn <= (near pairs + N)/2 entries, and
     // sum_items S <= near pairs sources (each source meets at least one target)
     const size_t ni = (size_t)t->nitems;
-    const long long slots = (t->near_pairs + b.N) / 2 + 1, nsrc = t->near_pairs + 1;
+    // sum_items S = sum_leaves ceil(n_leaf / 32) S_leaf <= near pairs / 32 + sum_leaves S_leaf, and
+    // a leaf is a neighbour of at most kFmmMaxNbr leaves, so sum_leaves S_leaf <= kFmmMaxNbr N;
+    // plus one padding entry per item, rounded up to even
+    const long long slots = (t->near_pairs + b.N) / 2 + 1;
+    long long nsrc = t->near_pairs / 32 + (long long)kFmmMaxNbr * b.N + (long long)ni + 2;
+    nsrc += nsrc & 1;
     const size_t bytes = (size_t)slots * sizeof(float4);
     if (nsrc > INT32_MAX || 2.0 * (double)bytes > kNqMaxBytes) return GNK_OK;
     long long *cnt = nullptr, *soff = nullptr;
@@ -1599,7 +1640,8 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
         pool_alloc(reinterpret_cast<void**>(&t->nq_im), bytes, st) != cudaSuccess ||
         pool_alloc(reinterpret_cast<void**>(&t->nq_item), ni * sizeof(int4), st) != cudaSuccess ||
         pool_alloc(reinterpret_cast<void**>(&t->nq_src), (size_t)nsrc * sizeof(int), st) != cudaSuccess ||
-        pool_alloc(reinterpret_cast<void**>(&t->xs), (size_t)kMaxRHS * b.N * sizeof(float2), st) != cudaSuccess) {
+        pool_alloc(reinterpret_cast<void**>(&t->xs), (size_t)kMaxRHS * b.N * sizeof(float2), st) != cudaSuccess ||
+        pool_alloc(reinterpret_cast<void**>(&t->xl), (size_t)kMaxRHS * nsrc * sizeof(float2), st) != cudaSuccess) {
         cudaGetLastError();
         pool_free(cnt, st);
         pool_free(soff, st);
@@ -1609,6 +1651,8 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
         pool_free(t->nq_item, st);
         pool_free(t->nq_src, st);
         pool_free(t->xs, st);
+        pool_free(t->xl, st);
+        t->xl = nullptr;
         t->nq_off = nullptr;
         t->nq_re = t->nq_im = nullptr;
         t->nq_item = nullptr;
@@ -1617,6 +1661,7 @@ static int ensure_near_cache(const Boundary& b, cudaStream_t st) {
         return GNK_OK;
     }
     t->nq_slots = slots;
+    t->nq_qb = nsrc;
     t->nq_cnt = cnt;
     t->nq_soff = soff;
     t->nq_state = 2;  // allocated; formed by near_cache_build before the first cached near field
@@ -1634,6 +1679,7 @@ static int near_cache_build(const Boundary& b, cudaStream_t st) {
     long long* cnt = t->nq_cnt;
     long long* scnt = cnt + ni;
     long long* soff = t->nq_soff;
+    GNK_TRY_CUDA(cudaMemsetAsync(t->nq_src, 0xff, (size_t)t->nq_qb * sizeof(int), st));  // -1: padding
     fmm_nq_count_kernel<<<(t->nitems + 255) / 256, 256, 0, st>>>(a, cnt, scnt);
     fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(cnt, t->nitems, t->nq_off);
     fmm_nq_scan_kernel<<<1, 1024, 0, st>>>(scnt, t->nitems, soff);
@@ -1650,6 +1696,29 @@ static int near_cache_build(const Boundary& b, cudaStream_t st) {
     t->nq_cnt = nullptr;
     t->nq_soff = nullptr;
     t->nq_state = 1;
+    return GNK_OK;
+}
+
+template <int R, int COMP>
+static int launch_near_bulk(const Boundary& b, const FmmArgs& a, cudaStream_t st) {
+    using L = NbLayout<R, COMP>;
+    static std::mutex mu;
+    static std::vector<char> ready;  // per device: the shared-memory attribute is set
+    int dev = 0;
+    GNK_TRY_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if ((int)ready.size() <= dev) ready.resize(dev + 1, 0);
+        if (!ready[dev]) {
+            GNK_TRY_CUDA(cudaFuncSetAttribute(fmm_near_bulk_kernel<R, COMP>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
+            ready[dev] = 1;
+        }
+    }
+    const FmmTree* t = b.fmm;
+    fmm_near_bulk_kernel<R, COMP><<<t->nitems, kNbThreads, L::kBytes, st>>>(a, t->nq_off, t->nq_item, t->nq_re,
+                                                                            t->nq_im, t->xl, t->nq_qb);
+    GNK_TRY_CUDA(cudaGetLastError());
     return GNK_OK;
 }
 
@@ -1702,17 +1771,22 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
     // is 0 (both parts of z) or 1 (Im z only)); the first cached product forms
     // the cache here, beside its far field
     if (cached >= 0) GNK_TRY(near_cache_build(b, st));
+    if (cached >= 0) {  // x in the items' list order
+        fmm_nq_xlist_kernel<<<(unsigned)((t->nq_qb + 255) / 256), 256, 0, st>>>(t->nq_src, t->nq_qb, R, b.N, a.xs,
+                                                                               t->xl, a.done);
+        GNK_TRY_CUDA(cudaGetLastError());
+        ++launches;
+    }
     const ProfToken tokn = prof_begin(st, PK_FMMNEAR);
     if (cached >= 0) {
-        const long long* off = t->nq_off;
         if (R == 2 && cached == 1)
-            fmm_near_cached_kernel<2, 1><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+            GNK_TRY((launch_near_bulk<2, 1>(b, a, st)));
         else if (R == 2)
-            fmm_near_cached_kernel<2, 0><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+            GNK_TRY((launch_near_bulk<2, 0>(b, a, st)));
         else if (cached == 1)
-            fmm_near_cached_kernel<1, 1><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+            GNK_TRY((launch_near_bulk<1, 1>(b, a, st)));
         else
-            fmm_near_cached_kernel<1, 0><<<t->nitems, kFmmNT, 0, st>>>(a, off, t->nq_item, t->nq_src, t->nq_re, t->nq_im);
+            GNK_TRY((launch_near_bulk<1, 0>(b, a, st)));
     } else if (R == 2 && EF)
         fmm_near_kernel<2, true><<<t->nitems, kFmmNT, 0, st>>>(a);
     else if (R == 2)
@@ -1787,6 +1861,7 @@ static void fmm_args(const Boundary& b, FmmArgs& a) {
     a.nbox = t->nbox;
     a.outF = nullptr;
     a.done = nullptr;
+    a.fault = t->fault;
 }
 
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st) {

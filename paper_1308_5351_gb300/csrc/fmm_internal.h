@@ -62,10 +62,14 @@ struct FmmTree {
     long long nq_slots = 0;     // float4 entries of each of nq_re, nq_im
     long long* nq_off = nullptr;  // per work item: first entry (nitems + 1)
     int4* nq_item = nullptr;    // per work item: (S sources, tn targets, first source in nq_src, -)
-    int* nq_src = nullptr;      // the items' sources (sorted node indices), item after item
+    int* nq_src = nullptr;      // the items' sources (sorted node indices), item after item, each
+                                // item's list padded to even length with -1 (nq_qb entries)
+    long long nq_qb = 0;        // entries of nq_src (a bound on the lists' total, even)
     float4* nq_re = nullptr;
     float4* nq_im = nullptr;
     float2* xs = nullptr;       // [R][N] x in sorted order, double-float (cached products)
+    float2* xl = nullptr;       // [R][nq_qb] x in the items' source-list order (0 at padding)
+    int* fault = nullptr;       // set by a bounded wait of an FMM kernel that gave up
     float4* tp = nullptr;       // [N][P] powers t^k of each node about its leaf centre (P2M), or null
     cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -292,6 +292,8 @@ int ensure_fmm(const Boundary& b, int R, cudaStream_t st);
 void release_fmm(Boundary& b);
 double fmm_instr(const Boundary& b, int R, int which);
 double fmm_near_instr(const Boundary& b, int R);
+// Device word set by an FMM kernel whose bounded wait gave up (null before the tree).
+const int* fmm_fault_word(const Boundary& b);
 // the chunk reduction and epilogue of the pair sums, for products formed elsewhere
 cudaError_t launch_reduce_public(const Boundary& b, const PairJob& job, int chunks, int ptype,
                                  cudaStream_t st);

@@ -26,6 +26,7 @@
 
 #include "gnk_internal.h"
 #include "pairmath.cuh"
+#include "tma.cuh"
 
 namespace gnk {
 namespace {
@@ -590,10 +591,6 @@ __device__ __forceinline__ df df_rcp(df a) {
 constexpr int kSliceBytes = 128 * 1024;
 constexpr size_t kArnoldiDfDyn = kArnoldiDyn + kSliceBytes;
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -622,49 +619,13 @@ __device__ __forceinline__ void grid_barrier_count(KState* s, unsigned target) {
     __syncthreads();
 }
 
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                     smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared memory
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_done(unsigned long long* bar, unsigned phase) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
 // Waits for phase `phase` of the mbarrier with a limit; on a timeout sets
 // bar_err and waits once more (also bounded) for the copies in flight.
 __device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsigned phase, KState* s) {
     const int limit = s->bar_limit;
-    int it = 0;
-    while (!mbar_done(bar, phase)) {
-        if (++it >= limit) {
-            atomicExch(&s->bar_err, 1);
-            for (int k = 0; k < limit && !mbar_done(bar, phase); ++k) {
-            }
-            return;
-        }
+    if (!mbar_wait(bar, phase, limit)) {
+        atomicExch(&s->bar_err, 1);
+        mbar_wait(bar, phase, limit);
     }
 }
 
@@ -886,7 +847,7 @@ __global__ void __launch_bounds__(KTD) k_arnoldi_df(double* __restrict__ V, floa
         ld = per;
         ws = s_slice + (size_t)nv * per;
         if (threadIdx.x == 0) {
-            mbar_init(&s_bar);
+            mbar_init(&s_bar, 1);
             if (len > 0) {
                 const unsigned row = (unsigned)len * sizeof(float2);
                 mbar_expect_tx(&s_bar, row * (nv + 1));
@@ -1153,7 +1114,14 @@ int apply_op(const Boundary& b, int op, const double* x, double* y, int prec, cu
 
 int read_state(const Boundary& b, KState* hs, cudaStream_t st) {
     GNK_TRY_CUDA(cudaMemcpyAsync(hs, b.kstate, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    int fault = 0;
+    const int* fw = fmm_fault_word(b);
+    if (fw) GNK_TRY_CUDA(cudaMemcpyAsync(&fault, fw, sizeof(int), cudaMemcpyDeviceToHost, st));
     GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    if (fault) {
+        set_error("FMM: a bounded wait of the near field timed out");
+        return GNK_ECUDA;
+    }
     return GNK_OK;
 }
 
