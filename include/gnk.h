@@ -483,6 +483,12 @@ int gnk_cauchy_sum_noalloc(int N, const double* et, const double* w,
  *   y0 (1 + e + e^2), e = 1 - x y0) and y_div[i] = 1.0 / x[i] by CUDA's IEEE
  *   division, for n doubles x (device arrays, n >= 0; GNK_EINVAL for host
  *   pointers).  Asynchronous on `stream`.
+ * gnk_debug_split_f64: hi[i], lo[i] = the double-float split of x[i] that the
+ *   FMM's gather and evaluation kernels use (from the bits of x: hi = x
+ *   truncated to 24 significant bits, lo = the next 23 bits, so
+ *   |x - (hi + lo)| < 2^-46 |x| for 2^-80 <= |x| < 2^101; other values take
+ *   hi = (float)x, lo = (float)(x - hi)), for n doubles x (device arrays,
+ *   n >= 0; GNK_EINVAL for host pointers).  Asynchronous on `stream`.
  * gnk_debug_barrier_fault: test hook of the bounded grid-barrier waits inside
  *   the cooperative Arnoldi step of every later GMRES solve (Sec. 3.5).  With
  *   skip_block >= 0 that block passes each barrier without arriving, so the
@@ -494,6 +500,7 @@ int gnk_cauchy_sum_noalloc(int N, const double* et, const double* w,
  *   threads.  GNK_EINVAL for skip_block < -1 or spin_limit < 0.
  * ------------------------------------------------------------------------- */
 int gnk_debug_recip_f64(int n, const double* x, double* y_lib, double* y_div, void* stream);
+int gnk_debug_split_f64(int n, const double* x, float* hi, float* lo, void* stream);
 int gnk_debug_barrier_fault(int skip_block, int spin_limit);
 
 #ifdef __cplusplus

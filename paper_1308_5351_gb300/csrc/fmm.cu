@@ -109,10 +109,10 @@ __global__ void fmm_gather_kernel(FmmArgs a) {
             const double x = (r == 0) ? a.x0[j] : a.x1[j];
             w = make_double2(sc.x * x, sc.y * x);
         }
-        const df wx = df_split(w.x), wy = df_split(w.y);
+        const df wx = df_split_fast(w.x), wy = df_split_fast(w.y);
         a.ws[(size_t)r * a.N + i] = make_float4(wx.h, wx.l, wy.h, wy.l);
         if (a.xs != nullptr) {  // x alone for the cached near field (W_SCALED)
-            const df xv = df_split((r == 0) ? a.x0[j] : a.x1[j]);
+            const df xv = df_split_fast((r == 0) ? a.x0[j] : a.x1[j]);
             a.xs[(size_t)r * a.N + i] = make_float2(xv.h, xv.l);
         }
     }
@@ -1000,7 +1000,9 @@ __global__ void __launch_bounds__(kNbThreads) fmm_near_bulk_kernel(FmmArgs a, co
 
 // L2P by Horner's rule in double-float plus the near-field sum; one thread per
 // node in sorted order (the nodes of a leaf are adjacent, so a warp reads the
-// same coefficients).  EPI: the operator epilogue of the product is applied at
+// same coefficients).  Without the derivative the order-32 polynomial is four
+// interleaved Horner chains of 8 coefficients joined by t^8 (a dependent chain
+// of 13 steps instead of 31).  EPI: the operator epilogue of the product is applied at
 // once (epilogue_apply: e.g. f_B(x) = 2x + diag(B1) x + (2/n) Im(A z)), so the
 // sums z never go to memory; otherwise z is written in node order.
 // EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
@@ -1012,21 +1014,43 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a, ReduceArgs e) {
     if (i >= a.N) return;
     const int box = a.node_box[i];
     const double2 c = a.center[box];
-    const double ir = 1.0 / a.width[box];
+    const double ir = recip_f64(a.width[box]);  // (GB300's FP64 division is a long dependent chain)
     const double2 p = a.ps[i];
-    const cdf t = cdf_split(make_double2((p.x - c.x) * ir, (p.y - c.y) * ir));
+    const cdf t = cdf{df_split_fast((p.x - c.x) * ir), df_split_fast((p.y - c.y) * ir)};
     const int node = a.perm[i];
     double zx[kMaxRHS] = {0.0, 0.0}, zy[kMaxRHS] = {0.0, 0.0};
+    cdf t8{};
+    if (!EF) t8 = cdf_sq(cdf_sq(cdf_sq(t)));
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float4* b = a.loc + ((size_t)r * a.nbox + box) * kFmmP;
-        cdf u = cdf_of(b[kFmmP - 1]);
-        cdf du = cdf_zero();
-        for (int l = kFmmP - 2; l >= 0; --l) {
-            if (EF) du = cdf_add(cdf_mul(du, t), u);
-            const cdf m = cdf_mul(u, t);
-            const cdf bl = cdf_of(b[l]);
-            u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+        cdf u, du = cdf_zero();
+        if (EF) {  // Horner's rule, carrying the derivative
+            u = cdf_of(b[kFmmP - 1]);
+            for (int l = kFmmP - 2; l >= 0; --l) {
+                du = cdf_add(cdf_mul(du, t), u);
+                const cdf m = cdf_mul(u, t);
+                const cdf bl = cdf_of(b[l]);
+                u = cdf{df_add(m.re, bl.re), df_add(m.im, bl.im)};
+            }
+        } else {  // four interleaved Horner chains of 8 coefficients, joined by powers of t^8
+            cdf h[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = cdf_of(b[8 * q + 7]);
+#pragma unroll
+            for (int m = 6; m >= 0; --m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const cdf mm = cdf_mul(h[q], t);
+                    const cdf bl = cdf_of(b[8 * q + m]);
+                    h[q] = cdf{df_add(mm.re, bl.re), df_add(mm.im, bl.im)};
+                }
+            u = h[3];
+#pragma unroll
+            for (int q = 2; q >= 0; --q) {
+                const cdf mm = cdf_mul(u, t8);
+                u = cdf{df_add(mm.re, h[q].re), df_add(mm.im, h[q].im)};
+            }
         }
         const double2 zn = a.zn[(size_t)r * a.N + i];
         zx[r] = ((double)u.re.h + (double)u.re.l) + zn.x;

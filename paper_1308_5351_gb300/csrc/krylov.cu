@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(KT) k_scale_first(const double* __restrict__ r
         const double v = r[i] * inv;
         v0[i] = v;
         if (vd0) {
-            const df d = df_split(v);
+            const df d = df_split_fast(v);
             vd0[i] = make_float2(d.h, d.l);
         }
     }
@@ -860,12 +860,12 @@ __global__ void __launch_bounds__(KTD) k_arnoldi_df(double* __restrict__ V, floa
         __syncthreads();
         mbar_wait_bounded(&s_bar, 0, s);
         const double* wsrc = reinterpret_cast<const double*>(ws);
-        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split(wsrc[e]));
+        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split_fast(wsrc[e]));
     } else {
         Vr = Vd + i0;
         ld = N;
         ws = wd + i0;
-        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split(w[i0 + e]));
+        for (int e = threadIdx.x; e < len; e += KTD) ws[e] = f2_of(df_split_fast(w[i0 + e]));
     }
     __syncthreads();
     // first pass: h1 = V^T w

@@ -92,6 +92,26 @@ static __device__ __forceinline__ df df_split(double v) {
     return r;
 }
 
+// df_split without the FP64 pipe (each conversion there is a 64-cycle
+// dependent step on GB300): from the bits of v, hi = v truncated to 24
+// significant bits (exact as a float) and lo = the next 23 bits, so
+// |v - (hi + lo)| < 2^-46 |v|.  For 2^-80 <= |v| < 2^101; zero, tiny, huge and
+// non-finite values take df_split.
+static __device__ __forceinline__ df df_split_fast(double v) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+    const unsigned e = (hi >> 20) & 0x7ffu;  // biased exponent
+    if (e - 943u > 180u) return df_split(v);
+    const unsigned sign = hi & 0x80000000u;
+    df r;
+    r.h = __uint_as_float(sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    // the low 29 bits of the significand: their top 23 exactly through the 2^23
+    // bias, scaled by 2^(e - 1069)
+    const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((lo & 0x1fffffffu) >> 6)), 8388608.0f);
+    r.l = __uint_as_float(__float_as_uint(__fmul_rn(m, __uint_as_float((e - 942u) << 23))) | sign);
+    return r;
+}
+
 // ------------------------------------------------------------------ packed double-float
 // Two independent double-float values per float2 (lane x, lane y) with the
 // sm_100 packed FP32 intrinsics: one instruction issues both lanes, so the

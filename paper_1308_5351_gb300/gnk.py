@@ -49,7 +49,7 @@ EXPORTED = (
     "gnk_solve_ie_transpose", "gnk_fbie_backward", "gnk_build_batch", "gnk_free_batch",
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
     "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval", "gnk_profile_mask",
-    "gnk_debug_recip_f64", "gnk_debug_barrier_fault", "gnk_profile_query_bytes",
+    "gnk_debug_recip_f64", "gnk_debug_split_f64", "gnk_debug_barrier_fault", "gnk_profile_query_bytes",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -141,6 +141,7 @@ def load(path: str = LIB_PATH):
     lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
     lib.gnk_slit_map_eval.argtypes = [P, P, P, P, P, P, I, P, P, I, P]
     lib.gnk_debug_recip_f64.argtypes = [I, P, P, P, P]
+    lib.gnk_debug_split_f64.argtypes = [I, P, P, P, P]
     lib.gnk_debug_barrier_fault.argtypes = [I, I]
     lib.gnk_kernel_launches.argtypes = []
     lib.gnk_kernel_launches.restype = ctypes.c_ulonglong
@@ -339,6 +340,18 @@ def gnk_debug_recip_f64(x, y_lib, y_div, stream=None):
         if a.numel() < n:
             raise GnkError(GNK_EINVAL, "gnk_debug_recip_f64: output shorter than x")
     return _check(load().gnk_debug_recip_f64(n, _ptr(x), _ptr(y_lib), _ptr(y_div), _stream(stream)))
+
+
+def gnk_debug_split_f64(x, hi, lo, stream=None):
+    """The FMM kernels' bit-level double-float split (hi, lo float32) of the device array x."""
+    n = int(x.numel())
+    for a in (hi, lo):
+        if a.numel() < n:
+            raise GnkError(GNK_EINVAL, "gnk_debug_split_f64: output shorter than x")
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise GnkError(GNK_EINVAL, "gnk_debug_split_f64: outputs must be contiguous float32")
+    return _check(load().gnk_debug_split_f64(n, _ptr(x), ctypes.c_void_p(hi.data_ptr()),
+                                             ctypes.c_void_p(lo.data_ptr()), _stream(stream)))
 
 
 def gnk_debug_barrier_fault(skip_block: int, spin_limit: int = 0):

@@ -96,3 +96,42 @@ def test_recip_f64_against_cuda_division(G):
     assert u.max() <= 1
     rel = np.abs(y_lib * x - 1.0)
     assert rel.max() <= 2.0 ** -51
+
+
+def _trunc24(x):
+    """x truncated toward zero to 24 significant bits (clears the low 29 bits
+    of the binary64 significand): the definition of the split's high part."""
+    b = x.view(np.uint64) & ~np.uint64((1 << 29) - 1)
+    return b.view(np.float64)
+
+
+def test_split_f64_bit_level_against_definition(G):
+    """The FMM kernels' double-float split from the bits of x: in its range
+    (2^-80 <= |x| < 2^101) hi is x truncated to 24 significant bits (exact as a
+    float) and |x - (hi + lo)| < 2^-46 |x|; elsewhere (0, tiny, huge, Inf, NaN)
+    it is the conversion split (float(x), float(x - float(x)))."""
+    rng = np.random.default_rng(9)
+    x = np.concatenate([
+        rng.choice([-1.0, 1.0], 1 << 18) * 10.0 ** rng.uniform(-24, 30, 1 << 18),
+        np.array([0.0, -0.0, 2.0 ** -80, -(2.0 ** -80), np.nextafter(2.0 ** -80, 0.0), 2.0 ** 101,
+                  np.nextafter(2.0 ** 101, 0.0), 1e-300, -1e300, 5e-324, np.inf, -np.inf, np.nan, 1.0, -1.0,
+                  1.0 + 2.0 ** -52, 3.0 - 2.0 ** -51]),
+    ])
+    xd = torch.as_tensor(x, device="cuda")
+    hi = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    lo = torch.empty_like(hi)
+    G.gnk_debug_split_f64(xd, hi, lo)
+    torch.cuda.synchronize()
+    hi, lo = hi.cpu().numpy().astype(np.float64), lo.cpu().numpy().astype(np.float64)
+    ax = np.abs(x)
+    fast = (ax >= 2.0 ** -80) & (ax < 2.0 ** 101)
+    assert np.array_equal(hi[fast], _trunc24(x[fast]))
+    err = np.abs(x[fast] - (hi[fast] + lo[fast]))  # exact: hi + lo spans < 53 bits
+    assert (err <= 2.0 ** -46 * ax[fast]).all(), err.max()
+    assert (np.sign(lo[fast]) * np.sign(x[fast]) >= 0).all()
+    slow = ~fast & np.isfinite(x)
+    f = x[slow].astype(np.float32).astype(np.float64)
+    assert np.array_equal(hi[slow], f)
+    assert np.array_equal(lo[slow], (x[slow] - f).astype(np.float32).astype(np.float64))
+    nonfin = ~np.isfinite(x)
+    assert np.array_equal(np.isnan(hi[nonfin]), np.isnan(x[nonfin]))
