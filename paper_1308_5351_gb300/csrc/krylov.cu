@@ -1202,7 +1202,18 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
         KLAUNCH((dfa ? 3 : 2) * vb, (k_scale_first<<<nb, KT, 0, st>>>(r, b.V, dfa ? basis_df(b) : nullptr, N, ks)));
         count_launches(2);
         GNK_TRY_CUDA(cudaGetLastError());
+        // The first cycle is enqueued without waiting for its starting norm: when
+        // x0 = 0 already meets the tolerance, k_norm sets the device flag `done`
+        // and the cycle's launches do nothing; the next cycle's residual then ends
+        // the solve (one product more in that case, one host round trip less in
+        // every other).
+        const bool wait_state = cycle > 0 || maxit == 0;
+        if (!wait_state) {
+            res->cycles++;
+            goto steps;
+        }
         GNK_TRY(read_state(b, &hs, st));
+        if (cycle == 1 && hs.last_k == 0 && maxit > 0) res->cycles--;  // the first cycle did no step
         if (hs.bar_err) {
             set_error("GMRES: a grid barrier of the Arnoldi step timed out");
             return GNK_ECUDA;
@@ -1232,6 +1243,7 @@ int gmres(Boundary& b, int adjoint /* OpId */, int prec, const double* rhs, doub
             break;
         }
         res->cycles++;
+    steps:
         for (int j = 0; j < restart; ++j) {
             double* vj = b.V + (size_t)j * N;
             double* w = b.V + (size_t)(j + 1) * N;
