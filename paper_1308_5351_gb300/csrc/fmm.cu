@@ -870,7 +870,8 @@ __global__ void fmm_nq_xlist_kernel(const int* __restrict__ src, long long qb, i
 
 // The near field of z = E(q x) from the cache, streamed into shared memory by
 // the Tensor Memory Accelerator: one block per work item; a producer warp
-// issues bulk copies of the item's cache entries (contiguous, pair-major) and
+// issues bulk copies of the item's cache entries (contiguous, pair-major,
+// evict-first in L2: the cache is larger than L2 and read once per product) and
 // of its sources' x (list order) in chunks of kNbPairs source pairs through a
 // ring of kNbStages buffers (full/empty mbarriers); 8 consumer warps, lane =
 // target, warp w taking pairs w, w + 8, ... of each chunk.  Even and odd
@@ -930,8 +931,8 @@ __global__ void __launch_bounds__(kNbThreads) fmm_near_bulk_kernel(FmmArgs a, co
                 const unsigned qbytes = (unsigned)(np * tn) * 16u, xbytes = (unsigned)np * 16u;
                 float4* stage = nb_buf + (size_t)st * L::kStage;
                 mbar_expect_tx(&full[st], L::kParts * qbytes + R * xbytes);
-                bulk_load(stage, nq_im + o0 + (long long)p0 * tn, qbytes, &full[st]);
-                if (COMP == 0) bulk_load(stage + L::kQ, nq_re + o0 + (long long)p0 * tn, qbytes, &full[st]);
+                bulk_load_stream(stage, nq_im + o0 + (long long)p0 * tn, qbytes, &full[st]);
+                if (COMP == 0) bulk_load_stream(stage + L::kQ, nq_re + o0 + (long long)p0 * tn, qbytes, &full[st]);
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     bulk_load(stage + L::kParts * L::kQ + r * L::kX, xl + (size_t)r * qb + src0 + 2 * p0, xbytes,

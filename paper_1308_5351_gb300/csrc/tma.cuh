@@ -43,6 +43,20 @@ static __device__ __forceinline__ void bulk_load(void* dst, const void* src, uns
                  : "memory");
 }
 
+// bulk_load of data read once (a stream larger than L2): the L2 lines it brings
+// in are marked evict-first, so that the stream does not push out data that is
+// reused.
+static __device__ __forceinline__ void bulk_load_stream(void* dst, const void* src, unsigned bytes,
+                                                        unsigned long long* bar) {
+    unsigned long long policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
 // True once the phase of parity `parity` has completed.
 static __device__ __forceinline__ bool mbar_done(unsigned long long* bar, unsigned parity) {
     unsigned ok;
