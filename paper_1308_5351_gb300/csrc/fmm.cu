@@ -344,7 +344,9 @@ __device__ __forceinline__ void p2m_leaf(const FmmArgs& a, int leaf, int box, in
 // P2M of one leaf from the cached powers t_j^k (a.tp, [node][k]): warp w
 // sums w_j t_j^k over the leaf's nodes j = j0 + w, j0 + w + kFmmTW, ...
 // (lane = k), with no block barrier until the warps' sums are added in warp
-// order.
+// order.  The powers (33.5 MB at 65,536 nodes) are read with the default L2
+// policy: with the near-field stream marked evict-first they stay in L2
+// between products.
 template <int R>
 __device__ __forceinline__ void p2m_leaf_cached(const FmmArgs& a, int leaf, int box, int wid, int lane,
                                                 float4 (*s_acc)[32]) {
@@ -359,7 +361,7 @@ __device__ __forceinline__ void p2m_leaf_cached(const FmmArgs& a, int leaf, int 
         for (int u = 0; u < U; ++u) {
             const int jj = j + u * kFmmTW;
             if (jj < j1) {
-                tv[u] = __ldcs(a.tp + (size_t)jj * kFmmP + lane);
+                tv[u] = __ldg(a.tp + (size_t)jj * kFmmP + lane);
 #pragma unroll
                 for (int r = 0; r < R; ++r) wv[r][u] = __ldcg(a.ws + (size_t)r * a.N + jj);
             }
