@@ -516,6 +516,9 @@ static int solve_common(const gnk_boundary* h, const double* gam, double* mu, co
     const TileOverride tile(b, o.tile_chunks);
     Phases ph(o.timing != 0, st);
     if (o.timing) GNK_TRY(timed_setup(b, outer_precision(o.precision), st));
+    // the products of the equation are z = E(q x): their near-field cache forms
+    // beside the work up to the first product
+    if (!adjoint && outer_precision(o.precision) == GNK_PREC_FMM) GNK_TRY(fmm_start_near_cache(b, st));
     GNK_TRY(ensure_eone(b, st));
     ph.mark();
     const double* dg;
@@ -569,6 +572,9 @@ int gnk_fbie(const gnk_boundary* hd, const double* gam, double* mu, double* hv, 
     Phases ph(o.timing != 0, st);
     // a timed call forms the deferred precompute and the tree as their own phase
     if (o.timing) GNK_TRY(timed_setup(b, outer, st));
+    // every product of the FBIE is z = E(q x): its near-field cache forms on a
+    // stream of its own beside the work up to the first product
+    if (outer == GNK_PREC_FMM) GNK_TRY(fmm_start_near_cache(b, st));
     ph.mark();
     const double* dg;
     GNK_TRY(stage_in(b, gam, b.N, 0, st, &dg));

@@ -1168,6 +1168,11 @@ void release_fmm(Boundary& b) {
         }
         if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
         if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
+        if (b.fmm->bst) {
+            cudaStreamSynchronize(b.fmm->bst);
+            cudaStreamDestroy(b.fmm->bst);
+        }
+        if (b.fmm->ev_nq) cudaEventDestroy(b.fmm->ev_nq);
 
         if (b.fmm->arena || b.fmm->sync || b.fmm->nq_re || b.fmm->tp || b.fmm->fault) {  // once no stream uses them
             cudaDeviceSynchronize();
@@ -1749,6 +1754,34 @@ static int launch_near_bulk(const Boundary& b, const FmmArgs& a, cudaStream_t st
     return GNK_OK;
 }
 
+// Starts forming the near-field cache right after the tree, on a stream of its
+// own, so that it overlaps whatever the caller enqueues before the first cached
+// product (the power table, the right-hand side's circulant, the first
+// product's gather and far field); that product waits for it.  For callers
+// whose products are z = E(q x) (the FBIE and the equation's solves).
+int fmm_start_near_cache(const Boundary& bc, cudaStream_t st) {
+    Boundary& b = const_cast<Boundary&>(bc);
+    if (b.plain) return GNK_OK;
+    GNK_TRY(ensure_fmm(b, kMaxRHS, st));
+    FmmTree* t = b.fmm;
+    GNK_TRY(ensure_near_cache(b, st));
+    if (t->nq_state != 2) return GNK_OK;
+    if (!t->bst) {
+        if (cudaStreamCreateWithFlags(&t->bst, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_nq, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return GNK_OK;  // formed by the first cached product instead
+        }
+    }
+    // the cache's buffers were allocated in the order of `st`
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_nq, st));
+    GNK_TRY_CUDA(cudaStreamWaitEvent(t->bst, t->ev_nq, 0));
+    GNK_TRY(near_cache_build(b, t->bst));
+    GNK_TRY_CUDA(cudaEventRecord(t->ev_nq, t->bst));
+    t->nq_wait = 1;
+    return GNK_OK;
+}
+
 // One FMM product on the argument block `a` (weights, outputs set by the caller):
 // gather, the far-field chain on the high-priority stream, the near field on
 // `st`, and L2P after they join.  EF: also the sums of w/d^2 (to a.outF).
@@ -1797,7 +1830,14 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
     // near field on the caller's stream (from the operator cache when `cached`
     // is 0 (both parts of z) or 1 (Im z only)); the first cached product forms
     // the cache here, beside its far field
-    if (cached >= 0) GNK_TRY(near_cache_build(b, st));
+    if (cached >= 0) {
+        if (t->nq_wait) {  // formed on its own stream since the tree was built
+            GNK_TRY_CUDA(cudaStreamWaitEvent(st, t->ev_nq, 0));
+            b.fmm->nq_wait = 0;
+        } else {
+            GNK_TRY(near_cache_build(b, st));
+        }
+    }
     if (cached >= 0) {  // x in the items' list order
         fmm_nq_xlist_kernel<<<(unsigned)((t->nq_qb + 255) / 256), 256, 0, st>>>(t->nq_src, t->nq_qb, R, b.N, a.xs,
                                                                                t->xl, a.done);

@@ -73,6 +73,9 @@ struct FmmTree {
     float4* tp = nullptr;       // [N][P] powers t^k of each node about its leaf centre (P2M), or null
     cudaStream_t aux = nullptr; // high-priority stream of the far field (the near field runs beside it)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t bst = nullptr; // stream of the near cache's formation when it starts early
+    cudaEvent_t ev_nq = nullptr;
+    int nq_wait = 0;            // the next cached product waits for ev_nq
 };
 
 // Builds the tree on the device (Morton keys, stable radix sort, boxes per level,

@@ -289,6 +289,7 @@ int fbie_backward_nodes(Boundary& b, const double* mu, const double* gam, const 
 int run_fmm(const Boundary& b, const PairJob& job, cudaStream_t st);
 int run_fmm_ef(const Boundary& b, const double2* w0, const double2* w1, double2* E, double2* F, cudaStream_t st);
 int ensure_fmm(const Boundary& b, int R, cudaStream_t st);
+int fmm_start_near_cache(const Boundary& b, cudaStream_t st);
 void release_fmm(Boundary& b);
 double fmm_instr(const Boundary& b, int R, int which);
 double fmm_near_instr(const Boundary& b, int R);
