@@ -75,16 +75,18 @@ PEAK_BASIS = {
 }
 KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pairdf": "pairsumdf2_kernel",
                "fmm": "fmm_m2l_kernel",
-               "fmm_near": "fmm_near_cached_kernel (near field from the operator cache)",
+               "fmm_near": "fmm_near_bulk_kernel (near field streamed from the operator cache by bulk copies)",
                "fmm_l2p": "fmm_l2p_kernel", "fmm_up": "fmm_up_kernel (P2M and the M2M chain)",
                "fmm_l2l": "fmm_l2l_kernel"}
 # DRAM bytes read + written per launch of the kernel at the headline size
-# (64 ellipses, n = 1024), from one ncu capture of the same command, with the
-# SHA-256 prefix of the kernel's source file at the time of the capture: a
-# figure whose source has changed since is reported as null (stale).
-TRAFFIC = {"fmm_near": (2.73e6, "csrc/fmm.cu", None), "fmm": (2.19e6, "csrc/fmm.cu", None),
-           "fmm_up": (2.24e6, "csrc/fmm.cu", None), "fmm_l2l": (1.91e6, "csrc/fmm.cu", None),
-           "fmm_l2p": (5.81e6, "csrc/fmm.cu", None)}
+# (64 ellipses, n = 1024; the R = 1 launches of the solve), from one ncu
+# capture of the same command (ncu's default cache control: caches flushed
+# before each captured launch), with the SHA-256 prefix of the kernel's source
+# file at the time of the capture: a figure whose source has changed since is
+# reported as null (stale).
+TRAFFIC = {"fmm_near": (1.8917e8, "csrc/fmm.cu", "15a1834bfb44a6a2"), "fmm": (1.07e6, "csrc/fmm.cu", "15a1834bfb44a6a2"),
+           "fmm_up": (3.465e7, "csrc/fmm.cu", "15a1834bfb44a6a2"), "fmm_l2l": (0.89e6, "csrc/fmm.cu", "15a1834bfb44a6a2"),
+           "fmm_l2p": (5.29e6, "csrc/fmm.cu", "15a1834bfb44a6a2")}
 # kinds whose work is pair evaluations actually performed
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm_near")
 ROOF_KINDS = ("pair64", "pair32", "pairdf", "fmm", "fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
