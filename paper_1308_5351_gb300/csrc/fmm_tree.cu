@@ -490,7 +490,11 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     GNK_TRY_CUDA(cudaMemsetAsync(fdh, 0, 18 * 4, st));
     tb_bbox<<<nbb, TB, 0, st>>>(b.et, N, (double4*)(tmp + o_part), (unsigned*)(tmp + o_ctr), geom);
     tb_keys<<<(N + TB - 1) / TB, TB, 0, st>>>(b.et, N, geom, k0, i0);
-    for (int pass = 0; pass < 4; ++pass) {
+    // LSD passes over bits 8..31 only: the device builder serves trees of at most
+    // kMaxGridLevel (11) levels, whose boxes are fixed by the top 22 bits, and the
+    // first-difference counts up to level 12 (which decide between this builder
+    // and the host's) need the top 24; the order inside a level-12 cell is free
+    for (int pass = 1; pass < 4; ++pass) {
         tb_hist<<<nbs, TB, 0, st>>>(k0, N, 8 * pass, hist, nbs);
         tb_scan<<<1, 1024, 0, st>>>(hist, 256 * nbs, nullptr);
         tb_scatter<<<nbs, TB, 0, st>>>(k0, i0, k1, i1, N, 8 * pass, hist, nbs);
