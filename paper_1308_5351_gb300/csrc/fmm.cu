@@ -13,12 +13,14 @@
 // sum_j |w_j / (eta_i - eta_j)| (about 2e-12 at P = 32 including round-off;
 // checked against direct sums in the tests).
 //
-// One product is six launches on two streams.  The weights are gathered into
-// tree order; the far field runs on a high-priority stream: the upward pass
-// (P2M, then the M2M chain carried by the block that completes each box's
-// last child, no launch per level), M2L for every box, L2L per leaf down its
-// ancestor path.  The near field runs beside it on the caller's stream; L2P
-// adds the two after they join.  M2M and L2L are
+// One product is six or seven launches on two streams.  The weights are
+// gathered into tree order; the far field runs on a high-priority stream: the
+// upward pass (P2M, then the M2M chain carried by the block that completes
+// each box's last child, no launch per level), M2L for every box, L2L per leaf
+// down its ancestor path.  The near field runs beside it on the caller's
+// stream (for the products z = E(q x) streamed from the near-field operator
+// cache by bulk asynchronous copies, after x is gathered in the near lists'
+// order); L2P adds the two after they join.  M2M and L2L are
 // fixed real Pascal matrices between exact Gaussian-integer scalings, M2L a
 // fixed real Pascal matrix between two complex scalings per offset: no P x P
 // table per relative position.  The far field runs in complex double-float on the FP32

@@ -12,8 +12,10 @@
 // passes.  A whole Arnoldi step (both passes, the norm, the Givens update and
 // the scaling of the new basis vector) is one cooperative launch whose blocks
 // meet at two bounded grid barriers (the new norm follows from the second
-// pass by Pythagoras unless it cancels, then a third); the norms at the start of a cycle
-// finish in the last block to arrive (atomic ticket + fence, no spinning).
+// pass by Pythagoras unless it cancels, then a third): in double-float on the
+// FP32 pipe from shared memory (k_arnoldi_df) for every operator precision but
+// plain FP64, in FP64 (k_arnoldi) for that one.  The norms at the start of a
+// cycle finish in the last block to arrive (atomic ticket + fence, no spinning).
 // Partial sums are added in a fixed order, so results are reproducible.
 // Inside a cycle every kernel first reads the device flag `done`, so the host
 // enqueues a whole cycle without waiting and synchronises once per cycle.
