@@ -1162,19 +1162,90 @@ uint32_t spread16(uint32_t v) {
 
 }  // namespace
 
+// The streams and events of FMM handles, kept per device for reuse (at most
+// kPoolKeep of each kind), so that a caller that builds and frees a handle
+// every step creates none after the first.  A stream returns to the pool only
+// after it has been synchronised.
+constexpr size_t kPoolKeep = 64;
+
+struct StreamPool {
+    std::mutex mu;
+    std::vector<std::vector<cudaStream_t>> hi, lo;  // per device: high-priority and normal streams
+    std::vector<std::vector<cudaEvent_t>> ev;
+};
+
+static StreamPool& stream_pool() {
+    static StreamPool* p = new StreamPool();  // never destroyed: the streams outlive static teardown
+    return *p;
+}
+
+static int fmm_high_priority();
+
+static cudaError_t take_stream(bool high, cudaStream_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    StreamPool& P = stream_pool();
+    {
+        std::lock_guard<std::mutex> lock(P.mu);
+        std::vector<std::vector<cudaStream_t>>& v = high ? P.hi : P.lo;
+        if ((int)v.size() > dev && !v[dev].empty()) {
+            *out = v[dev].back();
+            v[dev].pop_back();
+            return cudaSuccess;
+        }
+    }
+    return high ? cudaStreamCreateWithPriority(out, cudaStreamNonBlocking, fmm_high_priority())
+                : cudaStreamCreateWithFlags(out, cudaStreamNonBlocking);
+}
+
+static cudaError_t take_event(cudaEvent_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    StreamPool& P = stream_pool();
+    {
+        std::lock_guard<std::mutex> lock(P.mu);
+        if ((int)P.ev.size() > dev && !P.ev[dev].empty()) {
+            *out = P.ev[dev].back();
+            P.ev[dev].pop_back();
+            return cudaSuccess;
+        }
+    }
+    return cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+}
+
+static void give_stream(bool high, cudaStream_t s, int dev) {
+    if (!s) return;
+    cudaStreamSynchronize(s);
+    StreamPool& P = stream_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    std::vector<std::vector<cudaStream_t>>& v = high ? P.hi : P.lo;
+    if ((int)v.size() <= dev) v.resize(dev + 1);
+    if (v[dev].size() < kPoolKeep)
+        v[dev].push_back(s);
+    else
+        cudaStreamDestroy(s);
+}
+
+static void give_event(cudaEvent_t e, int dev) {
+    if (!e) return;
+    StreamPool& P = stream_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    if ((int)P.ev.size() <= dev) P.ev.resize(dev + 1);
+    if (P.ev[dev].size() < kPoolKeep)
+        P.ev[dev].push_back(e);
+    else
+        cudaEventDestroy(e);
+}
+
 void release_fmm(Boundary& b) {
     if (b.fmm) {
-        if (b.fmm->aux) {
-            cudaStreamSynchronize(b.fmm->aux);
-            cudaStreamDestroy(b.fmm->aux);
-        }
-        if (b.fmm->ev_fork) cudaEventDestroy(b.fmm->ev_fork);
-        if (b.fmm->ev_join) cudaEventDestroy(b.fmm->ev_join);
-        if (b.fmm->bst) {
-            cudaStreamSynchronize(b.fmm->bst);
-            cudaStreamDestroy(b.fmm->bst);
-        }
-        if (b.fmm->ev_nq) cudaEventDestroy(b.fmm->ev_nq);
+        give_stream(true, b.fmm->aux, b.device);
+        give_event(b.fmm->ev_fork, b.device);
+        give_event(b.fmm->ev_join, b.device);
+        give_stream(false, b.fmm->bst, b.device);
+        give_event(b.fmm->ev_nq, b.device);
 
         if (b.fmm->arena || b.fmm->sync || b.fmm->nq_re || b.fmm->tp || b.fmm->fault) {  // once no stream uses them
             cudaDeviceSynchronize();
@@ -1583,9 +1654,8 @@ int ensure_fmm(const Boundary& bc, int R, cudaStream_t st) {
     }
     cudaGetLastError();
     if (rc == GNK_OK &&
-        (cudaStreamCreateWithPriority(&t->aux, cudaStreamNonBlocking, fmm_high_priority()) != cudaSuccess ||
-         cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        (take_stream(true, &t->aux) != cudaSuccess || take_event(&t->ev_fork) != cudaSuccess ||
+         take_event(&t->ev_join) != cudaSuccess)) {
         cudaGetLastError();
         set_error("FMM: stream or event creation failed");
         rc = GNK_ECUDA;
@@ -1769,8 +1839,7 @@ int fmm_start_near_cache(const Boundary& bc, cudaStream_t st) {
     GNK_TRY(ensure_near_cache(b, st));
     if (t->nq_state != 2) return GNK_OK;
     if (!t->bst) {
-        if (cudaStreamCreateWithFlags(&t->bst, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&t->ev_nq, cudaEventDisableTiming) != cudaSuccess) {
+        if (take_stream(false, &t->bst) != cudaSuccess || take_event(&t->ev_nq) != cudaSuccess) {
             cudaGetLastError();
             return GNK_OK;  // formed by the first cached product instead
         }
