@@ -140,29 +140,58 @@ __global__ void __launch_bounds__(TB) tb_hist(const uint32_t* __restrict__ key, 
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];  // digit-major
 }
 
-// exclusive scan of a[0..len) in place by one block of 1024 threads; the total
-// goes to *total when non-null
-__global__ void __launch_bounds__(1024) tb_scan(unsigned* a, int len, unsigned* total) {
-    __shared__ unsigned s[1024];
+// Exclusive scans in place, one block of 1024 threads per array (up to three
+// arrays in one launch); each array's total goes to *total when non-null.
+// Every thread takes a contiguous range; the ranges' sums are scanned by warp
+// shuffles and one pass over the 32 warp totals.
+struct ScanArgs {
+    unsigned* a[3];
+    int len[3];
+    unsigned* total[3];
+};
+
+__global__ void __launch_bounds__(1024) tb_scan(ScanArgs sa) {
+    __shared__ unsigned ws[32];
+    unsigned* a = sa.a[blockIdx.x];
+    const int len = sa.len[blockIdx.x];
+    unsigned* total = sa.total[blockIdx.x];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int per = (len + 1023) / 1024;
-    const int b0 = threadIdx.x * per, b1 = min(b0 + per, len);
+    const int b0 = min(len, (int)threadIdx.x * per), b1 = min(b0 + per, len);
     unsigned sum = 0;
     for (int k = b0; k < b1; ++k) sum += a[k];
-    s[threadIdx.x] = sum;
+    unsigned v = sum;  // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(full, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) ws[wid] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-        const unsigned v = (threadIdx.x >= off) ? s[threadIdx.x - off] : 0u;
-        __syncthreads();
-        s[threadIdx.x] += v;
-        __syncthreads();
+    if (wid == 0) {  // inclusive scan of the warps' totals
+        unsigned w = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(full, w, o);
+            if (lane >= o) w += t;
+        }
+        ws[lane] = w;
     }
-    unsigned run = s[threadIdx.x] - sum;
+    __syncthreads();
+    unsigned run = (wid > 0 ? ws[wid - 1] : 0u) + v - sum;
     for (int k = b0; k < b1; ++k) {
-        const unsigned v = a[k];
+        const unsigned x = a[k];
         a[k] = run;
-        run += v;
+        run += x;
     }
-    if (total && threadIdx.x == 1023) *total = s[1023];
+    if (total && threadIdx.x == 1023) *total = ws[31];
+}
+
+static ScanArgs scan_of(unsigned* a, int len, unsigned* total) {
+    ScanArgs sa{};
+    sa.a[0] = a;
+    sa.len[0] = len;
+    sa.total[0] = total;
+    return sa;
 }
 
 // Stable scatter: warp w of a block owns nodes [base + 256 w, base + 256 (w + 1)),
@@ -496,7 +525,7 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     // and the host's) need the top 24; the order inside a level-12 cell is free
     for (int pass = 1; pass < 4; ++pass) {
         tb_hist<<<nbs, TB, 0, st>>>(k0, N, 8 * pass, hist, nbs);
-        tb_scan<<<1, 1024, 0, st>>>(hist, 256 * nbs, nullptr);
+        tb_scan<<<1, 1024, 0, st>>>(scan_of(hist, 256 * nbs, nullptr));
         tb_scatter<<<nbs, TB, 0, st>>>(k0, i0, k1, i1, N, 8 * pass, hist, nbs);
         std::swap(k0, k1);
         std::swap(i0, i1);
@@ -665,9 +694,19 @@ int fmm_tree_device(const Boundary& b, FmmTree* t, cudaStream_t st) {
     const int gb = (nbox + TB - 1) / TB;
     tb_boxes<<<gb, TB, 0, st>>>(d);
     tb_lists<<<gb, TB, 0, st>>>(d, 0);
-    tb_scan<<<1, 1024, 0, st>>>(d.il_cnt, nbox, totals + 0);
-    tb_scan<<<1, 1024, 0, st>>>(d.nl_cnt, nleaf, totals + 1);
-    tb_scan<<<1, 1024, 0, st>>>(d.it_cnt, nleaf, totals + 2);
+    {
+        ScanArgs sa{};
+        sa.a[0] = d.il_cnt;
+        sa.len[0] = nbox;
+        sa.total[0] = totals + 0;
+        sa.a[1] = d.nl_cnt;
+        sa.len[1] = nleaf;
+        sa.total[1] = totals + 1;
+        sa.a[2] = d.it_cnt;
+        sa.len[2] = nleaf;
+        sa.total[2] = totals + 2;
+        tb_scan<<<3, 1024, 0, st>>>(sa);
+    }
     tb_lists<<<gb, TB, 0, st>>>(d, 1);
     tb_nodes<<<(N + TB - 1) / TB, TB, 0, st>>>(b.et, N, i0, boxid + (size_t)(L - 2) * N, t->lvl_off[L - 2],
                                                t->perm, t->ps, t->p3, t->p3b, t->node_box);
