@@ -31,7 +31,12 @@
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *     on one handle must not overlap: the handle's workspace is shared.
  *   - Argument checks (sizes, NULL pointers, n even) happen before any launch
- *     and return GNK_EINVAL.  CUDA failures return GNK_ECUDA.
+ *     and return GNK_EINVAL.  CUDA failures return GNK_ECUDA, and so does a
+ *     solve in which a kernel's bounded wait gave up (the Arnoldi step's grid
+ *     barriers and bulk copies, the FMM near field's copy pipeline: no wait
+ *     spins without a limit); the message says which.
+ *   - GMRES orthogonalises in double-float (about 48 significant bits) for
+ *     every precision but GNK_PREC_FP64, which keeps it in FP64.
  *   - The caller owns all arrays it passes; the handle owns its own copies.
  */
 #ifndef GNK_H
