@@ -97,11 +97,15 @@ static __device__ __forceinline__ df df_split(double v) {
 // significant bits (exact as a float) and lo = the next 23 bits, so
 // |v - (hi + lo)| < 2^-46 |v|.  For 2^-80 <= |v| < 2^101; zero, tiny, huge and
 // non-finite values take df_split.
+// (out of line, so that the compiler branches to it instead of evaluating its
+// FP64 conversions beside every fast split)
+static __device__ __noinline__ df df_split_slow(double v) { return df_split(v); }
+
 static __device__ __forceinline__ df df_split_fast(double v) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
     const unsigned e = (hi >> 20) & 0x7ffu;  // biased exponent
-    if (e - 943u > 180u) return df_split(v);
+    if (e - 943u > 180u) return df_split_slow(v);
     const unsigned sign = hi & 0x80000000u;
     df r;
     r.h = __uint_as_float(sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
