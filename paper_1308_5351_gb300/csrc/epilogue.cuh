@@ -48,12 +48,16 @@ inline ReduceArgs reduce_args(const Boundary& b, const PairJob& job, int chunks,
     return ra;
 }
 
-// Writes the job's outputs at node i from the sums z0 and (a.R = 2) z1.
-__device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, double2 z0, double2 z1) {
+// Writes the outputs of epilogue kind `epi` at node i from the sums z0 and
+// (a.R = 2) z1.  A caller that knows the kind at compile time passes it as a
+// constant, so that only that case is compiled in (a runtime switch over the
+// kinds may be evaluated case by case under predication, and every case costs
+// FP64 operations on GB300's 2-lane FP64 pipe).
+__device__ __forceinline__ void epilogue_apply_as(const ReduceArgs& a, int epi, int i, double2 z0, double2 z1) {
     const PairJob& j = a.job;
     const int N = a.N;
     const double s2n = 2.0 / a.n;
-    switch (j.epi) {
+    switch (epi) {
         case EPI_Z:
             j.out_c[i] = z0;
             if (a.R > 1) j.out_c[(size_t)N + i] = z1;
@@ -64,7 +68,7 @@ __device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, doubl
             const double2 A = a.A[i];
             const double x = j.ex[i];
             const double fb = 2.0 * x + a.b1[i] * x + s2n * (A.x * z0.y + A.y * z0.x);
-            j.out[i] = (j.epi == EPI_RESID) ? j.rhs[i] - fb : fb;
+            j.out[i] = (epi == EPI_RESID) ? j.rhs[i] - fb : fb;
             break;
         }
         case EPI_M: {
@@ -80,7 +84,7 @@ __device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, doubl
             const double2 q = a.q[i];
             const double x = j.ex[i];
             const double gb = a.e[i] * x + s2n * (q.x * z0.y + q.y * z0.x) + j.means[i / a.n];
-            j.out[i] = (j.epi == EPI_RESID_ADJ) ? j.rhs[i] - gb : gb;
+            j.out[i] = (epi == EPI_RESID_ADJ) ? j.rhs[i] - gb : gb;
             break;
         }
         case EPI_H: {
@@ -113,7 +117,7 @@ __device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, doubl
             const double2 q = a.q[i];
             const double x = j.ex[i];
             const double kt = 2.0 * x + a.b1[i] * x - s2n * (q.x * z0.y + q.y * z0.x);
-            j.out[i] = (j.epi == EPI_RESID_T) ? j.rhs[i] - kt : kt;
+            j.out[i] = (epi == EPI_RESID_T) ? j.rhs[i] - kt : kt;
             break;
         }
         case EPI_MT: {
@@ -156,6 +160,11 @@ __device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, doubl
         default:
             break;
     }
+}
+
+// The job's own kind, read at run time (the pair-sum reduction).
+__device__ __forceinline__ void epilogue_apply(const ReduceArgs& a, int i, double2 z0, double2 z1) {
+    epilogue_apply_as(a, a.job.epi, i, z0, z1);
 }
 
 }  // namespace gnk

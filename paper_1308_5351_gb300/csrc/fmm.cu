@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(kNbThreads) fmm_near_bulk_kernel(FmmArgs a, co
 // sums z never go to memory; otherwise z is written in node order.
 // EF: also F = -d/dz of the far field (Horner's rule carries the derivative)
 // plus the near-field sums of w/d^2, written to outF.
-template <int R, bool EF, bool EPI>
+template <int R, bool EF, bool EPI, int EK = EPI_Z>
 __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a, ReduceArgs e) {
     if (a.done != nullptr && *a.done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1067,7 +1067,7 @@ __global__ void __launch_bounds__(256) fmm_l2p_kernel(FmmArgs a, ReduceArgs e) {
                                                           -ir * ((double)du.im.h + (double)du.im.l) + zf.y);
         }
     }
-    if (EPI) epilogue_apply(e, node, make_double2(zx[0], zy[0]), make_double2(zx[1], zy[1]));
+    if (EPI) epilogue_apply_as(e, EK, node, make_double2(zx[0], zy[0]), make_double2(zx[1], zy[1]));
 }
 
 // ---------------------------------------------------------------- host: tables
@@ -1803,6 +1803,37 @@ static int near_cache_build(const Boundary& b, cudaStream_t st) {
     return GNK_OK;
 }
 
+// L2P with the product's epilogue, one instantiation per epilogue kind (the
+// kind known at compile time: only its case is compiled in).
+template <int R, int EK>
+static void l2p_epi_launch(const FmmArgs& a, const ReduceArgs& e, int nb, cudaStream_t st) {
+    fmm_l2p_kernel<R, false, true, EK><<<nb, 256, 0, st>>>(a, e);
+}
+
+template <int R>
+static int l2p_epi(const FmmArgs& a, const ReduceArgs& e, int nb, cudaStream_t st) {
+    switch (e.job.epi) {
+        case EPI_Z: l2p_epi_launch<R, EPI_Z>(a, e, nb, st); break;
+        case EPI_IMINUSN: l2p_epi_launch<R, EPI_IMINUSN>(a, e, nb, st); break;
+        case EPI_M: l2p_epi_launch<R, EPI_M>(a, e, nb, st); break;
+        case EPI_ADJ: l2p_epi_launch<R, EPI_ADJ>(a, e, nb, st); break;
+        case EPI_RESID: l2p_epi_launch<R, EPI_RESID>(a, e, nb, st); break;
+        case EPI_RESID_ADJ: l2p_epi_launch<R, EPI_RESID_ADJ>(a, e, nb, st); break;
+        case EPI_H: l2p_epi_launch<R, EPI_H>(a, e, nb, st); break;
+        case EPI_EONE: l2p_epi_launch<R, EPI_EONE>(a, e, nb, st); break;
+        case EPI_RHS_FB: l2p_epi_launch<R, EPI_RHS_FB>(a, e, nb, st); break;
+        case EPI_RESID_FC: l2p_epi_launch<R, EPI_RESID_FC>(a, e, nb, st); break;
+        case EPI_IMINUSN_T: l2p_epi_launch<R, EPI_IMINUSN_T>(a, e, nb, st); break;
+        case EPI_RESID_T: l2p_epi_launch<R, EPI_RESID_T>(a, e, nb, st); break;
+        case EPI_MT: l2p_epi_launch<R, EPI_MT>(a, e, nb, st); break;
+        case EPI_EONE_RHS: l2p_epi_launch<R, EPI_EONE_RHS>(a, e, nb, st); break;
+        default:
+            set_error("FMM: unknown epilogue kind %d", e.job.epi);
+            return GNK_EINVAL;
+    }
+    return GNK_OK;
+}
+
 template <int R, int COMP>
 static int launch_near_bulk(const Boundary& b, const FmmArgs& a, cudaStream_t st) {
     using L = NbLayout<R, COMP>;
@@ -1945,13 +1976,13 @@ static int fmm_product(const Boundary& b, FmmArgs& a, int R, bool EF, const Redu
     if (R == 2 && EF)
         fmm_l2p_kernel<2, true, false><<<nb, 256, 0, st>>>(a, e);
     else if (R == 2 && epi)
-        fmm_l2p_kernel<2, false, true><<<nb, 256, 0, st>>>(a, e);
+        GNK_TRY(l2p_epi<2>(a, e, nb, st));
     else if (R == 2)
         fmm_l2p_kernel<2, false, false><<<nb, 256, 0, st>>>(a, e);
     else if (EF)
         fmm_l2p_kernel<1, true, false><<<nb, 256, 0, st>>>(a, e);
     else if (epi)
-        fmm_l2p_kernel<1, false, true><<<nb, 256, 0, st>>>(a, e);
+        GNK_TRY(l2p_epi<1>(a, e, nb, st));
     else
         fmm_l2p_kernel<1, false, false><<<nb, 256, 0, st>>>(a, e);
     ++launches;
