@@ -84,9 +84,9 @@ KERNEL_NAME = {"pair64": "pairsum64_kernel", "pair32": "pairsum32x2_kernel", "pa
 # before each captured launch), with the SHA-256 prefix of the kernel's source
 # file at the time of the capture: a figure whose source has changed since is
 # reported as null (stale).
-TRAFFIC = {"fmm_near": (1.8946e8, "csrc/fmm.cu", "8c918ec02b75953c"), "fmm": (1.07e6, "csrc/fmm.cu", "8c918ec02b75953c"),
-           "fmm_up": (3.466e7, "csrc/fmm.cu", "8c918ec02b75953c"), "fmm_l2l": (0.89e6, "csrc/fmm.cu", "8c918ec02b75953c"),
-           "fmm_l2p": (5.29e6, "csrc/fmm.cu", "8c918ec02b75953c")}
+TRAFFIC = {"fmm_near": (1.8917e8, "csrc/fmm.cu", "f9e02bb199254842"), "fmm": (1.07e6, "csrc/fmm.cu", "f9e02bb199254842"),
+           "fmm_up": (3.465e7, "csrc/fmm.cu", "f9e02bb199254842"), "fmm_l2l": (0.89e6, "csrc/fmm.cu", "f9e02bb199254842"),
+           "fmm_l2p": (5.28e6, "csrc/fmm.cu", "f9e02bb199254842")}
 # kinds whose work is pair evaluations actually performed
 PAIR_KINDS = ("pair64", "pair32", "pairdf", "fmm_near")
 ROOF_KINDS = ("pair64", "pair32", "pairdf", "fmm", "fmm_near", "fmm_l2p", "fmm_up", "fmm_l2l")
