@@ -22,6 +22,9 @@ with the generalized Neumann kernel"):
   * Cauchy integral formula                Sec. 5, Eqs. (cauchy4), (cauchy6)
   * slit maps by the FBIE route            Sec. 7, Ex. 3 (map formulas of the
                                            method the paper cites; see slit_map)
+  * slit maps by the adjoint route         Sec. 7, Ex. 3 and Ex. 4 (solves of
+                                           Eq. (ie*) only; the steps are derived
+                                           before slit_map_adjoint)
 
 Readings of the paper taken here (each is listed with its reason in the design
 notes of the repository):
@@ -38,7 +41,9 @@ notes of the repository):
 Parity: every function here is pinned by tests/test_oracle_pins.py against
 closed forms (disk, unit circle), manufactured analytic solutions, the
 eigen-identities of Eq. (NM-const), and adaptive quadrature of the continuous
-operators.
+operators; the slit maps by tests/test_slit_map.py and
+tests/test_slit_map_adjoint.py (closed forms, the two routes against each
+other, analyticity of the boundary values).
 """
 from __future__ import annotations
 
@@ -539,3 +544,132 @@ def slit_map(et, etp, n, alpha, theta, z=None, bounded=True):
         fz = cauchy_formula(et, etp, n, fb, z, bounded)
         wz = c * (z - alpha) * np.exp((z - alpha) * fz) if bounded else (z - alpha) * np.exp(fz)
     return w, c, hk, wz
+
+
+# ---------------------------------------------------------------------------
+# Sec. 7, Ex. 3 and Ex. 4: the same slit maps by the route of the adjoint
+# equation (the paper's FBIEad comparison): only solves of Eq. (ie*), then the
+# boundary correspondence integrated per boundary by the FFT.  The paper gives
+# the route's cost and count of solves but not its formulas (they are in its
+# references); the steps below are derived here from the kernel identities of
+# Sec. 2.2 and Cauchy's theorem:
+#
+# With A of Eq. (A) for the slit map and A~ = eta'/A (Eq. A*), the kernel
+# formed with A~ is -N* (Eq. Nt-N*).  For g analytic in G (bounded G; for
+# unbounded G with g(inf) = 0) write A~ g = a + i b on the boundary; Plemelj's
+# formula gives (I - N~) b = -M~ a, i.e. (I + N*) b = M* a.  For a function q
+# analytic in the holes and vanishing at infinity the sign of N~ flips:
+# (I + N~) b_q = M~ a_q.
+#
+# Write the map as w(z) = (z - alpha) exp(omega(z)), omega analytic in G
+# (omega(inf) = 0 for unbounded G).  On a circular-slit boundary (theta = pi/2)
+# w(eta(t)) = R_k exp(i th_k(t)), so eta' w'/w = i th_k'(t); on a radial-slit
+# boundary (theta = 0) w(eta(t)) = rho_k(t) exp(i phi_k), so eta' w'/w = (log
+# rho_k)'(t).  Hence, with psi = th' (circular) and psi = -(log rho)' (radial),
+#   bounded G:   H = (z - alpha) w'/w is analytic, H(alpha) = 1 and A~ H = i psi,
+#                so (I + N*) psi = 0; the winding of w along the boundaries
+#                gives J psi = (1, 0, ..., 0), so (I + N* + J) psi = e_0;
+#   unbounded G: w'/w = 1/(z - alpha) + omega' splits into a part analytic in
+#                G with value 0 at infinity and one analytic in the holes, and
+#                the two identities above give (I + N*) psi =
+#                2 Im[A~/(eta - alpha)]; every boundary is a slit, J psi = 0.
+# This is the one solve for the derivative of the boundary correspondence.
+# Its antiderivative along each boundary (zero at t = 0) is S(t): th_k =
+# th_k(0) + S and log rho_k = c_k - S.
+#
+# The parameters: the solutions psi_j of (I + N* + J) psi_j = e_j (j = 0..m)
+# lie in the null space of I + N* (J psi_j = e_j) and belong to analytic g_j
+# with A~ g_j = i psi_j; eta' g_j/(eta - alpha) (bounded) or eta' g_j
+# (unbounded) is i psi_j on a circular boundary and -psi_j on a radial one.
+# Cauchy's theorem for omega times that function gives, with
+#   T_j = (1/(2 pi)) int_Gamma c(t) omega^(t) psi_j(t) dt,   c = i (circular),
+#         c = -1 (radial), omega^ = omega without its per-boundary constants
+#         (circular: -log|eta - alpha| + i (S - arg(eta - alpha));
+#          radial:   -S - log|eta - alpha| - i arg(eta - alpha)),
+# and rho = log w'(alpha) = Im T_0 for bounded G (w'(alpha) > 0, R_0 = 1),
+# rho = 0 for unbounded G:
+#   circular k:  log R_k = rho - Im T_k,   th_k(0) = Re T_k;
+#   radial k:    c_k = rho + Re T_k,       phi_k = Im T_k.
+# (The residue of g_j/(z - alpha) at alpha is 1 for a circular j and i for a
+# radial j, which gives these two forms.)  Bounded G needs m + 1 solves
+# (psi_0 is also the derivative), unbounded G m + 2.
+# ---------------------------------------------------------------------------
+
+def periodic_antiderivative(psi, n):
+    """S(t_p) = int_0^{t_p} psi(t) dt on each boundary component for the
+    trigonometric interpolant of psi at the n nodes: the mean times t plus the
+    periodic part whose DFT coefficients are those of psi divided by i k
+    (k = 0 and the n/2 mode, whose antiderivative vanishes at the nodes,
+    dropped), shifted so that S(0) = 0."""
+    P = np.asarray(psi, dtype=np.float64).reshape(-1, n)
+    t = np.arange(n) * (2.0 * math.pi / n)
+    C = np.fft.fft(P, axis=1)
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    mean = C[:, 0].real / n
+    div = np.where(k == 0, 1.0, 1j * k)
+    Q = C / div
+    Q[:, 0] = 0.0
+    Q[:, n // 2] = 0.0
+    per = np.fft.ifft(Q, axis=1).real
+    return (mean[:, None] * t[None, :] + per - per[:, :1]).ravel()
+
+
+def slit_map_adjoint(et, etp, etpp, n, alpha, theta, bounded=True, z=None):
+    """The slit map of slit_map by solves of Eq. (ie*) only (the derivation
+    above).  Returns (w at the nodes, psi, params, scale, omega at the nodes,
+    w at z or None): psi is th' on circular and -(log rho)' on radial
+    boundaries; params[k] is R_k (circular) or phi_k (radial); scale is
+    w'(alpha) for bounded G and 1 for unbounded G."""
+    et = np.asarray(et, dtype=np.complex128)
+    etp = np.asarray(etp, dtype=np.complex128)
+    N, m1 = _sizes(et, n)
+    theta = np.asarray(theta, dtype=np.float64)
+    circ_k = theta == math.pi / 2
+    if not np.all(circ_k | (theta == 0.0)) or (bounded and not circ_k[0]):
+        raise ValueError("theta must be pi/2 or 0 per boundary (pi/2 on the outer one of bounded G)")
+    A, _ = slit_map_data(et, n, alpha, theta, bounded)
+    rot = np.repeat(np.exp(1j * (math.pi / 2 - theta)), n)
+    Ap = rot * etp if bounded else np.zeros(N, dtype=np.complex128)
+    c = 1 if bounded else -1
+    Mad = matrix_adjoint(et, etp, etpp, A, Ap, n, c)
+    comp = np.repeat(np.arange(m1), n)
+    # psi_j: (I + N* + J) psi_j = e_j (Eq. sys*), j = 0..m
+    psis = [np.linalg.solve(Mad, (comp == j).astype(np.float64)) for j in range(m1)]
+    if bounded:
+        psi = psis[0]
+    else:
+        At = etp / A
+        psi = np.linalg.solve(Mad, 2.0 * (At / (et - alpha)).imag)
+    S = periodic_antiderivative(psi, n)
+    # log(eta - alpha) with arg continuous along each boundary
+    lg = np.empty(N, dtype=np.complex128)
+    for k in range(m1):
+        d = et[k * n:(k + 1) * n] - alpha
+        lg[k * n:(k + 1) * n] = np.log(np.abs(d)) + 1j * np.unwrap(np.angle(d))
+    circ = np.repeat(circ_k, n)
+    om_hat = np.where(circ, -lg.real + 1j * (S - lg.imag), -S - lg.real - 1j * lg.imag)
+    cw = np.where(circ, 1j, -1.0)
+    T = np.array([np.sum(cw * om_hat * p) / n for p in psis])  # (1/2pi)(2pi/n) sum
+    rho = T[0].imag if bounded else 0.0
+    params = np.empty(m1)
+    kappa = np.empty(m1, dtype=np.complex128)
+    w = np.empty(N, dtype=np.complex128)
+    for k in range(m1):
+        s = slice(k * n, (k + 1) * n)
+        if circ_k[k]:
+            logR, th0 = rho - T[k].imag, T[k].real
+            params[k] = math.exp(logR)
+            kappa[k] = logR + 1j * th0
+            w[s] = params[k] * np.exp(1j * (th0 + S[s]))
+        else:
+            ck, phik = rho + T[k].real, T[k].imag
+            params[k] = phik
+            kappa[k] = ck + 1j * phik
+            w[s] = np.exp(ck - S[s]) * np.exp(1j * phik)
+    omega = om_hat + np.repeat(kappa, n)
+    wz = None
+    if z is not None:
+        z = np.asarray(z, dtype=np.complex128)
+        oz = cauchy_formula(et, etp, n, omega, z, bounded)
+        wz = (z - alpha) * np.exp(oz)
+    return w, psi, params, (math.exp(rho) if bounded else 1.0), omega, wz
