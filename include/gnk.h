@@ -398,6 +398,66 @@ int gnk_slit_map_eval(const gnk_boundary* b, const double* alpha,
                       int precision, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The same slit maps by solves of the adjoint equation only (Sec. 7, Ex. 3 and
+ * Ex. 4: the comparison route of the FBIEad function, whose map formulas the
+ * paper leaves to its references; the steps below follow from the identities
+ * of the generalized Neumann kernel formed with A~ = eta'/A (Eqs. A*, Nt-N*)
+ * and Cauchy's theorem).  theta_k = pi/2 (circular slit) or 0 (radial slit),
+ * pi/2 on the outer boundary of a bounded G.  With w = (z - alpha) exp(omega):
+ *   psi, the derivative of the boundary correspondence (th' where
+ *     w = R_k e^{i th_k(t)} on a circular boundary, -(log rho_k)' where
+ *     w = rho_k(t) e^{i phi_k} on a radial one), solves Eq. (ie*)
+ *     (I + N* + J) psi = e_0 for bounded G and
+ *     (I + N* + J) psi = 2 Im[A~/(eta - alpha)] for unbounded G;
+ *   S, its antiderivative along each boundary with S = 0 at t = 0, from the
+ *     FFT of its trigonometric interpolant (a direct circulant product when n
+ *     is not a power of two up to 4096);
+ *   psi_j solves (I + N* + J) psi_j = e_j (e_j = 1 on boundary j, 0 elsewhere),
+ *     j = 0..m, and T_j = (1/n) sum_i c_i om_i psi_j,i with c = i (circular)
+ *     or -1 (radial) and om = omega without its per-boundary constants
+ *     (circular: -log|eta - alpha| + i (S - arg(eta - alpha)); radial:
+ *     -S - log|eta - alpha| - i arg(eta - alpha), arg continuous along each
+ *     boundary); rho = log w'(alpha) = Im T_0 for bounded G, 0 for unbounded G;
+ *   circular k: R_k = e^{rho - Im T_k}, th_k(0) = Re T_k,
+ *               w = R_k e^{i (th_k(0) + S)};
+ *   radial k:   phi_k = Im T_k, w = e^{rho + Re T_k - S} e^{i phi_k}.
+ * Bounded G: m + 1 solves (psi = psi_0); unbounded G: m + 2.  The map is the
+ * one of gnk_slit_map: onto the unit disk with w(alpha) = 0, w'(alpha) > 0
+ * (bounded G) or onto the plane with w = z + O(1) at infinity (unbounded G).
+ *
+ * gnk_slit_map_adjoint_data: A' (2N doubles) = e^{i(pi/2 - theta)} eta' for
+ *   bounded G, 0 for unbounded G, from eta' (2N) and theta (m1): with
+ *   gnk_slit_map_data's A and eta'' the handle for this route is built by
+ *   gnk_build_boundary(_ex).
+ * gnk_slit_map_adjoint: on such a handle, for alpha (2 doubles, read on the
+ *   host) and theta (m1 doubles, host or device, read on the host), writes w at
+ *   the nodes (2N doubles); optionally (each nullable) omega at the nodes (2N),
+ *   psi (N) and params (m1 + 1: R_k on a circular boundary, phi_k on a radial
+ *   one, then w'(alpha) for bounded G or 1).  `opt` controls every GMRES solve
+ *   (any precision of gnk_solve_adjoint_ie); `info` sums the solves' counts
+ *   and keeps the largest final residual.  Returns GNK_OK, GNK_ENOTCONV (a
+ *   solve stopped at maxit; the outputs are written), GNK_ENONFINITE,
+ *   GNK_EINVAL (NULL handle or arrays, a handle without eta'', theta not pi/2
+ *   or 0, theta_0 != pi/2 for bounded G, bad options) or GNK_ENOMEM.
+ *   Allocates a workspace of about 6N + 2 m1 + n doubles from the pool.
+ * gnk_slit_map_adjoint_eval: w at nz points z of G (2 nz doubles in and out)
+ *   from omega at the nodes: omega(z) by the Cauchy formula (gnk_cauchy_eval,
+ *   omega(inf) = 0 for unbounded G; precision GNK_PREC_FP64 or GNK_PREC_DF32),
+ *   then w = (z - alpha) exp(omega(z)).
+ * Host arrays are staged; the calls synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+int gnk_slit_map_adjoint_data(int m1, int n, const double* etp,
+                              const double* theta, int bounded, double* Ap,
+                              void* stream);
+int gnk_slit_map_adjoint(const gnk_boundary* b, const double* alpha,
+                         const double* theta, const gnk_options* opt,
+                         double* w, double* omega, double* psi,
+                         double* params, gnk_result* info, void* stream);
+int gnk_slit_map_adjoint_eval(const gnk_boundary* b, const double* alpha,
+                              const double* omega, int nz, const double* z,
+                              double* wz, int precision, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched FBIE over many independent domains and right-hand sides (no
  * counterpart in the paper: many instances of Sec. 3 solved together).
  *

@@ -874,6 +874,133 @@ int gnk_slit_map_eval(const gnk_boundary* hd, const double* alpha, const double*
     return vw.finish(rc, out, st);
 }
 
+int gnk_slit_map_adjoint_data(int m1, int n, const double* etp, const double* theta, int bounded, double* Ap,
+                              void* stream) {
+    cudaGetLastError();
+    if (!etp || !theta || !Ap || m1 < 1 || n < 4 || (n % 2) != 0 || (long long)m1 * n > (1LL << 28)) {
+        set_error("gnk_slit_map_adjoint_data: NULL array or m1, n out of range");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)m1 * n;
+    Views vw;
+    void *detp, *dth, *dAp;
+    int rc = vw.add(etp, 16 * N, true, st, &detp);
+    if (rc == GNK_OK) rc = vw.add(theta, 8 * (size_t)m1, true, st, &dth);
+    if (rc == GNK_OK) rc = vw.add(Ap, 16 * N, false, st, &dAp);
+    if (rc == GNK_OK)
+        rc = slit_dA(m1, n, (const double2*)detp, (const double*)dth, bounded, (double2*)dAp, st);
+    const bool out[3] = {false, false, true};
+    return vw.finish(rc, out, st);
+}
+
+int gnk_slit_map_adjoint(const gnk_boundary* hd, const double* alpha, const double* theta, const gnk_options* opt,
+                         double* w, double* omega, double* psi, double* params, gnk_result* info, void* stream) {
+    cudaGetLastError();
+    GNK_TRY(check_handle(hd));
+    const Boundary& b = hd->b;
+    if (!alpha || !theta || !w) {
+        set_error("gnk_slit_map_adjoint: NULL array");
+        return GNK_EINVAL;
+    }
+    if (!b.has_adjoint) {
+        set_error("gnk_slit_map_adjoint needs a handle built with eta'' and A'");
+        return GNK_EINVAL;
+    }
+    gnk_options o;
+    GNK_TRY(options_from(opt, &o));
+    cudaStream_t st = (cudaStream_t)stream;
+    // theta is read on the host: each boundary is a circular (pi/2) or a radial
+    // (0) slit, and the outer boundary of bounded G maps to the unit circle
+    std::vector<double> th(b.m1);
+    if (is_device_ptr(theta)) {
+        GNK_TRY_CUDA(cudaMemcpyAsync(th.data(), theta, th.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GNK_TRY_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(th.data(), theta, th.size() * sizeof(double));
+    }
+    for (int k = 0; k < b.m1; ++k) {
+        if (th[k] != 0.5 * M_PI && th[k] != 0.0) {
+            set_error("gnk_slit_map_adjoint: theta[%d] = %g is neither pi/2 nor 0", k, th[k]);
+            return GNK_EINVAL;
+        }
+    }
+    if (b.bounded && th[0] != 0.5 * M_PI) {
+        set_error("gnk_slit_map_adjoint: the outer boundary of a bounded domain needs theta = pi/2");
+        return GNK_EINVAL;
+    }
+    const TileOverride tile(b, o.tile_chunks);
+    GNK_TRY(ensure_eone(b, st));
+    const size_t N = b.N;
+    Views vw;
+    bool out[5];
+    void *dth, *dw, *dom = nullptr, *dpsi = nullptr, *dpar = nullptr;
+    int rc = vw.add(theta, 8 * (size_t)b.m1, true, st, &dth);
+    out[0] = false;
+    if (rc == GNK_OK) rc = vw.add(w, 16 * N, false, st, &dw);
+    out[1] = true;
+    int k = 2;
+    if (rc == GNK_OK && omega) {
+        rc = vw.add(omega, 16 * N, false, st, &dom);
+        out[k++] = true;
+    }
+    if (rc == GNK_OK && psi) {
+        rc = vw.add(psi, 8 * N, false, st, &dpsi);
+        out[k++] = true;
+    }
+    if (rc == GNK_OK && params) {
+        rc = vw.add(params, 8 * ((size_t)b.m1 + 1), false, st, &dpar);
+        out[k++] = true;
+    }
+    int s = rc;
+    if (rc == GNK_OK)
+        s = slit_map_adjoint(b, make_double2(alpha[0], alpha[1]), (const double*)dth, o, (double2*)dw,
+                             (double2*)dom, (double*)dpsi, (double*)dpar, info, st);
+    // the outputs of a call whose solves stopped at maxit are still copied back
+    const int fin = vw.finish(s == GNK_ENOTCONV ? GNK_OK : s, out, st);
+    if (fin != GNK_OK) return fin;
+    if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles in one of the solves");
+    if (s == GNK_ENONFINITE) set_error("non-finite value in the GMRES iteration");
+    return s;
+}
+
+int gnk_slit_map_adjoint_eval(const gnk_boundary* hd, const double* alpha, const double* omega, int nz,
+                              const double* z, double* wz, int precision, void* stream) {
+    cudaGetLastError();
+    GNK_TRY(check_handle(hd));
+    const Boundary& b = hd->b;
+    if (precision != GNK_PREC_FP64 && precision != GNK_PREC_DF32) {
+        set_error("gnk_slit_map_adjoint_eval: precision must be GNK_PREC_FP64 or GNK_PREC_DF32, got %d",
+                  precision);
+        return GNK_EINVAL;
+    }
+    if (nz < 0) {
+        set_error("gnk_slit_map_adjoint_eval: nz < 0");
+        return GNK_EINVAL;
+    }
+    if (nz == 0) return GNK_OK;
+    if (!alpha || !omega || !z || !wz) {
+        set_error("gnk_slit_map_adjoint_eval: NULL array");
+        return GNK_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Views vw;
+    void *dom, *dz, *dw;
+    int rc = vw.add(omega, 16 * (size_t)b.N, true, st, &dom);
+    if (rc == GNK_OK) rc = vw.add(z, 16 * (size_t)nz, true, st, &dz);
+    if (rc == GNK_OK) rc = vw.add(wz, 16 * (size_t)nz, false, st, &dw);
+    // omega(z) by the Cauchy formula (omega(inf) = 0 for unbounded G) into wz,
+    // then w = (z - alpha) exp(omega) in place
+    if (rc == GNK_OK)
+        rc = cauchy_eval(b, nz, (const double2*)dz, (const double2*)dom, make_double2(0.0, 0.0), (double2*)dw,
+                         precision, st);
+    if (rc == GNK_OK)
+        rc = slit_w((const double2*)dz, (const double2*)dw, nz, make_double2(alpha[0], alpha[1]), nullptr, 0,
+                    (double2*)dw, st);
+    const bool out[3] = {false, false, true};
+    return vw.finish(rc, out, st);
+}
+
 int gnk_compute_h(const gnk_boundary* h, const double* mu, const double* gam, double* hv, double* hk,
                   void* stream) {
     GNK_TRY(check_handle(h));

@@ -14,38 +14,11 @@
 #include <cmath>
 #include <vector>
 
+#include "fft.cuh"
 #include "gnk_internal.h"
 
 namespace gnk {
 namespace {
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// Radix-2 Stockham autosort FFT over n = 2^k points in shared memory; returns
-// the buffer that holds the result.  Twiddles tw[k] = exp(-2 pi i k / n).
-__device__ double2* stockham(double2* X, double2* Y, int n, const double2* tw, bool inverse) {
-    const int half = n >> 1;
-    for (int Ns = 1; Ns < n; Ns <<= 1) {
-        const int stride = n / (2 * Ns);
-        for (int j = threadIdx.x; j < half; j += blockDim.x) {
-            const int k = j & (Ns - 1);
-            double2 w = tw[k * stride];
-            if (inverse) w.y = -w.y;
-            const double2 v0 = X[j];
-            const double2 v1 = cmul(X[j + half], w);
-            const int d = ((j - k) << 1) + k;
-            Y[d] = make_double2(v0.x + v1.x, v0.y + v1.y);
-            Y[d + Ns] = make_double2(v0.x - v1.x, v0.y - v1.y);
-        }
-        __syncthreads();
-        double2* t = X;
-        X = Y;
-        Y = t;
-    }
-    return X;
-}
 
 __global__ void circulant_fft_kernel(const double* __restrict__ x, double* __restrict__ y,
                                      int n, int m1, const double2* __restrict__ tw) {

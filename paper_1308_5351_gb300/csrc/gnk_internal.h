@@ -306,6 +306,11 @@ int slit_nodes_f(const Boundary& b, const double* gam, const double* mu, const d
                  cudaStream_t st);
 int slit_w(const double2* z, const double2* f, int M, double2 alpha, const double* hk, int bounded, double2* w,
            cudaStream_t st);
+// the adjoint route (slitmap_adj.cu): A' of the slit map's A, and the whole
+// route on a handle built with that A and A' (theta on the device, each pi/2 or 0)
+int slit_dA(int m1, int n, const double2* etp, const double* theta, int bounded, double2* Ap, cudaStream_t st);
+int slit_map_adjoint(const Boundary& b, double2 alpha, const double* theta, const gnk_options& opt, double2* w,
+                     double2* omega, double* psi_out, double* params, gnk_result* info, cudaStream_t st);
 
 // ---------------------------------------------------------------- Cauchy formula (cauchy_eval.cu)
 int cauchy_eval(const Boundary& b, int M, const double2* z, const double2* f, double2 finf, double2* out,

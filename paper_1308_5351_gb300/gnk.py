@@ -50,6 +50,7 @@ EXPORTED = (
     "gnk_batch_sizes", "gnk_batch_tuning", "gnk_batch_fbie", "gnk_batch_apply_IminusN",
     "gnk_cauchy_eval", "gnk_slit_map_data", "gnk_slit_map", "gnk_slit_map_eval", "gnk_profile_mask",
     "gnk_debug_recip_f64", "gnk_debug_split_f64", "gnk_debug_barrier_fault", "gnk_profile_query_bytes",
+    "gnk_slit_map_adjoint_data", "gnk_slit_map_adjoint", "gnk_slit_map_adjoint_eval",
 )
 
 PROF_PAIR64, PROF_PAIR32, PROF_REDUCE, PROF_CIRC, PROF_KRYLOV, PROF_OTHER, PROF_PAIRDF, PROF_FMM, \
@@ -140,6 +141,10 @@ def load(path: str = LIB_PATH):
     lib.gnk_slit_map_data.argtypes = [I, I, P, P, P, I, P, P, P]
     lib.gnk_slit_map.argtypes = [P, P, P, P, P, P, P, P]
     lib.gnk_slit_map_eval.argtypes = [P, P, P, P, P, P, I, P, P, I, P]
+    lib.gnk_slit_map_adjoint_data.argtypes = [I, I, P, P, I, P, P]
+    lib.gnk_slit_map_adjoint.argtypes = [P, P, P, ctypes.POINTER(gnk_options), P, P, P, P,
+                                         ctypes.POINTER(gnk_result), P]
+    lib.gnk_slit_map_adjoint_eval.argtypes = [P, P, P, I, P, P, I, P]
     lib.gnk_debug_recip_f64.argtypes = [I, P, P, P, P]
     lib.gnk_debug_split_f64.argtypes = [I, P, P, P, P]
     lib.gnk_debug_barrier_fault.argtypes = [I, I]
@@ -419,6 +424,65 @@ def slit_map(dom, alpha, theta, z=None, device="cuda", precision=GNK_PREC_FMM, t
             ep = GNK_PREC_DF32 if precision in (GNK_PREC_DF32, GNK_PREC_MIXED_DF) else GNK_PREC_FP64
             gnk_slit_map_eval(b.handle, alpha, gam, mu, h, hk, zt, wz, ep, stream)
     return w, hk, wz, res
+
+
+def gnk_slit_map_adjoint_data(m1, n, etp, theta, Ap, stream=None, bounded=True):
+    """A' of the slit map's A (e^{i(pi/2 - theta)} eta' for bounded G, 0 for
+    unbounded G), for a handle that solves Eq. (ie*)."""
+    return _check(load().gnk_slit_map_adjoint_data(int(m1), int(n), _ptr(etp, True), _ptr(theta),
+                                                   1 if bounded else 0, _ptr(Ap, True), _stream(stream)))
+
+
+def gnk_slit_map_adjoint(h, alpha, theta, w, omega=None, psi=None, params=None,
+                         options: Optional[gnk_options] = None, stream=None):
+    """The slit map by solves of the adjoint equation only (Sec. 7, Ex. 3 and
+    Ex. 4): w (and optionally omega, psi, params) at the nodes; returns the
+    gnk_result of the solves."""
+    res = gnk_result()
+    code = load().gnk_slit_map_adjoint(h, _c2(alpha), _ptr(theta), ctypes.byref(options) if options is not None
+                                       else None, _ptr(w, True), _ptr(omega, True), _ptr(psi), _ptr(params),
+                                       ctypes.byref(res), _stream(stream))
+    _check(code, (GNK_OK, GNK_ENOTCONV))
+    return res
+
+
+def gnk_slit_map_adjoint_eval(h, alpha, omega, z, wz, precision=GNK_PREC_FP64, stream=None):
+    """w at points z of G from omega at the nodes (Cauchy formula for omega)."""
+    nz = int(z.numel() if torch is not None and isinstance(z, torch.Tensor) else z.size)
+    return _check(load().gnk_slit_map_adjoint_eval(h, _c2(alpha), _ptr(omega, True), nz, _ptr(z, True),
+                                                   _ptr(wz, True), int(precision), _stream(stream)))
+
+
+def slit_map_adjoint(dom, alpha, theta, z=None, device="cuda", precision=GNK_PREC_FMM, tol=1e-12,
+                     restart=20, maxit=50, stream=None):
+    """The slit map of a domain by the adjoint route: returns (w at the nodes,
+    psi, params, omega at the nodes, w at z or None, gnk_result).  theta: one
+    value per boundary (pi/2 circular slit, 0 radial slit).  Cauchy sums by
+    `precision` (GNK_PREC_FMM by default)."""
+    et = torch.as_tensor(np.ascontiguousarray(dom.et), device=device)
+    etp = torch.as_tensor(np.ascontiguousarray(dom.etp), device=device)
+    etpp = torch.as_tensor(np.ascontiguousarray(dom.etpp), device=device)
+    th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=device)
+    A = torch.empty_like(et)
+    Ap = torch.empty_like(et)
+    gam = torch.empty(dom.N, dtype=torch.float64, device=device)
+    gnk_slit_map_data(dom.m1, dom.n, et, alpha, th, A, gam, stream, bounded=dom.bounded)
+    gnk_slit_map_adjoint_data(dom.m1, dom.n, etp, th, Ap, stream, bounded=dom.bounded)
+    bprec = GNK_PREC_FMM if precision in (GNK_PREC_FMM, GNK_PREC_MIXED_FMM) else GNK_PREC_FP64
+    with Boundary(dom.m1, dom.n, et, etp, A, etpp, Ap, dom.bounded, stream, bprec) as b:
+        w = torch.empty_like(et)
+        omega = torch.empty_like(et)
+        psi = torch.empty(dom.N, dtype=torch.float64, device=device)
+        params = torch.empty(dom.m1 + 1, dtype=torch.float64, device=device)
+        res = gnk_slit_map_adjoint(b.handle, alpha, th, w, omega, psi, params,
+                                   options(tol=tol, precision=precision, restart=restart, maxit=maxit), stream)
+        wz = None
+        if z is not None:
+            zt = torch.as_tensor(np.ascontiguousarray(z, dtype=np.complex128), device=device)
+            wz = torch.empty_like(zt)
+            ep = GNK_PREC_DF32 if precision in (GNK_PREC_DF32, GNK_PREC_MIXED_DF) else GNK_PREC_FP64
+            gnk_slit_map_adjoint_eval(b.handle, alpha, omega, zt, wz, ep, stream)
+    return w, psi, params, omega, wz, res
 
 
 def gnk_apply_IminusN(h, x, y, precision=GNK_PREC_FP64, stream=None):

@@ -186,3 +186,125 @@ def test_planted_mistakes_fail(monkeypatch):
     monkeypatch.setattr(O, "slit_map_data", lambda et, n_, al, th, b=True: good_data(et, n_, al, [HALF] * 5, b))
     w = O.slit_map_adjoint(d5.et, d5.etp, d5.etpp, 128, 0j, MIXED)[0]
     assert np.abs(w - w2).max() > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# GPU: the C-ABI route against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def G():
+    pytest.importorskip("torch")
+    from paper_1308_5351_gb300 import build, gnk
+    build.build()
+    gnk.load()
+    return gnk
+
+
+_GPU_CASES = {
+    "disk": (lambda: Dm.disk(64, 0.3 + 0.2j), 0.3 + 0.2j, [HALF]),
+    "ex2_circular": (lambda: Dm.ex2_circles(0.1, 256), 0j, [HALF] * 5),
+    "ex2_mixed": (lambda: Dm.ex2_circles(0.1, 256), 0j, MIXED),
+    "ex4_circular": (lambda: Dm.ex4_circles(0.1, 256), 2.5 + 0j, [HALF] * 5),
+    "ex4_mixed": (lambda: Dm.ex4_circles(0.1, 256), 2.5 + 0j, MIXED),
+    # n not a power of two (the direct antiderivative) and an odd number of boundaries
+    "three_circles_n100": (lambda: Dm.three_circles(100), 0.05j, [HALF, 0.0, HALF]),
+}
+
+
+def _points_in(d, count=24, seed=7):
+    """Points of G at least 0.05 away from every boundary circle."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    while len(pts) < count:
+        if d.bounded:
+            z = complex(rng.uniform(-0.95, 0.95), rng.uniform(-0.95, 0.95))
+            ok = abs(z) < d.curves[0].radius - 0.05 and all(
+                abs(z - cv.centre) > cv.radius + 0.05 for cv in d.curves[1:])
+        else:
+            z = complex(rng.uniform(-4, 4), rng.uniform(-4, 4))
+            ok = all(abs(z - cv.centre) > cv.radius + 0.05 for cv in d.curves)
+        if ok:
+            pts.append(z)
+    return np.array(pts)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", sorted(_GPU_CASES))
+def test_gpu_slit_map_adjoint_data(G, case):
+    import torch
+    mk, a, th = _GPU_CASES[case]
+    d = mk()
+    rot = np.repeat(np.exp(1j * (HALF - np.asarray(th))), d.n)
+    ref = rot * d.etp if d.bounded else np.zeros_like(d.etp)
+    Ap = torch.empty(d.N, dtype=torch.complex128, device="cuda")
+    G.gnk_slit_map_adjoint_data(d.m1, d.n, torch.as_tensor(d.etp, device="cuda"),
+                                torch.as_tensor(np.asarray(th, dtype=np.float64), device="cuda"), Ap,
+                                bounded=d.bounded)
+    assert np.abs(Ap.cpu().numpy() - ref).max() <= 4e-16 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", sorted(_GPU_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fmm"])
+def test_gpu_slit_map_adjoint_matches_oracle(G, case, prec):
+    """w, omega and psi at the nodes, the parameters and w inside G within 1e-9
+    of max(1, |.|): every solve to 1e-12 (condition numbers below 100 here), and
+    the constants are sums of omega^ psi_j that carry those errors into the
+    exponent."""
+    mk, a, th = _GPU_CASES[case]
+    d = mk()
+    z = _points_in(d)
+    w_r, psi_r, par_r, sc_r, om_r, wz_r = O.slit_map_adjoint(d.et, d.etp, d.etpp, d.n, a, th, d.bounded, z=z)
+    p = G.GNK_PREC_FMM if prec == "fmm" else G.GNK_PREC_FP64
+    w, psi, params, omega, wz, res = G.slit_map_adjoint(d, a, th, z=z, precision=p, restart=40, maxit=20)
+    assert res.status == 0 and res.relres <= 1e-12, (res.status, res.relres)
+    solves = d.m1 if d.bounded else d.m1 + 1
+    assert res.cycles >= solves
+    sw = max(1.0, np.abs(w_r).max())
+    assert np.abs(w.cpu().numpy() - w_r).max() <= 1e-9 * sw
+    assert np.abs(omega.cpu().numpy() - om_r).max() <= 1e-9 * max(1.0, np.abs(om_r).max())
+    assert np.abs(psi.cpu().numpy() - psi_r).max() <= 1e-9 * max(1.0, np.abs(psi_r).max())
+    par = params.cpu().numpy()
+    assert np.abs(par[:-1] - par_r).max() <= 1e-9 * max(1.0, np.abs(par_r).max())
+    assert abs(par[-1] - sc_r) <= 1e-9 * sc_r
+    assert np.all(np.abs(wz.cpu().numpy() - wz_r) <= 1e-9 * np.maximum(1.0, np.abs(wz_r)))
+
+
+@pytest.mark.gpu
+def test_gpu_slit_map_adjoint_large_n_disk():
+    """n = 8192 (beyond the shared-memory FFT: the direct antiderivative) on the
+    unit disk against the closed form w = (z - alpha)/(1 - conj(alpha) z), which
+    holds at any size."""
+    from paper_1308_5351_gb300 import build, gnk as G
+    build.build()
+    G.load()
+    a = 0.3 + 0.2j
+    d = Dm.disk(8192, a)
+    w, psi, params, omega, wz, res = G.slit_map_adjoint(d, a, [HALF], precision=G.GNK_PREC_FP64)
+    assert res.status == 0
+    ref = (d.et - a) / (1 - np.conj(a) * d.et)
+    assert np.abs(w.cpu().numpy() - ref).max() <= 1e-11
+    t = Dm.nodes(8192)
+    assert np.abs(psi.cpu().numpy() - (1 - abs(a) ** 2) / np.abs(np.exp(1j * t) - a) ** 2).max() <= 1e-10
+    assert abs(params.cpu().numpy()[-1] - 1 / (1 - abs(a) ** 2)) <= 1e-11
+
+
+@pytest.mark.gpu
+def test_gpu_slit_map_adjoint_rejects_bad_arguments(G):
+    import torch
+    d = Dm.ex2_circles(0.1, 64)
+    et = torch.as_tensor(d.et, device="cuda")
+    w = torch.empty_like(et)
+    with G.Boundary.from_domain(d, adjoint=False, device="cuda") as b:  # no eta''
+        with pytest.raises(G.GnkError):
+            G.gnk_slit_map_adjoint(b.handle, 0j, np.full(5, HALF), w)
+    A, _ = O.slit_map_data(d.et, d.n, 0j, MIXED, True)
+    rot = np.repeat(np.exp(1j * (HALF - np.asarray(MIXED))), d.n)
+    with G.Boundary(d.m1, d.n, d.et, d.etp, A, d.etpp, rot * d.etp, True) as b:
+        for th in ([HALF, 0.3, HALF, 0.0, HALF], [0.0, 0.0, HALF, 0.0, HALF]):
+            with pytest.raises(G.GnkError) as e:
+                G.gnk_slit_map_adjoint(b.handle, 0j, np.asarray(th), w)
+            assert e.value.code == G.GNK_EINVAL
+        with pytest.raises(G.GnkError):
+            G.gnk_slit_map_adjoint_eval(b.handle, 0j, w, w[:4], w[:4], precision=G.GNK_PREC_FP32)
