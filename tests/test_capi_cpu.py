@@ -56,6 +56,11 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.gnk_build_boundary(ctypes.byref(h), 2, 8, None, p, None, p, None, 1, None) == gnk.GNK_EINVAL
     assert lib.gnk_apply_IminusN(None, p, p, 0, None) == gnk.GNK_EINVAL
     assert lib.gnk_free_boundary(None) == gnk.GNK_OK
+    # the slit maps' adjoint route: NULL arrays, odd n and a NULL handle
+    assert lib.gnk_slit_map_adjoint_data(2, 8, None, p, 1, p, None) == gnk.GNK_EINVAL
+    assert lib.gnk_slit_map_adjoint_data(2, 7, p, p, 1, p, None) == gnk.GNK_EINVAL
+    assert lib.gnk_slit_map_adjoint(None, p, p, None, p, None, None, None, None, None) == gnk.GNK_EINVAL
+    assert lib.gnk_slit_map_adjoint_eval(None, p, p, 4, p, p, 0, None) == gnk.GNK_EINVAL
 
 
 def test_binding_refuses_missing_library(tmp_path):
