@@ -957,8 +957,9 @@ int gnk_slit_map_adjoint(const gnk_boundary* hd, const double* alpha, const doub
         s = slit_map_adjoint(b, make_double2(alpha[0], alpha[1]), (const double*)dth, o, (double2*)dw,
                              (double2*)dom, (double*)dpsi, (double*)dpar, info, st);
     // the outputs of a call whose solves stopped at maxit are still copied back
-    const int fin = vw.finish(s == GNK_ENOTCONV ? GNK_OK : s, out, st);
-    if (fin != GNK_OK) return fin;
+    const int rcf = (s == GNK_ENOTCONV) ? GNK_OK : s;
+    const int fin = vw.finish(rcf, out, st);
+    if (fin != rcf) return fin;  // a CUDA failure while copying back
     if (s == GNK_ENOTCONV) set_error("GMRES did not reach tol within maxit cycles in one of the solves");
     if (s == GNK_ENONFINITE) set_error("non-finite value in the GMRES iteration");
     return s;
