@@ -24,6 +24,8 @@ CPU pins of the oracle (independent of its formulas):
     the derivative solution has the winding numbers of the map;
   * the boundary values are those of a function analytic in G (the exterior
     Cauchy integral vanishes in every hole) with w(alpha) = 0;
+  * on a graded square hole (corners) the two routes converge to each other
+    like n^-2;
   * planted mistakes (the sign of the antiderivative, c of Eq. (c), the
     rotation of A) fail these pins.
 GPU: gnk_slit_map_adjoint / gnk_slit_map_adjoint_eval against the oracle.
@@ -158,6 +160,23 @@ def test_boundary_values_are_analytic_in_G(bounded):
             assert np.ptp(np.abs(W[k])) < 1e-13 * np.abs(W[k]).max()
         else:
             assert np.ptp(np.unwrap(np.angle(W[k]))) < 1e-13
+
+
+def test_graded_square_hole_converges_to_the_fbie_route():
+    """A square hole with graded corners (p = 3, Sec. 6): psi has a kink at
+    each corner (|t - c|^(2p/3 - 1)), so both routes converge algebraically;
+    their difference must fall like n^-2 and be below 1e-4 at n = 512."""
+    a = -0.3 + 0.5j
+    th = [HALF, 0.0, HALF]
+    diffs = []
+    for n in (128, 256, 512):
+        curves = [Dm.Circle(0j, 1.0, ccw=True), Dm.square(0.3 + 0.1j, 0.25, ccw=False),
+                  Dm.Circle(-0.4 - 0.2j, 0.2)]
+        d = Dm.build_domain(curves, n, bounded=True, alpha=a)
+        w = O.slit_map_adjoint(d.et, d.etp, d.etpp, n, a, th, True)[0]
+        w2 = O.slit_map(d.et, d.etp, n, a, th)[0]
+        diffs.append(np.abs(w - w2).max())
+    assert diffs[1] < diffs[0] / 3 and diffs[2] < diffs[1] / 3 and diffs[2] < 1e-4, diffs
 
 
 def test_planted_mistakes_fail(monkeypatch):
