@@ -2,7 +2,7 @@
 // this runs once per handle, on the first FMM product):
 //   1. bounding square of the nodes;
 //   2. 32-bit Morton keys of 16-bit box coordinates;
-//   3. stable LSD radix sort of (key, node), four passes of 8 bits;
+//   3. stable LSD radix sort of (key, node), three passes of 8 bits (bits 8-31);
 //   4. the level at which each node's key first differs from its predecessor's,
 //      whose histogram fixes the leaf level L (the deepest level whose non-empty
 //      boxes hold >= kFmmLeaf nodes on average);
