@@ -16,6 +16,8 @@ CPU pins of the oracle (independent of its formulas):
     w'(alpha) = 1/(1 - |alpha|^2), with exponential convergence;
   * exterior of the unit circle (unbounded): w = -conj(alpha) z (z - alpha)/
     (1 - conj(alpha) z), R_0 = |alpha|, psi = Im[eta' w'/w];
+  * exterior of a circle onto the plane minus one radial slit (theta = 0): a
+    Moebius map composed with Joukowski's, for both routes;
   * Ex. 2 (bounded) and Ex. 4 (unbounded) five circles with constant and mixed
     theta: the same map as the FBIE route (another equation, another solve):
     w on the boundary and inside, w'(alpha) = e^{-h_0}, R_k = e^{h_k - h_0}
@@ -86,6 +88,46 @@ def test_exterior_of_the_unit_circle():
         assert scale == 1.0
     # psi is exact at the nodes here; w converges with the interpolant of psi
     assert errs[-1] < 1e-13 and errs[2] < errs[1] / 1e4 and errs[1] < errs[0] / 1e2
+
+
+def _radial_exterior_closed_form(c, r, a):
+    """Exterior of the circle |z - c| = r onto the plane minus one radial slit,
+    w(a) = 0, w = z + O(1): with zeta = (z - c)/r and beta = (a - c)/r, the
+    Moebius map u = e^{i arg beta} (1 - conj(beta) zeta)/(zeta - beta) keeps the
+    exterior of the unit circle, sends a to infinity and infinity to
+    u_inf = -|beta| (real); Joukowski J(u) = u + 1/u maps it onto the plane
+    minus [-2, 2], and g = J(u) - J(u_inf) moves the segment along the real
+    axis away from 0 with g(inf) = 0, g(a) = inf; w = lambda/g with lambda the
+    limit of z g(z)."""
+    beta = (a - c) / r
+    e = np.exp(1j * np.angle(beta))
+    uinf = -abs(beta)
+    lam = (1 - 1 / uinf ** 2) * e * (1 - abs(beta) ** 2) * r
+
+    def w(z):
+        zeta = (z - c) / r
+        u = e * (1 - np.conj(beta) * zeta) / (zeta - beta)
+        return lam / (u + 1 / u - (uinf + 1 / uinf))
+    return w
+
+
+def test_exterior_radial_slit_closed_form():
+    """theta = 0 on the one boundary of an unbounded domain: both routes against
+    the closed form, with exponential convergence; arg w is constant on the
+    boundary and w(z)/z -> 1 at infinity."""
+    c, r, a = 0.2j, 0.8, 1.5 + 0.7j
+    ex = _radial_exterior_closed_form(c, r, a)
+    z = np.array([3 + 1j, -2 - 2j, 0.5 - 1.5j])
+    assert abs(ex(np.array([1e7 * np.exp(0.3j)]))[0] / (1e7 * np.exp(0.3j)) - 1) < 1e-6
+    errs = []
+    for n in (32, 64, 128):
+        d = Dm.build_domain([Dm.Circle(c, r)], n, bounded=False, theta=[0.0])
+        w, psi, params, scale, omega, wz = O.slit_map_adjoint(d.et, d.etp, d.etpp, n, a, [0.0], False, z=z)
+        w2, c2, hk, wz2 = O.slit_map(d.et, d.etp, n, a, [0.0], z=z, bounded=False)
+        errs.append(max(np.abs(w - ex(d.et)).max(), np.abs(wz - ex(z)).max(),
+                        np.abs(w2 - ex(d.et)).max(), np.abs(wz2 - ex(z)).max(),
+                        abs(math.remainder(params[0] - np.angle(ex(d.et[:1]))[0], 2 * math.pi))))
+    assert errs[-1] < 1e-13 and errs[1] < errs[0] / 1e4, errs
 
 
 _ROUTE_CASES = {
